@@ -1,0 +1,559 @@
+/*
+ * hb_oracle.c -- plain, slow FP64 CPU oracle for the hipBone hot path.
+ *
+ * TEST INFRASTRUCTURE. This is the independent reference the CUDA library is
+ * checked against. Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may build, load or call it; the product path never does.
+ * It shares no code, header, table or constant generator with the CUDA
+ * library: GLL points, the derivative matrix, the mesh, the numbering, the
+ * geometric factors and the random numbers are all computed here on their own.
+ *
+ * What it computes (hipBone, arXiv 2202.12477):
+ *   - Sec. 2, Eq. (poisson):   A = S + lambda I
+ *   - Sec. 2, Eq. (stiffness): S = Z^T S_L Z, S_L^e = Dbold^T G^e Dbold with
+ *     Dbold = [D(x)I(x)I; I(x)D(x)I; I(x)I(x)D] and G^e the symmetric 3x3 block
+ *     of diagonal metric factors combined with GLL weights.
+ *   - Algorithm 1: unpreconditioned conjugate gradients.
+ * Textbook pieces the paper cites (Canuto et al.; Deville, Fischer & Mund):
+ *   - GLL nodes: +-1 and the roots of P_N'; weights 2 / (N(N+1) P_N(xi)^2).
+ *   - D_ij = l_j'(xi_i) in the closed Legendre form.
+ *   - G_ab = w_i w_j w_k detJ sum_c (J^-1)_ac (J^-1)_bc for the trilinear map.
+ * Readings where the paper is silent (all listed with the design notes):
+ *   - the box is [0,1]^3 split into Ex x Ey x Ez hexahedra; vertices strictly
+ *     inside the box move by U[-rho h, rho h] per axis; maps are trilinear;
+ *   - Dirichlet nodes are left out of the global numbering; global ids are
+ *     lexicographic over the remaining lattice nodes, I fastest;
+ *   - the lambda W term: W Z x summed by Z^T gives lambda x once per DOF
+ *     (identity screening); mass screening adds lambda Z^T (Jw . Z x);
+ *   - CG starts from the caller's x, stops when ||r|| <= rtol ||b|| or after
+ *     max_it iterations (rtol = 0 runs exactly max_it iterations).
+ * Random numbers: u01(seed, stream, idx) = (splitmix64(seed ^ (stream * G)
+ * + idx) >> 11) * 2^-53 with G = 0x9E3779B97F4A7C15 and the published
+ * SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014).
+ *
+ * Built with -ffp-contract=off: no fused multiply-adds are formed, every
+ * product and sum rounds on its own, in the order written.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Random numbers                                                      */
+/* ------------------------------------------------------------------ */
+
+/* SplitMix64 output for the state value s (the generator adds the golden
+ * gamma to its state and then mixes; this is that step for one state). */
+static uint64_t splitmix64_at(uint64_t s)
+{
+    uint64_t z = s + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t or_splitmix64(uint64_t s) { return splitmix64_at(s); }
+
+double or_u01(uint64_t seed, uint64_t stream, uint64_t idx)
+{
+    uint64_t s = (seed ^ (stream * 0x9E3779B97F4A7C15ULL)) + idx;
+    return (double)(splitmix64_at(s) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* ------------------------------------------------------------------ */
+/* GLL nodes, weights and the 1-D derivative matrix                    */
+/* ------------------------------------------------------------------ */
+
+/* Legendre P_N(x) and P_N'(x) by the three-term recurrence
+ * k P_k = (2k-1) x P_{k-1} - (k-1) P_{k-2}, and P_k' = P_{k-2}' + (2k-1) P_{k-1}. */
+static void legendre(int N, double x, double *P, double *dP)
+{
+    double p_km2 = 1.0, p_km1 = x;      /* P_0, P_1 */
+    double d_km2 = 0.0, d_km1 = 1.0;    /* P_0', P_1' */
+    if (N == 0) { *P = 1.0; *dP = 0.0; return; }
+    for (int k = 2; k <= N; k++) {
+        double p_k = ((2.0 * k - 1.0) * x * p_km1 - (k - 1.0) * p_km2) / k;
+        double d_k = d_km2 + (2.0 * k - 1.0) * p_km1;
+        p_km2 = p_km1; p_km1 = p_k;
+        d_km2 = d_km1; d_km1 = d_k;
+    }
+    *P = p_km1;
+    *dP = d_km1;
+}
+
+/* GLL nodes xi[0..N] (ascending) and weights w[0..N]. Interior nodes are the
+ * roots of P_N', found by Newton's method from the Chebyshev-Gauss-Lobatto
+ * points; P_N'' comes from Legendre's equation
+ * (1-x^2) P'' = 2x P' - N(N+1) P. Returns 0 on success. */
+int or_gll(int N, double *xi, double *w)
+{
+    if (N < 1) return 1;
+    const double pi = 3.14159265358979323846;
+    xi[0] = -1.0;
+    xi[N] = 1.0;
+    for (int i = 1; i < N; i++) {
+        double x = -cos(pi * i / N);
+        for (int it = 0; it < 100; it++) {
+            double P, dP;
+            legendre(N, x, &P, &dP);
+            double d2P = (2.0 * x * dP - N * (N + 1.0) * P) / (1.0 - x * x);
+            double dx = dP / d2P;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        xi[i] = x;
+    }
+    /* The node set is symmetric about 0; make the computed set exactly so. */
+    for (int i = 0; i < (N + 1) / 2; i++) {
+        double a = 0.5 * (xi[N - i] - xi[i]);
+        xi[i] = -a;
+        xi[N - i] = a;
+    }
+    if (N % 2 == 0) xi[N / 2] = 0.0;
+    for (int i = 0; i <= N; i++) {
+        double P, dP;
+        legendre(N, xi[i], &P, &dP);
+        w[i] = 2.0 / (N * (N + 1.0) * P * P);
+    }
+    return 0;
+}
+
+/* D[i*(N+1)+j] = l_j'(xi_i) for the Lagrange basis on the GLL nodes:
+ * off-diagonal P_N(xi_i) / (P_N(xi_j) (xi_i - xi_j)); D_00 = -N(N+1)/4,
+ * D_NN = N(N+1)/4, other diagonal entries 0. */
+int or_deriv(int N, const double *xi, double *D)
+{
+    int n = N + 1;
+    double *P = (double *)malloc(sizeof(double) * n);
+    if (!P) return 1;
+    for (int i = 0; i < n; i++) {
+        double dP;
+        legendre(N, xi[i], &P[i], &dP);
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            double v;
+            if (i != j) v = P[i] / (P[j] * (xi[i] - xi[j]));
+            else if (i == 0) v = -N * (N + 1.0) / 4.0;
+            else if (i == N) v = N * (N + 1.0) / 4.0;
+            else v = 0.0;
+            D[i * n + j] = v;
+        }
+    free(P);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Mesh                                                                */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int Ex, Ey, Ez, N, n;
+    int64_t E, n_local, n_global;
+    unsigned faces;
+    double rho;
+    uint64_t seed;
+    double *xi, *w, *D;      /* GLL nodes, weights, derivative matrix */
+    double *V;               /* vertices [(Ez+1)(Ey+1)(Ex+1)][3] */
+    int32_t *l2g;            /* [E][n^3], -1 for a Dirichlet node */
+    double *G;               /* [E][n^3][6]: rr rs rt ss st tt */
+    double *Jw;              /* [E][n^3] */
+    double *X;               /* physical coordinates of local nodes [E][n^3][3] */
+    double min_detJ;
+    double *yL;              /* work: one element's local output [E][n^3] */
+} or_mesh;
+
+static int64_t vidx(const or_mesh *m, int a, int b, int c)
+{
+    return ((int64_t)c * (m->Ey + 1) + b) * (m->Ex + 1) + a;
+}
+
+/* Box vertices: lattice points (a/Ex, b/Ey, c/Ez); each vertex strictly inside
+ * the box moves by (2u-1) rho h_axis along each axis. */
+static void make_vertices(or_mesh *m)
+{
+    double h[3] = {1.0 / m->Ex, 1.0 / m->Ey, 1.0 / m->Ez};
+    for (int c = 0; c <= m->Ez; c++)
+        for (int b = 0; b <= m->Ey; b++)
+            for (int a = 0; a <= m->Ex; a++) {
+                int64_t v = vidx(m, a, b, c);
+                double X[3] = {(double)a / m->Ex, (double)b / m->Ey, (double)c / m->Ez};
+                int inside = a > 0 && a < m->Ex && b > 0 && b < m->Ey && c > 0 && c < m->Ez;
+                for (int ax = 0; ax < 3; ax++) {
+                    double off = 0.0;
+                    if (inside) {
+                        double u = or_u01(m->seed, 1, (uint64_t)(3 * v + ax));
+                        off = (2.0 * u - 1.0) * m->rho * h[ax];
+                    }
+                    m->V[3 * v + ax] = X[ax] + off;
+                }
+            }
+}
+
+/* Global numbering: lexicographic over the lattice nodes (I,J,K), I fastest,
+ * skipping the nodes on masked faces. Face bits: 0 x=0, 1 x=1, 2 y=0, 3 y=1,
+ * 4 z=0, 5 z=1. */
+static int make_numbering(or_mesh *m)
+{
+    int N = m->N, n = m->n;
+    int64_t NX = (int64_t)N * m->Ex + 1, NY = (int64_t)N * m->Ey + 1, NZ = (int64_t)N * m->Ez + 1;
+    int64_t *id = (int64_t *)malloc(sizeof(int64_t) * NX * NY * NZ);
+    if (!id) return 1;
+    int64_t next = 0;
+    for (int64_t K = 0; K < NZ; K++)
+        for (int64_t J = 0; J < NY; J++)
+            for (int64_t I = 0; I < NX; I++) {
+                int masked = ((m->faces & 1u) && I == 0) || ((m->faces & 2u) && I == NX - 1) ||
+                             ((m->faces & 4u) && J == 0) || ((m->faces & 8u) && J == NY - 1) ||
+                             ((m->faces & 16u) && K == 0) || ((m->faces & 32u) && K == NZ - 1);
+                id[I + NX * (J + NY * K)] = masked ? -1 : next++;
+            }
+    m->n_global = next;
+    for (int ez = 0; ez < m->Ez; ez++)
+        for (int ey = 0; ey < m->Ey; ey++)
+            for (int ex = 0; ex < m->Ex; ex++) {
+                int64_t e = ex + (int64_t)m->Ex * (ey + (int64_t)m->Ey * ez);
+                for (int k = 0; k < n; k++)
+                    for (int j = 0; j < n; j++)
+                        for (int i = 0; i < n; i++) {
+                            int64_t I = (int64_t)N * ex + i, J = (int64_t)N * ey + j, K = (int64_t)N * ez + k;
+                            m->l2g[e * n * n * n + (k * n + j) * n + i] = (int32_t)id[I + NX * (J + NY * K)];
+                        }
+            }
+    free(id);
+    return 0;
+}
+
+/* Geometric factors from the analytic Jacobian of the trilinear map
+ * x(r,s,t) = sum_{abc} V_abc phi_a(r) phi_b(s) phi_c(t), phi_0 = (1-r)/2,
+ * phi_1 = (1+r)/2, evaluated at each GLL node. */
+static void make_geometry(or_mesh *m)
+{
+    int n = m->n;
+    int64_t n3 = (int64_t)n * n * n;
+    double mind = INFINITY;
+    for (int ez = 0; ez < m->Ez; ez++)
+        for (int ey = 0; ey < m->Ey; ey++)
+            for (int ex = 0; ex < m->Ex; ex++) {
+                int64_t e = ex + (int64_t)m->Ex * (ey + (int64_t)m->Ey * ez);
+                double Ve[2][2][2][3];
+                for (int c = 0; c < 2; c++)
+                    for (int b = 0; b < 2; b++)
+                        for (int a = 0; a < 2; a++)
+                            for (int ax = 0; ax < 3; ax++)
+                                Ve[c][b][a][ax] = m->V[3 * vidx(m, ex + a, ey + b, ez + c) + ax];
+                for (int k = 0; k < n; k++)
+                    for (int j = 0; j < n; j++)
+                        for (int i = 0; i < n; i++) {
+                            double r = m->xi[i], s = m->xi[j], t = m->xi[k];
+                            double ph[3][2] = {{0.5 * (1 - r), 0.5 * (1 + r)},
+                                               {0.5 * (1 - s), 0.5 * (1 + s)},
+                                               {0.5 * (1 - t), 0.5 * (1 + t)}};
+                            double dph[2] = {-0.5, 0.5};
+                            /* J[x][l] = d x_x / d r_l, l = r, s, t */
+                            double J[3][3] = {{0}}, X[3] = {0};
+                            for (int c = 0; c < 2; c++)
+                                for (int b = 0; b < 2; b++)
+                                    for (int a = 0; a < 2; a++)
+                                        for (int ax = 0; ax < 3; ax++) {
+                                            double v = Ve[c][b][a][ax];
+                                            X[ax] += v * ph[0][a] * ph[1][b] * ph[2][c];
+                                            J[ax][0] += v * dph[a] * ph[1][b] * ph[2][c];
+                                            J[ax][1] += v * ph[0][a] * dph[b] * ph[2][c];
+                                            J[ax][2] += v * ph[0][a] * ph[1][b] * dph[c];
+                                        }
+                            double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+                            /* inverse by cofactors: Ji[l][x] = d r_l / d x_x */
+                            double Ji[3][3];
+                            Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+                            Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+                            Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+                            Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+                            Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+                            Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+                            Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+                            Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+                            Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+                            double wq = m->w[i] * m->w[j] * m->w[k] * det;
+                            int64_t q = e * n3 + (k * n + j) * n + i;
+                            const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+                            for (int f = 0; f < 6; f++) {
+                                double g = 0.0;
+                                for (int x = 0; x < 3; x++) g += Ji[pa[f]][x] * Ji[pb[f]][x];
+                                m->G[6 * q + f] = wq * g;
+                            }
+                            m->Jw[q] = wq;
+                            for (int ax = 0; ax < 3; ax++) m->X[3 * q + ax] = X[ax];
+                            if (det < mind) mind = det;
+                        }
+            }
+    m->min_detJ = mind;
+}
+
+void or_mesh_free(or_mesh *m)
+{
+    if (!m) return;
+    free(m->xi); free(m->w); free(m->D); free(m->V); free(m->l2g);
+    free(m->G); free(m->Jw); free(m->X); free(m->yL);
+    free(m);
+}
+
+or_mesh *or_mesh_create(int Ex, int Ey, int Ez, int N, double rho, uint64_t seed, unsigned faces)
+{
+    if (Ex < 1 || Ey < 1 || Ez < 1 || N < 1) return NULL;
+    or_mesh *m = (or_mesh *)calloc(1, sizeof(or_mesh));
+    if (!m) return NULL;
+    m->Ex = Ex; m->Ey = Ey; m->Ez = Ez; m->N = N; m->n = N + 1;
+    m->E = (int64_t)Ex * Ey * Ez;
+    m->n_local = m->E * m->n * m->n * m->n;
+    m->faces = faces; m->rho = rho; m->seed = seed;
+    int n = m->n;
+    int64_t nv = (int64_t)(Ex + 1) * (Ey + 1) * (Ez + 1);
+    m->xi = (double *)malloc(sizeof(double) * n);
+    m->w = (double *)malloc(sizeof(double) * n);
+    m->D = (double *)malloc(sizeof(double) * n * n);
+    m->V = (double *)malloc(sizeof(double) * 3 * nv);
+    m->l2g = (int32_t *)malloc(sizeof(int32_t) * m->n_local);
+    m->G = (double *)malloc(sizeof(double) * 6 * m->n_local);
+    m->Jw = (double *)malloc(sizeof(double) * m->n_local);
+    m->X = (double *)malloc(sizeof(double) * 3 * m->n_local);
+    m->yL = (double *)malloc(sizeof(double) * m->n_local);
+    if (!m->xi || !m->w || !m->D || !m->V || !m->l2g || !m->G || !m->Jw || !m->X || !m->yL) {
+        or_mesh_free(m);
+        return NULL;
+    }
+    or_gll(N, m->xi, m->w);
+    or_deriv(N, m->xi, m->D);
+    make_vertices(m);
+    if (make_numbering(m)) { or_mesh_free(m); return NULL; }
+    make_geometry(m);
+    return m;
+}
+
+/* Sizes: out[0] = E, out[1] = n_local, out[2] = n_global. */
+void or_mesh_sizes(const or_mesh *m, int64_t *out)
+{
+    out[0] = m->E; out[1] = m->n_local; out[2] = m->n_global;
+}
+double or_mesh_min_detJ(const or_mesh *m) { return m->min_detJ; }
+void or_mesh_copy_l2g(const or_mesh *m, int32_t *out) { memcpy(out, m->l2g, sizeof(int32_t) * m->n_local); }
+void or_mesh_copy_geo(const or_mesh *m, double *G6, double *Jw)
+{
+    memcpy(G6, m->G, sizeof(double) * 6 * m->n_local);
+    memcpy(Jw, m->Jw, sizeof(double) * m->n_local);
+}
+void or_mesh_copy_coords(const or_mesh *m, double *X) { memcpy(X, m->X, sizeof(double) * 3 * m->n_local); }
+void or_mesh_copy_vertices(const or_mesh *m, double *V)
+{
+    memcpy(V, m->V, sizeof(double) * 3 * (m->Ex + 1) * (m->Ey + 1) * (m->Ez + 1));
+}
+void or_mesh_copy_ref(const or_mesh *m, double *xi, double *w, double *D)
+{
+    memcpy(xi, m->xi, sizeof(double) * m->n);
+    memcpy(w, m->w, sizeof(double) * m->n);
+    memcpy(D, m->D, sizeof(double) * m->n * m->n);
+}
+
+/* ------------------------------------------------------------------ */
+/* The operator                                                        */
+/* ------------------------------------------------------------------ */
+
+/* y_e = S_L^e u_e = Dbold^T G^e Dbold u_e for one element, with u_e = Z_e x. */
+static void local_stiffness(const or_mesh *m, int64_t e, const double *x, double *ye,
+                            double *u, double *ur, double *us, double *ut)
+{
+    int n = m->n;
+    int64_t n3 = (int64_t)n * n * n;
+    const double *D = m->D;
+    const int32_t *l2g = m->l2g + e * n3;
+    const double *G = m->G + 6 * e * n3;
+#define IX(i, j, k) (((k) * n + (j)) * n + (i))
+    /* u = Z_e x (a Dirichlet node carries 0) */
+    for (int q = 0; q < n3; q++) u[q] = l2g[q] >= 0 ? x[l2g[q]] : 0.0;
+    /* Dbold u: (D (x) I (x) I) u, (I (x) D (x) I) u, (I (x) I (x) D) u */
+    for (int k = 0; k < n; k++)
+        for (int j = 0; j < n; j++)
+            for (int i = 0; i < n; i++) {
+                double a = 0.0, b = 0.0, c = 0.0;
+                for (int p = 0; p < n; p++) {
+                    a += D[i * n + p] * u[IX(p, j, k)];
+                    b += D[j * n + p] * u[IX(i, p, k)];
+                    c += D[k * n + p] * u[IX(i, j, p)];
+                }
+                ur[IX(i, j, k)] = a;
+                us[IX(i, j, k)] = b;
+                ut[IX(i, j, k)] = c;
+            }
+    /* G^e applied pointwise to (ur, us, ut) */
+    for (int q = 0; q < n3; q++) {
+        const double *g = G + 6 * q;
+        double a = ur[q], b = us[q], c = ut[q];
+        ur[q] = g[0] * a + g[1] * b + g[2] * c;
+        us[q] = g[1] * a + g[3] * b + g[4] * c;
+        ut[q] = g[2] * a + g[4] * b + g[5] * c;
+    }
+    /* Dbold^T (vr, vs, vt) */
+    for (int k = 0; k < n; k++)
+        for (int j = 0; j < n; j++)
+            for (int i = 0; i < n; i++) {
+                double a = 0.0, b = 0.0, c = 0.0;
+                for (int p = 0; p < n; p++) {
+                    a += D[p * n + i] * ur[IX(p, j, k)];
+                    b += D[p * n + j] * us[IX(i, p, k)];
+                    c += D[p * n + k] * ut[IX(i, j, p)];
+                }
+                ye[IX(i, j, k)] = a + b + c;
+            }
+#undef IX
+}
+
+/* y = A x = Z^T S_L Z x + lambda x (screen 0, Eq. poisson) or
+ *         = Z^T S_L Z x + lambda Z^T (Jw . Z x) (screen 1, mass screening).
+ * Local products of different elements are independent (computed in
+ * parallel when built with OpenMP); Z^T then sums them serially in element
+ * order, node order, so the result does not depend on the thread count. */
+int or_apply_A(or_mesh *m, int screen, double lambda, const double *x, double *y)
+{
+    int n = m->n;
+    int64_t n3 = (int64_t)n * n * n;
+    int err = 0;
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+        double *wk = (double *)malloc(sizeof(double) * 4 * n3);
+        if (!wk) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            err = 1;
+        }
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t e = 0; e < m->E; e++)
+            if (wk) local_stiffness(m, e, x, m->yL + e * n3, wk, wk + n3, wk + 2 * n3, wk + 3 * n3);
+        free(wk);
+    }
+    if (err) return 1;
+    for (int64_t g = 0; g < m->n_global; g++) y[g] = 0.0;
+    for (int64_t q = 0; q < m->n_local; q++) {
+        int32_t g = m->l2g[q];
+        if (g >= 0) y[g] += m->yL[q];
+    }
+    if (screen == 0) {
+        for (int64_t g = 0; g < m->n_global; g++) y[g] += lambda * x[g];
+    } else {
+        for (int64_t q = 0; q < m->n_local; q++) {
+            int32_t g = m->l2g[q];
+            if (g >= 0) y[g] += lambda * (m->Jw[q] * x[g]);
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Right-hand sides                                                    */
+/* ------------------------------------------------------------------ */
+
+/* kind 0: b_g = 2 u01(seed, 2, lattice index) - 1 at every global DOF.
+ * kind 1: b = Z^T (Jw . f), f = (3 pi^2 + lambda) sin(pi x) sin(pi y) sin(pi z),
+ *         the load for u = sin sin sin under -Laplace u + lambda u = f. */
+void or_rhs(const or_mesh *m, int kind, uint64_t seed, double lambda, double *b)
+{
+    int N = m->N, n = m->n;
+    int64_t n3 = (int64_t)n * n * n;
+    const double pi = 3.14159265358979323846;
+    for (int64_t g = 0; g < m->n_global; g++) b[g] = 0.0;
+    for (int ez = 0; ez < m->Ez; ez++)
+        for (int ey = 0; ey < m->Ey; ey++)
+            for (int ex = 0; ex < m->Ex; ex++) {
+                int64_t e = ex + (int64_t)m->Ex * (ey + (int64_t)m->Ey * ez);
+                for (int k = 0; k < n; k++)
+                    for (int j = 0; j < n; j++)
+                        for (int i = 0; i < n; i++) {
+                            int64_t q = e * n3 + (k * n + j) * n + i;
+                            int32_t g = m->l2g[q];
+                            if (g < 0) continue;
+                            if (kind == 0) {
+                                int64_t I = (int64_t)N * ex + i, J = (int64_t)N * ey + j, K = (int64_t)N * ez + k;
+                                int64_t lat = I + ((int64_t)N * m->Ex + 1) * (J + ((int64_t)N * m->Ey + 1) * K);
+                                b[g] = 2.0 * or_u01(seed, 2, (uint64_t)lat) - 1.0;
+                            } else {
+                                const double *X = m->X + 3 * q;
+                                double f = (3.0 * pi * pi + lambda) * sin(pi * X[0]) * sin(pi * X[1]) * sin(pi * X[2]);
+                                b[g] += m->Jw[q] * f;
+                            }
+                        }
+            }
+}
+
+/* ------------------------------------------------------------------ */
+/* Conjugate gradients (Algorithm 1)                                   */
+/* ------------------------------------------------------------------ */
+
+static double dot(int64_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+/* Algorithm 1 on A = S + lambda I (or mass screening). x holds x0 on entry
+ * and the solution on exit. Stops when r.r <= rtol^2 b.b (rtol > 0) or after
+ * max_it iterations. hist (may be NULL) receives r_j.r_j for j = 0..iters.
+ * Returns 0 (done), 2 on breakdown (p.Ap <= 0 or not finite), 1 on no memory. */
+int or_cg(or_mesh *m, int screen, double lambda, const double *b, double *x,
+          double rtol, int max_it, int *iters, double *rel_res, double *hist)
+{
+    int64_t ng = m->n_global;
+    double *r = (double *)malloc(sizeof(double) * ng);
+    double *p = (double *)malloc(sizeof(double) * ng);
+    double *Ap = (double *)malloc(sizeof(double) * ng);
+    if (!r || !p || !Ap) { free(r); free(p); free(Ap); return 1; }
+    int status = 0;
+    /* r_0 = b - A x, p = r */
+    or_apply_A(m, screen, lambda, x, Ap);
+    for (int64_t i = 0; i < ng; i++) r[i] = b[i] - Ap[i];
+    for (int64_t i = 0; i < ng; i++) p[i] = r[i];
+    double bb = dot(ng, b, b);
+    double rr = dot(ng, r, r);
+    double tol2 = rtol * rtol * bb;
+    if (hist) hist[0] = rr;
+    int j = 0;
+    while (j < max_it && rr > tol2) {
+        or_apply_A(m, screen, lambda, p, Ap);
+        double pAp = dot(ng, p, Ap);
+        if (!(pAp > 0.0) || !isfinite(pAp)) { status = 2; break; }
+        double alpha = rr / pAp;
+        for (int64_t i = 0; i < ng; i++) x[i] = x[i] + alpha * p[i];
+        for (int64_t i = 0; i < ng; i++) r[i] = r[i] - alpha * Ap[i];
+        double rr_new = dot(ng, r, r);
+        double beta = rr_new / rr;
+        for (int64_t i = 0; i < ng; i++) p[i] = r[i] + beta * p[i];
+        rr = rr_new;
+        j++;
+        if (hist) hist[j] = rr;
+    }
+    *iters = j;
+    *rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    free(r); free(p); free(Ap);
+    return status;
+}
+
+/* Number of threads the parallel element loop uses (1 without OpenMP). */
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
