@@ -1,0 +1,193 @@
+/*
+ * hipbone_gb300.h -- C ABI of the GB300 (sm_103a) matrix-free spectral-element
+ * screened-Poisson operator and its conjugate-gradient solvers.
+ *
+ * The problem is the one hipBone (Chalmers, Mishra, McDougall & Warburton,
+ * arXiv 2202.12477) benchmarks:
+ *   - Sec. 2: a box of E hexahedral elements, polynomial degree N,
+ *     (N+1)^3 Gauss-Lobatto-Legendre (GLL) nodes per element, N_L = E (N+1)^3
+ *     element-local nodes and N_G assembled (global) degrees of freedom;
+ *   - Eq. (poisson):   A = S + lambda I;
+ *   - Eq. (stiffness): S = Z^T S_L Z with S_L^e = Dbold^T G^e Dbold;
+ *   - Sec. 3.1 (DOF storage): every vector lives in assembled form, length N_G;
+ *   - Algorithm 1: unpreconditioned conjugate gradients.
+ *
+ * Conventions for every call:
+ *   - Vectors are caller-owned DEVICE buffers of length n_global (hb_mesh_info),
+ *     contiguous, of the element type the precision argument names
+ *     (double for HB_F64, float for HB_F32). The library never frees them.
+ *   - Mesh arrays (node map, geometric factors, CSR of Z^T, workspace) are
+ *     library-owned device memory, released by hb_mesh_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Calls enqueue work on it and return without waiting, except
+ *     where a call says it synchronises.
+ *   - A mesh carries one workspace: calls on one mesh must not overlap in
+ *     time on different streams (issue them on one stream, or synchronise).
+ *   - Errors come back as hb_status; hb_last_error() gives a message for the
+ *     calling thread. Nothing throws across the ABI.
+ *   - The device is the current CUDA device at hb_mesh_create; later calls on
+ *     the mesh switch to it for their duration.
+ */
+#ifndef HIPBONE_GB300_H
+#define HIPBONE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HB_OK = 0,
+    HB_ERR_ARG = 1,            /* invalid argument (null pointer, size, mode) */
+    HB_ERR_NOMEM = 2,          /* device or host allocation failed */
+    HB_ERR_CUDA = 3,           /* a CUDA runtime call failed (see hb_last_error) */
+    HB_ERR_GEOMETRY = 4,       /* a Jacobian determinant <= 0 at some GLL node */
+    HB_ERR_BREAKDOWN = 5,      /* CG: p.Ap <= 0 or not finite (A not SPD) */
+    HB_ERR_NOT_CONVERGED = 6,  /* CG: max_it reached above the requested rtol */
+    HB_ERR_TIMEOUT = 7,        /* a bounded device wait ran out */
+    HB_ERR_BUSY = 8,           /* resource in use (server full, slot held) */
+    HB_ERR_NOT_FOUND = 9       /* unknown ticket or name */
+} hb_status;
+
+typedef enum {
+    HB_F64 = 0,    /* IEEE FP64 storage and arithmetic */
+    HB_F32 = 1,    /* FP32 storage and arithmetic, FP64 dot accumulation */
+    HB_MIXED = 2   /* CG only: FP32 inner CG inside an FP64 defect-correction loop */
+} hb_precision;
+
+typedef enum {
+    HB_SCREEN_IDENTITY = 0,  /* A = S + lambda I, Eq. (poisson) */
+    HB_SCREEN_MASS = 1       /* A = S + lambda M, M = Z^T diag(J w) Z (lumped GLL mass) */
+} hb_screen;
+
+/* Mesh description (Sec. 2: "regular mesh of E hexahedral elements" with a
+ * degree-N tensor GLL basis). The box is [0,1]^3 split into ex*ey*ez equal
+ * hexahedra; every vertex strictly inside the box is moved along each axis by
+ * (2u-1)*perturb*h_axis with u = u01(seed, 1, 3*vertex_index+axis) (see
+ * hb_u01); elements map trilinearly from their 8 vertices. */
+typedef struct {
+    int ex, ey, ez;            /* elements per axis, each >= 1 */
+    int N;                     /* polynomial degree, 1..15 */
+    double perturb;            /* rho, 0 <= rho < 0.5 */
+    uint64_t seed;             /* seed of the vertex perturbation */
+    unsigned dirichlet_faces;  /* bit f masks face f: 0 x=0, 1 x=1, 2 y=0, 3 y=1,
+                                  4 z=0, 5 z=1; 0x3F = all faces (the paper's case) */
+    int keep_fp32_copy;        /* 1: also keep FP32 geometric factors (HB_F32 and
+                                  HB_MIXED need them) */
+} hb_mesh_desc;
+
+/* Read-only view of a mesh. Device pointers stay valid until hb_mesh_destroy.
+ * Layouts (element e = ex + Ex*(ey + Ey*ez); local node (i,j,k), i fastest):
+ *   l2g[e*(N+1)^3 + (k*(N+1)+j)*(N+1)+i]  global id of the node, -1 on a
+ *       Dirichlet face (this is the mask: masked <=> l2g < 0). Global ids are
+ *       lexicographic over the unmasked lattice nodes (N*ex+i, N*ey+j, N*ez+k),
+ *       first coordinate fastest.
+ *   geo[((e*(N+1)+k)*7 + c)*(N+1)^2 + j*(N+1)+i]  FP64 factor c of node (i,j,k):
+ *       c = 0..5 the metric entries G_rr G_rs G_rt G_ss G_st G_tt (GLL weights
+ *       and det J included, Sec. 2), c = 6 the quadrature weight w_i w_j w_k det J.
+ *   geo32: the same in FP32 (NULL unless keep_fp32_copy).
+ *   csr_rowptr[n_global+1], csr_cols[nnz]: Z^T as CSR; row g lists the local
+ *       node ids that carry global id g, ascending. */
+typedef struct {
+    int64_t n_local;           /* N_L = E (N+1)^3 */
+    int64_t n_global;          /* N_G */
+    int64_t n_elem;            /* E */
+    int64_t nnz;               /* unmasked local nodes = entries of Z */
+    int N;
+    const int32_t *l2g;
+    const double *geo;
+    const float *geo32;
+    const int32_t *csr_rowptr;
+    const int32_t *csr_cols;
+    double min_detJ;           /* smallest det J over all GLL nodes */
+    size_t device_bytes;       /* device memory the mesh holds */
+} hb_mesh_info_t;
+
+typedef struct hb_mesh hb_mesh;
+
+/* Builds the mesh on the current device: GLL nodes, derivative matrix, node
+ * map, CSR of Z^T and the geometric factors (Sec. 2, Sec. 3.2). Synchronises
+ * `stream` once at the end. Returns HB_ERR_GEOMETRY (and no mesh) if det J <= 0
+ * at any GLL node; HB_ERR_ARG for N outside 1..15, non-positive element counts,
+ * perturb outside [0, 0.5) or more than 2^31-1 local nodes. */
+hb_status hb_mesh_create(const hb_mesh_desc *desc, void *stream, hb_mesh **out);
+hb_status hb_mesh_destroy(hb_mesh *mesh);
+hb_status hb_mesh_info(const hb_mesh *mesh, hb_mesh_info_t *out);
+
+/* Copies of mesh data to HOST buffers, for inspection and tests (synchronous).
+ * l2g: n_local int32; geo: 7*n_local doubles in the geo layout above. */
+hb_status hb_mesh_copy_l2g(const hb_mesh *mesh, int32_t *host_l2g);
+hb_status hb_mesh_copy_geo(const hb_mesh *mesh, double *host_geo);
+
+/* y = A x on assembled vectors (Eq. poisson with Eq. stiffness; Sec. 3.2):
+ * gathers x through Z, applies S_L element by element (tensor-product
+ * derivatives with the geometric factors), sums back with Z^T in a fixed order
+ * (no atomics: results are bitwise reproducible), and adds lambda x
+ * (identity screening) or lambda M x (mass screening).
+ * prec HB_F64: x, y are double*; HB_F32: float* (needs keep_fp32_copy).
+ * x and y must not overlap. */
+hb_status hb_apply_A(const hb_mesh *mesh, hb_precision prec, hb_screen screen,
+                     double lambda, const void *x, void *y, void *stream);
+
+/* a.b over n_global entries, accumulated in FP64 (warp shuffles, then a fixed
+ * block order: bitwise reproducible). prec names the element type of a and b.
+ * Writes the result to *out_dev (device double, may be NULL) and, if out_host
+ * is not NULL, also to *out_host -- which synchronises `stream`. */
+hb_status hb_dot(const hb_mesh *mesh, hb_precision prec, const void *a, const void *b,
+                 double *out_dev, double *out_host, void *stream);
+
+/* Right-hand side on the assembled DOFs (FP64, length n_global).
+ * kind 0: b_g = 2 u01(seed, 2, I + (N ex+1)(J + (N ey+1) K)) - 1 at the global
+ *         node with lattice coordinates (I,J,K) -- hipBone's pseudo-random
+ *         forcing (Sec. 3), uniform in [-1, 1).
+ * kind 1: b = Z^T (Jw . f), f = (3 pi^2 + lambda) sin(pi x) sin(pi y) sin(pi z):
+ *         the load whose exact solution is u = sin sin sin for
+ *         -Laplace u + lambda u = f (exact under mass screening; lambda = 0 for
+ *         identity screening). */
+hb_status hb_fill_rhs(const hb_mesh *mesh, int kind, uint64_t seed, double lambda,
+                      double *b, void *stream);
+
+typedef struct {
+    hb_precision prec;     /* HB_F64, HB_F32 or HB_MIXED */
+    hb_screen screen;
+    double lambda;
+    double rtol;           /* stop when ||r||_2 <= rtol ||b||_2; 0 runs exactly max_it */
+    int max_it;            /* iteration cap (inner iterations in HB_MIXED) */
+    double inner_rtol;     /* HB_MIXED: inner FP32 CG reduces its residual by this */
+    int max_outer;         /* HB_MIXED: cap on FP64 defect-correction steps */
+} hb_cg_opts;
+
+typedef struct {
+    int iters;             /* CG iterations (all inner iterations in HB_MIXED) */
+    int outer_iters;       /* HB_MIXED: defect-correction steps; else 0 */
+    double rel_res;        /* ||r||_2 / ||b||_2 at exit (FP64 residual in HB_MIXED) */
+    double time_ms;        /* device time of the solve (CUDA events) */
+    hb_status status;
+} hb_cg_result;
+
+/* Solves A x = b with Algorithm 1 (x holds x0 on entry, the solution on exit;
+ * both FP64 device vectors of length n_global). HB_F64 runs Algorithm 1 in FP64.
+ * HB_MIXED runs FP64 defect correction: r = b - A x in FP64, an FP32 CG on
+ * A d = r to inner_rtol (FP64 dot accumulation), x += d in FP64, until
+ * ||b - A x|| <= rtol ||b||. The p.Ap and r.r reductions are fused into the
+ * kernels that produce their operands (Sec. 3.5). Synchronises `stream`.
+ * Returns HB_ERR_BREAKDOWN, HB_ERR_NOT_CONVERGED (rtol > 0 only) or HB_OK;
+ * res (may be NULL) receives the counts, residual and device time. */
+hb_status hb_cg_solve(const hb_mesh *mesh, const hb_cg_opts *opts, const double *b,
+                      double *x, hb_cg_result *res, void *stream);
+
+/* The library's uniform random number, u01(seed, stream, idx) =
+ * (splitmix64(seed ^ (stream * 0x9E3779B97F4A7C15) + idx) >> 11) * 2^-53, with
+ * splitmix64(s) the SplitMix64 output for state s (Steele, Lea & Flood 2014). */
+double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *hb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIPBONE_GB300_H */

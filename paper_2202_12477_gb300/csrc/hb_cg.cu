@@ -1,0 +1,570 @@
+// Assembly Z^T, dot products and conjugate gradients (hipBone, arXiv
+// 2202.12477: Eq. poisson, Sec. 3.2 for the gather, Sec. 3.5 and Algorithm 1
+// for CG).
+//
+// Every reduction runs on a fixed grid (a function of the vector length only);
+// each block reduces its grid-stride share with warp shuffles, stores one
+// partial, and the block that finishes last adds the partials in index order.
+// Results are therefore bitwise reproducible and need no atomics on data.
+//
+// The CG scalars of Algorithm 1 (r.r, p.Ap, alpha, beta, the iteration count)
+// stay in device memory: p.Ap is reduced inside the assembly kernel that
+// produces Ap, r.r inside the kernel that updates r, and the kernels of a
+// finished solve return at once, so iterations are enqueued in runs without
+// host round trips.
+#include <cmath>
+
+#include "hb_internal.h"
+
+namespace hb {
+
+// ---------------------------------------------------------------- accumulators
+
+// FP64 accumulation of products. For FP32 operands the FP64 pipe of GB300 is
+// slow, so the running sum is carried as an unevaluated pair of floats with
+// error-free transformations (Dekker's two-product via fma, Knuth's two-sum):
+// about 48 significant bits, the accuracy of an FP64 sum of these products.
+template <typename T>
+struct dot_acc;
+
+template <>
+struct dot_acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct dot_acc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float a, float b)
+    {
+        float p = a * b;
+        float pe = fmaf(a, b, -p);
+        float t = hi + p;
+        float bp = t - hi;
+        float err = (hi - (t - bp)) + (p - bp);
+        hi = t;
+        lo += err + pe;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// ---------------------------------------------------------------- grid reduction
+
+// Sums NV values over the grid in a fixed order. Returns true in the block that
+// arrives last (in all of its threads), with tot[] holding the grid totals.
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], double *partials, unsigned *counter, double (&tot)[NV])
+{
+    __shared__ double sh[NV][32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        double a = v[q];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) sh[q][wid] = a;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            double a = lane < nw ? sh[q][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) partials[q * HB_RED_BLOCKS + blockIdx.x] = a;
+        }
+        if (lane == 0) {
+            __threadfence();
+            unsigned t = atomicAdd(counter, 1u);
+            s_last = (t == gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        double a = 0.0;
+        for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) a += __ldcg(&partials[q * HB_RED_BLOCKS + p]);
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        __syncthreads();
+        if (lane == 0) sh[q][wid] = a;
+        __syncthreads();
+        if (wid == 0) {
+            double b = lane < nw ? sh[q][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+            if (lane == 0) sh[q][0] = b;
+        }
+        __syncthreads();
+        tot[q] = sh[q][0];
+    }
+    if (threadIdx.x == 0) *counter = 0;
+    return true;
+}
+
+static inline int red_grid(int64_t n)
+{
+    int64_t g = (n + HB_RED_THREADS * 4 - 1) / (HB_RED_THREADS * 4);
+    if (g > HB_RED_BLOCKS) g = HB_RED_BLOCKS;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------- assembly
+
+// y_g = sum_{p in row g} y_L[cols[p]] + lambda (x_g | M_gg x_g); optional x.y.
+template <typename T, int SCREEN, int DOT>
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    assemble_kernel(const T *__restrict__ yL, const int32_t *__restrict__ rowptr,
+                    const int32_t *__restrict__ cols, const T *__restrict__ x, const T *__restrict__ mdiag,
+                    double lambda, T *__restrict__ y, int64_t ng, double *partials, unsigned *counter,
+                    hb_cg_state *st)
+{
+    if (DOT == HB_DOT_CG_PAP && st->run == 0) return;
+    const T lam = (T)lambda;
+    dot_acc<T> acc;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        const int a = __ldg(rowptr + g), z = __ldg(rowptr + g + 1);
+        T s = T(0);
+        for (int p = a; p < z; p++) s += __ldcs(yL + __ldcs(cols + p));
+        const T xv = x[g];
+        s += SCREEN ? lam * (mdiag[g] * xv) : lam * xv;
+        y[g] = s;
+        if (DOT) acc.add(xv, s);
+    }
+    if (DOT) {
+        double v[1] = {acc.value()}, tot[1];
+        if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+            if (DOT == HB_DOT_CG_PAP) {
+                const double pAp = tot[0];
+                st->pAp = pAp;
+                if (!(pAp > 0.0) || !isfinite(pAp)) {
+                    st->status = HB_ERR_BREAKDOWN;
+                    st->run = 0;
+                } else {
+                    st->alpha = st->rr / pAp;
+                }
+            } else {
+                st->dot_tmp = tot[0];
+            }
+        }
+    }
+}
+
+template <typename T>
+hb_status launch_assemble(const hb_mesh *m, const T *yL, const T *x, T *y, const T *mdiag, int screen,
+                          double lambda, hb_cg_state *st, int dot_mode, cudaStream_t s)
+{
+    const int64_t ng = m->n_global;
+    if (ng == 0) return HB_OK;
+    const int grid = red_grid(ng);
+    unsigned *ctr = m->counters + 0;
+#define HB_ASM(SC, DM)                                                                                   \
+    assemble_kernel<T, SC, DM><<<grid, HB_RED_THREADS, 0, s>>>(yL, m->rowptr, m->cols, x, mdiag, lambda, \
+                                                               y, ng, m->partials, ctr, st)
+    if (screen == 0) {
+        if (dot_mode == HB_DOT_NONE) HB_ASM(0, HB_DOT_NONE);
+        else if (dot_mode == HB_DOT_TO_TMP) HB_ASM(0, HB_DOT_TO_TMP);
+        else HB_ASM(0, HB_DOT_CG_PAP);
+    } else {
+        if (dot_mode == HB_DOT_NONE) HB_ASM(1, HB_DOT_NONE);
+        else if (dot_mode == HB_DOT_TO_TMP) HB_ASM(1, HB_DOT_TO_TMP);
+        else HB_ASM(1, HB_DOT_CG_PAP);
+    }
+#undef HB_ASM
+    HB_CHECK_LAUNCH();
+    return HB_OK;
+}
+
+// ---------------------------------------------------------------- dot
+
+template <typename T>
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    dot_kernel(const T *__restrict__ a, const T *__restrict__ b, int64_t n, double *out, double *partials,
+               unsigned *counter)
+{
+    dot_acc<T> acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc.add(a[i], b[i]);
+    double v[1] = {acc.value()}, tot[1];
+    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
+}
+
+// ---------------------------------------------------------------- CG kernels
+
+// r = b - Ax; p = r; r.r and b.b; state set up for Algorithm 1.
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    cg_init_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
+                   double *__restrict__ p, int64_t n, double rtol, int max_it, double *partials,
+                   unsigned *counter, hb_cg_state *st)
+{
+    dot_acc<double> rr, bb;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double bi = b[i];
+        const double ri = bi - Ax[i];
+        r[i] = ri;
+        p[i] = ri;
+        rr.add(ri, ri);
+        bb.add(bi, bi);
+    }
+    double v[2] = {rr.value(), bb.value()}, tot[2];
+    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        st->rr = tot[0];
+        st->bb = tot[1];
+        st->tol2 = rtol * rtol * tot[1];
+        st->it = 0;
+        st->max_it = max_it;
+        st->status = HB_OK;
+        st->alpha = st->beta = st->pAp = 0.0;
+        st->run = (max_it > 0 && tot[0] > st->tol2) ? 1 : 0;
+        st->next_run = st->run;
+    }
+}
+
+// Algorithm 1, line 9 and the r.r of line 10: r -= alpha Ap.
+template <typename T>
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    cg_update_r_kernel(T *__restrict__ r, const T *__restrict__ Ap, int64_t n, double *partials,
+                       unsigned *counter, hb_cg_state *st)
+{
+    if (st->run == 0) return;
+    const T alpha = (T)st->alpha;
+    dot_acc<T> acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T ri = r[i] - alpha * Ap[i];
+        r[i] = ri;
+        acc.add(ri, ri);
+    }
+    double v[1] = {acc.value()}, tot[1];
+    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+        const double rr_new = tot[0];
+        st->rr_new = rr_new;
+        st->beta = rr_new / st->rr;
+        st->rr = rr_new;
+        st->it += 1;
+        st->next_run = (st->it < st->max_it && rr_new > st->tol2) ? 1 : 0;
+    }
+}
+
+// Algorithm 1, lines 8 and 11 (x += alpha p with the old p, then p = r + beta p).
+// The block that finishes last ends the iteration: run <- next_run.
+template <typename T>
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    cg_update_xp_kernel(T *__restrict__ x, T *__restrict__ p, const T *__restrict__ r, int64_t n,
+                        unsigned *counter, hb_cg_state *st)
+{
+    __shared__ int s_last;
+    if (st->run == 0) return;
+    const T alpha = (T)st->alpha, beta = (T)st->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T pi = p[i];
+        x[i] = x[i] + alpha * pi;
+        p[i] = r[i] + beta * pi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        s_last = (t == gridDim.x - 1);
+        if (s_last) {
+            *counter = 0;
+            st->run = st->next_run;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- mixed precision
+
+// Outer residual: r = b - A x (FP64) with r.r and b.b into the outer state.
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    residual_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
+                    int64_t n, double *partials, unsigned *counter, hb_cg_state *st)
+{
+    dot_acc<double> rr, bb;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double bi = b[i];
+        const double ri = bi - Ax[i];
+        r[i] = ri;
+        rr.add(ri, ri);
+        bb.add(bi, bi);
+    }
+    double v[2] = {rr.value(), bb.value()}, tot[2];
+    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        st->rr = tot[0];
+        st->bb = tot[1];
+    }
+}
+
+// Inner start: r32 = r / ||r|| (so the inner system is well scaled in FP32),
+// p32 = r32, d32 = 0; inner state for A d = r32 with relative target rtol_in.
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    inner_init_kernel(const double *__restrict__ r, float *__restrict__ r32, float *__restrict__ p32,
+                      float *__restrict__ d32, int64_t n, double rtol_in, int max_it, double *partials,
+                      unsigned *counter, const hb_cg_state *outer, hb_cg_state *st)
+{
+    const double scale = 1.0 / sqrt(outer->rr);
+    dot_acc<float> acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = (float)(r[i] * scale);
+        r32[i] = v;
+        p32[i] = v;
+        d32[i] = 0.0f;
+        acc.add(v, v);
+    }
+    double v[1] = {acc.value()}, tot[1];
+    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+        st->rr = tot[0];
+        st->bb = tot[0];
+        st->tol2 = rtol_in * rtol_in * tot[0];
+        st->it = 0;
+        st->max_it = max_it;
+        st->status = HB_OK;
+        st->alpha = st->beta = st->pAp = 0.0;
+        st->run = (max_it > 0 && tot[0] > st->tol2) ? 1 : 0;
+        st->next_run = st->run;
+    }
+}
+
+// x += ||r|| d32 (FP64 solution update).
+__global__ void update_x_kernel(double *__restrict__ x, const float *__restrict__ d32, int64_t n,
+                                const hb_cg_state *outer)
+{
+    const double s = sqrt(outer->rr);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += s * (double)d32[i];
+}
+
+}  // namespace hb
+
+using namespace hb;
+
+// ---------------------------------------------------------------- internal entry points
+
+hb_status hb_launch_assemble_f64(const hb_mesh *m, const double *yL, const double *x, double *y, int screen,
+                                 double lambda, hb_cg_state *st, int dot_mode, cudaStream_t s)
+{
+    return launch_assemble<double>(m, yL, x, y, m->mdiag, screen, lambda, st, dot_mode, s);
+}
+
+hb_status hb_launch_assemble_f32(const hb_mesh *m, const float *yL, const float *x, float *y, int screen,
+                                 double lambda, hb_cg_state *st, int dot_mode, cudaStream_t s)
+{
+    if (!m->mdiag32) { hb_set_error("mesh has no FP32 data (keep_fp32_copy = 0)"); return HB_ERR_ARG; }
+    return launch_assemble<float>(m, yL, x, y, m->mdiag32, screen, lambda, st, dot_mode, s);
+}
+
+hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, double lambda, const void *x, void *y,
+                          hb_cg_state *st, int dot_mode, cudaStream_t s)
+{
+    const int *run = (dot_mode == HB_DOT_CG_PAP && st) ? &st->run : nullptr;
+    hb_status r;
+    if (prec == HB_F64) {
+        r = hb_launch_ax_local_f64(m, (const double *)x, (double *)m->yL, run, s);
+        if (r != HB_OK) return r;
+        return hb_launch_assemble_f64(m, (const double *)m->yL, (const double *)x, (double *)y, screen, lambda, st,
+                                      dot_mode, s);
+    }
+    if (prec == HB_F32) {
+        r = hb_launch_ax_local_f32(m, (const float *)x, (float *)m->yL, run, s);
+        if (r != HB_OK) return r;
+        return hb_launch_assemble_f32(m, (const float *)m->yL, (const float *)x, (float *)y, screen, lambda, st,
+                                      dot_mode, s);
+    }
+    hb_set_error("precision %d not valid for the operator", (int)prec);
+    return HB_ERR_ARG;
+}
+
+hb_status hb_launch_dot_f64(const hb_mesh *m, const double *a, const double *b, int64_t n, double *out,
+                            cudaStream_t s)
+{
+    dot_kernel<double><<<red_grid(n), HB_RED_THREADS, 0, s>>>(a, b, n, out, m->partials, m->counters + 1);
+    HB_CHECK_LAUNCH();
+    return HB_OK;
+}
+
+hb_status hb_launch_dot_f32(const hb_mesh *m, const float *a, const float *b, int64_t n, double *out,
+                            cudaStream_t s)
+{
+    dot_kernel<float><<<red_grid(n), HB_RED_THREADS, 0, s>>>(a, b, n, out, m->partials, m->counters + 1);
+    HB_CHECK_LAUNCH();
+    return HB_OK;
+}
+
+// ---------------------------------------------------------------- C ABI
+
+static bool valid_screen(int s) { return s == HB_SCREEN_IDENTITY || s == HB_SCREEN_MASS; }
+
+extern "C" hb_status hb_apply_A(const hb_mesh *m, hb_precision prec, hb_screen screen, double lambda,
+                                const void *x, void *y, void *stream)
+{
+    hb_clear_error();
+    if (!m || (!x && m->n_global) || (!y && m->n_global)) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (!valid_screen(screen)) { hb_set_error("bad screen mode %d", (int)screen); return HB_ERR_ARG; }
+    if (prec != HB_F64 && prec != HB_F32) { hb_set_error("hb_apply_A takes HB_F64 or HB_F32"); return HB_ERR_ARG; }
+    if (m->n_global == 0) return HB_OK;
+    const size_t esz = prec == HB_F64 ? 8 : 4;
+    const char *xa = (const char *)x, *ya = (const char *)y;
+    if (xa < ya + esz * m->n_global && ya < xa + esz * m->n_global) { hb_set_error("x and y overlap"); return HB_ERR_ARG; }
+    hb_device_guard dg(m->device);
+    return hb_apply_A_impl(m, prec, screen, lambda, x, y, nullptr, HB_DOT_NONE, (cudaStream_t)stream);
+}
+
+extern "C" hb_status hb_dot(const hb_mesh *m, hb_precision prec, const void *a, const void *b, double *out_dev,
+                            double *out_host, void *stream)
+{
+    hb_clear_error();
+    if (!m || ((!a || !b) && m->n_global)) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (prec != HB_F64 && prec != HB_F32) { hb_set_error("hb_dot takes HB_F64 or HB_F32"); return HB_ERR_ARG; }
+    hb_device_guard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    double *dst = out_dev ? out_dev : &m->state[1].dot_tmp;
+    if (m->n_global == 0) {
+        HB_TRY_CUDA(cudaMemsetAsync(dst, 0, sizeof(double), s));
+    } else {
+        hb_status r = prec == HB_F64
+                          ? hb_launch_dot_f64(m, (const double *)a, (const double *)b, m->n_global, dst, s)
+                          : hb_launch_dot_f32(m, (const float *)a, (const float *)b, m->n_global, dst, s);
+        if (r != HB_OK) return r;
+    }
+    if (out_host) {
+        HB_TRY_CUDA(cudaMemcpyAsync(out_host, dst, sizeof(double), cudaMemcpyDeviceToHost, s));
+        HB_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    return HB_OK;
+}
+
+// Workspace vectors for the solvers, grown on demand (FP64 r, p, Ap; FP32 r, p, Ap, d).
+static hb_status cg_workspace(hb_mesh *m)
+{
+    const size_t need = (size_t)m->n_global * (3 * sizeof(double) + 4 * sizeof(float)) + 256;
+    if (m->cg_vec_bytes >= need) return HB_OK;
+    if (m->cg_vec) cudaFree(m->cg_vec);
+    m->cg_vec = nullptr;
+    m->cg_vec_bytes = 0;
+    HB_TRY_CUDA(cudaMalloc(&m->cg_vec, need));
+    m->cg_vec_bytes = need;
+    return HB_OK;
+}
+
+// Enqueues `count` iterations of Algorithm 1 on the vectors (x, r, p, Ap).
+template <typename T>
+static hb_status cg_iterations(const hb_mesh *m, hb_precision prec, int screen, double lambda, T *x, T *r, T *p,
+                               T *Ap, hb_cg_state *st, int count, cudaStream_t s)
+{
+    const int64_t n = m->n_global;
+    const int grid = red_grid(n);
+    for (int it = 0; it < count; it++) {
+        hb_status rs = hb_apply_A_impl(m, prec, screen, lambda, p, Ap, st, HB_DOT_CG_PAP, s);
+        if (rs != HB_OK) return rs;
+        cg_update_r_kernel<T><<<grid, HB_RED_THREADS, 0, s>>>(r, Ap, n, m->partials, m->counters + 2, st);
+        HB_CHECK_LAUNCH();
+        cg_update_xp_kernel<T><<<grid, HB_RED_THREADS, 0, s>>>(x, p, r, n, m->counters + 3, st);
+        HB_CHECK_LAUNCH();
+    }
+    return HB_OK;
+}
+
+// Runs iterations until the device state says stop; returns the final state.
+template <typename T>
+static hb_status cg_drive(const hb_mesh *m, hb_precision prec, int screen, double lambda, T *x, T *r, T *p, T *Ap,
+                          hb_cg_state *st, int max_it, cudaStream_t s, hb_cg_state *out)
+{
+    int done = 0;
+    const int chunk_first = 25;
+    HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
+    HB_TRY_CUDA(cudaStreamSynchronize(s));
+    while (m->state_host->run && done < max_it) {
+        int count = max_it - done;
+        if (count > chunk_first && m->state_host->tol2 > 0.0) count = chunk_first;
+        hb_status rs = cg_iterations<T>(m, prec, screen, lambda, x, r, p, Ap, st, count, s);
+        if (rs != HB_OK) return rs;
+        done += count;
+        HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
+        HB_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    *out = *m->state_host;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const double *b, double *x,
+                                 hb_cg_result *res, void *stream)
+{
+    hb_clear_error();
+    hb_mesh *m = const_cast<hb_mesh *>(mc);
+    if (!m || !o || ((!b || !x) && m->n_global)) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (!valid_screen(o->screen)) { hb_set_error("bad screen mode"); return HB_ERR_ARG; }
+    if (o->prec != HB_F64 && o->prec != HB_MIXED) { hb_set_error("hb_cg_solve takes HB_F64 or HB_MIXED"); return HB_ERR_ARG; }
+    if (o->max_it < 0 || !(o->rtol >= 0.0)) { hb_set_error("bad max_it or rtol"); return HB_ERR_ARG; }
+    if (o->prec == HB_MIXED && (!m->geo32 || !m->mdiag32)) { hb_set_error("HB_MIXED needs keep_fp32_copy"); return HB_ERR_ARG; }
+    hb_device_guard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    hb_cg_result R{};
+    R.status = HB_OK;
+    const int64_t n = m->n_global;
+    if (n == 0) {
+        if (res) *res = R;
+        return HB_OK;
+    }
+    hb_status rs = cg_workspace(m);
+    if (rs != HB_OK) return rs;
+    double *r = (double *)m->cg_vec, *p = r + n, *Ap = p + n;
+    float *r32 = (float *)(Ap + n), *p32 = r32 + n, *Ap32 = p32 + n, *d32 = Ap32 + n;
+    const int grid = red_grid(n);
+    hb_cg_state *st = m->state, *st_in = m->state + 1;
+    HB_TRY_CUDA(cudaEventRecord(m->ev0, s));
+    hb_cg_state fin{};
+    if (o->prec == HB_F64) {
+        // r0 = b - A x0, p = r0 (Algorithm 1, lines 4-5)
+        rs = hb_apply_A_impl(m, HB_F64, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
+        if (rs != HB_OK) return rs;
+        cg_init_kernel<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, p, n, o->rtol, o->max_it, m->partials,
+                                                       m->counters + 2, st);
+        HB_CHECK_LAUNCH();
+        rs = cg_drive<double>(m, HB_F64, o->screen, o->lambda, x, r, p, Ap, st, o->max_it, s, &fin);
+        if (rs != HB_OK) return rs;
+        R.iters = fin.it;
+        R.rel_res = fin.bb > 0.0 ? sqrt(fin.rr / fin.bb) : 0.0;
+        if (fin.status == HB_ERR_BREAKDOWN) R.status = HB_ERR_BREAKDOWN;
+        else if (o->rtol > 0.0 && fin.rr > fin.tol2) R.status = HB_ERR_NOT_CONVERGED;
+    } else {
+        const double rtol_in = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-4;
+        const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
+        int used = 0, outer = 0;
+        double rel = 0.0;
+        for (;;) {
+            rs = hb_apply_A_impl(m, HB_F64, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
+            if (rs != HB_OK) return rs;
+            residual_kernel<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, n, m->partials, m->counters + 2, st);
+            HB_CHECK_LAUNCH();
+            HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
+            HB_TRY_CUDA(cudaStreamSynchronize(s));
+            const double rr = m->state_host->rr, bb = m->state_host->bb;
+            rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+            if (!std::isfinite(rel)) { R.status = HB_ERR_BREAKDOWN; break; }
+            if (bb == 0.0 || rr <= o->rtol * o->rtol * bb) break;
+            if (outer >= max_outer || used >= o->max_it) { R.status = HB_ERR_NOT_CONVERGED; break; }
+            inner_init_kernel<<<grid, HB_RED_THREADS, 0, s>>>(r, r32, p32, d32, n, rtol_in, o->max_it - used,
+                                                              m->partials, m->counters + 2, st, st_in);
+            HB_CHECK_LAUNCH();
+            rs = cg_drive<float>(m, HB_F32, o->screen, o->lambda, d32, r32, p32, Ap32, st_in, o->max_it - used, s,
+                                 &fin);
+            if (rs != HB_OK) return rs;
+            used += fin.it;
+            outer++;
+            if (fin.status == HB_ERR_BREAKDOWN && fin.it == 0) { R.status = HB_ERR_BREAKDOWN; break; }
+            update_x_kernel<<<grid, HB_RED_THREADS, 0, s>>>(x, d32, n, st);
+            HB_CHECK_LAUNCH();
+        }
+        R.iters = used;
+        R.outer_iters = outer;
+        R.rel_res = rel;
+    }
+    HB_TRY_CUDA(cudaEventRecord(m->ev1, s));
+    HB_TRY_CUDA(cudaEventSynchronize(m->ev1));
+    float ms = 0.f;
+    HB_TRY_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+    R.time_ms = ms;
+    if (res) *res = R;
+    return R.status;
+}

@@ -1,0 +1,130 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "hipbone_gb300.h"
+
+#define HB_MAX_N 15
+#define HB_RED_BLOCKS 608   // fixed grid of every reduction kernel (4 x 152 SMs)
+#define HB_RED_THREADS 256
+
+// ---------------------------------------------------------------- errors
+
+void hb_set_error(const char *fmt, ...);
+void hb_clear_error();
+
+#define HB_TRY_CUDA(call)                                                          \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            hb_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                \
+                         cudaGetErrorString(e_));                                  \
+            return e_ == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;   \
+        }                                                                          \
+    } while (0)
+
+#define HB_CHECK_LAUNCH() HB_TRY_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- CG device state
+
+// Scalars of Algorithm 1 kept on the device so that no iteration waits on the
+// host. `run` says whether the current iteration does any work; kernels of a
+// finished solve return at once, so a captured run of iterations may overshoot.
+struct hb_cg_state {
+    double rr;        // r_j . r_j
+    double rr_new;    // r_{j+1} . r_{j+1}
+    double pAp;       // p . A p
+    double alpha, beta;
+    double tol2;      // rtol^2 b.b
+    double bb;        // b . b
+    double dot_tmp;   // scratch result of a stand-alone dot
+    int it;           // iterations done
+    int max_it;
+    int run;          // 1 while the solve is running
+    int next_run;
+    int status;       // hb_status
+    int pad;
+};
+
+// ---------------------------------------------------------------- mesh
+
+struct hb_mesh {
+    int device;
+    hb_mesh_desc desc;
+    int N, n;
+    int64_t E, n_local, n_global, nnz;
+    int32_t *l2g;       // [E][n^3]
+    double *geo;        // [E][n][7][n^2]
+    float *geo32;       // same layout (optional)
+    int32_t *rowptr;    // [n_global + 1]
+    int32_t *cols;      // [nnz]
+    double *mdiag;      // [n_global] assembled J w (lumped mass)
+    float *mdiag32;
+    void *yL;           // [n_local] doubles: element-local operator output
+    // workspace for reductions and CG
+    double *partials;   // [2 * HB_RED_BLOCKS]
+    unsigned *counters; // [4]
+    hb_cg_state *state; // device CG states [4]: 0 outer/FP64, 1 inner/dot
+    hb_cg_state *state_host;  // pinned mirror
+    void *cg_vec;       // r, p, Ap (FP64) then FP32 inner vectors
+    size_t cg_vec_bytes;
+    double min_detJ;
+    size_t device_bytes;
+    cudaEvent_t ev0, ev1;
+};
+
+// Reference element data computed on the host for every degree 1..15 (GLL
+// nodes by Newton, derivative matrix by barycentric weights).
+void hb_reference_element(int N, double *xi, double *w, double *D);
+
+// Uploads the derivative matrices (FP64 and FP32, D and D^T) of all degrees to
+// the current device once per device.
+hb_status hb_ensure_device_tables();
+const double *hb_dev_D64(int N);
+const float *hb_dev_D32(int N);
+
+// ---------------------------------------------------------------- launchers
+
+// y_L = S_L Z x for every element (FP64 / FP32).
+hb_status hb_launch_ax_local_f64(const hb_mesh *m, const double *x, double *yL, const int *run, cudaStream_t s);
+hb_status hb_launch_ax_local_f32(const hb_mesh *m, const float *x, float *yL, const int *run, cudaStream_t s);
+
+// y = Z^T y_L + lambda (x or M x); optional fused x.y into st->pAp (and the
+// CG breakdown test / alpha when `cg` is set).
+hb_status hb_launch_assemble_f64(const hb_mesh *m, const double *yL, const double *x, double *y,
+                                 int screen, double lambda, hb_cg_state *st, int dot_mode,
+                                 cudaStream_t s);
+hb_status hb_launch_assemble_f32(const hb_mesh *m, const float *yL, const float *x, float *y,
+                                 int screen, double lambda, hb_cg_state *st, int dot_mode,
+                                 cudaStream_t s);
+
+hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, double lambda,
+                          const void *x, void *y, hb_cg_state *st, int dot_mode, cudaStream_t s);
+
+// a.b in FP64 into *out (device).
+hb_status hb_launch_dot_f64(const hb_mesh *m, const double *a, const double *b, int64_t n,
+                            double *out, cudaStream_t s);
+hb_status hb_launch_dot_f32(const hb_mesh *m, const float *a, const float *b, int64_t n,
+                            double *out, cudaStream_t s);
+
+// dot_mode of the assembly kernel
+enum { HB_DOT_NONE = 0, HB_DOT_TO_TMP = 1, HB_DOT_CG_PAP = 2 };
+
+struct hb_device_guard {
+    int prev;
+    bool ok;
+    explicit hb_device_guard(int dev) : prev(-1), ok(true)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~hb_device_guard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};

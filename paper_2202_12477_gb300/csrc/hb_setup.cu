@@ -1,0 +1,703 @@
+// Mesh setup on the device: reference element, node map, Z^T as CSR and the
+// geometric factors (hipBone, arXiv 2202.12477, Sec. 2 and Sec. 3.2).
+//
+// Routes chosen here on purpose differ from the textbook closed forms:
+//   - GLL nodes by Newton's method on q(x) = (1-x^2) P_N'(x) written as
+//     N (P_{N-1}(x) - x P_N(x)), with q'(x) = -N(N+1) P_N(x);
+//   - the derivative matrix from barycentric weights, diagonal by negative sums;
+//   - the Jacobian by applying that derivative matrix to the nodal coordinates
+//     (exact, since a trilinear map is a polynomial of degree 1 <= N per axis).
+#include <cmath>
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "hb_internal.h"
+
+// ---------------------------------------------------------------- errors
+
+static thread_local char g_err[512];
+
+void hb_set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+void hb_clear_error() { g_err[0] = 0; }
+
+extern "C" const char *hb_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------- random numbers
+
+__host__ __device__ static inline uint64_t hb_splitmix64(uint64_t state)
+{
+    uint64_t z = state + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ static inline double hb_u01_impl(uint64_t seed, uint64_t stream, uint64_t idx)
+{
+    uint64_t s = (seed ^ (stream * 0x9E3779B97F4A7C15ull)) + idx;
+    return (double)(hb_splitmix64(s) >> 11) * 0x1.0p-53;
+}
+
+extern "C" double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx)
+{
+    return hb_u01_impl(seed, stream, idx);
+}
+
+// ---------------------------------------------------------------- reference element
+
+static void legendre_pair(int N, double x, double *PN, double *PNm1)
+{
+    double a = 1.0, b = x;  // P_0, P_1
+    if (N == 1) { *PN = b; *PNm1 = a; return; }
+    for (int k = 2; k <= N; k++) {
+        double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+        a = b;
+        b = c;
+    }
+    *PN = b;
+    *PNm1 = a;
+}
+
+void hb_reference_element(int N, double *xi, double *w, double *D)
+{
+    const int n = N + 1;
+    xi[0] = -1.0;
+    xi[N] = 1.0;
+    for (int i = 1; i < N; i++) {
+        double x = -std::cos(M_PI * i / N);
+        for (int it = 0; it < 200; it++) {
+            double P, Pm;
+            legendre_pair(N, x, &P, &Pm);
+            // q = N (P_{N-1} - x P_N), q' = -N (N+1) P_N  =>  dx = -q / q'
+            double dx = (Pm - x * P) / ((N + 1) * P);
+            x += dx;
+            if (std::fabs(dx) <= 1e-17) break;
+        }
+        xi[i] = x;
+    }
+    for (int i = 0; i < n / 2; i++) {  // symmetric node set
+        double a = 0.5 * (xi[N - i] - xi[i]);
+        xi[i] = -a;
+        xi[N - i] = a;
+    }
+    if (N % 2 == 0) xi[N / 2] = 0.0;
+    for (int i = 0; i < n; i++) {
+        double P, Pm;
+        legendre_pair(N, xi[i], &P, &Pm);
+        w[i] = 2.0 / (N * (N + 1.0) * P * P);
+    }
+    // barycentric weights lambda_j = 1 / prod_{k != j} (x_j - x_k)
+    std::vector<double> lam(n);
+    for (int j = 0; j < n; j++) {
+        double p = 1.0;
+        for (int k = 0; k < n; k++)
+            if (k != j) p *= (xi[j] - xi[k]);
+        lam[j] = 1.0 / p;
+    }
+    for (int i = 0; i < n; i++) {
+        double diag = 0.0;
+        for (int j = 0; j < n; j++) {
+            if (i == j) continue;
+            double v = (lam[j] / lam[i]) / (xi[i] - xi[j]);
+            D[i * n + j] = v;
+            diag -= v;
+        }
+        D[i * n + i] = diag;
+    }
+    // D is centro-antisymmetric; make the computed matrix exactly so
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            int ii = N - i, jj = N - j;
+            if (i * n + j < ii * n + jj) {
+                double a = 0.5 * (D[i * n + j] - D[ii * n + jj]);
+                D[i * n + j] = a;
+                D[ii * n + jj] = -a;
+            } else if (i == ii && j == jj) {
+                D[i * n + j] = 0.0;
+            }
+        }
+}
+
+// ---------------------------------------------------------------- device tables
+
+static int d_offset(int N)
+{
+    int o = 0;
+    for (int M = 1; M < N; M++) o += (M + 1) * (M + 1);
+    return o;
+}
+static const int kTableSize = 1496;  // sum_{N=1..15} (N+1)^2 = 1495
+
+__device__ double g_D64[kTableSize];
+__device__ float g_D32[kTableSize];
+__device__ double g_xi64[16 * 16];   // [N][i]
+__device__ double g_w64[16 * 16];
+
+static std::mutex g_table_mu;
+static unsigned g_table_done = 0;  // bit per device (devices 0..31)
+static double *g_dev_D64[32];
+static float *g_dev_D32[32];
+
+hb_status hb_ensure_device_tables()
+{
+    int dev = 0;
+    HB_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 32) { hb_set_error("device index %d unsupported", dev); return HB_ERR_ARG; }
+    std::lock_guard<std::mutex> lk(g_table_mu);
+    if (g_table_done & (1u << dev)) return HB_OK;
+    std::vector<double> D64(kTableSize, 0.0), xi(256, 0.0), w(256, 0.0);
+    std::vector<float> D32(kTableSize, 0.0f);
+    for (int N = 1; N <= HB_MAX_N; N++) {
+        int n = N + 1;
+        std::vector<double> x(n), ww(n), D(n * n);
+        hb_reference_element(N, x.data(), ww.data(), D.data());
+        for (int q = 0; q < n * n; q++) {
+            D64[d_offset(N) + q] = D[q];
+            D32[d_offset(N) + q] = (float)D[q];
+        }
+        for (int i = 0; i < n; i++) { xi[N * 16 + i] = x[i]; w[N * 16 + i] = ww[i]; }
+    }
+    HB_TRY_CUDA(cudaMemcpyToSymbol(g_D64, D64.data(), sizeof(double) * kTableSize));
+    HB_TRY_CUDA(cudaMemcpyToSymbol(g_D32, D32.data(), sizeof(float) * kTableSize));
+    HB_TRY_CUDA(cudaMemcpyToSymbol(g_xi64, xi.data(), sizeof(double) * 256));
+    HB_TRY_CUDA(cudaMemcpyToSymbol(g_w64, w.data(), sizeof(double) * 256));
+    void *p64 = nullptr, *p32 = nullptr;
+    HB_TRY_CUDA(cudaGetSymbolAddress(&p64, g_D64));
+    HB_TRY_CUDA(cudaGetSymbolAddress(&p32, g_D32));
+    g_dev_D64[dev] = (double *)p64;
+    g_dev_D32[dev] = (float *)p32;
+    g_table_done |= 1u << dev;
+    return HB_OK;
+}
+
+const double *hb_dev_D64(int N)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return g_dev_D64[dev] + d_offset(N);
+}
+const float *hb_dev_D32(int N)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return g_dev_D32[dev] + d_offset(N);
+}
+
+// ---------------------------------------------------------------- setup kernels
+
+struct box_t {
+    int Ex, Ey, Ez, N;
+    unsigned faces;
+};
+
+// Node map: lexicographic ids over unmasked lattice nodes, by closed form.
+__global__ void k_l2g(box_t b, int64_t n_local, int32_t *l2g)
+{
+    const int n = b.N + 1;
+    const int64_t n3 = (int64_t)n * n * n;
+    const int64_t NX = (int64_t)b.N * b.Ex + 1, NY = (int64_t)b.N * b.Ey + 1, NZ = (int64_t)b.N * b.Ez + 1;
+    const int x0 = b.faces & 1u ? 1 : 0, x1 = b.faces & 2u ? 1 : 0;
+    const int y0 = b.faces & 4u ? 1 : 0, y1 = b.faces & 8u ? 1 : 0;
+    const int z0 = b.faces & 16u ? 1 : 0, z1 = b.faces & 32u ? 1 : 0;
+    const int64_t NXu = NX - x0 - x1, NYu = NY - y0 - y1;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_local;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = q / n3;
+        int node = (int)(q - e * n3);
+        int i = node % n, j = (node / n) % n, k = node / (n * n);
+        int64_t ex = e % b.Ex, ey = (e / b.Ex) % b.Ey, ez = e / ((int64_t)b.Ex * b.Ey);
+        int64_t I = b.N * ex + i, J = b.N * ey + j, K = b.N * ez + k;
+        bool masked = (x0 && I == 0) || (x1 && I == NX - 1) || (y0 && J == 0) || (y1 && J == NY - 1) ||
+                      (z0 && K == 0) || (z1 && K == NZ - 1);
+        l2g[q] = masked ? -1 : (int32_t)((I - x0) + NXu * ((J - y0) + NYu * (K - z0)));
+    }
+}
+
+__device__ inline void vertex_pos(const box_t &b, double rho, uint64_t seed, int a, int bb, int c,
+                                  double X[3])
+{
+    X[0] = (double)a / b.Ex;
+    X[1] = (double)bb / b.Ey;
+    X[2] = (double)c / b.Ez;
+    if (a > 0 && a < b.Ex && bb > 0 && bb < b.Ey && c > 0 && c < b.Ez) {
+        const double h[3] = {1.0 / b.Ex, 1.0 / b.Ey, 1.0 / b.Ez};
+        uint64_t v = ((uint64_t)c * (b.Ey + 1) + bb) * (b.Ex + 1) + a;
+        for (int ax = 0; ax < 3; ax++) {
+            double u = hb_u01_impl(seed, 1, 3 * v + ax);
+            X[ax] += (2.0 * u - 1.0) * rho * h[ax];
+        }
+    }
+}
+
+// Geometric factors, one element per block. Nodal coordinates from the
+// trilinear map, then J = D applied to them along r, s, t.
+__global__ void k_geometry(box_t b, double rho, uint64_t seed, int64_t E, double *geo, float *geo32,
+                           double *detmin_blk)
+{
+    extern __shared__ double smem[];
+    const int N = b.N, n = N + 1, n2 = n * n, n3 = n2 * n;
+    double *X = smem;            // [3][n3]
+    double *sD = smem + 3 * n3;  // [n][n]
+    __shared__ double red[32];
+    const double *Dg = g_D64;
+    int off = 0;
+    for (int M = 1; M < N; M++) off += (M + 1) * (M + 1);
+    for (int q = threadIdx.x; q < n2; q += blockDim.x) sD[q] = Dg[off + q];
+    const double *xi = g_xi64 + N * 16, *w = g_w64 + N * 16;
+    double dmin = INFINITY;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        int ex = (int)(e % b.Ex), ey = (int)((e / b.Ex) % b.Ey), ez = (int)(e / ((int64_t)b.Ex * b.Ey));
+        double V[8][3];
+        for (int c = 0; c < 2; c++)
+            for (int bb = 0; bb < 2; bb++)
+                for (int a = 0; a < 2; a++) vertex_pos(b, rho, seed, ex + a, ey + bb, ez + c, V[(c * 2 + bb) * 2 + a]);
+        __syncthreads();
+        for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+            int i = q % n, j = (q / n) % n, k = q / n2;
+            double r = xi[i], s = xi[j], t = xi[k];
+            double fr[2] = {0.5 * (1 - r), 0.5 * (1 + r)};
+            double fs[2] = {0.5 * (1 - s), 0.5 * (1 + s)};
+            double ft[2] = {0.5 * (1 - t), 0.5 * (1 + t)};
+            for (int ax = 0; ax < 3; ax++) {
+                double acc = 0.0;
+                for (int c = 0; c < 2; c++)
+                    for (int bb = 0; bb < 2; bb++)
+                        for (int a = 0; a < 2; a++) acc += V[(c * 2 + bb) * 2 + a][ax] * fr[a] * fs[bb] * ft[c];
+                X[ax * n3 + q] = acc;
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+            int i = q % n, j = (q / n) % n, k = q / n2;
+            double J[3][3];
+            for (int ax = 0; ax < 3; ax++) {
+                const double *Xa = X + ax * n3;
+                double dr = 0, ds = 0, dt = 0;
+                for (int m = 0; m < n; m++) {
+                    dr += sD[i * n + m] * Xa[(k * n + j) * n + m];
+                    ds += sD[j * n + m] * Xa[(k * n + m) * n + i];
+                    dt += sD[k * n + m] * Xa[(m * n + j) * n + i];
+                }
+                J[ax][0] = dr;
+                J[ax][1] = ds;
+                J[ax][2] = dt;
+            }
+            double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+            double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+            double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+            double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+            double id = 1.0 / det;
+            // inverse: Ji[l][x] = d r_l / d x_x
+            double Ji[3][3];
+            Ji[0][0] = c00 * id;
+            Ji[1][0] = c01 * id;
+            Ji[2][0] = c02 * id;
+            Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+            Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+            Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+            Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+            Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+            Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+            double wd = w[i] * w[j] * w[k] * det;
+            double g[7];
+            const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+            for (int f = 0; f < 6; f++)
+                g[f] = wd * (Ji[pa[f]][0] * Ji[pb[f]][0] + Ji[pa[f]][1] * Ji[pb[f]][1] + Ji[pa[f]][2] * Ji[pb[f]][2]);
+            g[6] = wd;
+            int64_t base = ((e * n + k) * 7) * (int64_t)n2 + j * n + i;
+            for (int c = 0; c < 7; c++) {
+                geo[base + (int64_t)c * n2] = g[c];
+                if (geo32) geo32[base + (int64_t)c * n2] = (float)g[c];
+            }
+            dmin = fmin(dmin, det);
+        }
+    }
+    // block minimum of det J
+    for (int o = 16; o > 0; o >>= 1) dmin = fmin(dmin, __shfl_down_sync(0xffffffffu, dmin, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmin;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = red[0];
+        for (int q = 1; q < (int)(blockDim.x + 31) / 32; q++) m = fmin(m, red[q]);
+        detmin_blk[blockIdx.x] = m;
+    }
+}
+
+__global__ void k_count(const int32_t *l2g, int64_t n_local, int32_t *cnt)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_local;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = l2g[q];
+        if (g >= 0) atomicAdd(&cnt[g], 1);
+    }
+}
+
+// Exclusive scan in three passes over chunks of 1024 entries.
+__global__ void k_scan_chunks(const int32_t *in, int64_t n, int32_t *out, int64_t *chunk_sum)
+{
+    __shared__ int64_t s[1024];
+    int64_t base = (int64_t)blockIdx.x * 1024;
+    int t = threadIdx.x;
+    int64_t v = base + t < n ? in[base + t] : 0;
+    s[t] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int64_t a = t >= o ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += a;
+        __syncthreads();
+    }
+    if (base + t < n) out[base + t] = (int32_t)(s[t] - v);
+    if (t == 1023) chunk_sum[blockIdx.x] = s[t];
+}
+
+__global__ void k_scan_sums(int64_t *chunk_sum, int64_t nchunks)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int64_t acc = 0;
+        for (int64_t c = 0; c < nchunks; c++) {
+            int64_t v = chunk_sum[c];
+            chunk_sum[c] = acc;
+            acc += v;
+        }
+        chunk_sum[nchunks] = acc;
+    }
+}
+
+__global__ void k_scan_add(int32_t *out, int64_t n, const int64_t *chunk_sum)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = (int32_t)(out[q] + chunk_sum[q / 1024]);
+}
+
+__global__ void k_fill(const int32_t *l2g, int64_t n_local, const int32_t *rowptr, int32_t *cursor,
+                       int32_t *cols)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_local;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = l2g[q];
+        if (g >= 0) {
+            int slot = atomicAdd(&cursor[g], 1);
+            cols[rowptr[g] + slot] = (int32_t)q;
+        }
+    }
+}
+
+// Sort every row ascending (rows are short) and sum the mass diagonal in that order.
+__global__ void k_sort_rows(const int32_t *rowptr, int32_t *cols, int64_t ng, const double *geo, int n,
+                            double *mdiag, float *mdiag32)
+{
+    const int n2 = n * n, n3 = n2 * n;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int a = rowptr[g], z = rowptr[g + 1];
+        for (int p = a + 1; p < z; p++) {
+            int32_t v = cols[p];
+            int q = p - 1;
+            while (q >= a && cols[q] > v) { cols[q + 1] = cols[q]; q--; }
+            cols[q + 1] = v;
+        }
+        double m = 0.0;
+        for (int p = a; p < z; p++) {
+            int64_t lq = cols[p];
+            int64_t e = lq / n3;
+            int node = (int)(lq - e * n3);
+            int k = node / n2, ij = node - k * n2;
+            m += geo[((e * n + k) * 7 + 6) * (int64_t)n2 + ij];
+        }
+        mdiag[g] = m;
+        if (mdiag32) mdiag32[g] = (float)m;
+    }
+}
+
+__global__ void k_min_reduce(const double *v, int n, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double m = INFINITY;
+        for (int q = 0; q < n; q++) m = fmin(m, v[q]);
+        *out = m;
+    }
+}
+
+// ---------------------------------------------------------------- mesh lifetime
+
+static int grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)(g < 1 ? 1 : g);
+}
+
+extern "C" hb_status hb_mesh_destroy(hb_mesh *m)
+{
+    if (!m) return HB_OK;
+    hb_device_guard dg(m->device);
+    cudaFree(m->l2g);
+    cudaFree(m->geo);
+    cudaFree(m->geo32);
+    cudaFree(m->rowptr);
+    cudaFree(m->cols);
+    cudaFree(m->mdiag);
+    cudaFree(m->mdiag32);
+    cudaFree(m->yL);
+    cudaFree(m->partials);
+    cudaFree(m->counters);
+    cudaFree(m->state);
+    cudaFree(m->cg_vec);
+    if (m->state_host) cudaFreeHost(m->state_host);
+    if (m->ev0) cudaEventDestroy(m->ev0);
+    if (m->ev1) cudaEventDestroy(m->ev1);
+    delete m;
+    return HB_OK;
+}
+
+#define HB_TRY_MESH(call)                                                        \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            hb_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,              \
+                         cudaGetErrorString(e_));                                \
+            hb_mesh_destroy(m);                                                  \
+            cudaFree(tmp_cnt);                                                   \
+            cudaFree(tmp_sum);                                                   \
+            cudaFree(tmp_det);                                                   \
+            return e_ == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA; \
+        }                                                                        \
+    } while (0)
+
+extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh **out)
+{
+    hb_clear_error();
+    if (!d || !out) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    *out = nullptr;
+    if (d->N < 1 || d->N > HB_MAX_N) { hb_set_error("N=%d outside 1..%d", d->N, HB_MAX_N); return HB_ERR_ARG; }
+    if (d->ex < 1 || d->ey < 1 || d->ez < 1) { hb_set_error("element counts must be >= 1"); return HB_ERR_ARG; }
+    if (!(d->perturb >= 0.0 && d->perturb < 0.5)) { hb_set_error("perturb must be in [0, 0.5)"); return HB_ERR_ARG; }
+    if (d->dirichlet_faces > 0x3Fu) { hb_set_error("dirichlet_faces has bits above 0x3F"); return HB_ERR_ARG; }
+    const int N = d->N, n = N + 1;
+    const int64_t E = (int64_t)d->ex * d->ey * d->ez;
+    const int64_t n_local = E * n * n * n;
+    if (n_local > 2147483647LL) { hb_set_error("n_local=%lld exceeds 2^31-1", (long long)n_local); return HB_ERR_ARG; }
+    hb_status st = hb_ensure_device_tables();
+    if (st != HB_OK) return st;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    hb_mesh *m = new hb_mesh();
+    memset((void *)m, 0, sizeof(hb_mesh));
+    int32_t *tmp_cnt = nullptr;
+    int64_t *tmp_sum = nullptr;
+    double *tmp_det = nullptr;
+    HB_TRY_MESH(cudaGetDevice(&m->device));
+    m->desc = *d;
+    m->N = N;
+    m->n = n;
+    m->E = E;
+    m->n_local = n_local;
+    // global count by closed form, checked against the CSR below
+    const int64_t NX = (int64_t)N * d->ex + 1, NY = (int64_t)N * d->ey + 1, NZ = (int64_t)N * d->ez + 1;
+    const unsigned f = d->dirichlet_faces;
+    const int64_t NXu = NX - (f & 1u ? 1 : 0) - (f & 2u ? 1 : 0);
+    const int64_t NYu = NY - (f & 4u ? 1 : 0) - (f & 8u ? 1 : 0);
+    const int64_t NZu = NZ - (f & 16u ? 1 : 0) - (f & 32u ? 1 : 0);
+    m->n_global = (NXu > 0 && NYu > 0 && NZu > 0) ? NXu * NYu * NZu : 0;
+    const int64_t ng = m->n_global;
+
+    size_t bytes = 0;
+    auto alloc = [&](void **p, size_t b) {
+        bytes += b;
+        return cudaMalloc(p, b > 0 ? b : 16);
+    };
+    HB_TRY_MESH(alloc((void **)&m->l2g, sizeof(int32_t) * n_local));
+    HB_TRY_MESH(alloc((void **)&m->geo, sizeof(double) * 7 * n_local));
+    if (d->keep_fp32_copy) HB_TRY_MESH(alloc((void **)&m->geo32, sizeof(float) * 7 * n_local));
+    HB_TRY_MESH(alloc((void **)&m->rowptr, sizeof(int32_t) * (ng + 1)));
+    HB_TRY_MESH(alloc((void **)&m->mdiag, sizeof(double) * (ng + 1)));
+    if (d->keep_fp32_copy) HB_TRY_MESH(alloc((void **)&m->mdiag32, sizeof(float) * (ng + 1)));
+    HB_TRY_MESH(alloc((void **)&m->yL, sizeof(double) * n_local));
+    HB_TRY_MESH(alloc((void **)&m->partials, sizeof(double) * 2 * HB_RED_BLOCKS));
+    HB_TRY_MESH(alloc((void **)&m->counters, sizeof(unsigned) * 8));
+    HB_TRY_MESH(alloc((void **)&m->state, sizeof(hb_cg_state) * 4));
+    HB_TRY_MESH(cudaMallocHost((void **)&m->state_host, sizeof(hb_cg_state)));
+    HB_TRY_MESH(cudaEventCreate(&m->ev0));
+    HB_TRY_MESH(cudaEventCreate(&m->ev1));
+    HB_TRY_MESH(cudaMemsetAsync(m->counters, 0, sizeof(unsigned) * 8, s));
+    HB_TRY_MESH(cudaMemsetAsync(m->state, 0, sizeof(hb_cg_state) * 4, s));
+
+    box_t b{d->ex, d->ey, d->ez, N, d->dirichlet_faces};
+    k_l2g<<<grid_for(n_local, 256), 256, 0, s>>>(b, n_local, m->l2g);
+    HB_TRY_MESH(cudaGetLastError());
+
+    // geometry: one element per block
+    int gthreads = n * n * n < 256 ? ((n * n * n + 31) / 32) * 32 : 256;
+    int gblocks = (int)(E < 152 * 64 ? E : 152 * 64);
+    size_t gsmem = sizeof(double) * (3 * n * n * n + n * n);
+    HB_TRY_MESH(cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
+    HB_TRY_MESH(cudaMalloc((void **)&tmp_det, sizeof(double) * (gblocks + 1)));
+    k_geometry<<<gblocks, gthreads, gsmem, s>>>(b, d->perturb, d->seed, E, m->geo, m->geo32, tmp_det);
+    HB_TRY_MESH(cudaGetLastError());
+    k_min_reduce<<<1, 32, 0, s>>>(tmp_det, gblocks, tmp_det + gblocks);
+    HB_TRY_MESH(cudaGetLastError());
+
+    // CSR of Z^T: count, scan, fill, sort rows
+    HB_TRY_MESH(cudaMalloc((void **)&tmp_cnt, sizeof(int32_t) * (ng + 1)));
+    HB_TRY_MESH(cudaMemsetAsync(tmp_cnt, 0, sizeof(int32_t) * (ng + 1), s));
+    k_count<<<grid_for(n_local, 256), 256, 0, s>>>(m->l2g, n_local, tmp_cnt);
+    HB_TRY_MESH(cudaGetLastError());
+    const int64_t nchunks = (ng + 1 + 1023) / 1024;
+    HB_TRY_MESH(cudaMalloc((void **)&tmp_sum, sizeof(int64_t) * (nchunks + 1)));
+    k_scan_chunks<<<(unsigned)nchunks, 1024, 0, s>>>(tmp_cnt, ng + 1, m->rowptr, tmp_sum);
+    HB_TRY_MESH(cudaGetLastError());
+    k_scan_sums<<<1, 32, 0, s>>>(tmp_sum, nchunks);
+    HB_TRY_MESH(cudaGetLastError());
+    k_scan_add<<<grid_for(ng + 1, 256), 256, 0, s>>>(m->rowptr, ng + 1, tmp_sum);
+    HB_TRY_MESH(cudaGetLastError());
+    int32_t nnz32 = 0;
+    HB_TRY_MESH(cudaMemcpyAsync(&nnz32, m->rowptr + ng, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    double detmin = 0.0;
+    HB_TRY_MESH(cudaMemcpyAsync(&detmin, tmp_det + gblocks, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HB_TRY_MESH(cudaStreamSynchronize(s));
+    m->nnz = nnz32;
+    m->min_detJ = detmin;
+    HB_TRY_MESH(alloc((void **)&m->cols, sizeof(int32_t) * (m->nnz > 0 ? m->nnz : 1)));
+    HB_TRY_MESH(cudaMemsetAsync(tmp_cnt, 0, sizeof(int32_t) * (ng + 1), s));
+    k_fill<<<grid_for(n_local, 256), 256, 0, s>>>(m->l2g, n_local, m->rowptr, tmp_cnt, m->cols);
+    HB_TRY_MESH(cudaGetLastError());
+    k_sort_rows<<<grid_for(ng, 256), 256, 0, s>>>(m->rowptr, m->cols, ng, m->geo, n, m->mdiag, m->mdiag32);
+    HB_TRY_MESH(cudaGetLastError());
+    HB_TRY_MESH(cudaStreamSynchronize(s));
+    cudaFree(tmp_cnt);
+    cudaFree(tmp_sum);
+    cudaFree(tmp_det);
+    tmp_cnt = nullptr;
+    tmp_sum = nullptr;
+    tmp_det = nullptr;
+    m->device_bytes = bytes;
+    if (!(m->min_detJ > 0.0)) {
+        hb_set_error("non-positive Jacobian determinant (min det J = %g)", m->min_detJ);
+        hb_mesh_destroy(m);
+        return HB_ERR_GEOMETRY;
+    }
+    *out = m;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_mesh_info(const hb_mesh *m, hb_mesh_info_t *o)
+{
+    if (!m || !o) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    o->n_local = m->n_local;
+    o->n_global = m->n_global;
+    o->n_elem = m->E;
+    o->nnz = m->nnz;
+    o->N = m->N;
+    o->l2g = m->l2g;
+    o->geo = m->geo;
+    o->geo32 = m->geo32;
+    o->csr_rowptr = m->rowptr;
+    o->csr_cols = m->cols;
+    o->min_detJ = m->min_detJ;
+    o->device_bytes = m->device_bytes;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_mesh_copy_l2g(const hb_mesh *m, int32_t *host)
+{
+    if (!m || !host) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    hb_device_guard dg(m->device);
+    HB_TRY_CUDA(cudaMemcpy(host, m->l2g, sizeof(int32_t) * m->n_local, cudaMemcpyDeviceToHost));
+    return HB_OK;
+}
+
+extern "C" hb_status hb_mesh_copy_geo(const hb_mesh *m, double *host)
+{
+    if (!m || !host) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    hb_device_guard dg(m->device);
+    HB_TRY_CUDA(cudaMemcpy(host, m->geo, sizeof(double) * 7 * m->n_local, cudaMemcpyDeviceToHost));
+    return HB_OK;
+}
+
+// ---------------------------------------------------------------- right-hand sides
+
+__global__ void k_rhs_uniform(const int32_t *l2g, box_t b, int64_t n_local, uint64_t seed, double *out)
+{
+    const int n = b.N + 1;
+    const int64_t n3 = (int64_t)n * n * n;
+    const int64_t NX = (int64_t)b.N * b.Ex + 1, NY = (int64_t)b.N * b.Ey + 1;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_local;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = l2g[q];
+        if (g < 0) continue;
+        int64_t e = q / n3;
+        int node = (int)(q - e * n3);
+        int i = node % n, j = (node / n) % n, k = node / (n * n);
+        int64_t ex = e % b.Ex, ey = (e / b.Ex) % b.Ey, ez = e / ((int64_t)b.Ex * b.Ey);
+        int64_t lat = (b.N * ex + i) + NX * ((b.N * ey + j) + NY * (b.N * ez + k));
+        out[g] = 2.0 * hb_u01_impl(seed, 2, (uint64_t)lat) - 1.0;  // same value from every copy
+    }
+}
+
+// Manufactured load: one thread per global DOF sums Jw f over its copies
+// (CSR order), with the physical position recomputed from the element map.
+__global__ void k_rhs_manufactured(const int32_t *rowptr, const int32_t *cols, int64_t ng, box_t b,
+                                   double rho, uint64_t seed, const double *geo, double lambda, double *out)
+{
+    const int N = b.N, n = N + 1, n2 = n * n;
+    const int64_t n3 = (int64_t)n2 * n;
+    const double *xi = g_xi64 + N * 16;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int p = rowptr[g]; p < rowptr[g + 1]; p++) {
+            int64_t lq = cols[p];
+            int64_t e = lq / n3;
+            int node = (int)(lq - e * n3);
+            int i = node % n, j = (node / n) % n, k = node / n2;
+            int ex = (int)(e % b.Ex), ey = (int)((e / b.Ex) % b.Ey), ez = (int)(e / ((int64_t)b.Ex * b.Ey));
+            double r = xi[i], s = xi[j], t = xi[k];
+            double fr[2] = {0.5 * (1 - r), 0.5 * (1 + r)};
+            double fs[2] = {0.5 * (1 - s), 0.5 * (1 + s)};
+            double ft[2] = {0.5 * (1 - t), 0.5 * (1 + t)};
+            double X[3] = {0, 0, 0};
+            for (int c = 0; c < 2; c++)
+                for (int bb = 0; bb < 2; bb++)
+                    for (int a = 0; a < 2; a++) {
+                        double V[3];
+                        vertex_pos(b, rho, seed, ex + a, ey + bb, ez + c, V);
+                        double wgt = fr[a] * fs[bb] * ft[c];
+                        for (int ax = 0; ax < 3; ax++) X[ax] += V[ax] * wgt;
+                    }
+            double f = (3.0 * M_PI * M_PI + lambda) * sin(M_PI * X[0]) * sin(M_PI * X[1]) * sin(M_PI * X[2]);
+            acc += geo[((e * n + k) * 7 + 6) * (int64_t)n2 + j * n + i] * f;
+        }
+        out[g] = acc;
+    }
+}
+
+extern "C" hb_status hb_fill_rhs(const hb_mesh *m, int kind, uint64_t seed, double lambda, double *bvec,
+                                 void *stream)
+{
+    hb_clear_error();
+    if (!m || !bvec) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (kind != 0 && kind != 1) { hb_set_error("kind must be 0 or 1"); return HB_ERR_ARG; }
+    hb_device_guard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    box_t b{m->desc.ex, m->desc.ey, m->desc.ez, m->N, m->desc.dirichlet_faces};
+    if (m->n_global == 0) return HB_OK;
+    if (kind == 0) {
+        k_rhs_uniform<<<grid_for(m->n_local, 256), 256, 0, s>>>(m->l2g, b, m->n_local, seed, bvec);
+    } else {
+        k_rhs_manufactured<<<grid_for(m->n_global, 128), 128, 0, s>>>(
+            m->rowptr, m->cols, m->n_global, b, m->desc.perturb, m->desc.seed, m->geo, lambda, bvec);
+    }
+    HB_CHECK_LAUNCH();
+    return HB_OK;
+}

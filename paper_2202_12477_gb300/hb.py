@@ -1,0 +1,228 @@
+"""ctypes binding of the C ABI in ``include/hipbone_gb300.h``.
+
+Argument marshalling only: every step of the operator and the solvers runs in
+the CUDA library ``_lib/libhbgb300.so``. The functions keep the C names; the
+``Mesh`` class is a small convenience owner of a mesh handle that takes torch
+CUDA tensors (torch provides device memory and streams, nothing else).
+
+If the library is missing this module raises at import of ``lib()``: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libhbgb300.so")
+
+# hb_status
+HB_OK, HB_ERR_ARG, HB_ERR_NOMEM, HB_ERR_CUDA, HB_ERR_GEOMETRY = 0, 1, 2, 3, 4
+HB_ERR_BREAKDOWN, HB_ERR_NOT_CONVERGED, HB_ERR_TIMEOUT, HB_ERR_BUSY, HB_ERR_NOT_FOUND = 5, 6, 7, 8, 9
+STATUS_NAMES = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_NOMEM", 3: "HB_ERR_CUDA", 4: "HB_ERR_GEOMETRY",
+                5: "HB_ERR_BREAKDOWN", 6: "HB_ERR_NOT_CONVERGED", 7: "HB_ERR_TIMEOUT", 8: "HB_ERR_BUSY",
+                9: "HB_ERR_NOT_FOUND"}
+# hb_precision
+HB_F64, HB_F32, HB_MIXED = 0, 1, 2
+# hb_screen
+HB_SCREEN_IDENTITY, HB_SCREEN_MASS = 0, 1
+ALL_FACES = 0x3F
+
+
+class hb_mesh_desc(C.Structure):
+    _fields_ = [("ex", C.c_int), ("ey", C.c_int), ("ez", C.c_int), ("N", C.c_int),
+                ("perturb", C.c_double), ("seed", C.c_uint64), ("dirichlet_faces", C.c_uint),
+                ("keep_fp32_copy", C.c_int)]
+
+
+class hb_mesh_info_t(C.Structure):
+    _fields_ = [("n_local", C.c_int64), ("n_global", C.c_int64), ("n_elem", C.c_int64),
+                ("nnz", C.c_int64), ("N", C.c_int), ("l2g", C.c_void_p), ("geo", C.c_void_p),
+                ("geo32", C.c_void_p), ("csr_rowptr", C.c_void_p), ("csr_cols", C.c_void_p),
+                ("min_detJ", C.c_double), ("device_bytes", C.c_size_t)]
+
+
+class hb_cg_opts(C.Structure):
+    _fields_ = [("prec", C.c_int), ("screen", C.c_int), ("lambda_", C.c_double), ("rtol", C.c_double),
+                ("max_it", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int)]
+
+
+class hb_cg_result(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer_iters", C.c_int), ("rel_res", C.c_double),
+                ("time_ms", C.c_double), ("status", C.c_int)]
+
+
+class HBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_SIGS = [
+    ("hb_mesh_create", C.c_int, [C.POINTER(hb_mesh_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("hb_mesh_destroy", C.c_int, [C.c_void_p]),
+    ("hb_mesh_info", C.c_int, [C.c_void_p, C.POINTER(hb_mesh_info_t)]),
+    ("hb_mesh_copy_l2g", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("hb_mesh_copy_geo", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("hb_apply_A", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("hb_dot", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                         C.c_void_p]),
+    ("hb_fill_rhs", C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_double, C.c_void_p, C.c_void_p]),
+    ("hb_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
+                              C.POINTER(hb_cg_result), C.c_void_p]),
+    ("hb_u01", C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64]),
+    ("hb_last_error", C.c_char_p, []),
+]
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run paper_2202_12477_gb300.build.build())")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_names():
+    return [name for name, _, _ in _SIGS]
+
+
+def _check(status):
+    if status != HB_OK:
+        raise HBError(status, lib().hb_last_error().decode(errors="replace"))
+    return status
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- C names
+
+def hb_mesh_create(desc: hb_mesh_desc, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().hb_mesh_create(C.byref(desc), _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def hb_mesh_destroy(h) -> None:
+    _check(lib().hb_mesh_destroy(h))
+
+
+def hb_mesh_info(h) -> hb_mesh_info_t:
+    info = hb_mesh_info_t()
+    _check(lib().hb_mesh_info(h, C.byref(info)))
+    return info
+
+
+def hb_apply_A(h, prec, screen, lam, x_ptr, y_ptr, stream=None) -> None:
+    _check(lib().hb_apply_A(h, prec, screen, lam, C.c_void_p(x_ptr), C.c_void_p(y_ptr), _stream_ptr(stream)))
+
+
+def hb_dot(h, prec, a_ptr, b_ptr, out_dev_ptr=None, want_host=True, stream=None):
+    out = C.c_double(0.0)
+    _check(lib().hb_dot(h, prec, C.c_void_p(a_ptr), C.c_void_p(b_ptr), C.c_void_p(out_dev_ptr or 0),
+                        C.byref(out) if want_host else None, _stream_ptr(stream)))
+    return out.value if want_host else None
+
+
+def hb_fill_rhs(h, kind, seed, lam, b_ptr, stream=None) -> None:
+    _check(lib().hb_fill_rhs(h, kind, seed, lam, C.c_void_p(b_ptr), _stream_ptr(stream)))
+
+
+def hb_cg_solve(h, opts: hb_cg_opts, b_ptr, x_ptr, stream=None, check=True) -> hb_cg_result:
+    res = hb_cg_result()
+    st = lib().hb_cg_solve(h, C.byref(opts), C.c_void_p(b_ptr), C.c_void_p(x_ptr), C.byref(res),
+                           _stream_ptr(stream))
+    if check and st not in (HB_OK, HB_ERR_NOT_CONVERGED, HB_ERR_BREAKDOWN):
+        _check(st)
+    return res
+
+
+def hb_u01(seed, stream, idx) -> float:
+    return lib().hb_u01(seed, stream, idx)
+
+
+# ---------------------------------------------------------------- convenience owner
+
+class Mesh:
+    """Owns one hb_mesh; vectors are torch CUDA tensors of length n_global."""
+
+    def __init__(self, ex, ey, ez, N, perturb=0.0, seed=0, faces=ALL_FACES, fp32=True, stream=None):
+        self.desc = hb_mesh_desc(ex, ey, ez, N, perturb, seed, faces, 1 if fp32 else 0)
+        self.handle = hb_mesh_create(self.desc, stream)
+        self.info = hb_mesh_info(self.handle)
+        self.n_global = self.info.n_global
+        self.n_local = self.info.n_local
+        self.E = self.info.n_elem
+        self.N = N
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hb_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vec(self, dtype=None):
+        import torch
+        return torch.zeros(self.n_global, dtype=dtype or torch.float64, device="cuda")
+
+    def apply_A(self, x, y=None, lam=0.0, screen=HB_SCREEN_IDENTITY, stream=None):
+        import torch
+        prec = HB_F64 if x.dtype == torch.float64 else HB_F32
+        if y is None:
+            y = torch.empty_like(x)
+        assert x.is_cuda and x.is_contiguous() and x.numel() == self.n_global
+        hb_apply_A(self.handle, prec, screen, lam, x.data_ptr(), y.data_ptr(), stream)
+        return y
+
+    def dot(self, a, b, stream=None):
+        import torch
+        prec = HB_F64 if a.dtype == torch.float64 else HB_F32
+        return hb_dot(self.handle, prec, a.data_ptr(), b.data_ptr(), None, True, stream)
+
+    def rhs(self, kind=0, seed=0, lam=0.0, stream=None):
+        b = self.vec()
+        hb_fill_rhs(self.handle, kind, seed, lam, b.data_ptr(), stream)
+        return b
+
+    def cg(self, b, x=None, lam=0.0, rtol=0.0, max_it=100, prec=HB_F64, screen=HB_SCREEN_IDENTITY,
+           inner_rtol=1e-4, max_outer=30, stream=None):
+        if x is None:
+            x = self.vec()
+        opts = hb_cg_opts(prec, screen, lam, rtol, max_it, inner_rtol, max_outer)
+        res = hb_cg_solve(self.handle, opts, b.data_ptr(), x.data_ptr(), stream)
+        return x, res
+
+    def l2g(self):
+        import numpy as np
+        out = np.zeros(self.n_local, dtype=np.int32)
+        _check(lib().hb_mesh_copy_l2g(self.handle, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def geo(self):
+        import numpy as np
+        out = np.zeros(7 * self.n_local, dtype=np.float64)
+        _check(lib().hb_mesh_copy_geo(self.handle, out.ctypes.data_as(C.c_void_p)))
+        return out

@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the FP64
+oracle on the same seeded inputs.
+
+Bars (from the arithmetic; see the design notes):
+  - node map and DOF counts: bit-exact;
+  - geometric factors: 1e-13 of the largest factor (two routes to the Jacobian);
+  - FP64 A x: ||y - y_oracle||_2 <= 1e-12 ||y_oracle||_2 and
+    max |y - y_oracle| <= 1e-12 max |y_oracle| (a few units of rounding times the
+    ~6(N+1) terms of each contraction and the summation over copies);
+  - FP32 A x: 2e-5 relative (FP32 rounding, 2^-24, times the same term counts);
+  - dot: 1e-14 relative to the correctly rounded sum (math.fsum);
+  - CG, fixed 100 iterations: 1e-12 relative to the oracle's iterate;
+  - converged CG: both reach rtol and agree to 10 rtol.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as orc  # noqa: E402
+from paper_2202_12477_gb300 import hb, inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    hb.lib()
+
+
+def _pair(dims, N, rho=0.1, seed=0, faces=0x3F):
+    m = hb.Mesh(*dims, N, perturb=rho, seed=seed, faces=faces, fp32=True)
+    o = orc.Mesh(*dims, N, rho=rho, seed=seed, faces=faces)
+    return m, o
+
+
+def _to_dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ---------------------------------------------------------------- mesh
+
+@pytest.mark.parametrize("dims,N,faces", [((2, 3, 2), 3, 0x3F), ((3, 2, 2), 2, 0x00), ((2, 2, 3), 4, 0x15),
+                                          ((1, 1, 1), 1, 0x3F), ((5, 5, 5), 7, 0x3F), ((2, 2, 2), 15, 0x2A)])
+def test_node_map_bit_exact(dims, N, faces):
+    m, o = _pair(dims, N, faces=faces)
+    assert m.n_global == o.n_global
+    np.testing.assert_array_equal(m.l2g(), o.l2g().ravel())
+
+
+@pytest.mark.parametrize("N,Ex,Ey,Ez,NG", [(7, 50, 50, 50, 42508549), (15, 24, 24, 24, 46268279),
+                                           (7, 5, 10, 15, 243984), (15, 2, 2, 6, 74849)])
+def test_dof_counts_of_paper_meshes(N, Ex, Ey, Ez, NG):
+    m = hb.Mesh(Ex, Ey, Ez, N, fp32=False)
+    assert m.n_global == NG
+    m.close()
+
+
+@pytest.mark.parametrize("dims,N,rho", [((2, 3, 2), 1, 0.2), ((3, 2, 2), 4, 0.3), ((2, 2, 2), 7, 0.1),
+                                        ((2, 1, 2), 12, 0.25), ((1, 2, 1), 15, 0.1)])
+def test_geometric_factors(dims, N, rho):
+    m, o = _pair(dims, N, rho=rho, seed=7)
+    n = N + 1
+    geo = m.geo().reshape(m.E, n, 7, n, n)          # [e][k][c][j][i]
+    G, Jw = o.geo()                                  # [e][k][j][i][6], [e][k][j][i]
+    ref = np.concatenate([np.moveaxis(G, -1, 2), Jw[:, :, None]], axis=2)  # [e][k][c][j][i]
+    # the off-diagonal entries are sums of products of the same Jacobian-inverse
+    # entries as the diagonal ones: their rounding scales with the whole tensor
+    gscale = np.abs(ref[:, :, :6]).max()
+    for c in range(6):
+        assert np.abs(geo[:, :, c] - ref[:, :, c]).max() <= 1e-13 * gscale, c
+    assert np.abs(geo[:, :, 6] - ref[:, :, 6]).max() <= 1e-13 * np.abs(ref[:, :, 6]).max()
+    assert abs(m.info.min_detJ - o.min_detJ) <= 1e-13 * o.min_detJ
+
+
+# ---------------------------------------------------------------- operator
+
+OP_CASES = [((2, 2, 2), 1), ((5, 3, 2), 2), ((3, 3, 3), 3), ((4, 3, 3), 4), ((3, 2, 3), 5), ((3, 3, 2), 6),
+            ((3, 3, 3), 7), ((2, 3, 2), 8), ((2, 2, 3), 9), ((2, 2, 2), 10), ((3, 1, 2), 11), ((2, 2, 1), 12),
+            ((1, 2, 2), 13), ((2, 1, 1), 14), ((1, 2, 2), 15)]
+
+
+@pytest.mark.parametrize("dims,N", OP_CASES)
+@pytest.mark.parametrize("screen,lam", [(0, 0.1), (1, 0.7), (0, 0.0)])
+def test_apply_A_fp64(dims, N, screen, lam):
+    m, o = _pair(dims, N, rho=0.15, seed=N)
+    x = inputs.random_vector(m.n_global, seed=100 + N)
+    y_or = o.apply_A(x, lam, screen)
+    y = m.apply_A(_to_dev(x), lam=lam, screen=screen).cpu().numpy()
+    assert _rel(y, y_or) <= 1e-12
+    assert np.abs(y - y_or).max() <= 1e-12 * np.abs(y_or).max()
+
+
+@pytest.mark.parametrize("dims,N", OP_CASES[::2])
+def test_apply_A_fp32(dims, N):
+    m, o = _pair(dims, N, rho=0.15, seed=N)
+    x = inputs.random_vector(m.n_global, seed=200 + N)
+    x32 = x.astype(np.float32)
+    y_or = o.apply_A(x32.astype(np.float64), 0.1, 0)
+    y = m.apply_A(_to_dev(x32, torch.float32), lam=0.1).cpu().numpy().astype(np.float64)
+    assert _rel(y, y_or) <= 2e-5
+
+
+def test_apply_A_reproducible_and_linear():
+    m, o = _pair((4, 4, 3), 5, rho=0.2, seed=3)
+    x = _to_dev(inputs.random_vector(m.n_global, seed=1))
+    z = _to_dev(inputs.random_vector(m.n_global, seed=2))
+    y1 = m.apply_A(x, lam=0.3)
+    y2 = m.apply_A(x, lam=0.3)
+    assert torch.equal(y1, y2)  # bitwise: fixed summation order, no atomics
+    yz = m.apply_A(z, lam=0.3)
+    ysum = m.apply_A(x + 2 * z, lam=0.3)
+    assert torch.linalg.norm(ysum - (y1 + 2 * yz)) <= 1e-13 * torch.linalg.norm(ysum)
+    # symmetry x.Az = z.Ax
+    a, b = m.dot(x, yz), m.dot(z, y1)
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_apply_A_empty_and_neumann():
+    m = hb.Mesh(1, 1, 1, 1)  # every node on a Dirichlet face: no DOFs
+    assert m.n_global == 0
+    x = torch.zeros(0, dtype=torch.float64, device="cuda")
+    m.apply_A(x, torch.zeros(0, dtype=torch.float64, device="cuda"))
+    m2, o2 = _pair((2, 2, 2), 3, rho=0.2, faces=0)
+    one = torch.ones(m2.n_global, dtype=torch.float64, device="cuda")
+    y = m2.apply_A(one, lam=0.0)
+    assert y.abs().max().item() < 1e-12  # S 1 = 0 without Dirichlet faces
+
+
+def test_invalid_arguments():
+    for bad in [dict(N=0), dict(N=16), dict(perturb=0.5), dict(ex=0)]:
+        kw = dict(ex=2, ey=2, ez=2, N=3, perturb=0.1)
+        kw.update(bad)
+        with pytest.raises(hb.HBError) as ei:
+            hb.Mesh(kw["ex"], kw["ey"], kw["ez"], kw["N"], perturb=kw["perturb"])
+        assert ei.value.status == hb.HB_ERR_ARG
+    m = hb.Mesh(2, 2, 2, 2)
+    x = m.vec()
+    with pytest.raises(hb.HBError):
+        hb.hb_apply_A(m.handle, hb.HB_F64, 5, 0.0, x.data_ptr(), x.data_ptr() + 8)
+    with pytest.raises(hb.HBError):  # x and y overlap
+        hb.hb_apply_A(m.handle, hb.HB_F64, 0, 0.0, x.data_ptr(), x.data_ptr())
+
+
+def test_geometry_error_on_inverted_elements():
+    """A perturbation that the oracle finds inverts an element must be refused."""
+    found = None
+    for seed in range(200):
+        o = orc.Mesh(3, 3, 3, 2, rho=0.49, seed=seed)
+        if o.min_detJ <= 0:
+            found = seed
+            break
+    if found is None:
+        pytest.skip("no inverted element among the seeds tried")
+    with pytest.raises(hb.HBError) as ei:
+        hb.Mesh(3, 3, 3, 2, perturb=0.49, seed=found)
+    assert ei.value.status == hb.HB_ERR_GEOMETRY
+
+
+# ---------------------------------------------------------------- dot and rhs
+
+@pytest.mark.parametrize("n_dims,N", [((3, 3, 3), 5), ((8, 8, 8), 7), ((2, 2, 2), 1)])
+def test_dot(n_dims, N):
+    m = hb.Mesh(*n_dims, N)
+    a = inputs.random_vector(m.n_global, 5, "normal")
+    b = inputs.random_vector(m.n_global, 6, "normal")
+    exact = math.fsum((a * b).tolist())
+    got = m.dot(_to_dev(a), _to_dev(b))
+    assert abs(got - exact) <= 1e-14 * np.abs(a * b).sum()
+    a32, b32 = a.astype(np.float32), b.astype(np.float32)
+    exact32 = math.fsum((a32.astype(np.float64) * b32.astype(np.float64)).tolist())
+    got32 = m.dot(_to_dev(a32, torch.float32), _to_dev(b32, torch.float32))
+    assert abs(got32 - exact32) <= 1e-13 * np.abs(a32.astype(np.float64) * b32).sum()
+
+
+def test_rhs_uniform_bit_exact_and_manufactured():
+    m, o = _pair((3, 2, 4), 5, rho=0.2, seed=11)
+    b = m.rhs(kind=0, seed=9).cpu().numpy()
+    np.testing.assert_array_equal(b, o.rhs(kind=0, seed=9))
+    bm = m.rhs(kind=1, lam=0.25).cpu().numpy()
+    bo = o.rhs(kind=1, lam=0.25)
+    assert np.abs(bm - bo).max() <= 1e-13 * np.abs(bo).max()
+
+
+# ---------------------------------------------------------------- CG
+
+def test_cg_fixed_100_iterations_small_box():
+    """4x4x4 elements, N=7, rho=0.1, lambda=0.1, uniform rhs, 100 iterations."""
+    m, o = _pair((4, 4, 4), 7, rho=0.1, seed=0)
+    b_or = o.rhs(kind=0, seed=0)
+    b = m.rhs(kind=0, seed=0)
+    np.testing.assert_array_equal(b.cpu().numpy(), b_or)
+    x_or, it_or, rel_or, st_or, hist = o.cg(b_or, 0.1, rtol=0.0, max_it=100, history=True)
+    x, res = m.cg(b, lam=0.1, rtol=0.0, max_it=100)
+    assert res.status == hb.HB_OK and res.iters == 100 and it_or == 100
+    assert _rel(x.cpu().numpy(), x_or) <= 1e-12
+    # This box is well conditioned: after 100 iterations the recursive residual
+    # r.r is ~1e-26 relative, ten orders below what the true residual can reach
+    # in FP64. There each step's rounding perturbs it relatively, so the two
+    # recursions agree to ~1e-8 relative, not to 1e-12 (x above does).
+    assert abs(res.rel_res - rel_or) <= 1e-7 * rel_or
+    r_true = b_or - o.apply_A(x.cpu().numpy(), 0.1)
+    assert np.linalg.norm(r_true) <= 1e-13 * np.linalg.norm(b_or)
+
+
+@pytest.mark.parametrize("N,lam,screen", [(3, 0.1, 0), (7, 0.0, 0), (5, 1.0, 1)])
+def test_cg_converged(N, lam, screen):
+    m, o = _pair((3, 3, 3), N, rho=0.2, seed=4)
+    b = m.rhs(kind=0, seed=2)
+    x_or, it_or, rel_or, st_or = o.cg(b.cpu().numpy(), lam, rtol=1e-10, max_it=5000, screen=screen)
+    x, res = m.cg(b, lam=lam, rtol=1e-10, max_it=5000, screen=screen)
+    assert res.status == hb.HB_OK and st_or == 0
+    assert res.rel_res <= 1e-10 and rel_or <= 1e-10
+    r = b.cpu().numpy() - o.apply_A(x.cpu().numpy(), lam, screen)
+    assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b.cpu().numpy())
+    assert _rel(x.cpu().numpy(), x_or) <= 10 * 1e-10 * max(1.0, it_or / 100)
+
+
+@pytest.mark.parametrize("N,lam", [(3, 0.1), (7, 0.0), (9, 10.0)])
+def test_cg_mixed_precision_reaches_fp64_residual(N, lam):
+    m, o = _pair((3, 3, 2), N, rho=0.2, seed=5)
+    b = m.rhs(kind=0, seed=3)
+    x, res = m.cg(b, lam=lam, rtol=1e-10, max_it=20000, prec=hb.HB_MIXED, inner_rtol=1e-4)
+    assert res.status == hb.HB_OK, (res.status, res.rel_res, res.iters, res.outer_iters)
+    bn = b.cpu().numpy()
+    r = bn - o.apply_A(x.cpu().numpy(), lam)
+    assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(bn)
+    x_or, *_ = o.cg(bn, lam, rtol=1e-12, max_it=20000)
+    err = _rel(x.cpu().numpy(), x_or)
+    print(f"mixed N={N} lam={lam}: outer {res.outer_iters} inner {res.iters} err vs oracle {err:.2e}")
+    assert err <= 1e-6
+
+
+def test_cg_zero_rhs_and_breakdown():
+    m = hb.Mesh(2, 2, 2, 3)
+    b = m.vec()
+    x, res = m.cg(b, lam=0.1, rtol=1e-10, max_it=50)
+    assert res.iters == 0 and res.status == hb.HB_OK and x.abs().max().item() == 0
+    b = m.rhs(kind=0, seed=1)
+    x, res = m.cg(b, lam=-1e6, rtol=1e-10, max_it=50)
+    assert res.status == hb.HB_ERR_BREAKDOWN
