@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 screened-Poisson operator and CG.
+
+Default workload (one GPU): the degree-sweep configuration at N=7, a perturbed
+box of 64 x 64 x 61 hexahedra (about 128M local nodes), FP64, lambda = 0.1,
+seeded uniform right-hand side. One step is one conjugate-gradient iteration
+(one application of A plus the fused vector stage of Algorithm 1); the value is
+the paper's throughput, global DOFs x iterations / s, in GDOF/s.
+
+Prints one JSON line. Other workloads (--workload sweep | c1 | c3 | c4) print
+their own lines; only the default is the headline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 FMA issue rate of one GB300 SM, measured with an FMA-chain probe
+# (1.194 TFLOP/s with 152 SMs at 1.98 GHz): 2 FMA per clock per SM.
+FP64_FMA_PER_CLK_SM = 2.0
+FP32_FMA_PER_CLK_SM = 128.0
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def peaks():
+    hbm, src = FALLBACK_HBM_GBS, "fallback"
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        hbm, src = float(d["hbm_gbs"]), "measured"
+    except Exception:
+        pass
+    return {"hbm_gbs": hbm, "hbm_src": src,
+            "fp64_tflops": 2 * FP64_FMA_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12,
+            "fp32_tflops": 2 * FP32_FMA_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12}
+
+
+# ---------------------------------------------------------------- workloads
+
+def c2_dims(N: int):
+    """Elements per axis so that local nodes ~ 1.28e8 (Ex = Ey multiple of 8)."""
+    n = N + 1
+    T = 1.28e8 / n ** 3
+    ex = int(math.ceil(T ** (1.0 / 3.0) / 8.0)) * 8
+    ez = int(T // (ex * ex))
+    return ex, ex, ez
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid():
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        return str(torch.cuda.current_device())
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Dist:
+    def __init__(self, world, local, backend):
+        self.world = world
+        self.pg = None
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.init_process_group(backend=backend)
+            self.pg = tdist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- CPU baseline (the oracle)
+
+def cpu_baseline(N, budget_s=12.0, dims=(16, 16, 16), lam=0.1, iters=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: the
+    same degree and mesh recipe on a smaller box, timed over CG iterations."""
+    from oracle import oracle as orc
+    m = orc.Mesh(*dims, N, rho=0.1, seed=0)
+    b = m.rhs(kind=0, seed=0)
+    m.cg(b, lam, rtol=0.0, max_it=1)  # warm
+    done, t_used = 0, 0.0
+    if iters is None:
+        k = 1
+        while t_used < budget_s:
+            t0 = time.perf_counter()
+            m.cg(b, lam, rtol=0.0, max_it=k)
+            dt = time.perf_counter() - t0
+            done += k
+            t_used += dt
+            k = min(2 * k, 64)
+    else:
+        t0 = time.perf_counter()
+        m.cg(b, lam, rtol=0.0, max_it=iters)
+        t_used = time.perf_counter() - t0
+        done = iters
+    return {"value": m.n_global * done / t_used / 1e9, "unit": "GDOF/s", "cores": orc.num_threads(),
+            "kind": "oracle",
+            "sample": f"N={N}, {dims[0]}x{dims[1]}x{dims[2]} elements (N_G={m.n_global}), {done} FP64 CG "
+                      f"iterations (each = one A x plus the vector stage) in {t_used:.1f} s"}
+
+
+# ---------------------------------------------------------------- GB300 arm
+
+def run_gb300(args, rank, world, local):
+    import torch
+
+    from paper_2202_12477_gb300 import accounting as acc
+    from paper_2202_12477_gb300 import hb
+
+    torch.cuda.set_device(local)
+    dist = Dist(world, local, "nccl")
+    N = args.N
+    ex, ey, ez = c2_dims(N)
+    lam = 0.1
+    m = hb.Mesh(ex, ey, ez, N, perturb=0.1, seed=0, fp32=False)
+    NG, NL, E = m.n_global, m.n_local, m.E
+    stream = torch.cuda.current_stream()
+    b = m.rhs(kind=0, seed=0)
+    x = m.vec()
+
+    # warm-up: W iterations
+    m.cg(b, x=x.zero_(), lam=lam, rtol=0.0, max_it=args.warmup)
+    torch.cuda.synchronize()
+
+    hb.hb_profile_reset()
+    hb.hb_profile_enable(True)
+    launches0 = hb.hb_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x.zero_()
+    with ClockSampler(gpu_uuid()) as clk:
+        dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        _, res = m.cg(b, x=x, lam=lam, rtol=0.0, max_it=args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+    launches = hb.hb_kernel_launches() - launches0
+    hb.hb_profile_enable(False)
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = dist.max(t_ms)
+    kern = {}
+    for name in ("ax_local", "assemble", "cg_update_r", "cg_update_xp"):
+        ms, cnt = hb.hb_profile_read(name)
+        kern[name] = {"ms_total": ms, "launches": cnt, "ms_avg": ms / cnt if cnt else None}
+    assert res.iters == args.steps, (res.iters, args.steps)
+
+    # end to end: pinned host b in, solve through the C ABI, x back to pinned host
+    b_host = b.cpu().pin_memory()
+    x_host = torch.empty(NG, dtype=torch.float64).pin_memory()
+    b_dev = torch.empty_like(b)
+    x_dev = torch.zeros_like(b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b_dev.copy_(b_host, non_blocking=True)
+    x_dev.zero_()
+    m.cg(b_dev, x=x_dev, lam=lam, rtol=0.0, max_it=args.steps)
+    x_host.copy_(x_dev, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = dist.max(e0.elapsed_time(e1))
+
+    pk = peaks()
+    ax = kern["ax_local"]
+    ax_flops = acc.op_local_flops(E, N)
+    ax_bytes = acc.ax_local_bytes(NG, NL, 8)
+    achieved_tf = ax_flops / (ax["ms_avg"] * 1e-3) / 1e12
+    out = {
+        "metric": "Ax GDOF/s (FP64; one CG iteration = one A x and its fused vector stage)",
+        "value": world * NG * args.steps / (t_max * 1e-3) / 1e9,
+        "unit": "GDOF/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded perturbed box, SplitMix64 uniform rhs)",
+        "config": {"workload": f"degree sweep config at N={N}: {ex}x{ey}x{ez} hexahedra, perturb 0.1h, "
+                               f"lambda 0.1, FP64 CG, 100-iteration style fixed count",
+                   "N": N, "elements": [ex, ey, ez], "n_local": NL, "n_global": NG,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": f"inputs larger than L2: {7 * 8 * NL / 1e9:.1f} GB of geometric factors streamed "
+                         f"per step (L2 129 MB)"},
+        "roofline": {"bound": "alu", "kernel": "ax_local (FP64)", "achieved": achieved_tf,
+                     "peak": pk["fp64_tflops"], "unit": "TFLOP/s", "frac": achieved_tf / pk["fp64_tflops"],
+                     "peak_src": "derived: 2 FP64 FMA/clk/SM (measured probe) x 152 SMs x 2070 MHz",
+                     "flops_per_launch": ax_flops, "ms_per_launch": ax["ms_avg"],
+                     "traffic": None,
+                     "hbm_view": {"algorithmic_bytes_per_launch": ax_bytes,
+                                  "achieved_gbs": ax_bytes / (ax["ms_avg"] * 1e-3) / 1e9,
+                                  "peak_gbs": pk["hbm_gbs"], "peak_src": pk["hbm_src"],
+                                  "frac": ax_bytes / (ax["ms_avg"] * 1e-3) / 1e9 / pk["hbm_gbs"]}},
+        "kernels": kern,
+        "ax_only_gdofs": NG / ((kern["ax_local"]["ms_avg"] + kern["assemble"]["ms_avg"]) * 1e-3) / 1e9,
+        "fom_gflops_nekbone": acc.nekbone_flops(E, N) * args.steps / (t_max * 1e-3) / 1e9,
+        "e2e": {"value": world * NG * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
+                "h2d_bytes_per_step": 8 * NG / args.steps, "d2h_bytes_per_step": 8 * NG / args.steps,
+                "note": f"one hb_cg_solve of {args.steps} iterations per host round trip"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(N)
+    dist.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+
+def run_reference(args, rank, world, local):
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    N = args.N
+    ex, ey, ez = c2_dims(N)
+    dims = (16, 16, 16)
+    m = orc.Mesh(*dims, N, rho=0.1, seed=0)
+    b = m.rhs(kind=0, seed=0)
+    if args.warmup:
+        m.cg(b, 0.1, rtol=0.0, max_it=args.warmup)
+    t0 = time.perf_counter()
+    m.cg(b, 0.1, rtol=0.0, max_it=args.steps)
+    dt = time.perf_counter() - t0
+    v = m.n_global * args.steps / dt / 1e9
+    out = {
+        "impl": "reference",
+        "metric": "Ax GDOF/s (FP64; one CG iteration = one A x and its fused vector stage)",
+        "value": v, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded perturbed box, SplitMix64 uniform rhs)",
+        "config": {"workload": f"degree sweep config at N={N}: {ex}x{ey}x{ez} hexahedra (bounded sample "
+                               f"{dims[0]}x{dims[1]}x{dims[2]} on the host cores)", "N": N},
+        "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": orc.num_threads(), "kind": "oracle",
+                         "sample": f"N={N}, {dims[0]}x{dims[1]}x{dims[2]} elements (N_G={m.n_global}), "
+                                   f"{args.steps} FP64 CG iterations"},
+        "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- operator sweep
+
+def run_sweep(args, rank, world, local):
+    """Operator-only degree sweep (mean of 50 back-to-back launches, as the paper's Sec. 4.1)."""
+    import torch
+
+    from paper_2202_12477_gb300 import accounting as acc
+    from paper_2202_12477_gb300 import hb, inputs
+
+    torch.cuda.set_device(local)
+    pk = peaks()
+    Ns = [int(v) for v in args.degrees.split(",")] if args.degrees else list(range(1, 16))
+    for N in Ns:
+        for prec in args.precisions.split(","):
+            dims = c2_dims(N)
+            m = hb.Mesh(*dims, N, perturb=0.1, seed=0, fp32=(prec == "f32"))
+            dt = torch.float64 if prec == "f64" else torch.float32
+            x = torch.from_numpy(inputs.random_vector(m.n_global, 1)).to("cuda", dt)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                m.apply_A(x, y, lam=0.1)
+            torch.cuda.synchronize()
+            hb.hb_profile_reset()
+            hb.hb_profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            reps = 50
+            for _ in range(reps):
+                m.apply_A(x, y, lam=0.1)
+            e1.record()
+            torch.cuda.synchronize()
+            hb.hb_profile_enable(False)
+            t = e0.elapsed_time(e1) / reps
+            axm, axn = hb.hb_profile_read("ax_local")
+            asm, asn = hb.hb_profile_read("assemble")
+            esz = 8 if prec == "f64" else 4
+            fl = acc.op_flops(m.E, N)
+            rec = {"workload": "operator sweep", "N": N, "prec": prec, "elements": list(dims),
+                   "n_local": m.n_local, "n_global": m.n_global, "ms": t,
+                   "ax_local_ms": axm / axn, "assemble_ms": asm / asn,
+                   "gdofs": m.n_global / (t * 1e-3) / 1e9, "gflops_paper": fl / (t * 1e-3) / 1e9,
+                   "eff_gbs_method_min": acc.ax_min_bytes(m.n_global, m.n_local, esz) / (t * 1e-3) / 1e9,
+                   "hbm_peak_gbs": pk["hbm_gbs"]}
+            rec["hbm_frac_method_min"] = rec["eff_gbs_method_min"] / pk["hbm_gbs"]
+            rec["alu_frac"] = (acc.op_local_flops(m.E, N) / (axm / axn * 1e-3) / 1e12
+                               / (pk["fp64_tflops"] if prec == "f64" else pk["fp32_tflops"]))
+            print(json.dumps(rec), flush=True)
+            m.close()
+            del x, y
+            torch.cuda.empty_cache()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "sweep"])
+    ap.add_argument("--N", type=int, default=7)
+    ap.add_argument("--degrees", default="")
+    ap.add_argument("--precisions", default="f64,f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300" and args.workload == "c2":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+        return
+    from paper_2202_12477_gb300 import build
+    build.build()
+    if args.workload == "sweep":
+        run_sweep(args, rank, world, local)
+    else:
+        run_gb300(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

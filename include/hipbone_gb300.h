@@ -183,6 +183,23 @@ hb_status hb_cg_solve(const hb_mesh *mesh, const hb_cg_opts *opts, const double 
  * splitmix64(s) the SplitMix64 output for state s (Steele, Lea & Flood 2014). */
 double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx);
 
+/* Measurement support (the paper times its kernels with wall clocks over
+ * back-to-back launches, Sec. 4.1; here each kernel is bracketed on its own
+ * stream).
+ * hb_kernel_launches: number of CUDA kernels this library has launched in the
+ *   process so far (all entry points, all devices).
+ * hb_profile_enable(1): from now on every library kernel launch is bracketed
+ *   by a pair of CUDA events recorded on its launch stream (adds two event
+ *   records per launch; off by default).
+ * hb_profile_read: waits for the recorded events of kernel `name` ("ax_local",
+ *   "assemble", "dot", "cg_update_r", "cg_update_xp") and returns the summed
+ *   device time in ms and the number of launches since the last reset.
+ * hb_profile_reset: forgets the recorded launches. */
+unsigned long long hb_kernel_launches(void);
+hb_status hb_profile_enable(int on);
+hb_status hb_profile_reset(void);
+hb_status hb_profile_read(const char *name, double *total_ms, long long *launches);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *hb_last_error(void);
 

@@ -133,6 +133,7 @@ hb_status launch_ax_local(const T *x, const int32_t *l2g, const T *geo, T *yL, i
         attr_set[dev] = 1;
     }
     const int64_t blocks = (E + S::EB - 1) / S::EB;
+    hb_prof_scope prof("ax_local", s);
     ax_local_kernel<N, T, S::EB><<<(unsigned)blocks, S::threads, smem, s>>>(x, l2g, geo, yL, E, Dg, run);
     HB_CHECK_LAUNCH();
     return HB_OK;

@@ -160,6 +160,7 @@ hb_status launch_assemble(const hb_mesh *m, const T *yL, const T *x, T *y, const
     if (ng == 0) return HB_OK;
     const int grid = red_grid(ng);
     unsigned *ctr = m->counters + 0;
+    hb_prof_scope prof("assemble", s);
 #define HB_ASM(SC, DM)                                                                                   \
     assemble_kernel<T, SC, DM><<<grid, HB_RED_THREADS, 0, s>>>(yL, m->rowptr, m->cols, x, mdiag, lambda, \
                                                                y, ng, m->partials, ctr, st)
@@ -378,6 +379,7 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
 hb_status hb_launch_dot_f64(const hb_mesh *m, const double *a, const double *b, int64_t n, double *out,
                             cudaStream_t s)
 {
+    hb_prof_scope prof("dot", s);
     dot_kernel<double><<<red_grid(n), HB_RED_THREADS, 0, s>>>(a, b, n, out, m->partials, m->counters + 1);
     HB_CHECK_LAUNCH();
     return HB_OK;
@@ -386,6 +388,7 @@ hb_status hb_launch_dot_f64(const hb_mesh *m, const double *a, const double *b, 
 hb_status hb_launch_dot_f32(const hb_mesh *m, const float *a, const float *b, int64_t n, double *out,
                             cudaStream_t s)
 {
+    hb_prof_scope prof("dot", s);
     dot_kernel<float><<<red_grid(n), HB_RED_THREADS, 0, s>>>(a, b, n, out, m->partials, m->counters + 1);
     HB_CHECK_LAUNCH();
     return HB_OK;
@@ -457,10 +460,16 @@ static hb_status cg_iterations(const hb_mesh *m, hb_precision prec, int screen, 
     for (int it = 0; it < count; it++) {
         hb_status rs = hb_apply_A_impl(m, prec, screen, lambda, p, Ap, st, HB_DOT_CG_PAP, s);
         if (rs != HB_OK) return rs;
-        cg_update_r_kernel<T><<<grid, HB_RED_THREADS, 0, s>>>(r, Ap, n, m->partials, m->counters + 2, st);
-        HB_CHECK_LAUNCH();
-        cg_update_xp_kernel<T><<<grid, HB_RED_THREADS, 0, s>>>(x, p, r, n, m->counters + 3, st);
-        HB_CHECK_LAUNCH();
+        {
+            hb_prof_scope prof("cg_update_r", s);
+            cg_update_r_kernel<T><<<grid, HB_RED_THREADS, 0, s>>>(r, Ap, n, m->partials, m->counters + 2, st);
+            HB_CHECK_LAUNCH();
+        }
+        {
+            hb_prof_scope prof("cg_update_xp", s);
+            cg_update_xp_kernel<T><<<grid, HB_RED_THREADS, 0, s>>>(x, p, r, n, m->counters + 3, st);
+            HB_CHECK_LAUNCH();
+        }
     }
     return HB_OK;
 }
@@ -518,6 +527,7 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
         // r0 = b - A x0, p = r0 (Algorithm 1, lines 4-5)
         rs = hb_apply_A_impl(m, HB_F64, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
         if (rs != HB_OK) return rs;
+        hb_count_launch();
         cg_init_kernel<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, p, n, o->rtol, o->max_it, m->partials,
                                                        m->counters + 2, st);
         HB_CHECK_LAUNCH();
@@ -535,6 +545,7 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
         for (;;) {
             rs = hb_apply_A_impl(m, HB_F64, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
             if (rs != HB_OK) return rs;
+            hb_count_launch();
             residual_kernel<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, n, m->partials, m->counters + 2, st);
             HB_CHECK_LAUNCH();
             HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
@@ -544,6 +555,7 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
             if (!std::isfinite(rel)) { R.status = HB_ERR_BREAKDOWN; break; }
             if (bb == 0.0 || rr <= o->rtol * o->rtol * bb) break;
             if (outer >= max_outer || used >= o->max_it) { R.status = HB_ERR_NOT_CONVERGED; break; }
+            hb_count_launch();
             inner_init_kernel<<<grid, HB_RED_THREADS, 0, s>>>(r, r32, p32, d32, n, rtol_in, o->max_it - used,
                                                               m->partials, m->counters + 2, st, st_in);
             HB_CHECK_LAUNCH();
@@ -553,6 +565,7 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
             used += fin.it;
             outer++;
             if (fin.status == HB_ERR_BREAKDOWN && fin.it == 0) { R.status = HB_ERR_BREAKDOWN; break; }
+            hb_count_launch();
             update_x_kernel<<<grid, HB_RED_THREADS, 0, s>>>(x, d32, n, st);
             HB_CHECK_LAUNCH();
         }

@@ -30,6 +30,16 @@ void hb_clear_error();
 
 #define HB_CHECK_LAUNCH() HB_TRY_CUDA(cudaGetLastError())
 
+// Counts one kernel launch; with timing enabled also records a CUDA event pair
+// around it on its stream (see hb_profile_* in the C header).
+void hb_count_launch();
+struct hb_prof_scope {
+    cudaStream_t stream;
+    cudaEvent_t stop;
+    hb_prof_scope(const char *name, cudaStream_t s);
+    ~hb_prof_scope();
+};
+
 // ---------------------------------------------------------------- CG device state
 
 // Scalars of Algorithm 1 kept on the device so that no iteration waits on the

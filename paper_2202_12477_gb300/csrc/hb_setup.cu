@@ -534,6 +534,7 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     HB_TRY_MESH(cudaMemsetAsync(m->state, 0, sizeof(hb_cg_state) * 4, s));
 
     box_t b{d->ex, d->ey, d->ez, N, d->dirichlet_faces};
+    hb_count_launch();
     k_l2g<<<grid_for(n_local, 256), 256, 0, s>>>(b, n_local, m->l2g);
     HB_TRY_MESH(cudaGetLastError());
 
@@ -543,22 +544,28 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     size_t gsmem = sizeof(double) * (3 * n * n * n + n * n);
     HB_TRY_MESH(cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
     HB_TRY_MESH(cudaMalloc((void **)&tmp_det, sizeof(double) * (gblocks + 1)));
+    hb_count_launch();
     k_geometry<<<gblocks, gthreads, gsmem, s>>>(b, d->perturb, d->seed, E, m->geo, m->geo32, tmp_det);
     HB_TRY_MESH(cudaGetLastError());
+    hb_count_launch();
     k_min_reduce<<<1, 32, 0, s>>>(tmp_det, gblocks, tmp_det + gblocks);
     HB_TRY_MESH(cudaGetLastError());
 
     // CSR of Z^T: count, scan, fill, sort rows
     HB_TRY_MESH(cudaMalloc((void **)&tmp_cnt, sizeof(int32_t) * (ng + 1)));
     HB_TRY_MESH(cudaMemsetAsync(tmp_cnt, 0, sizeof(int32_t) * (ng + 1), s));
+    hb_count_launch();
     k_count<<<grid_for(n_local, 256), 256, 0, s>>>(m->l2g, n_local, tmp_cnt);
     HB_TRY_MESH(cudaGetLastError());
     const int64_t nchunks = (ng + 1 + 1023) / 1024;
     HB_TRY_MESH(cudaMalloc((void **)&tmp_sum, sizeof(int64_t) * (nchunks + 1)));
+    hb_count_launch();
     k_scan_chunks<<<(unsigned)nchunks, 1024, 0, s>>>(tmp_cnt, ng + 1, m->rowptr, tmp_sum);
     HB_TRY_MESH(cudaGetLastError());
+    hb_count_launch();
     k_scan_sums<<<1, 32, 0, s>>>(tmp_sum, nchunks);
     HB_TRY_MESH(cudaGetLastError());
+    hb_count_launch();
     k_scan_add<<<grid_for(ng + 1, 256), 256, 0, s>>>(m->rowptr, ng + 1, tmp_sum);
     HB_TRY_MESH(cudaGetLastError());
     int32_t nnz32 = 0;
@@ -570,8 +577,10 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     m->min_detJ = detmin;
     HB_TRY_MESH(alloc((void **)&m->cols, sizeof(int32_t) * (m->nnz > 0 ? m->nnz : 1)));
     HB_TRY_MESH(cudaMemsetAsync(tmp_cnt, 0, sizeof(int32_t) * (ng + 1), s));
+    hb_count_launch();
     k_fill<<<grid_for(n_local, 256), 256, 0, s>>>(m->l2g, n_local, m->rowptr, tmp_cnt, m->cols);
     HB_TRY_MESH(cudaGetLastError());
+    hb_count_launch();
     k_sort_rows<<<grid_for(ng, 256), 256, 0, s>>>(m->rowptr, m->cols, ng, m->geo, n, m->mdiag, m->mdiag32);
     HB_TRY_MESH(cudaGetLastError());
     HB_TRY_MESH(cudaStreamSynchronize(s));
@@ -693,8 +702,10 @@ extern "C" hb_status hb_fill_rhs(const hb_mesh *m, int kind, uint64_t seed, doub
     box_t b{m->desc.ex, m->desc.ey, m->desc.ez, m->N, m->desc.dirichlet_faces};
     if (m->n_global == 0) return HB_OK;
     if (kind == 0) {
+        hb_count_launch();
         k_rhs_uniform<<<grid_for(m->n_local, 256), 256, 0, s>>>(m->l2g, b, m->n_local, seed, bvec);
     } else {
+        hb_count_launch();
         k_rhs_manufactured<<<grid_for(m->n_global, 128), 128, 0, s>>>(
             m->rowptr, m->cols, m->n_global, b, m->desc.perturb, m->desc.seed, m->geo, lambda, bvec);
     }

@@ -74,6 +74,10 @@ _SIGS = [
     ("hb_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
                               C.POINTER(hb_cg_result), C.c_void_p]),
     ("hb_u01", C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64]),
+    ("hb_kernel_launches", C.c_ulonglong, []),
+    ("hb_profile_enable", C.c_int, [C.c_int]),
+    ("hb_profile_reset", C.c_int, []),
+    ("hb_profile_read", C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     ("hb_last_error", C.c_char_p, []),
 ]
 
@@ -157,6 +161,26 @@ def hb_cg_solve(h, opts: hb_cg_opts, b_ptr, x_ptr, stream=None, check=True) -> h
 
 def hb_u01(seed, stream, idx) -> float:
     return lib().hb_u01(seed, stream, idx)
+
+
+def hb_kernel_launches() -> int:
+    return lib().hb_kernel_launches()
+
+
+def hb_profile_enable(on: bool) -> None:
+    _check(lib().hb_profile_enable(1 if on else 0))
+
+
+def hb_profile_reset() -> None:
+    _check(lib().hb_profile_reset())
+
+
+def hb_profile_read(name: str):
+    """(total device ms, launches) recorded for kernel `name`."""
+    ms = C.c_double(0.0)
+    cnt = C.c_longlong(0)
+    _check(lib().hb_profile_read(name.encode(), C.byref(ms), C.byref(cnt)))
+    return ms.value, cnt.value
 
 
 # ---------------------------------------------------------------- convenience owner
