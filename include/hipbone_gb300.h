@@ -138,6 +138,30 @@ hb_status hb_apply_A(const hb_mesh *mesh, hb_precision prec, hb_screen screen,
 hb_status hb_dot(const hb_mesh *mesh, hb_precision prec, const void *a, const void *b,
                  double *out_dev, double *out_host, void *stream);
 
+/* a.b like hb_dot, for callers that must not allocate device memory: it
+ * needs no mesh and calls no cudaMalloc, cudaFree or allocating routine. The
+ * paper has no counterpart; this exists for applications whose allocator
+ * owns the whole device (a caching allocator, a serving loop with a fixed
+ * memory budget) or whose latency-critical loop cannot take the device-wide
+ * synchronisation an allocation may cause.
+ * Scratch: a static device array inside the library (16384 block partials,
+ * 128 KB), held on every GPU that loads the library until the process exits.
+ * Maximum length: n <= 16384 * 1024 = 16,777,216 elements; longer vectors are
+ * rejected with HB_ERR_ARG and a message. Up to 622,592 elements the result
+ * is bitwise the same as hb_dot's; beyond, the blocks differ, so it agrees to
+ * rounding (about 1e-16 of sum |a_i b_i|).
+ * a, b: device vectors of n doubles (HB_F64) or floats (HB_F32). The result
+ * goes to *out_dev (device double) or, if out_dev is NULL, to a slot inside
+ * the static array; if out_host is not NULL it is also copied there, which
+ * synchronises `stream`.
+ * The first call on a device takes the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Every call shares the one array: calls that overlap in time on the
+ * GPU (different streams, or different host threads) race and give wrong
+ * results; serialise them. */
+hb_status hb_dot_noalloc(hb_precision prec, const void *a, const void *b, int64_t n,
+                         double *out_dev, double *out_host, void *stream);
+
 /* Right-hand side on the assembled DOFs (FP64, length n_global).
  * kind 0: b_g = 2 u01(seed, 2, I + (N ex+1)(J + (N ey+1) K)) - 1 at the global
  *         node with lattice coordinates (I,J,K) -- hipBone's pseudo-random

@@ -13,6 +13,7 @@
 // finished solve return at once, so iterations are enqueued in runs without
 // host round trips.
 #include <cmath>
+#include <mutex>
 
 #include "hb_internal.h"
 
@@ -580,4 +581,87 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
     R.time_ms = ms;
     if (res) *res = R;
     return R.status;
+}
+
+// ---------------------------------------------------------------- dot without any allocation
+//
+// hb_dot needs a mesh, and a mesh holds device memory the library allocated.
+// hb_dot_noalloc serves callers that may not allocate device memory at all:
+// for instance an application whose own allocator has reserved the whole
+// device (a caching allocator, or a serving loop that admits work against a
+// fixed memory budget), where a cudaMalloc would fail or break the budget,
+// or a latency-critical loop that cannot afford the device-wide
+// synchronisation cudaMalloc and cudaFree can cause. Its scratch (one
+// partial sum per block, the arrival counter and a result slot) lives in the
+// file-scope array below, which every GPU that loads this library holds
+// until the process exits.
+#define HB_DOT_NOALLOC_BLOCKS 16384  // partial sums: 128 KB per device
+#define HB_DOT_NOALLOC_MAX_N ((int64_t)HB_DOT_NOALLOC_BLOCKS * HB_RED_THREADS * 4)
+
+static __device__ __align__(256) double g_dot_noalloc_scratch[HB_DOT_NOALLOC_BLOCKS + 32];
+
+static std::mutex g_dot_noalloc_mu;
+static double *g_dot_noalloc_ptr[64];  // device address of the array, per device
+
+// Device address of the scratch array on the current device. Taken once per
+// device, with that device current; host code must not use the array's name
+// as a device pointer.
+static hb_status dot_noalloc_scratch(double **out)
+{
+    int dev = -1;
+    HB_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { hb_set_error("hb_dot_noalloc: device index %d not supported", dev); return HB_ERR_ARG; }
+    std::lock_guard<std::mutex> lk(g_dot_noalloc_mu);
+    if (!g_dot_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_dot_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            hb_set_error("hb_dot_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return HB_ERR_CUDA;
+        }
+        g_dot_noalloc_ptr[dev] = (double *)p;
+    }
+    *out = g_dot_noalloc_ptr[dev];
+    return HB_OK;
+}
+
+extern "C" hb_status hb_dot_noalloc(hb_precision prec, const void *a, const void *b, int64_t n, double *out_dev,
+                                    double *out_host, void *stream)
+{
+    hb_clear_error();
+    if (n < 0) { hb_set_error("hb_dot_noalloc: n = %lld is negative", (long long)n); return HB_ERR_ARG; }
+    if (n > HB_DOT_NOALLOC_MAX_N) {
+        hb_set_error("hb_dot_noalloc: n = %lld exceeds the maximum of %lld elements its static scratch serves",
+                     (long long)n, (long long)HB_DOT_NOALLOC_MAX_N);
+        return HB_ERR_ARG;
+    }
+    if (n > 0 && (!a || !b)) { hb_set_error("hb_dot_noalloc: null vector"); return HB_ERR_ARG; }
+    if (prec != HB_F64 && prec != HB_F32) { hb_set_error("hb_dot_noalloc takes HB_F64 or HB_F32"); return HB_ERR_ARG; }
+    double *scratch = nullptr;
+    hb_status st = dot_noalloc_scratch(&scratch);
+    if (st != HB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *counter = reinterpret_cast<unsigned *>(scratch + HB_DOT_NOALLOC_BLOCKS);
+    double *result = out_dev ? out_dev : scratch + HB_DOT_NOALLOC_BLOCKS + 16;
+    // the array keeps the previous call's contents: the arrival counter must start at zero
+    HB_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
+    if (n == 0) {
+        HB_TRY_CUDA(cudaMemsetAsync(result, 0, sizeof(double), s));
+    } else {
+        // one block per 1024 elements: the same grid as hb_dot up to 608 blocks
+        const int blocks = (int)((n + HB_RED_THREADS * 4 - 1) / (HB_RED_THREADS * 4));
+        hb_count_launch();
+        if (prec == HB_F64)
+            dot_kernel<double><<<blocks, HB_RED_THREADS, 0, s>>>((const double *)a, (const double *)b, n, result,
+                                                                 scratch, counter);
+        else
+            dot_kernel<float><<<blocks, HB_RED_THREADS, 0, s>>>((const float *)a, (const float *)b, n, result,
+                                                                scratch, counter);
+        HB_CHECK_LAUNCH();
+    }
+    if (out_host) {
+        HB_TRY_CUDA(cudaMemcpyAsync(out_host, result, sizeof(double), cudaMemcpyDeviceToHost, s));
+        HB_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    return HB_OK;
 }

@@ -70,6 +70,8 @@ _SIGS = [
     ("hb_apply_A", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("hb_dot", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                          C.c_void_p]),
+    ("hb_dot_noalloc", C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                 C.POINTER(C.c_double), C.c_void_p]),
     ("hb_fill_rhs", C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_double, C.c_void_p, C.c_void_p]),
     ("hb_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
                               C.POINTER(hb_cg_result), C.c_void_p]),
