@@ -211,6 +211,8 @@ def run_gb300(args, rank, world, local):
     m = hb.Mesh(ex, ey, ez, N, perturb=0.1, seed=0, fp32=False)
     NG, NL, E = m.n_global, m.n_local, m.E
     stream = torch.cuda.current_stream()
+    from paper_2202_12477_gb300 import autotune
+    variant = autotune.tune_mesh(m, precs=(hb.HB_F64,), lam=0.1)[hb.HB_F64]
     b = m.rhs(kind=0, seed=0)
     x = m.vec()
 
@@ -279,6 +281,7 @@ def run_gb300(args, rank, world, local):
         "config": {"workload": f"degree sweep config at N={N}: {ex}x{ey}x{ez} hexahedra, perturb 0.1h, "
                                f"lambda 0.1, FP64 CG, 100-iteration style fixed count",
                    "N": N, "elements": [ex, ey, ez], "n_local": NL, "n_global": NG,
+                   "kernel_variant": variant,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": f"inputs larger than L2: {7 * 8 * NL / 1e9:.1f} GB of geometric factors streamed "
                          f"per step (L2 129 MB)"},
@@ -352,44 +355,134 @@ def run_sweep(args, rank, world, local):
     torch.cuda.set_device(local)
     pk = peaks()
     Ns = [int(v) for v in args.degrees.split(",")] if args.degrees else list(range(1, 16))
+    variants = [int(v) for v in args.variants.split(",")] if args.variants else [None]
     for N in Ns:
         for prec in args.precisions.split(","):
             dims = c2_dims(N)
             m = hb.Mesh(*dims, N, perturb=0.1, seed=0, fp32=(prec == "f32"))
+            hbprec = hb.HB_F64 if prec == "f64" else hb.HB_F32
             dt = torch.float64 if prec == "f64" else torch.float32
             x = torch.from_numpy(inputs.random_vector(m.n_global, 1)).to("cuda", dt)
             y = torch.empty_like(x)
-            for _ in range(3):
-                m.apply_A(x, y, lam=0.1)
-            torch.cuda.synchronize()
-            hb.hb_profile_reset()
-            hb.hb_profile_enable(True)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            reps = 50
-            for _ in range(reps):
-                m.apply_A(x, y, lam=0.1)
-            e1.record()
-            torch.cuda.synchronize()
-            hb.hb_profile_enable(False)
-            t = e0.elapsed_time(e1) / reps
-            axm, axn = hb.hb_profile_read("ax_local")
-            asm, asn = hb.hb_profile_read("assemble")
-            esz = 8 if prec == "f64" else 4
-            fl = acc.op_flops(m.E, N)
-            rec = {"workload": "operator sweep", "N": N, "prec": prec, "elements": list(dims),
-                   "n_local": m.n_local, "n_global": m.n_global, "ms": t,
-                   "ax_local_ms": axm / axn, "assemble_ms": asm / asn,
-                   "gdofs": m.n_global / (t * 1e-3) / 1e9, "gflops_paper": fl / (t * 1e-3) / 1e9,
-                   "eff_gbs_method_min": acc.ax_min_bytes(m.n_global, m.n_local, esz) / (t * 1e-3) / 1e9,
-                   "hbm_peak_gbs": pk["hbm_gbs"]}
-            rec["hbm_frac_method_min"] = rec["eff_gbs_method_min"] / pk["hbm_gbs"]
-            rec["alu_frac"] = (acc.op_local_flops(m.E, N) / (axm / axn * 1e-3) / 1e12
-                               / (pk["fp64_tflops"] if prec == "f64" else pk["fp32_tflops"]))
-            print(json.dumps(rec), flush=True)
+            for var in variants:
+                if var is not None:
+                    hb.hb_set_kernel_variant(m.handle, hbprec, var)
+                var = hb.hb_get_kernel_variant(m.handle, hbprec)
+                for _ in range(3):
+                    m.apply_A(x, y, lam=0.1)
+                torch.cuda.synchronize()
+                hb.hb_profile_reset()
+                hb.hb_profile_enable(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                reps = args.reps
+                for _ in range(reps):
+                    m.apply_A(x, y, lam=0.1)
+                e1.record()
+                torch.cuda.synchronize()
+                hb.hb_profile_enable(False)
+                t = e0.elapsed_time(e1) / reps
+                axm, axn = hb.hb_profile_read("ax_local")
+                asm, asn = hb.hb_profile_read("assemble")
+                esz = 8 if prec == "f64" else 4
+                fl = acc.op_flops(m.E, N)
+                rec = {"workload": "operator sweep", "N": N, "prec": prec, "variant": var, "elements": list(dims),
+                       "n_local": m.n_local, "n_global": m.n_global, "ms": t,
+                       "ax_local_ms": axm / axn, "assemble_ms": asm / asn,
+                       "gdofs": m.n_global / (t * 1e-3) / 1e9, "gflops_paper": fl / (t * 1e-3) / 1e9,
+                       "eff_gbs_method_min": acc.ax_min_bytes(m.n_global, m.n_local, esz) / (t * 1e-3) / 1e9,
+                       "ax_local_gbs": acc.ax_local_bytes(m.n_global, m.n_local, esz) / (axm / axn * 1e-3) / 1e9,
+                       "assemble_gbs": acc.assemble_bytes(m.n_global, m.info.nnz, esz) / (asm / asn * 1e-3) / 1e9,
+                       "hbm_peak_gbs": pk["hbm_gbs"]}
+                rec["hbm_frac_method_min"] = rec["eff_gbs_method_min"] / pk["hbm_gbs"]
+                rec["alu_frac"] = (acc.op_local_flops(m.E, N) / (axm / axn * 1e-3) / 1e12
+                                   / (pk["fp64_tflops"] if prec == "f64" else pk["fp32_tflops"]))
+                print(json.dumps(rec), flush=True)
             m.close()
             del x, y
             torch.cuda.empty_cache()
+
+
+def _solve_report(m, b, lam, prec, rtol, screen=0, max_it=200000, inner_rtol=1e-4):
+    import torch
+
+    from paper_2202_12477_gb300 import hb
+    x = m.vec()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    x, res = m.cg(b, x=x, lam=lam, rtol=rtol, max_it=max_it, prec=prec, screen=screen, inner_rtol=inner_rtol)
+    e1.record()
+    torch.cuda.synchronize()
+    # FP64 residual of the returned solution, recomputed with the FP64 operator
+    r = b - m.apply_A(x, lam=lam, screen=screen)
+    rel = float(torch.linalg.norm(r) / torch.linalg.norm(b))
+    return x, {"prec": {hb.HB_F64: "f64", hb.HB_MIXED: "mixed"}[prec], "time_s": e0.elapsed_time(e1) / 1e3,
+               "iters": res.iters, "outer_iters": res.outer_iters, "status": hb.STATUS_NAMES[res.status],
+               "rel_res_fp64": rel}
+
+
+def run_c3(args, rank, world, local):
+    """Single large solve: N=7, 80^3 elements, manufactured rhs, FP64 CG vs
+    FP32-inner / FP64 defect correction, both to relative residual 1e-10."""
+    import torch
+
+    from paper_2202_12477_gb300 import autotune, hb
+    torch.cuda.set_device(local)
+    N, E1 = args.N if args.N != 7 else 7, args.c3_elems
+    m = hb.Mesh(E1, E1, E1, N, perturb=0.1, seed=0, fp32=True)
+    autotune.tune_mesh(m, lam=0.0)
+    b = m.rhs(kind=1, lam=0.0)
+    out = {"workload": f"single large solve N={N}, {E1}^3 elements, perturb 0.1h, manufactured rhs "
+                       f"(u = sin sin sin), lambda 0, rtol 1e-10", "n_global": m.n_global, "n_local": m.n_local,
+           "results": []}
+    xs = {}
+    for prec in (hb.HB_F64, hb.HB_MIXED):
+        x, rec = _solve_report(m, b, 0.0, prec, 1e-10)
+        xs[prec] = x
+        out["results"].append(rec)
+    d = xs[hb.HB_MIXED] - xs[hb.HB_F64]
+    out["mixed_vs_fp64_rel_err"] = float(torch.linalg.norm(d) / torch.linalg.norm(xs[hb.HB_F64]))
+    out["speedup_mixed_over_fp64"] = out["results"][0]["time_s"] / out["results"][1]["time_s"]
+    print(json.dumps(out), flush=True)
+
+
+def run_c4(args, rank, world, local):
+    """Mixed-precision stress: N=15, 24^3 elements, vertex perturbation 0.3h,
+    lambda in {0, 1e-3, 10}; FP32 operator / inner CG with FP64 residual, dots
+    and update against plain FP64 CG; error of the mixed solution against the
+    FP64 solution per lambda."""
+    import torch
+
+    from paper_2202_12477_gb300 import autotune, hb
+    torch.cuda.set_device(local)
+    E1 = args.c4_elems
+    # 0.3h perturbations can invert an element; the library refuses such a mesh
+    # (HB_ERR_GEOMETRY). Every refused seed is reported and the first valid one used.
+    refused, m = [], None
+    for seed in range(20):
+        try:
+            m = hb.Mesh(E1, E1, E1, 15, perturb=0.3, seed=seed, fp32=True)
+            break
+        except hb.HBError as err:
+            if err.status != hb.HB_ERR_GEOMETRY:
+                raise
+            refused.append({"seed": seed, "error": str(err)})
+    if m is None:
+        print(json.dumps({"workload": "mixed-precision stress", "refused": refused}), flush=True)
+        return
+    autotune.tune_mesh(m)
+    b = m.rhs(kind=0, seed=0)
+    out = {"workload": f"mixed-precision stress N=15, {E1}^3 elements, perturb 0.3h, uniform rhs, rtol 1e-10",
+           "n_global": m.n_global, "mesh_seed": seed, "refused_seeds": refused, "min_detJ": m.info.min_detJ,
+           "per_lambda": []}
+    for lam in (0.0, 1e-3, 10.0):
+        x64, r64 = _solve_report(m, b, lam, hb.HB_F64, 1e-10)
+        xm, rm = _solve_report(m, b, lam, hb.HB_MIXED, 1e-10)
+        err = float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))
+        out["per_lambda"].append({"lambda": lam, "fp64": r64, "mixed": rm, "mixed_vs_fp64_rel_err": err,
+                                  "speedup": r64["time_s"] / rm["time_s"]})
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -398,10 +491,14 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "sweep"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "sweep", "c3", "c4"])
+    ap.add_argument("--c3-elems", type=int, default=80)
+    ap.add_argument("--c4-elems", type=int, default=24)
     ap.add_argument("--N", type=int, default=7)
     ap.add_argument("--degrees", default="")
     ap.add_argument("--precisions", default="f64,f32")
+    ap.add_argument("--variants", default="")
+    ap.add_argument("--reps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300" and args.workload == "c2":
@@ -414,6 +511,10 @@ def main():
     build.build()
     if args.workload == "sweep":
         run_sweep(args, rank, world, local)
+    elif args.workload == "c3":
+        run_c3(args, rank, world, local)
+    elif args.workload == "c4":
+        run_c4(args, rank, world, local)
     else:
         run_gb300(args, rank, world, local)
 

@@ -147,7 +147,7 @@ hb_status hb_dot(const hb_mesh *mesh, hb_precision prec, const void *a, const vo
  * Scratch: a static device array inside the library (16384 block partials,
  * 128 KB), held on every GPU that loads the library until the process exits.
  * Maximum length: n <= 16384 * 1024 = 16,777,216 elements; longer vectors are
- * rejected with HB_ERR_ARG and a message. Up to 622,592 elements the result
+ * rejected with HB_ERR_ARG and a message. Up to 1,245,184 elements the result
  * is bitwise the same as hb_dot's; beyond, the blocks differ, so it agrees to
  * rounding (about 1e-16 of sum |a_i b_i|).
  * a, b: device vectors of n doubles (HB_F64) or floats (HB_F32). The result
@@ -206,6 +206,30 @@ hb_status hb_cg_solve(const hb_mesh *mesh, const hb_cg_opts *opts, const double 
  * (splitmix64(seed ^ (stream * 0x9E3779B97F4A7C15) + idx) >> 11) * 2^-53, with
  * splitmix64(s) the SplitMix64 output for state s (Steele, Lea & Flood 2014). */
 double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx);
+
+/* Element-kernel variants of the operator (all compute the same A x; they
+ * differ in thread mapping and operation count). Bit flags:
+ *   0                     one thread per t-line, D and the element in shared memory
+ *   HB_VARIANT_PENCIL     every 1-D contraction by a thread owning the whole line,
+ *                         D from constant memory
+ *   HB_VARIANT_EVEN_ODD   (with PENCIL) even-odd split of the centro-antisymmetric D:
+ *                         n^2/2 + 2n operations per line instead of n^2
+ *   HB_VARIANT_EB2        (with PENCIL, N <= 10) two element groups per thread block
+ * The default is PENCIL | EVEN_ODD; hb_autotune measures and picks per mesh. */
+enum { HB_VARIANT_PENCIL = 1, HB_VARIANT_EVEN_ODD = 2, HB_VARIANT_EB2 = 4 };
+hb_status hb_set_kernel_variant(hb_mesh *mesh, hb_precision prec, int variant);
+hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *variant);
+
+/* Autotuner (the paper makes its 3-D / 2-D kernel switch a configurable choice
+ * made from measurements, Sec. 3.2; here every variant is timed on the mesh
+ * itself). Runs one untimed and `reps` timed applications of A for each
+ * variant (0, PENCIL, PENCIL|EVEN_ODD, PENCIL|EB2, PENCIL|EVEN_ODD|EB2) on
+ * `stream`, keeps the fastest for `prec` on this mesh and returns it in
+ * *best_variant. ms_per_variant (may be NULL) has 8 slots indexed by variant
+ * and receives the mean time of each. Allocates two scratch vectors for the
+ * duration of the call; synchronises `stream`. */
+hb_status hb_autotune(hb_mesh *mesh, hb_precision prec, hb_screen screen, double lambda, int reps,
+                      int *best_variant, double *ms_per_variant, void *stream);
 
 /* Measurement support (the paper times its kernels with wall clocks over
  * back-to-back launches, Sec. 4.1; here each kernel is bracketed on its own

@@ -1,0 +1,95 @@
+"""Persistent choice of the element-kernel variant per GPU, degree and precision.
+
+The library's hb_autotune times every variant on a given mesh (C ABI). This
+module keeps the winners in a JSON cache keyed by GPU name, SM count, degree
+N and precision, so later meshes of the same kind reuse the choice without
+re-timing. The cache file is HB_AUTOTUNE_CACHE if set, else
+~/.cache/hipbone_gb300/autotune.json.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+from . import hb
+
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    p = os.environ.get("HB_AUTOTUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "hipbone_gb300", "autotune.json")
+
+
+def device_key(name: str, sms: int) -> str:
+    return f"{name.strip()}|{sms}SM"
+
+
+def entry_key(N: int, prec: int) -> str:
+    return f"N{N}|{'f64' if prec == hb.HB_F64 else 'f32'}"
+
+
+def load(path: str | None = None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def store(cache: dict, path: str | None = None) -> None:
+    path = path or cache_path()
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def lookup(cache: dict, dev: str, N: int, prec: int):
+    e = cache.get(dev, {}).get(entry_key(N, prec))
+    if isinstance(e, dict) and e.get("variant") in hb.VARIANTS:
+        return e["variant"]
+    return None
+
+
+def record(cache: dict, dev: str, N: int, prec: int, variant: int, timings: dict) -> dict:
+    cache.setdefault(dev, {})[entry_key(N, prec)] = {
+        "variant": int(variant), "ms": {str(k): float(v) for k, v in timings.items()}}
+    return cache
+
+
+def current_device_key() -> str:
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return device_key(p.name, p.multi_processor_count)
+
+
+def tune_mesh(mesh, precs=(hb.HB_F64, hb.HB_F32), screen=hb.HB_SCREEN_IDENTITY, lam=0.1, reps=5,
+              path: str | None = None, force: bool = False) -> dict:
+    """Sets the best variant on `mesh` for each precision, from the cache when
+    present (unless force), else by timing and then recording it."""
+    dev = current_device_key()
+    chosen = {}
+    with _lock:
+        cache = load(path)
+        changed = False
+        for prec in precs:
+            if prec == hb.HB_F32 and not mesh.info.geo32:
+                continue
+            v = None if force else lookup(cache, dev, mesh.N, prec)
+            if v is None:
+                v, timings = hb.hb_autotune(mesh.handle, prec, screen, lam, reps)
+                record(cache, dev, mesh.N, prec, v, timings)
+                changed = True
+            else:
+                hb.hb_set_kernel_variant(mesh.handle, prec, v)
+            chosen[prec] = v
+        if changed:
+            store(cache, path)
+    return chosen

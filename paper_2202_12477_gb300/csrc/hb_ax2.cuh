@@ -1,0 +1,371 @@
+// Element-local operator, "pencil" variant (v2):
+//   y_L = S_L Z x,  S_L^e = Dbold^T G^e Dbold   (hipBone Sec. 2, Sec. 3.2).
+//
+// Every 1-D contraction is done by a thread that owns a whole line of n = N+1
+// nodes, so the n x n matrix D is applied with compile-time indices and read
+// from __constant__ memory (one address per warp: a constant-bank operand,
+// no registers or shared-memory reads for D). Per element, n^2 threads:
+//   1. thread (i,j) gathers its t-line u(i,j,.) through l2g, forms u_t in
+//      registers and copies u to shared memory;
+//   2. thread (j,k) forms u_r along its r-line, thread (i,k) u_s along its
+//      s-line (shared memory in, shared memory out);
+//   3. thread (i,j) applies the six metric factors at its t-line (factors
+//      streamed from HBM once), keeps v_t in registers, writes v_r, v_s;
+//   4. D^T along r-lines, then along s-lines (accumulated), then along the
+//      t-line in registers, and y_L is written.
+// EO = true uses the even-odd split of D: D is centro-antisymmetric
+// (D_{N-i,N-m} = -D_{i,m}), so with a_m = u_m + u_{N-m}, b_m = u_m - u_{N-m}
+// (m < n/2), P_i = sum_m E_im a_m and Q_i = sum_m O_im b_m
+// (E = (D_im + D_{i,N-m})/2, O = (D_im - D_{i,N-m})/2), the outputs are
+// y_i = P_i + Q_i and y_{N-i} = Q_i - P_i: n^2/2 + 2n operations per line
+// instead of n^2.
+#pragma once
+
+#include "hb_internal.h"
+#include "hb_acc.cuh"
+
+#ifndef HB_AX2_T
+#error "define HB_AX2_T (double or float) before including hb_ax2.cuh"
+#endif
+
+namespace hb2 {
+// Internal linkage: this header is compiled once per precision (T differs by
+// translation unit), so nothing in it may share a symbol name across units.
+namespace {
+
+using T = HB_AX2_T;
+
+// ------------------------------------------------------------ constant tables
+// Per degree N (n = N+1, h = ceil(n/2)): D and D^T at offset off(N) =
+// sum_{M<N} (M+1)^2, and the even-odd halves E, O of D and of D^T ([i][m],
+// i, m < h) at offset offh(N) = sum_{M<N} h(M)^2. One copy per precision,
+// in this translation unit's constant bank.
+__host__ __device__ constexpr int off(int N)
+{
+    int o = 0;
+    for (int M = 1; M < N; M++) o += (M + 1) * (M + 1);
+    return o;
+}
+__host__ __device__ constexpr int hh(int N) { return (N + 2) / 2; }
+__host__ __device__ constexpr int offh(int N)
+{
+    int o = 0;
+    for (int M = 1; M < N; M++) o += hh(M) * hh(M);
+    return o;
+}
+constexpr int kTable = off(HB_MAX_N + 1);
+constexpr int kHalf = offh(HB_MAX_N + 1);
+
+static __constant__ T c_D[kTable], c_Dt[kTable], c_E[kHalf], c_O[kHalf], c_Et[kHalf], c_Ot[kHalf];
+
+// Uploads the tables of all degrees to the current device from the FP64
+// derivative matrices D_all (laid out at off(N)).
+static inline hb_status upload_tables(const double *D_all)
+{
+    static T hD[kTable], hDt[kTable], hE[kHalf], hO[kHalf], hEt[kHalf], hOt[kHalf];
+    for (int N = 1; N <= HB_MAX_N; N++) {
+        const int n = N + 1, h = hh(N), o = off(N), oh = offh(N);
+        const double *D = D_all + o;
+        for (int i = 0; i < n; i++)
+            for (int m = 0; m < n; m++) {
+                hD[o + i * n + m] = (T)D[i * n + m];
+                hDt[o + i * n + m] = (T)D[m * n + i];
+            }
+        for (int i = 0; i < h; i++)
+            for (int m = 0; m < h; m++) {
+                const int mm = N - m;
+                double e, od, et, ot;
+                if (m == mm) {  // middle column (odd n)
+                    e = D[i * n + m];
+                    od = 0.0;
+                    et = D[m * n + i];
+                    ot = 0.0;
+                } else {
+                    e = 0.5 * (D[i * n + m] + D[i * n + mm]);
+                    od = 0.5 * (D[i * n + m] - D[i * n + mm]);
+                    et = 0.5 * (D[m * n + i] + D[mm * n + i]);
+                    ot = 0.5 * (D[m * n + i] - D[mm * n + i]);
+                }
+                hE[oh + i * h + m] = (T)e;
+                hO[oh + i * h + m] = (T)od;
+                hEt[oh + i * h + m] = (T)et;
+                hOt[oh + i * h + m] = (T)ot;
+            }
+    }
+    HB_TRY_CUDA(cudaMemcpyToSymbol(c_D, hD, sizeof hD));
+    HB_TRY_CUDA(cudaMemcpyToSymbol(c_Dt, hDt, sizeof hDt));
+    HB_TRY_CUDA(cudaMemcpyToSymbol(c_E, hE, sizeof hE));
+    HB_TRY_CUDA(cudaMemcpyToSymbol(c_O, hO, sizeof hO));
+    HB_TRY_CUDA(cudaMemcpyToSymbol(c_Et, hEt, sizeof hEt));
+    HB_TRY_CUDA(cudaMemcpyToSymbol(c_Ot, hOt, sizeof hOt));
+    return HB_OK;
+}
+
+// ------------------------------------------------------------ line contractions
+
+// Applies M = D (TR = false) or D^T (TR = true) to one line held in `in`
+// (clobbered) and hands each output to store(i, value) as soon as it is
+// formed, so only the n inputs stay live in registers. With EO the line is
+// folded in place into a_m = in_m + in_{N-m} (kept in in[m]) and
+// b_m = in_m - in_{N-m} (kept in in[N-m]).
+template <int N, bool TR, bool EO, class F>
+__device__ __forceinline__ void line_st(T (&in)[N + 1], F &&store)
+{
+    constexpr int n = N + 1, o = off(N);
+    const T *M = TR ? c_Dt : c_D;
+    if constexpr (!EO) {
+#pragma unroll
+        for (int i = 0; i < n; i++) {
+            T acc = M[o + i * n] * in[0];
+#pragma unroll
+            for (int m = 1; m < n; m++) acc = fma(M[o + i * n + m], in[m], acc);
+            store(i, acc);
+        }
+    } else {
+        constexpr int h = hh(N), oh = offh(N), half = n / 2;
+        constexpr bool odd = (n & 1) != 0;
+        const T *Ec = TR ? c_Et : c_E;
+        const T *Oc = TR ? c_Ot : c_O;
+#pragma unroll
+        for (int m = 0; m < half; m++) {
+            const T u = in[m], v = in[N - m];
+            in[m] = u + v;
+            in[N - m] = u - v;
+        }
+#pragma unroll
+        for (int i = 0; i < half; i++) {
+            T P = Ec[oh + i * h] * in[0];
+            T Q = Oc[oh + i * h] * in[N];
+#pragma unroll
+            for (int m = 1; m < half; m++) {
+                P = fma(Ec[oh + i * h + m], in[m], P);
+                Q = fma(Oc[oh + i * h + m], in[N - m], Q);
+            }
+            if constexpr (odd) P = fma(Ec[oh + i * h + half], in[half], P);  // middle node
+            store(i, P + Q);
+            store(N - i, Q - P);
+        }
+        if constexpr (odd) {
+            // middle row c = n/2: y_c = sum_{m<c} M[c][m] b_m
+            T Q = M[o + half * n] * in[N];
+#pragma unroll
+            for (int m = 1; m < half; m++) Q = fma(M[o + half * n + m], in[N - m], Q);
+            store(half, Q);
+        }
+    }
+}
+
+template <int N>
+struct shape {
+    static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+};
+
+// ------------------------------------------------------------ the kernel
+
+// Arguments of the pencil kernel. Element-interior nodes (1 <= i,j,k <= N-1)
+// carry a DOF no other element touches: their y = (S_L u)_node + lambda (x or
+// Jw x) goes straight to y[g], and x_g y_g into this block's partial of x.y
+// (partials[blockIdx.x], if partials is not null). Surface nodes go to ysurf
+// in the per-element surface order of surf_index() for the Z^T gather.
+struct pencil_args {
+    const T *x;
+    const int32_t *l2g;
+    const T *geo;
+    T *ysurf;
+    T *y;
+    int64_t E;
+    const int *run;
+    T lambda;
+    int screen;
+    double *partials;
+};
+
+// Position of surface node (i,j,k) in its element's surface block:
+// the k = 0 face, the k = N face, then for k = 1..N-1 the ring of 4N nodes of
+// that slab (j = 0 row, j = N row, then i = 0 / i = N for j = 1..N-1).
+template <int N>
+__host__ __device__ constexpr int surf_count() { return 2 * (N + 1) * (N + 1) + 4 * N * (N - 1); }
+template <int N>
+__device__ __forceinline__ int ring_index(int i, int j)
+{
+    return j == 0 ? i : (j == N ? N + 1 + i : 2 * (N + 1) + 2 * (j - 1) + (i == N ? 1 : 0));
+}
+
+// Shared-memory layout of one element buffer: node (i,j,k) at
+// k*n*(n+1) + j*(n+1) + i (rows padded by one to spread banks).
+template <int N>
+struct pad {
+    static constexpr int n = N + 1, rs = n + 1, ss = n * (n + 1), size = n * n * (n + 1);
+    static __device__ __forceinline__ int at(int i, int j, int k) { return k * ss + j * rs + i; }
+};
+
+// Blocks per SM that shared memory allows (228 KB per SM, 1 KB reserved per
+// block); the register budget is set to match so occupancy is not lost to it.
+template <int N, int EB>
+__host__ __device__ constexpr int pencil_min_blocks()
+{
+    constexpr int smem = (int)sizeof(T) * 4 * EB * pad<N>::size + 1024;
+    constexpr int by_smem = (228 * 1024) / smem;
+    constexpr int by_threads = 2048 / (EB * (N + 1) * (N + 1));
+    constexpr int b = by_smem < by_threads ? by_smem : by_threads;
+    // FP64 is bound by the FP64 pipe: no register cap (a cap only adds spills).
+    // FP32 is bound by memory: ask for the resident blocks shared memory
+    // allows, up to 4 (2 for the large degrees, whose lines need registers).
+    if constexpr (sizeof(T) == 8) return 1;
+    constexpr int cap = (N + 1) * (N + 1) > 128 ? 2 : 4;
+    return b < 1 ? 1 : (b > cap ? cap : b);
+}
+
+template <int N, bool EO, int EB>
+__global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, EB>()))
+    ax_pencil_kernel(const pencil_args A)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    using P = pad<N>;
+    if (A.run && *A.run == 0) return;
+    const T *__restrict__ x = A.x;
+    const int32_t *__restrict__ l2g = A.l2g;
+    const T *__restrict__ geo = A.geo;
+    const int64_t E = A.E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int el = tid / n2;
+    const int a = tid - el * n2;       // 0 .. n^2-1
+    const int p0 = a % n, p1 = a / n;  // line owned in each direction
+    const int64_t e = (int64_t)blockIdx.x * EB + el;
+    const bool active = e < E;
+    T *U = sm + el * 4 * P::size;  // gathered u (kept: the x values of the epilogue)
+    T *B1 = U + P::size;           // r: u_r, v_r, D^T_r v_r
+    T *B2 = B1 + P::size;          // s
+    T *B3 = B2 + P::size;          // t
+
+    int gl[n];  // node ids of this thread's t-line (i,j) = (p0,p1)
+    if (active) {
+        const int32_t *lg = l2g + e * n3 + a;
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            const int g = __ldcs(lg + k * n2);
+            gl[k] = g;
+            U[P::at(p0, p1, k)] = g >= 0 ? __ldg(x + g) : T(0);
+        }
+    }
+    __syncthreads();
+    if (active) {
+        T in[n];
+        // r-line (j,k) = (p0,p1)
+#pragma unroll
+        for (int m = 0; m < n; m++) in[m] = U[P::at(m, p0, p1)];
+        line_st<N, false, EO>(in, [&](int m, T v) { B1[P::at(m, p0, p1)] = v; });
+        // s-line (i,k) = (p0,p1)
+#pragma unroll
+        for (int m = 0; m < n; m++) in[m] = U[P::at(p0, m, p1)];
+        line_st<N, false, EO>(in, [&](int m, T v) { B2[P::at(p0, m, p1)] = v; });
+        // t-line (i,j) = (p0,p1)
+#pragma unroll
+        for (int m = 0; m < n; m++) in[m] = U[P::at(p0, p1, m)];
+        line_st<N, false, EO>(in, [&](int m, T v) { B3[P::at(p0, p1, m)] = v; });
+    }
+    __syncthreads();
+    if (active) {
+        // metric factors at the t-line's nodes (coalesced rows of n^2 per factor)
+        const T *ge = geo + e * 7 * n3 + a;
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            const T *g = ge + k * 7 * n2;
+            const T grr = __ldcs(g), grs = __ldcs(g + n2), grt = __ldcs(g + 2 * n2);
+            const T gss = __ldcs(g + 3 * n2), gst = __ldcs(g + 4 * n2), gtt = __ldcs(g + 5 * n2);
+            const int q = P::at(p0, p1, k);
+            const T ur = B1[q], us = B2[q], ut = B3[q];
+            B1[q] = grr * ur + grs * us + grt * ut;
+            B2[q] = grs * ur + gss * us + gst * ut;
+            B3[q] = grt * ur + gst * us + gtt * ut;
+        }
+    }
+    __syncthreads();
+    if (active) {
+        // D^T along each direction, in place (the whole line is in registers
+        // before any output of it is stored)
+        T in[n];
+#pragma unroll
+        for (int m = 0; m < n; m++) in[m] = B1[P::at(m, p0, p1)];
+        line_st<N, true, EO>(in, [&](int m, T v) { B1[P::at(m, p0, p1)] = v; });
+#pragma unroll
+        for (int m = 0; m < n; m++) in[m] = B2[P::at(p0, m, p1)];
+        line_st<N, true, EO>(in, [&](int m, T v) { B2[P::at(p0, m, p1)] = v; });
+#pragma unroll
+        for (int m = 0; m < n; m++) in[m] = B3[P::at(p0, p1, m)];
+        line_st<N, true, EO>(in, [&](int m, T v) { B3[P::at(p0, p1, m)] = v; });
+    }
+    __syncthreads();
+    hbacc::dot_acc<T> acc;
+    if (active) {
+        constexpr int NS = surf_count<N>();
+        T *ys = A.ysurf + e * NS;
+        const bool ring = p0 == 0 || p0 == N || p1 == 0 || p1 == N;
+        const int r = ring ? ring_index<N>(p0, p1) : 0;
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            const int q = P::at(p0, p1, k);
+            T y = B1[q] + B2[q] + B3[q];
+            if (k == 0) {
+                ys[a] = y;
+            } else if (k == N) {
+                ys[n2 + a] = y;
+            } else if (ring) {
+                ys[2 * n2 + (k - 1) * 4 * N + r] = y;
+            } else {
+                // element-interior node: its DOF has no other copy (never masked)
+                const T xv = U[q];
+                const T jw = A.screen ? __ldg(geo + (e * n + k) * 7 * n2 + 6 * n2 + a) : T(1);
+                y += A.lambda * (jw * xv);
+                A.y[gl[k]] = y;
+                acc.add(xv, y);
+            }
+        }
+    }
+    if (A.partials) {
+        const double v = hbacc::block_sum(acc.value());
+        if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
+    }
+}
+
+}  // namespace
+}  // namespace hb2
+
+namespace hb2 {
+// Internal linkage: this header is compiled once per precision (T differs by
+// translation unit), so nothing in it may share a symbol name across units.
+namespace {
+
+template <int N, bool EO>
+hb_status launch(const pencil_args &A, int eb_mult, cudaStream_t s, int64_t *nblocks_out)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    constexpr int EB1 = n2 >= 256 ? 1 : 256 / n2;
+    if (A.E <= 0) return HB_OK;
+    static int attr_set[2][32] = {{0}};
+    int dev = 0;
+    HB_TRY_CUDA(cudaGetDevice(&dev));
+    const int which = eb_mult == 2 && n2 <= 128 ? 1 : 0;
+    auto go = [&](auto kern, int EB) -> hb_status {
+        const size_t smem = sizeof(T) * 4 * (size_t)EB * pad<N>::size;
+        if (dev >= 0 && dev < 32 && !attr_set[which][dev]) {
+            HB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set[which][dev] = 1;
+        }
+        const int64_t blocks = (A.E + EB - 1) / EB;
+        if (nblocks_out) *nblocks_out = blocks;
+        hb_prof_scope prof("ax_local", s);
+        kern<<<(unsigned)blocks, EB * n2, smem, s>>>(A);
+        HB_CHECK_LAUNCH();
+        return HB_OK;
+    };
+    if constexpr (n2 <= 128) {
+        if (which == 1) return go(ax_pencil_kernel<N, EO, EB1 * 2>, EB1 * 2);
+    }
+    return go(ax_pencil_kernel<N, EO, EB1>, EB1);
+}
+
+}  // namespace
+}  // namespace hb2

@@ -16,40 +16,11 @@
 #include <mutex>
 
 #include "hb_internal.h"
+#include "hb_acc.cuh"
 
 namespace hb {
 
-// ---------------------------------------------------------------- accumulators
-
-// FP64 accumulation of products. For FP32 operands the FP64 pipe of GB300 is
-// slow, so the running sum is carried as an unevaluated pair of floats with
-// error-free transformations (Dekker's two-product via fma, Knuth's two-sum):
-// about 48 significant bits, the accuracy of an FP64 sum of these products.
-template <typename T>
-struct dot_acc;
-
-template <>
-struct dot_acc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double value() const { return s; }
-};
-
-template <>
-struct dot_acc<float> {
-    float hi = 0.0f, lo = 0.0f;
-    __device__ __forceinline__ void add(float a, float b)
-    {
-        float p = a * b;
-        float pe = fmaf(a, b, -p);
-        float t = hi + p;
-        float bp = t - hi;
-        float err = (hi - (t - bp)) + (p - bp);
-        hi = t;
-        lo += err + pe;
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
+using hbacc::dot_acc;
 
 // ---------------------------------------------------------------- grid reduction
 
@@ -179,6 +150,109 @@ hb_status launch_assemble(const hb_mesh *m, const T *yL, const T *x, T *y, const
     return HB_OK;
 }
 
+// ---------------------------------------------------------------- surface assembly
+
+// Z^T on the DOFs that have a copy on an element surface: y_g = sum over the
+// copies of ysurf (ascending: element order) + lambda (x_g | M_gg x_g).
+// With a dot mode, x.y over these rows plus the element kernel's per-block
+// partials (interior DOFs) is reduced on the fixed grid.
+template <typename T, int SCREEN, int DOT>
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    assemble_surf_kernel(const T *__restrict__ ys, const int32_t *__restrict__ srow_g,
+                         const int32_t *__restrict__ rowptr, const int32_t *__restrict__ cols,
+                         const T *__restrict__ x, const T *__restrict__ mdiag, double lambda, T *__restrict__ y,
+                         int64_t nrows, const double *__restrict__ ax_partials, int64_t n_axp, double *partials,
+                         unsigned *counter, hb_cg_state *st)
+{
+    if (DOT == HB_DOT_CG_PAP && st->run == 0) return;
+    const T lam = (T)lambda;
+    dot_acc<T> acc;
+    // four independent rows per pass keep several dependent load chains
+    // (row pointer -> column -> value) in flight per thread
+    constexpr int U4 = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r0 < nrows; r0 += U4 * stride) {
+        int g[U4], a[U4], z[U4], c0[U4], c1[U4];
+        T xv[U4], s[U4];
+#pragma unroll
+        for (int u = 0; u < U4; u++) {
+            const int64_t r = r0 + u * stride;
+            const bool ok = r < nrows;
+            g[u] = ok ? __ldg(srow_g + r) : -1;
+            a[u] = ok ? __ldg(rowptr + r) : 0;
+            z[u] = ok ? __ldg(rowptr + r + 1) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U4; u++) {
+            c0[u] = a[u] < z[u] ? __ldcs(cols + a[u]) : -1;
+            c1[u] = a[u] + 1 < z[u] ? __ldcs(cols + a[u] + 1) : -1;
+            xv[u] = g[u] >= 0 ? x[g[u]] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U4; u++) {
+            T v0 = c0[u] >= 0 ? __ldcs(ys + c0[u]) : T(0);
+            T v1 = c1[u] >= 0 ? __ldcs(ys + c1[u]) : T(0);
+            s[u] = v0 + v1;
+        }
+#pragma unroll
+        for (int u = 0; u < U4; u++) {
+            if (g[u] < 0) continue;
+            T t = s[u];
+            for (int p = a[u] + 2; p < z[u]; p++) t += __ldcs(ys + __ldcs(cols + p));
+            t += SCREEN ? lam * (mdiag[g[u]] * xv[u]) : lam * xv[u];
+            y[g[u]] = t;
+            if (DOT) acc.add(xv[u], t);
+        }
+    }
+    if (DOT) {
+        double v = acc.value();
+        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_axp;
+             q += (int64_t)gridDim.x * blockDim.x)
+            v += ax_partials[q];
+        double vv[1] = {v}, tot[1];
+        if (grid_sum<1>(vv, partials, counter, tot) && threadIdx.x == 0) {
+            if (DOT == HB_DOT_CG_PAP) {
+                const double pAp = tot[0];
+                st->pAp = pAp;
+                if (!(pAp > 0.0) || !isfinite(pAp)) {
+                    st->status = HB_ERR_BREAKDOWN;
+                    st->run = 0;
+                } else {
+                    st->alpha = st->rr / pAp;
+                }
+            } else {
+                st->dot_tmp = tot[0];
+            }
+        }
+    }
+}
+
+template <typename T>
+hb_status launch_assemble_surf(const hb_mesh *m, const T *ys, const T *x, T *y, const T *mdiag, int screen,
+                               double lambda, int64_t n_axp, hb_cg_state *st, int dot_mode, cudaStream_t s)
+{
+    const int64_t nr = m->nsr;
+    const int grid = red_grid(nr > 0 ? nr : 1);
+    unsigned *ctr = m->counters + 0;
+    hb_prof_scope prof("assemble", s);
+#define HB_ASM(SC, DM)                                                                                      \
+    assemble_surf_kernel<T, SC, DM><<<grid, HB_RED_THREADS, 0, s>>>(ys, m->srow_g, m->srowptr, m->scols, x,  \
+                                                                    mdiag, lambda, y, nr, m->ax_partials,    \
+                                                                    n_axp, m->partials, ctr, st)
+    if (screen == 0) {
+        if (dot_mode == HB_DOT_NONE) HB_ASM(0, HB_DOT_NONE);
+        else if (dot_mode == HB_DOT_TO_TMP) HB_ASM(0, HB_DOT_TO_TMP);
+        else HB_ASM(0, HB_DOT_CG_PAP);
+    } else {
+        if (dot_mode == HB_DOT_NONE) HB_ASM(1, HB_DOT_NONE);
+        else if (dot_mode == HB_DOT_TO_TMP) HB_ASM(1, HB_DOT_TO_TMP);
+        else HB_ASM(1, HB_DOT_CG_PAP);
+    }
+#undef HB_ASM
+    HB_CHECK_LAUNCH();
+    return HB_OK;
+}
+
 // ---------------------------------------------------------------- dot
 
 template <typename T>
@@ -187,8 +261,19 @@ __global__ void __launch_bounds__(HB_RED_THREADS)
                unsigned *counter)
 {
     dot_acc<T> acc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc.add(a[i], b[i]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = i0 + u * stride;
+            av[u] = i < n ? a[i] : T(0);
+            bv[u] = i < n ? b[i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (i0 + u * stride < n) acc.add(av[u], bv[u]);
+    }
     double v[1] = {acc.value()}, tot[1];
     if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
 }
@@ -233,10 +318,24 @@ __global__ void __launch_bounds__(HB_RED_THREADS)
     if (st->run == 0) return;
     const T alpha = (T)st->alpha;
     dot_acc<T> acc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const T ri = r[i] - alpha * Ap[i];
-        r[i] = ri;
-        acc.add(ri, ri);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        T rv[4], av[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = i0 + u * stride;
+            rv[u] = i < n ? r[i] : T(0);
+            av[u] = i < n ? __ldcs(Ap + i) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                const T ri = rv[u] - alpha * av[u];
+                r[i] = ri;
+                acc.add(ri, ri);
+            }
+        }
     }
     double v[1] = {acc.value()}, tot[1];
     if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
@@ -259,10 +358,24 @@ __global__ void __launch_bounds__(HB_RED_THREADS)
     __shared__ int s_last;
     if (st->run == 0) return;
     const T alpha = (T)st->alpha, beta = (T)st->beta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const T pi = p[i];
-        x[i] = x[i] + alpha * pi;
-        p[i] = r[i] + beta * pi;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        T pv[4], xv[4], rv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = i0 + u * stride;
+            pv[u] = i < n ? p[i] : T(0);
+            xv[u] = i < n ? x[i] : T(0);
+            rv[u] = i < n ? r[i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                x[i] = xv[u] + alpha * pv[u];
+                p[i] = rv[u] + beta * pv[u];
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -356,25 +469,47 @@ hb_status hb_launch_assemble_f32(const hb_mesh *m, const float *yL, const float 
     return launch_assemble<float>(m, yL, x, y, m->mdiag32, screen, lambda, st, dot_mode, s);
 }
 
+// A x: the element kernel, then Z^T. Pencil variants finish element-interior
+// DOFs in the element kernel and gather only surface DOFs; variant 0 writes
+// every local node and gathers all DOFs.
 hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, double lambda, const void *x, void *y,
                           hb_cg_state *st, int dot_mode, cudaStream_t s)
 {
     const int *run = (dot_mode == HB_DOT_CG_PAP && st) ? &st->run : nullptr;
-    hb_status r;
-    if (prec == HB_F64) {
-        r = hb_launch_ax_local_f64(m, (const double *)x, (double *)m->yL, run, s);
-        if (r != HB_OK) return r;
-        return hb_launch_assemble_f64(m, (const double *)m->yL, (const double *)x, (double *)y, screen, lambda, st,
-                                      dot_mode, s);
+    if (prec != HB_F64 && prec != HB_F32) {
+        hb_set_error("precision %d not valid for the operator", (int)prec);
+        return HB_ERR_ARG;
     }
-    if (prec == HB_F32) {
+    const int v = m->variant[prec == HB_F64 ? 0 : 1];
+    const int eo = (v & HB_VAR_EO) ? 1 : 0, ebm = (v & HB_VAR_EB2) ? 2 : 1;
+    hb_status r;
+    if (!(v & HB_VAR_PENCIL)) {
+        if (prec == HB_F64) {
+            r = hb_launch_ax_local_f64(m, (const double *)x, (double *)m->yL, run, s);
+            if (r != HB_OK) return r;
+            return hb_launch_assemble_f64(m, (const double *)m->yL, (const double *)x, (double *)y, screen, lambda,
+                                          st, dot_mode, s);
+        }
         r = hb_launch_ax_local_f32(m, (const float *)x, (float *)m->yL, run, s);
         if (r != HB_OK) return r;
         return hb_launch_assemble_f32(m, (const float *)m->yL, (const float *)x, (float *)y, screen, lambda, st,
                                       dot_mode, s);
     }
-    hb_set_error("precision %d not valid for the operator", (int)prec);
-    return HB_ERR_ARG;
+    double *partials = dot_mode != HB_DOT_NONE ? m->ax_partials : nullptr;
+    int64_t nblk = 0;
+    if (prec == HB_F64) {
+        r = hb_launch_ax2_f64(m, (const double *)x, (double *)m->yL, (double *)y, lambda, screen, partials, run, eo,
+                              ebm, s, &nblk);
+        if (r != HB_OK) return r;
+        return launch_assemble_surf<double>(m, (const double *)m->yL, (const double *)x, (double *)y, m->mdiag,
+                                            screen, lambda, partials ? nblk : 0, st, dot_mode, s);
+    }
+    if (!m->mdiag32) { hb_set_error("mesh has no FP32 data (keep_fp32_copy = 0)"); return HB_ERR_ARG; }
+    r = hb_launch_ax2_f32(m, (const float *)x, (float *)m->yL, (float *)y, lambda, screen, partials, run, eo, ebm, s,
+                          &nblk);
+    if (r != HB_OK) return r;
+    return launch_assemble_surf<float>(m, (const float *)m->yL, (const float *)x, (float *)y, m->mdiag32, screen,
+                                       lambda, partials ? nblk : 0, st, dot_mode, s);
 }
 
 hb_status hb_launch_dot_f64(const hb_mesh *m, const double *a, const double *b, int64_t n, double *out,
@@ -398,6 +533,27 @@ hb_status hb_launch_dot_f32(const hb_mesh *m, const float *a, const float *b, in
 // ---------------------------------------------------------------- C ABI
 
 static bool valid_screen(int s) { return s == HB_SCREEN_IDENTITY || s == HB_SCREEN_MASS; }
+
+extern "C" hb_status hb_set_kernel_variant(hb_mesh *m, hb_precision prec, int variant)
+{
+    hb_clear_error();
+    if (!m) { hb_set_error("null mesh"); return HB_ERR_ARG; }
+    if (prec != HB_F64 && prec != HB_F32) { hb_set_error("variant precision must be HB_F64 or HB_F32"); return HB_ERR_ARG; }
+    if (variant < 0 || variant > HB_VAR_MAX || (!(variant & HB_VAR_PENCIL) && variant != 0)) {
+        hb_set_error("invalid kernel variant %d", variant);
+        return HB_ERR_ARG;
+    }
+    m->variant[prec == HB_F64 ? 0 : 1] = variant;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_get_kernel_variant(const hb_mesh *m, hb_precision prec, int *variant)
+{
+    if (!m || !variant) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (prec != HB_F64 && prec != HB_F32) { hb_set_error("variant precision must be HB_F64 or HB_F32"); return HB_ERR_ARG; }
+    *variant = m->variant[prec == HB_F64 ? 0 : 1];
+    return HB_OK;
+}
 
 extern "C" hb_status hb_apply_A(const hb_mesh *m, hb_precision prec, hb_screen screen, double lambda,
                                 const void *x, void *y, void *stream)
@@ -438,10 +594,80 @@ extern "C" hb_status hb_dot(const hb_mesh *m, hb_precision prec, const void *a, 
     return HB_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+
+extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen, double lambda, int reps,
+                                 int *best_variant, double *ms_per_variant, void *stream)
+{
+    hb_clear_error();
+    if (!m) { hb_set_error("null mesh"); return HB_ERR_ARG; }
+    if (prec != HB_F64 && prec != HB_F32) { hb_set_error("hb_autotune takes HB_F64 or HB_F32"); return HB_ERR_ARG; }
+    if (prec == HB_F32 && !m->geo32) { hb_set_error("HB_F32 needs keep_fp32_copy"); return HB_ERR_ARG; }
+    if (!valid_screen(screen)) { hb_set_error("bad screen mode"); return HB_ERR_ARG; }
+    if (reps < 1) reps = 1;
+    hb_device_guard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int pi = prec == HB_F64 ? 0 : 1;
+    const int64_t n = m->n_global;
+    const size_t esz = prec == HB_F64 ? 8 : 4;
+    if (n == 0) {
+        if (best_variant) *best_variant = m->variant[pi];
+        return HB_OK;
+    }
+    void *x = nullptr, *y = nullptr;
+    HB_TRY_CUDA(cudaMalloc(&x, esz * n));
+    cudaError_t e = cudaMalloc(&y, esz * n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, esz * n, s);
+    if (e != cudaSuccess) {
+        cudaFree(x);
+        cudaFree(y);
+        hb_set_error("autotune scratch: %s", cudaGetErrorString(e));
+        return HB_ERR_NOMEM;
+    }
+    const int candidates[] = {0, HB_VAR_PENCIL, HB_VAR_PENCIL | HB_VAR_EO, HB_VAR_PENCIL | HB_VAR_EB2,
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_EB2};
+    const int saved = m->variant[pi];
+    int best = saved;
+    float best_ms = 1e30f;
+    hb_status st = HB_OK;
+    for (int c : candidates) {
+        m->variant[pi] = c;
+        // one untimed application (first launch, attribute setup), then `reps` timed ones
+        st = hb_apply_A_impl(m, prec, screen, lambda, x, y, nullptr, HB_DOT_NONE, s);
+        if (st != HB_OK) break;
+        if ((e = cudaEventRecord(m->ev0, s)) != cudaSuccess) break;
+        for (int r = 0; r < reps && st == HB_OK; r++)
+            st = hb_apply_A_impl(m, prec, screen, lambda, x, y, nullptr, HB_DOT_NONE, s);
+        if (st != HB_OK) break;
+        if ((e = cudaEventRecord(m->ev1, s)) != cudaSuccess) break;
+        if ((e = cudaEventSynchronize(m->ev1)) != cudaSuccess) break;
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, m->ev0, m->ev1)) != cudaSuccess) break;
+        ms /= reps;
+        if (ms_per_variant) ms_per_variant[c] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaFree(x);
+    cudaFree(y);
+    if (st == HB_OK && e != cudaSuccess) {
+        hb_set_error("autotune: %s", cudaGetErrorString(e));
+        st = HB_ERR_CUDA;
+    }
+    m->variant[pi] = st == HB_OK ? best : saved;
+    if (best_variant) *best_variant = m->variant[pi];
+    return st;
+}
+
+// Workspace vectors for the solvers, grown on demand (FP64 r, p, Ap; FP32 r, p,
+// Ap, d), each starting on a 256-byte boundary.
+static inline int64_t cg_stride(int64_t n) { return (n + 63) / 64 * 64; }
 // Workspace vectors for the solvers, grown on demand (FP64 r, p, Ap; FP32 r, p, Ap, d).
 static hb_status cg_workspace(hb_mesh *m)
 {
-    const size_t need = (size_t)m->n_global * (3 * sizeof(double) + 4 * sizeof(float)) + 256;
+    const size_t need = (size_t)cg_stride(m->n_global) * (3 * sizeof(double) + 4 * sizeof(float)) + 256;
     if (m->cg_vec_bytes >= need) return HB_OK;
     if (m->cg_vec) cudaFree(m->cg_vec);
     m->cg_vec = nullptr;
@@ -518,8 +744,9 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
     }
     hb_status rs = cg_workspace(m);
     if (rs != HB_OK) return rs;
-    double *r = (double *)m->cg_vec, *p = r + n, *Ap = p + n;
-    float *r32 = (float *)(Ap + n), *p32 = r32 + n, *Ap32 = p32 + n, *d32 = Ap32 + n;
+    const int64_t ns = cg_stride(n);
+    double *r = (double *)m->cg_vec, *p = r + ns, *Ap = p + ns;
+    float *r32 = (float *)(Ap + ns), *p32 = r32 + ns, *Ap32 = p32 + ns, *d32 = Ap32 + ns;
     const int grid = red_grid(n);
     hb_cg_state *st = m->state, *st_in = m->state + 1;
     HB_TRY_CUDA(cudaEventRecord(m->ev0, s));
@@ -648,7 +875,7 @@ extern "C" hb_status hb_dot_noalloc(hb_precision prec, const void *a, const void
     if (n == 0) {
         HB_TRY_CUDA(cudaMemsetAsync(result, 0, sizeof(double), s));
     } else {
-        // one block per 1024 elements: the same grid as hb_dot up to 608 blocks
+        // one block per 1024 elements: the same grid as hb_dot up to 1216 blocks
         const int blocks = (int)((n + HB_RED_THREADS * 4 - 1) / (HB_RED_THREADS * 4));
         hb_count_launch();
         if (prec == HB_F64)

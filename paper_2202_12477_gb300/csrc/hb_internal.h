@@ -10,7 +10,7 @@
 #include "hipbone_gb300.h"
 
 #define HB_MAX_N 15
-#define HB_RED_BLOCKS 608   // fixed grid of every reduction kernel (4 x 152 SMs)
+#define HB_RED_BLOCKS 1216  // fixed grid of every reduction kernel (8 x 152 SMs)
 #define HB_RED_THREADS 256
 
 // ---------------------------------------------------------------- errors
@@ -86,6 +86,15 @@ struct hb_mesh {
     double min_detJ;
     size_t device_bytes;
     cudaEvent_t ev0, ev1;
+    int variant[2];     // element-kernel variant per precision (HB_F64, HB_F32)
+    // Z^T restricted to DOFs with a copy on an element surface (the pencil
+    // kernels finish element-interior DOFs themselves)
+    int64_t nsr, nnz_s;
+    int32_t *srow_g;    // [nsr] global id of each surface row (ascending)
+    int32_t *srowptr;   // [nsr + 1]
+    int32_t *scols;     // [nnz_s] e * surf_count + surface index, ascending
+    double *ax_partials;  // [max element-kernel blocks] per-block partials of x.y
+    int64_t n_ax_partials;
 };
 
 // Reference element data computed on the host for every degree 1..15 (GLL
@@ -103,6 +112,20 @@ const float *hb_dev_D32(int N);
 // y_L = S_L Z x for every element (FP64 / FP32).
 hb_status hb_launch_ax_local_f64(const hb_mesh *m, const double *x, double *yL, const int *run, cudaStream_t s);
 hb_status hb_launch_ax_local_f32(const hb_mesh *m, const float *x, float *yL, const int *run, cudaStream_t s);
+hb_status hb_launch_ax2_f64(const hb_mesh *m, const double *x, double *ysurf, double *y, double lambda, int screen,
+                            double *partials, const int *run, int eo, int eb_mult, cudaStream_t s,
+                            int64_t *nblocks);
+hb_status hb_launch_ax2_f32(const hb_mesh *m, const float *x, float *ysurf, float *y, double lambda, int screen,
+                            double *partials, const int *run, int eo, int eb_mult, cudaStream_t s,
+                            int64_t *nblocks);
+int hb_surf_count(int N);  // surface nodes of one element: 2 n^2 + 4 N (N-1)
+hb_status hb_ax2_upload_f64(const double *D_all);
+hb_status hb_ax2_upload_f32(const double *D_all);
+
+// Element-kernel variants (bit flags): v1 = 0; HB_VAR_PENCIL = pencil kernel;
+// HB_VAR_EO = even-odd split (pencil only); HB_VAR_EB2 = two element groups per block.
+enum { HB_VAR_PENCIL = 1, HB_VAR_EO = 2, HB_VAR_EB2 = 4, HB_VAR_MAX = 7 };
+
 
 // y = Z^T y_L + lambda (x or M x); optional fused x.y into st->pAp (and the
 // CG breakdown test / alpha when `cg` is set).

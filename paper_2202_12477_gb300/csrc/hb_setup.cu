@@ -166,6 +166,8 @@ hb_status hb_ensure_device_tables()
         }
         for (int i = 0; i < n; i++) { xi[N * 16 + i] = x[i]; w[N * 16 + i] = ww[i]; }
     }
+    { hb_status st2 = hb_ax2_upload_f64(D64.data()); if (st2 != HB_OK) return st2; }
+    { hb_status st2 = hb_ax2_upload_f32(D64.data()); if (st2 != HB_OK) return st2; }
     HB_TRY_CUDA(cudaMemcpyToSymbol(g_D64, D64.data(), sizeof(double) * kTableSize));
     HB_TRY_CUDA(cudaMemcpyToSymbol(g_D32, D32.data(), sizeof(float) * kTableSize));
     HB_TRY_CUDA(cudaMemcpyToSymbol(g_xi64, xi.data(), sizeof(double) * 256));
@@ -193,6 +195,14 @@ const float *hb_dev_D32(int N)
 }
 
 // ---------------------------------------------------------------- setup kernels
+
+static int grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)(g < 1 ? 1 : g);
+}
+
 
 struct box_t {
     int Ex, Ey, Ez, N;
@@ -429,14 +439,163 @@ __global__ void k_min_reduce(const double *v, int n, double *out)
     }
 }
 
+// ---------------------------------------------------------------- surface CSR
+
+__device__ __forceinline__ bool on_surface(int i, int j, int k, int N)
+{
+    return i == 0 || i == N || j == 0 || j == N || k == 0 || k == N;
+}
+
+// Same order as the element kernels: k = 0 face, k = N face, then the ring
+// of 4N nodes of each slab k = 1..N-1.
+__device__ __forceinline__ int surf_index(int i, int j, int k, int N)
+{
+    const int n = N + 1, n2 = n * n;
+    if (k == 0) return j * n + i;
+    if (k == N) return n2 + j * n + i;
+    const int r = j == 0 ? i : (j == N ? n + i : 2 * n + 2 * (j - 1) + (i == N ? 1 : 0));
+    return 2 * n2 + (k - 1) * 4 * N + r;
+}
+
+__global__ void k_surf_count(const int32_t *l2g, int64_t n_local, int N, int32_t *cnt)
+{
+    const int n = N + 1;
+    const int64_t n3 = (int64_t)n * n * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_local;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = l2g[q];
+        if (g < 0) continue;
+        const int node = (int)(q % n3);
+        const int i = node % n, j = (node / n) % n, k = node / (n * n);
+        if (on_surface(i, j, k, N)) atomicAdd(&cnt[g], 1);
+    }
+}
+
+__global__ void k_flag(const int32_t *cnt, int64_t ng, int32_t *flag)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x)
+        flag[g] = cnt[g] > 0 ? 1 : 0;
+}
+
+__global__ void k_compact_rows(const int32_t *cnt, const int32_t *srow_of, int64_t ng, int32_t *srow_g,
+                               int32_t *scnt)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x)
+        if (cnt[g] > 0) {
+            srow_g[srow_of[g]] = (int32_t)g;
+            scnt[srow_of[g]] = cnt[g];
+        }
+}
+
+__global__ void k_surf_fill(const int32_t *l2g, int64_t n_local, int N, const int32_t *srow_of,
+                            const int32_t *srowptr, int32_t *cursor, int32_t *scols)
+{
+    const int n = N + 1;
+    const int64_t n3 = (int64_t)n * n * n;
+    const int NS = 2 * n * n + 4 * N * (N - 1);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_local;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = l2g[q];
+        if (g < 0) continue;
+        const int64_t e = q / n3;
+        const int node = (int)(q - e * n3);
+        const int i = node % n, j = (node / n) % n, k = node / (n * n);
+        if (!on_surface(i, j, k, N)) continue;
+        const int r = srow_of[g];
+        const int slot = atomicAdd(&cursor[r], 1);
+        scols[srowptr[r] + slot] = (int32_t)(e * NS + surf_index(i, j, k, N));
+    }
+}
+
+__global__ void k_sort_surf_rows(const int32_t *rowptr, int32_t *cols, int64_t nrows)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
+        const int a = rowptr[r], z = rowptr[r + 1];
+        for (int p = a + 1; p < z; p++) {
+            const int32_t v = cols[p];
+            int q = p - 1;
+            while (q >= a && cols[q] > v) { cols[q + 1] = cols[q]; q--; }
+            cols[q + 1] = v;
+        }
+    }
+}
+
+// Exclusive scan of n int32 values (out may equal in); returns the total.
+static hb_status scan_exclusive(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, int64_t *total)
+{
+    const int64_t nchunks = (n + 1023) / 1024;
+    int64_t *sums = nullptr;
+    HB_TRY_CUDA(cudaMalloc((void **)&sums, sizeof(int64_t) * (nchunks + 1)));
+    hb_count_launch();
+    k_scan_chunks<<<(unsigned)nchunks, 1024, 0, s>>>(in, n, out, sums);
+    hb_count_launch();
+    k_scan_sums<<<1, 32, 0, s>>>(sums, nchunks);
+    hb_count_launch();
+    k_scan_add<<<grid_for(n, 256), 256, 0, s>>>(out, n, sums);
+    cudaError_t e = cudaGetLastError();
+    int64_t tot = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, sums + nchunks, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(sums);
+    if (e != cudaSuccess) {
+        hb_set_error("scan: %s", cudaGetErrorString(e));
+        return HB_ERR_CUDA;
+    }
+    *total = tot;
+    return HB_OK;
+}
+
+// Builds srow_g, srowptr, scols of the mesh (after l2g exists).
+static hb_status build_surface_csr(hb_mesh *m, cudaStream_t s)
+{
+    const int64_t ng = m->n_global, nl = m->n_local;
+    int32_t *cnt = nullptr, *srow_of = nullptr, *scnt = nullptr;
+    hb_status st = HB_OK;
+    int64_t nsr = 0, nnz = 0;
+    auto fail = [&](cudaError_t e) {
+        hb_set_error("surface CSR: %s", cudaGetErrorString(e));
+        st = e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;
+    };
+    cudaError_t e = cudaMalloc((void **)&cnt, sizeof(int32_t) * (ng + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&srow_of, sizeof(int32_t) * (ng + 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (ng + 1), s);
+    if (e != cudaSuccess) { fail(e); goto done; }
+    hb_count_launch();
+    k_surf_count<<<grid_for(nl, 256), 256, 0, s>>>(m->l2g, nl, m->N, cnt);
+    hb_count_launch();
+    k_flag<<<grid_for(ng + 1, 256), 256, 0, s>>>(cnt, ng + 1, srow_of);
+    if ((e = cudaGetLastError()) != cudaSuccess) { fail(e); goto done; }
+    if ((st = scan_exclusive(srow_of, srow_of, ng + 1, s, &nsr)) != HB_OK) goto done;
+    m->nsr = nsr;
+    e = cudaMalloc((void **)&m->srow_g, sizeof(int32_t) * (nsr + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&m->srowptr, sizeof(int32_t) * (nsr + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&scnt, sizeof(int32_t) * (nsr + 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(scnt, 0, sizeof(int32_t) * (nsr + 1), s);
+    if (e != cudaSuccess) { fail(e); goto done; }
+    hb_count_launch();
+    k_compact_rows<<<grid_for(ng, 256), 256, 0, s>>>(cnt, srow_of, ng, m->srow_g, scnt);
+    if ((e = cudaGetLastError()) != cudaSuccess) { fail(e); goto done; }
+    if ((st = scan_exclusive(scnt, m->srowptr, nsr + 1, s, &nnz)) != HB_OK) goto done;
+    m->nnz_s = nnz;
+    e = cudaMalloc((void **)&m->scols, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(scnt, 0, sizeof(int32_t) * (nsr + 1), s);
+    if (e != cudaSuccess) { fail(e); goto done; }
+    hb_count_launch();
+    k_surf_fill<<<grid_for(nl, 256), 256, 0, s>>>(m->l2g, nl, m->N, srow_of, m->srowptr, scnt, m->scols);
+    hb_count_launch();
+    k_sort_surf_rows<<<grid_for(nsr, 256), 256, 0, s>>>(m->srowptr, m->scols, nsr);
+    if ((e = cudaGetLastError()) != cudaSuccess) { fail(e); goto done; }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e); goto done; }
+    m->device_bytes += sizeof(int32_t) * (2 * (nsr + 1) + nnz);
+done:
+    cudaFree(cnt);
+    cudaFree(srow_of);
+    cudaFree(scnt);
+    return st;
+}
+
 // ---------------------------------------------------------------- mesh lifetime
 
-static int grid_for(int64_t n, int threads)
-{
-    int64_t g = (n + threads - 1) / threads;
-    if (g > 152 * 32) g = 152 * 32;
-    return (int)(g < 1 ? 1 : g);
-}
 
 extern "C" hb_status hb_mesh_destroy(hb_mesh *m)
 {
@@ -454,6 +613,10 @@ extern "C" hb_status hb_mesh_destroy(hb_mesh *m)
     cudaFree(m->counters);
     cudaFree(m->state);
     cudaFree(m->cg_vec);
+    cudaFree(m->srow_g);
+    cudaFree(m->srowptr);
+    cudaFree(m->scols);
+    cudaFree(m->ax_partials);
     if (m->state_host) cudaFreeHost(m->state_host);
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);
@@ -499,6 +662,8 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     double *tmp_det = nullptr;
     HB_TRY_MESH(cudaGetDevice(&m->device));
     m->desc = *d;
+    m->variant[0] = HB_VAR_PENCIL | HB_VAR_EO;
+    m->variant[1] = HB_VAR_PENCIL | HB_VAR_EO;
     m->N = N;
     m->n = n;
     m->E = E;
@@ -591,6 +756,20 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     tmp_sum = nullptr;
     tmp_det = nullptr;
     m->device_bytes = bytes;
+    {
+        hb_status sst = build_surface_csr(m, s);
+        if (sst != HB_OK) { hb_mesh_destroy(m); return sst; }
+        // one partial per element-kernel block (at most one block per element)
+        const int EB1 = n * n >= 256 ? 1 : 256 / (n * n);
+        m->n_ax_partials = (E + EB1 - 1) / EB1 + 1;
+        cudaError_t ae = cudaMalloc((void **)&m->ax_partials, sizeof(double) * m->n_ax_partials);
+        if (ae != cudaSuccess) {
+            hb_set_error("ax partials: %s", cudaGetErrorString(ae));
+            hb_mesh_destroy(m);
+            return ae == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;
+        }
+        m->device_bytes += sizeof(double) * m->n_ax_partials;
+    }
     if (!(m->min_detJ > 0.0)) {
         hb_set_error("non-positive Jacobian determinant (min det J = %g)", m->min_detJ);
         hb_mesh_destroy(m);

@@ -76,6 +76,10 @@ _SIGS = [
     ("hb_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
                               C.POINTER(hb_cg_result), C.c_void_p]),
     ("hb_u01", C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64]),
+    ("hb_set_kernel_variant", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    ("hb_get_kernel_variant", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    ("hb_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
+                              C.POINTER(C.c_double), C.c_void_p]),
     ("hb_kernel_launches", C.c_ulonglong, []),
     ("hb_profile_enable", C.c_int, [C.c_int]),
     ("hb_profile_reset", C.c_int, []),
@@ -163,6 +167,29 @@ def hb_cg_solve(h, opts: hb_cg_opts, b_ptr, x_ptr, stream=None, check=True) -> h
 
 def hb_u01(seed, stream, idx) -> float:
     return lib().hb_u01(seed, stream, idx)
+
+
+HB_VARIANT_PENCIL, HB_VARIANT_EVEN_ODD, HB_VARIANT_EB2 = 1, 2, 4
+VARIANTS = [0, 1, 3, 5, 7]  # every valid combination
+
+
+def hb_set_kernel_variant(h, prec, variant) -> None:
+    _check(lib().hb_set_kernel_variant(h, prec, variant))
+
+
+def hb_get_kernel_variant(h, prec) -> int:
+    v = C.c_int(-1)
+    _check(lib().hb_get_kernel_variant(h, prec, C.byref(v)))
+    return v.value
+
+
+def hb_autotune(h, prec, screen=HB_SCREEN_IDENTITY, lam=0.1, reps=5, stream=None):
+    """Times every kernel variant on this mesh, keeps the fastest; returns
+    (best variant, {variant: ms})."""
+    best = C.c_int(-1)
+    ms = (C.c_double * 8)(*([-1.0] * 8))
+    _check(lib().hb_autotune(h, prec, screen, lam, reps, C.byref(best), ms, _stream_ptr(stream)))
+    return best.value, {v: ms[v] for v in VARIANTS if ms[v] >= 0}
 
 
 def hb_kernel_launches() -> int:

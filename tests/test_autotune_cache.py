@@ -1,0 +1,33 @@
+"""Host logic of the autotuner cache (no GPU)."""
+import json
+
+from paper_2202_12477_gb300 import autotune as at
+from paper_2202_12477_gb300 import hb
+
+
+def test_cache_roundtrip(tmp_path):
+    path = str(tmp_path / "sub" / "cache.json")
+    assert at.load(path) == {}
+    dev = at.device_key("NVIDIA GB300", 152)
+    c = at.record({}, dev, 7, hb.HB_F64, 3, {0: 12.9, 3: 12.5})
+    at.record(c, dev, 7, hb.HB_F32, 7, {3: 1.48, 7: 1.45})
+    at.store(c, path)
+    c2 = at.load(path)
+    assert at.lookup(c2, dev, 7, hb.HB_F64) == 3
+    assert at.lookup(c2, dev, 7, hb.HB_F32) == 7
+    assert at.lookup(c2, dev, 9, hb.HB_F64) is None
+    assert at.lookup(c2, at.device_key("other", 80), 7, hb.HB_F64) is None
+
+
+def test_cache_rejects_garbage(tmp_path):
+    path = tmp_path / "c.json"
+    path.write_text("not json")
+    assert at.load(str(path)) == {}
+    dev = at.device_key("g", 1)
+    path.write_text(json.dumps({dev: {at.entry_key(3, hb.HB_F64): {"variant": 6}}}))
+    assert at.lookup(at.load(str(path)), dev, 3, hb.HB_F64) is None  # 6 is not a valid variant
+
+
+def test_env_override(monkeypatch, tmp_path):
+    monkeypatch.setenv("HB_AUTOTUNE_CACHE", str(tmp_path / "x.json"))
+    assert at.cache_path() == str(tmp_path / "x.json")

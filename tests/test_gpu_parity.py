@@ -99,6 +99,23 @@ def test_apply_A_fp64(dims, N, screen, lam):
     assert np.abs(y - y_or).max() <= 1e-12 * np.abs(y_or).max()
 
 
+@pytest.mark.parametrize("variant", hb.VARIANTS)
+@pytest.mark.parametrize("dims,N", OP_CASES)
+def test_apply_A_fp64_every_variant(dims, N, variant):
+    m, o = _pair(dims, N, rho=0.2, seed=N + 1)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, variant)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F32, variant)
+    x = inputs.random_vector(m.n_global, seed=300 + N)
+    y_or = o.apply_A(x, 0.1, 0)
+    y = m.apply_A(_to_dev(x), lam=0.1).cpu().numpy()
+    assert _rel(y, y_or) <= 1e-12
+    assert np.abs(y - y_or).max() <= 1e-12 * np.abs(y_or).max()
+    x32 = x.astype(np.float32)
+    y32_or = o.apply_A(x32.astype(np.float64), 0.1, 0)
+    y32 = m.apply_A(_to_dev(x32, torch.float32), lam=0.1).cpu().numpy().astype(np.float64)
+    assert _rel(y32, y32_or) <= 2e-5
+
+
 @pytest.mark.parametrize("dims,N", OP_CASES[::2])
 def test_apply_A_fp32(dims, N):
     m, o = _pair(dims, N, rho=0.15, seed=N)
@@ -247,3 +264,17 @@ def test_cg_zero_rhs_and_breakdown():
     b = m.rhs(kind=0, seed=1)
     x, res = m.cg(b, lam=-1e6, rtol=1e-10, max_it=50)
     assert res.status == hb.HB_ERR_BREAKDOWN
+
+
+def test_autotune_keeps_parity(tmp_path):
+    from paper_2202_12477_gb300 import autotune
+    m, o = _pair((3, 3, 2), 6, rho=0.2, seed=8)
+    chosen = autotune.tune_mesh(m, path=str(tmp_path / "cache.json"), reps=2)
+    assert chosen[hb.HB_F64] in hb.VARIANTS and chosen[hb.HB_F32] in hb.VARIANTS
+    assert hb.hb_get_kernel_variant(m.handle, hb.HB_F64) == chosen[hb.HB_F64]
+    # the cached choice is reused on a new mesh of the same degree
+    m2 = hb.Mesh(2, 2, 2, 6, perturb=0.1)
+    again = autotune.tune_mesh(m2, path=str(tmp_path / "cache.json"))
+    assert again == chosen
+    x = inputs.random_vector(m.n_global, seed=5)
+    assert _rel(m.apply_A(_to_dev(x), lam=0.1).cpu().numpy(), o.apply_A(x, 0.1)) <= 1e-12
