@@ -485,13 +485,111 @@ def run_c4(args, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+def _c5_requests(n, emin, emax, seed=0):
+    """Seeded request stream: Ek uniform in emin..emax, N in {3,5,7,9,11},
+    rtol in {1e-8, 1e-10}, perturbation 0.1h, uniform rhs, lambda 0.1."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        out.append(dict(ex=int(rng.integers(emin, emax + 1)), N=int(rng.choice([3, 5, 7, 9, 11])),
+                        rtol=float(rng.choice([1e-8, 1e-10])), seed=int(i), rhs_seed=int(i)))
+    for r in out:
+        r["ey"] = r["ez"] = r["ex"]
+    return out
+
+
+def _serve_run(reqs, arrivals, budget, slots, k):
+    """Submits reqs at the given arrival times (s from start), waits for all;
+    returns per-request latencies (ms), statuses and the makespan."""
+    from paper_2202_12477_gb300 import hb
+    srv = hb.Server(budget, max_slots=slots, iters_per_launch=k)
+    t0 = time.perf_counter()
+    tickets, lat, status = [], {}, {}
+    i = 0
+    while len(lat) < len(reqs):
+        now = time.perf_counter() - t0
+        while i < len(reqs) and arrivals[i] <= now:
+            r = reqs[i]
+            tickets.append(srv.submit(ex=r["ex"], ey=r["ey"], ez=r["ez"], N=r["N"], perturb=0.1, seed=r["seed"],
+                                      rhs_seed=r["rhs_seed"], lam=0.1, rtol=r["rtol"]))
+            i += 1
+        for t in tickets:
+            if t in lat:
+                continue
+            p = srv.poll(t)
+            if p is not None:
+                lat[t] = p[0].time_ms
+                status[t] = p[0].status
+        time.sleep(0.0005)
+    makespan = time.perf_counter() - t0
+    st = srv.stats()
+    rounds = st.rounds
+    srv.close()
+    return [lat[t] for t in tickets], [status[t] for t in tickets], makespan, rounds
+
+
+def run_c5(args, rank, world, local):
+    """Serving stream with Poisson arrivals at fractions of the measured
+    capacity; mixed precision; p50/p99 latency and solves/s, beside solving
+    the same requests one at a time with hb_cg_solve in FP64 and in mixed."""
+    import numpy as np
+    import torch
+
+    from paper_2202_12477_gb300 import hb
+    torch.cuda.set_device(local)
+    reqs = _c5_requests(args.c5_requests, 2, args.c5_emax)
+    budget = int(args.c5_budget_gb * (1 << 30))
+    out = {"workload": f"serving stream: {len(reqs)} requests, Ek uniform 2..{args.c5_emax}, N in 3..11 odd, "
+                       f"rtol 1e-8 / 1e-10, mixed precision, {args.c5_slots} slots, {args.c5_k} inner "
+                       f"iterations per launch, budget {args.c5_budget_gb} GB",
+           "runs": []}
+    # capacity: everything submitted at once
+    lat, sts, mk, rounds = _serve_run(reqs, [0.0] * len(reqs), budget, args.c5_slots, args.c5_k)
+    cap = len(reqs) / mk
+    out["capacity_solves_per_s"] = cap
+    out["runs"].append({"offered": "all at t=0", "solves_per_s": cap, "p50_ms": float(np.percentile(lat, 50)),
+                        "p99_ms": float(np.percentile(lat, 99)), "rounds": rounds,
+                        "ok": int(sum(1 for s in sts if s == hb.HB_OK))})
+    rng = np.random.Generator(np.random.PCG64(1))
+    for f in (0.5, 0.8, 1.0):
+        rate = f * cap
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+        arr -= arr[0]
+        lat, sts, mk, rounds = _serve_run(reqs, list(arr), budget, args.c5_slots, args.c5_k)
+        out["runs"].append({"offered": f"{f:.1f} x capacity (Poisson)", "solves_per_s": len(reqs) / mk,
+                            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                            "rounds": rounds, "ok": int(sum(1 for s in sts if s == hb.HB_OK))})
+    # one at a time through hb_cg_solve, FP64 and mixed
+    for prec, name in ((hb.HB_F64, "sequential_fp64"), (hb.HB_MIXED, "sequential_mixed")):
+        t0 = time.perf_counter()
+        lat = []
+        for r in reqs:
+            ts = time.perf_counter()
+            m = hb.Mesh(r["ex"], r["ey"], r["ez"], r["N"], perturb=0.1, seed=r["seed"], fp32=True)
+            b = m.rhs(kind=0, seed=r["rhs_seed"])
+            m.cg(b, lam=0.1, rtol=r["rtol"], max_it=200000, prec=prec)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - ts) * 1e3)
+            m.close()
+        mk = time.perf_counter() - t0
+        out[name] = {"solves_per_s": len(reqs) / mk, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99))}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "sweep", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "sweep", "c3", "c4", "c5"])
+    ap.add_argument("--c5-requests", type=int, default=200)
+    ap.add_argument("--c5-emax", type=int, default=32)
+    ap.add_argument("--c5-slots", type=int, default=32)
+    ap.add_argument("--c5-k", type=int, default=16)
+    ap.add_argument("--c5-budget-gb", type=float, default=160.0)
     ap.add_argument("--c3-elems", type=int, default=80)
     ap.add_argument("--c4-elems", type=int, default=24)
     ap.add_argument("--N", type=int, default=7)
@@ -515,6 +613,8 @@ def main():
         run_c3(args, rank, world, local)
     elif args.workload == "c4":
         run_c4(args, rank, world, local)
+    elif args.workload == "c5":
+        run_c5(args, rank, world, local)
     else:
         run_gb300(args, rank, world, local)
 

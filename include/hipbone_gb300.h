@@ -202,6 +202,48 @@ typedef struct {
 hb_status hb_cg_solve(const hb_mesh *mesh, const hb_cg_opts *opts, const double *b,
                       double *x, hb_cg_result *res, void *stream);
 
+/* ---------------------------------------------------------------- serving
+ * A CG server with continuous batching on one GPU (the paper runs one solve at
+ * a time; the server applies Algorithm 1 in the FP32-inner / FP64
+ * defect-correction form of hb_cg_solve to many concurrent requests).
+ * Requests queue on submit; a worker thread admits them first come, first
+ * served, into free slots while the device-memory budget allows, keeps each
+ * solve's mesh and vectors resident, and advances all resident solves with
+ * one launch of a CUDA graph (captured once at creation) per round of
+ * iters_per_launch inner iterations. Finished solves are retired between
+ * rounds and queued ones admitted. Every slot runs on fixed grids with its own
+ * reductions: a request's result does not depend on which others share the
+ * GPU. The right-hand side is hb_fill_rhs kind 0 with the request's seed and
+ * x0 = 0. Degrees N = 1..11; opts.prec must be HB_MIXED and opts.rtol > 0. */
+typedef struct hb_server hb_server;
+typedef struct {
+    size_t mem_budget_bytes;   /* device memory the resident solves may hold */
+    int max_slots;             /* concurrent solves, 1..256 */
+    int iters_per_launch;      /* inner CG iterations per round, 1..256 */
+} hb_server_opts;
+typedef struct {
+    int64_t submitted, admitted, completed, rejected, rounds;
+    int active, pending;
+    size_t mem_used;
+} hb_server_stats_t;
+
+hb_status hb_server_create(const hb_server_opts *opts, hb_server **out);
+/* Queues a request and returns its ticket. keep_x = 1 keeps the solution for
+ * hb_server_poll. The mesh description's keep_fp32_copy is ignored (always 1). */
+hb_status hb_server_submit(hb_server *srv, const hb_mesh_desc *desc, const hb_cg_opts *opts,
+                           uint64_t rhs_seed, int keep_x, int64_t *ticket);
+/* HB_ERR_BUSY while the request is queued or running; HB_OK once it finished:
+ * res receives the iteration counts, the FP64 relative residual, the solve's
+ * status (HB_OK, HB_ERR_NOT_CONVERGED, HB_ERR_BREAKDOWN, or HB_ERR_NOMEM when it
+ * can never fit the budget) and, in time_ms, the latency from submit to
+ * completion; n_global and x_host (n_global doubles, if keep_x) as asked. A
+ * finished ticket is forgotten after a successful poll (HB_ERR_NOT_FOUND then). */
+hb_status hb_server_poll(hb_server *srv, int64_t ticket, hb_cg_result *res, int64_t *n_global,
+                         double *x_host);
+hb_status hb_server_stats(hb_server *srv, hb_server_stats_t *out);
+/* Stops the worker after its current round and frees every resident solve. */
+hb_status hb_server_destroy(hb_server *srv);
+
 /* The library's uniform random number, u01(seed, stream, idx) =
  * (splitmix64(seed ^ (stream * 0x9E3779B97F4A7C15) + idx) >> 11) * 2^-53, with
  * splitmix64(s) the SplitMix64 output for state s (Steele, Lea & Flood 2014). */

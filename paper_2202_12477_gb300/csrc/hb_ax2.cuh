@@ -216,25 +216,26 @@ __host__ __device__ constexpr int pencil_min_blocks()
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
+// One group of EB elements (group index `grp`), by the first EB*(N+1)^2
+// threads of the block; further threads only join the barriers. Adds the
+// group's interior-node x.y to `acc`. Every thread of the block must call it
+// (it synchronises the block).
 template <int N, bool EO, int EB>
-__global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, EB>()))
-    ax_pencil_kernel(const pencil_args A)
+__device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, T *sm,
+                                             hbacc::dot_acc<T> &acc)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     using P = pad<N>;
-    if (A.run && *A.run == 0) return;
     const T *__restrict__ x = A.x;
     const int32_t *__restrict__ l2g = A.l2g;
     const T *__restrict__ geo = A.geo;
     const int64_t E = A.E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
     const int tid = threadIdx.x;
     const int el = tid / n2;
     const int a = tid - el * n2;       // 0 .. n^2-1
     const int p0 = a % n, p1 = a / n;  // line owned in each direction
-    const int64_t e = (int64_t)blockIdx.x * EB + el;
-    const bool active = e < E;
+    const int64_t e = grp * EB + el;
+    const bool active = el < EB && e < E;
     T *U = sm + el * 4 * P::size;  // gathered u (kept: the x values of the epilogue)
     T *B1 = U + P::size;           // r: u_r, v_r, D^T_r v_r
     T *B2 = B1 + P::size;          // s
@@ -298,7 +299,6 @@ __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, E
         line_st<N, true, EO>(in, [&](int m, T v) { B3[P::at(p0, p1, m)] = v; });
     }
     __syncthreads();
-    hbacc::dot_acc<T> acc;
     if (active) {
         constexpr int NS = surf_count<N>();
         T *ys = A.ysurf + e * NS;
@@ -324,6 +324,17 @@ __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, E
             }
         }
     }
+    __syncthreads();  // the block's buffers are reused by the next group
+}
+
+template <int N, bool EO, int EB>
+__global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, EB>()))
+    ax_pencil_kernel(const pencil_args A)
+{
+    if (A.run && *A.run == 0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    hbacc::dot_acc<T> acc;
+    pencil_group<N, EO, EB>(A, blockIdx.x, reinterpret_cast<T *>(smem_raw), acc);
     if (A.partials) {
         const double v = hbacc::block_sum(acc.value());
         if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
@@ -341,7 +352,7 @@ namespace {
 template <int N, bool EO>
 hb_status launch(const pencil_args &A, int eb_mult, cudaStream_t s, int64_t *nblocks_out)
 {
-    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    constexpr int n = N + 1, n2 = n * n;
     constexpr int EB1 = n2 >= 256 ? 1 : 256 / n2;
     if (A.E <= 0) return HB_OK;
     static int attr_set[2][32] = {{0}};

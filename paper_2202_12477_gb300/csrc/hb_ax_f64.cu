@@ -40,3 +40,95 @@ hb_status hb_launch_ax2_f64(const hb_mesh *m, const double *x, double *ysurf, do
 }
 
 int hb_surf_count(int N) { return 2 * (N + 1) * (N + 1) + 4 * N * (N - 1); }
+
+// ---------------------------------------------------------------- serving
+
+#include "hb_serve.h"
+
+namespace hb2 {
+namespace {
+
+template <int N>
+__host__ __device__ constexpr int serve_eb() { return HB_SERVE_THREADS / ((N + 1) * (N + 1)); }
+
+template <int N>
+__host__ __device__ constexpr size_t serve_smem_of() { return sizeof(T) * 4 * serve_eb<N>() * pad<N>::size; }
+
+constexpr size_t serve_smem_max()
+{
+    size_t m = 0;
+    m = serve_smem_of<1>() > m ? serve_smem_of<1>() : m;
+    m = serve_smem_of<2>() > m ? serve_smem_of<2>() : m;
+    m = serve_smem_of<3>() > m ? serve_smem_of<3>() : m;
+    m = serve_smem_of<4>() > m ? serve_smem_of<4>() : m;
+    m = serve_smem_of<5>() > m ? serve_smem_of<5>() : m;
+    m = serve_smem_of<6>() > m ? serve_smem_of<6>() : m;
+    m = serve_smem_of<7>() > m ? serve_smem_of<7>() : m;
+    m = serve_smem_of<8>() > m ? serve_smem_of<8>() : m;
+    m = serve_smem_of<9>() > m ? serve_smem_of<9>() : m;
+    m = serve_smem_of<10>() > m ? serve_smem_of<10>() : m;
+    m = serve_smem_of<11>() > m ? serve_smem_of<11>() : m;
+    return m;
+}
+
+template <int N>
+__device__ __forceinline__ void serve_groups(const pencil_args &A, T *sm, hbacc::dot_acc<T> &acc)
+{
+    constexpr int EB = serve_eb<N>();
+    const int64_t ngroups = (A.E + EB - 1) / EB;
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) pencil_group<N, true, EB>(A, g, sm, acc);
+}
+
+// One slot's element kernel on a fixed grid: the degree is read from the
+// slot descriptor, each block walks element groups grid-stride.
+__global__ void __launch_bounds__(HB_SERVE_THREADS, 1)
+    serve_ax_kernel(const hb_slot_desc *__restrict__ D, const hb_slot_state *__restrict__ S)
+{
+    const hb_slot_desc &d = *D;
+    if (!d.active || S->phase != HB_SLOT_OUTER) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    pencil_args A{(const T *)d.x, d.l2g, d.geo, (T *)d.ysurf, (T *)d.Ap, d.E, nullptr, (T)d.lambda,
+                  d.screen, nullptr};
+    hbacc::dot_acc<T> acc;
+    switch (d.N) {
+    case 1: serve_groups<1>(A, sm, acc); break;
+    case 2: serve_groups<2>(A, sm, acc); break;
+    case 3: serve_groups<3>(A, sm, acc); break;
+    case 4: serve_groups<4>(A, sm, acc); break;
+    case 5: serve_groups<5>(A, sm, acc); break;
+    case 6: serve_groups<6>(A, sm, acc); break;
+    case 7: serve_groups<7>(A, sm, acc); break;
+    case 8: serve_groups<8>(A, sm, acc); break;
+    case 9: serve_groups<9>(A, sm, acc); break;
+    case 10: serve_groups<10>(A, sm, acc); break;
+    case 11: serve_groups<11>(A, sm, acc); break;
+    default: break;
+    }
+    if (A.partials) {
+        const double v = hbacc::block_sum(acc.value());
+        if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
+    }
+}
+
+}  // namespace
+}  // namespace hb2
+
+size_t hb_serve_ax_smem_f64() { return hb2::serve_smem_max(); }
+
+hb_status hb_serve_launch_ax_f64(const hb_slot_desc *d, const hb_slot_state *st, cudaStream_t s)
+{
+    static int attr_set[32] = {0};
+    int dev = 0;
+    HB_TRY_CUDA(cudaGetDevice(&dev));
+    const size_t smem = hb2::serve_smem_max();
+    if (dev >= 0 && dev < 32 && !attr_set[dev]) {
+        HB_TRY_CUDA(cudaFuncSetAttribute(hb2::serve_ax_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        attr_set[dev] = 1;
+    }
+    hb_count_launch();
+    hb2::serve_ax_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, smem, s>>>(d, st);
+    HB_CHECK_LAUNCH();
+    return HB_OK;
+}

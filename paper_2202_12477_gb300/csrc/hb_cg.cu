@@ -16,65 +16,9 @@
 #include <mutex>
 
 #include "hb_internal.h"
-#include "hb_acc.cuh"
+#include "hb_vec.cuh"
 
 namespace hb {
-
-using hbacc::dot_acc;
-
-// ---------------------------------------------------------------- grid reduction
-
-// Sums NV values over the grid in a fixed order. Returns true in the block that
-// arrives last (in all of its threads), with tot[] holding the grid totals.
-template <int NV>
-__device__ bool grid_sum(double (&v)[NV], double *partials, unsigned *counter, double (&tot)[NV])
-{
-    __shared__ double sh[NV][32];
-    __shared__ int s_last;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int q = 0; q < NV; q++) {
-        double a = v[q];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) sh[q][wid] = a;
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; q++) {
-            double a = lane < nw ? sh[q][lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) partials[q * HB_RED_BLOCKS + blockIdx.x] = a;
-        }
-        if (lane == 0) {
-            __threadfence();
-            unsigned t = atomicAdd(counter, 1u);
-            s_last = (t == gridDim.x - 1);
-        }
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-#pragma unroll
-    for (int q = 0; q < NV; q++) {
-        double a = 0.0;
-        for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) a += __ldcg(&partials[q * HB_RED_BLOCKS + p]);
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        __syncthreads();
-        if (lane == 0) sh[q][wid] = a;
-        __syncthreads();
-        if (wid == 0) {
-            double b = lane < nw ? sh[q][lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
-            if (lane == 0) sh[q][0] = b;
-        }
-        __syncthreads();
-        tot[q] = sh[q][0];
-    }
-    if (threadIdx.x == 0) *counter = 0;
-    return true;
-}
 
 static inline int red_grid(int64_t n)
 {
@@ -83,45 +27,81 @@ static inline int red_grid(int64_t n)
     return (int)(g < 1 ? 1 : g);
 }
 
-// ---------------------------------------------------------------- assembly
 
-// y_g = sum_{p in row g} y_L[cols[p]] + lambda (x_g | M_gg x_g); optional x.y.
+// ---------------------------------------------------------------- kernels
+
 template <typename T, int SCREEN, int DOT>
 __global__ void __launch_bounds__(HB_RED_THREADS)
-    assemble_kernel(const T *__restrict__ yL, const int32_t *__restrict__ rowptr,
-                    const int32_t *__restrict__ cols, const T *__restrict__ x, const T *__restrict__ mdiag,
-                    double lambda, T *__restrict__ y, int64_t ng, double *partials, unsigned *counter,
-                    hb_cg_state *st)
+    assemble_kernel(const T *__restrict__ yL, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ cols,
+                    const T *__restrict__ x, const T *__restrict__ mdiag, double lambda, T *__restrict__ y,
+                    int64_t ng, double *partials, unsigned *counter, hb_cg_state *st)
 {
-    if (DOT == HB_DOT_CG_PAP && st->run == 0) return;
-    const T lam = (T)lambda;
-    dot_acc<T> acc;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
-        const int a = __ldg(rowptr + g), z = __ldg(rowptr + g + 1);
-        T s = T(0);
-        for (int p = a; p < z; p++) s += __ldcs(yL + __ldcs(cols + p));
-        const T xv = x[g];
-        s += SCREEN ? lam * (mdiag[g] * xv) : lam * xv;
-        y[g] = s;
-        if (DOT) acc.add(xv, s);
-    }
-    if (DOT) {
-        double v[1] = {acc.value()}, tot[1];
-        if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-            if (DOT == HB_DOT_CG_PAP) {
-                const double pAp = tot[0];
-                st->pAp = pAp;
-                if (!(pAp > 0.0) || !isfinite(pAp)) {
-                    st->status = HB_ERR_BREAKDOWN;
-                    st->run = 0;
-                } else {
-                    st->alpha = st->rr / pAp;
-                }
-            } else {
-                st->dot_tmp = tot[0];
-            }
-        }
-    }
+    assemble_body<T, SCREEN, DOT>(yL, rowptr, cols, x, mdiag, lambda, y, ng, partials, counter, st);
+}
+
+template <typename T, int SCREEN, int DOT>
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    assemble_surf_kernel(const T *__restrict__ ys, const int32_t *__restrict__ srow_g,
+                         const int32_t *__restrict__ rowptr, const int32_t *__restrict__ cols,
+                         const T *__restrict__ x, const T *__restrict__ mdiag, double lambda, T *__restrict__ y,
+                         int64_t nrows, const double *__restrict__ ax_partials, int64_t n_axp, double *partials,
+                         unsigned *counter, hb_cg_state *st)
+{
+    assemble_surf_body<T, SCREEN, DOT>(ys, srow_g, rowptr, cols, x, mdiag, lambda, y, nrows, ax_partials, n_axp,
+                                       partials, counter, st);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    dot_kernel(const T *__restrict__ a, const T *__restrict__ b, int64_t n, double *out, double *partials,
+               unsigned *counter)
+{
+    dot_body<T>(a, b, n, out, partials, counter);
+}
+
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    cg_init_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
+                   double *__restrict__ p, int64_t n, double rtol, int max_it, double *partials, unsigned *counter,
+                   hb_cg_state *st)
+{
+    cg_init_body(b, Ax, r, p, n, rtol, max_it, partials, counter, st);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    cg_update_r_kernel(T *__restrict__ r, const T *__restrict__ Ap, int64_t n, double *partials, unsigned *counter,
+                       hb_cg_state *st)
+{
+    cg_update_r_body<T>(r, Ap, n, partials, counter, st);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    cg_update_xp_kernel(T *__restrict__ x, T *__restrict__ p, const T *__restrict__ r, int64_t n, unsigned *counter,
+                        hb_cg_state *st)
+{
+    cg_update_xp_body<T>(x, p, r, n, counter, st);
+}
+
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    residual_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r, int64_t n,
+                    double *partials, unsigned *counter, hb_cg_state *st)
+{
+    residual_body(b, Ax, r, n, partials, counter, st);
+}
+
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    inner_init_kernel(const double *__restrict__ r, float *__restrict__ r32, float *__restrict__ p32,
+                      float *__restrict__ d32, int64_t n, double rtol_in, int max_it, double *partials,
+                      unsigned *counter, const hb_cg_state *outer, hb_cg_state *st)
+{
+    inner_init_body(r, r32, p32, d32, n, rtol_in, max_it, partials, counter, outer, st);
+}
+
+__global__ void update_x_kernel(double *__restrict__ x, const float *__restrict__ d32, int64_t n,
+                                const hb_cg_state *outer)
+{
+    update_x_body(x, d32, n, outer);
 }
 
 template <typename T>
@@ -150,83 +130,6 @@ hb_status launch_assemble(const hb_mesh *m, const T *yL, const T *x, T *y, const
     return HB_OK;
 }
 
-// ---------------------------------------------------------------- surface assembly
-
-// Z^T on the DOFs that have a copy on an element surface: y_g = sum over the
-// copies of ysurf (ascending: element order) + lambda (x_g | M_gg x_g).
-// With a dot mode, x.y over these rows plus the element kernel's per-block
-// partials (interior DOFs) is reduced on the fixed grid.
-template <typename T, int SCREEN, int DOT>
-__global__ void __launch_bounds__(HB_RED_THREADS)
-    assemble_surf_kernel(const T *__restrict__ ys, const int32_t *__restrict__ srow_g,
-                         const int32_t *__restrict__ rowptr, const int32_t *__restrict__ cols,
-                         const T *__restrict__ x, const T *__restrict__ mdiag, double lambda, T *__restrict__ y,
-                         int64_t nrows, const double *__restrict__ ax_partials, int64_t n_axp, double *partials,
-                         unsigned *counter, hb_cg_state *st)
-{
-    if (DOT == HB_DOT_CG_PAP && st->run == 0) return;
-    const T lam = (T)lambda;
-    dot_acc<T> acc;
-    // four independent rows per pass keep several dependent load chains
-    // (row pointer -> column -> value) in flight per thread
-    constexpr int U4 = 4;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r0 < nrows; r0 += U4 * stride) {
-        int g[U4], a[U4], z[U4], c0[U4], c1[U4];
-        T xv[U4], s[U4];
-#pragma unroll
-        for (int u = 0; u < U4; u++) {
-            const int64_t r = r0 + u * stride;
-            const bool ok = r < nrows;
-            g[u] = ok ? __ldg(srow_g + r) : -1;
-            a[u] = ok ? __ldg(rowptr + r) : 0;
-            z[u] = ok ? __ldg(rowptr + r + 1) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < U4; u++) {
-            c0[u] = a[u] < z[u] ? __ldcs(cols + a[u]) : -1;
-            c1[u] = a[u] + 1 < z[u] ? __ldcs(cols + a[u] + 1) : -1;
-            xv[u] = g[u] >= 0 ? x[g[u]] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < U4; u++) {
-            T v0 = c0[u] >= 0 ? __ldcs(ys + c0[u]) : T(0);
-            T v1 = c1[u] >= 0 ? __ldcs(ys + c1[u]) : T(0);
-            s[u] = v0 + v1;
-        }
-#pragma unroll
-        for (int u = 0; u < U4; u++) {
-            if (g[u] < 0) continue;
-            T t = s[u];
-            for (int p = a[u] + 2; p < z[u]; p++) t += __ldcs(ys + __ldcs(cols + p));
-            t += SCREEN ? lam * (mdiag[g[u]] * xv[u]) : lam * xv[u];
-            y[g[u]] = t;
-            if (DOT) acc.add(xv[u], t);
-        }
-    }
-    if (DOT) {
-        double v = acc.value();
-        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_axp;
-             q += (int64_t)gridDim.x * blockDim.x)
-            v += ax_partials[q];
-        double vv[1] = {v}, tot[1];
-        if (grid_sum<1>(vv, partials, counter, tot) && threadIdx.x == 0) {
-            if (DOT == HB_DOT_CG_PAP) {
-                const double pAp = tot[0];
-                st->pAp = pAp;
-                if (!(pAp > 0.0) || !isfinite(pAp)) {
-                    st->status = HB_ERR_BREAKDOWN;
-                    st->run = 0;
-                } else {
-                    st->alpha = st->rr / pAp;
-                }
-            } else {
-                st->dot_tmp = tot[0];
-            }
-        }
-    }
-}
-
 template <typename T>
 hb_status launch_assemble_surf(const hb_mesh *m, const T *ys, const T *x, T *y, const T *mdiag, int screen,
                                double lambda, int64_t n_axp, hb_cg_state *st, int dot_mode, cudaStream_t s)
@@ -251,203 +154,6 @@ hb_status launch_assemble_surf(const hb_mesh *m, const T *ys, const T *x, T *y, 
 #undef HB_ASM
     HB_CHECK_LAUNCH();
     return HB_OK;
-}
-
-// ---------------------------------------------------------------- dot
-
-template <typename T>
-__global__ void __launch_bounds__(HB_RED_THREADS)
-    dot_kernel(const T *__restrict__ a, const T *__restrict__ b, int64_t n, double *out, double *partials,
-               unsigned *counter)
-{
-    dot_acc<T> acc;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
-        T av[4], bv[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int64_t i = i0 + u * stride;
-            av[u] = i < n ? a[i] : T(0);
-            bv[u] = i < n ? b[i] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-            if (i0 + u * stride < n) acc.add(av[u], bv[u]);
-    }
-    double v[1] = {acc.value()}, tot[1];
-    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
-}
-
-// ---------------------------------------------------------------- CG kernels
-
-// r = b - Ax; p = r; r.r and b.b; state set up for Algorithm 1.
-__global__ void __launch_bounds__(HB_RED_THREADS)
-    cg_init_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
-                   double *__restrict__ p, int64_t n, double rtol, int max_it, double *partials,
-                   unsigned *counter, hb_cg_state *st)
-{
-    dot_acc<double> rr, bb;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double bi = b[i];
-        const double ri = bi - Ax[i];
-        r[i] = ri;
-        p[i] = ri;
-        rr.add(ri, ri);
-        bb.add(bi, bi);
-    }
-    double v[2] = {rr.value(), bb.value()}, tot[2];
-    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
-        st->rr = tot[0];
-        st->bb = tot[1];
-        st->tol2 = rtol * rtol * tot[1];
-        st->it = 0;
-        st->max_it = max_it;
-        st->status = HB_OK;
-        st->alpha = st->beta = st->pAp = 0.0;
-        st->run = (max_it > 0 && tot[0] > st->tol2) ? 1 : 0;
-        st->next_run = st->run;
-    }
-}
-
-// Algorithm 1, line 9 and the r.r of line 10: r -= alpha Ap.
-template <typename T>
-__global__ void __launch_bounds__(HB_RED_THREADS)
-    cg_update_r_kernel(T *__restrict__ r, const T *__restrict__ Ap, int64_t n, double *partials,
-                       unsigned *counter, hb_cg_state *st)
-{
-    if (st->run == 0) return;
-    const T alpha = (T)st->alpha;
-    dot_acc<T> acc;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
-        T rv[4], av[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int64_t i = i0 + u * stride;
-            rv[u] = i < n ? r[i] : T(0);
-            av[u] = i < n ? __ldcs(Ap + i) : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int64_t i = i0 + u * stride;
-            if (i < n) {
-                const T ri = rv[u] - alpha * av[u];
-                r[i] = ri;
-                acc.add(ri, ri);
-            }
-        }
-    }
-    double v[1] = {acc.value()}, tot[1];
-    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-        const double rr_new = tot[0];
-        st->rr_new = rr_new;
-        st->beta = rr_new / st->rr;
-        st->rr = rr_new;
-        st->it += 1;
-        st->next_run = (st->it < st->max_it && rr_new > st->tol2) ? 1 : 0;
-    }
-}
-
-// Algorithm 1, lines 8 and 11 (x += alpha p with the old p, then p = r + beta p).
-// The block that finishes last ends the iteration: run <- next_run.
-template <typename T>
-__global__ void __launch_bounds__(HB_RED_THREADS)
-    cg_update_xp_kernel(T *__restrict__ x, T *__restrict__ p, const T *__restrict__ r, int64_t n,
-                        unsigned *counter, hb_cg_state *st)
-{
-    __shared__ int s_last;
-    if (st->run == 0) return;
-    const T alpha = (T)st->alpha, beta = (T)st->beta;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
-        T pv[4], xv[4], rv[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int64_t i = i0 + u * stride;
-            pv[u] = i < n ? p[i] : T(0);
-            xv[u] = i < n ? x[i] : T(0);
-            rv[u] = i < n ? r[i] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int64_t i = i0 + u * stride;
-            if (i < n) {
-                x[i] = xv[u] + alpha * pv[u];
-                p[i] = rv[u] + beta * pv[u];
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned t = atomicAdd(counter, 1u);
-        s_last = (t == gridDim.x - 1);
-        if (s_last) {
-            *counter = 0;
-            st->run = st->next_run;
-        }
-    }
-}
-
-// ---------------------------------------------------------------- mixed precision
-
-// Outer residual: r = b - A x (FP64) with r.r and b.b into the outer state.
-__global__ void __launch_bounds__(HB_RED_THREADS)
-    residual_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
-                    int64_t n, double *partials, unsigned *counter, hb_cg_state *st)
-{
-    dot_acc<double> rr, bb;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double bi = b[i];
-        const double ri = bi - Ax[i];
-        r[i] = ri;
-        rr.add(ri, ri);
-        bb.add(bi, bi);
-    }
-    double v[2] = {rr.value(), bb.value()}, tot[2];
-    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
-        st->rr = tot[0];
-        st->bb = tot[1];
-    }
-}
-
-// Inner start: r32 = r / ||r|| (so the inner system is well scaled in FP32),
-// p32 = r32, d32 = 0; inner state for A d = r32 with relative target rtol_in.
-__global__ void __launch_bounds__(HB_RED_THREADS)
-    inner_init_kernel(const double *__restrict__ r, float *__restrict__ r32, float *__restrict__ p32,
-                      float *__restrict__ d32, int64_t n, double rtol_in, int max_it, double *partials,
-                      unsigned *counter, const hb_cg_state *outer, hb_cg_state *st)
-{
-    const double scale = 1.0 / sqrt(outer->rr);
-    dot_acc<float> acc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = (float)(r[i] * scale);
-        r32[i] = v;
-        p32[i] = v;
-        d32[i] = 0.0f;
-        acc.add(v, v);
-    }
-    double v[1] = {acc.value()}, tot[1];
-    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-        st->rr = tot[0];
-        st->bb = tot[0];
-        st->tol2 = rtol_in * rtol_in * tot[0];
-        st->it = 0;
-        st->max_it = max_it;
-        st->status = HB_OK;
-        st->alpha = st->beta = st->pAp = 0.0;
-        st->run = (max_it > 0 && tot[0] > st->tol2) ? 1 : 0;
-        st->next_run = st->run;
-    }
-}
-
-// x += ||r|| d32 (FP64 solution update).
-__global__ void update_x_kernel(double *__restrict__ x, const float *__restrict__ d32, int64_t n,
-                                const hb_cg_state *outer)
-{
-    const double s = sqrt(outer->rr);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] += s * (double)d32[i];
 }
 
 }  // namespace hb

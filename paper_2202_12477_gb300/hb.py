@@ -52,6 +52,16 @@ class hb_cg_result(C.Structure):
                 ("time_ms", C.c_double), ("status", C.c_int)]
 
 
+class hb_server_opts(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("iters_per_launch", C.c_int)]
+
+
+class hb_server_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("rejected", C.c_int64), ("rounds", C.c_int64), ("active", C.c_int), ("pending", C.c_int),
+                ("mem_used", C.c_size_t)]
+
+
 class HBError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -76,6 +86,13 @@ _SIGS = [
     ("hb_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
                               C.POINTER(hb_cg_result), C.c_void_p]),
     ("hb_u01", C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64]),
+    ("hb_server_create", C.c_int, [C.POINTER(hb_server_opts), C.POINTER(C.c_void_p)]),
+    ("hb_server_submit", C.c_int, [C.c_void_p, C.POINTER(hb_mesh_desc), C.POINTER(hb_cg_opts), C.c_uint64,
+                                   C.c_int, C.POINTER(C.c_int64)]),
+    ("hb_server_poll", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(hb_cg_result), C.POINTER(C.c_int64),
+                                 C.c_void_p]),
+    ("hb_server_stats", C.c_int, [C.c_void_p, C.POINTER(hb_server_stats_t)]),
+    ("hb_server_destroy", C.c_int, [C.c_void_p]),
     ("hb_set_kernel_variant", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     ("hb_get_kernel_variant", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     ("hb_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -279,3 +296,64 @@ class Mesh:
         out = np.zeros(7 * self.n_local, dtype=np.float64)
         _check(lib().hb_mesh_copy_geo(self.handle, out.ctypes.data_as(C.c_void_p)))
         return out
+
+
+# ---------------------------------------------------------------- server
+
+class Server:
+    """Owns an hb_server (continuous-batching CG server on the current GPU)."""
+
+    def __init__(self, mem_budget_bytes, max_slots=16, iters_per_launch=8):
+        o = hb_server_opts(int(mem_budget_bytes), max_slots, iters_per_launch)
+        h = C.c_void_p()
+        _check(lib().hb_server_create(C.byref(o), C.byref(h)))
+        self.handle = h
+
+    def submit(self, ex, ey, ez, N, perturb=0.1, seed=0, rhs_seed=0, lam=0.1, rtol=1e-8, max_it=100000,
+               inner_rtol=1e-4, max_outer=30, screen=HB_SCREEN_IDENTITY, faces=ALL_FACES, keep_x=False) -> int:
+        d = hb_mesh_desc(ex, ey, ez, N, perturb, seed, faces, 1)
+        o = hb_cg_opts(HB_MIXED, screen, lam, rtol, max_it, inner_rtol, max_outer)
+        t = C.c_int64(0)
+        _check(lib().hb_server_submit(self.handle, C.byref(d), C.byref(o), rhs_seed, 1 if keep_x else 0,
+                                      C.byref(t)))
+        return t.value
+
+    def poll(self, ticket, n_global=None):
+        """None while queued or running; else (hb_cg_result, x or None)."""
+        import numpy as np
+        res = hb_cg_result()
+        ng = C.c_int64(0)
+        x = np.zeros(n_global, dtype=np.float64) if n_global else None
+        st = lib().hb_server_poll(self.handle, ticket, C.byref(res), C.byref(ng),
+                                  x.ctypes.data_as(C.c_void_p) if x is not None else None)
+        if st == HB_ERR_BUSY:
+            return None
+        _check(st)
+        return res, x
+
+    def wait(self, ticket, n_global=None, timeout=600.0, interval=0.0005):
+        import time
+        t0 = time.time()
+        while True:
+            r = self.poll(ticket, n_global)
+            if r is not None:
+                return r
+            if time.time() - t0 > timeout:
+                raise TimeoutError(f"ticket {ticket} not done after {timeout} s")
+            time.sleep(interval)
+
+    def stats(self) -> hb_server_stats_t:
+        st = hb_server_stats_t()
+        _check(lib().hb_server_stats(self.handle, C.byref(st)))
+        return st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().hb_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
