@@ -290,6 +290,18 @@ hb_status hb_profile_enable(int on);
 hb_status hb_profile_reset(void);
 hb_status hb_profile_read(const char *name, double *total_ms, long long *launches);
 
+/* Calibration probes (the paper calibrates its roofline with an 8-read /
+ * 1-write streaming kernel, Sec. 4.1). Runs `reps` timed launches after one
+ * untimed one on a scratch buffer of `bytes` bytes (allocated for the call)
+ * and returns the best rate in *rate: GB/s (read + write bytes) for the
+ * stream and copy kinds, GFLOP/s for HB_PROBE_FMA (bytes ignored).
+ *   HB_PROBE_STREAM81_FP   8 reads, 1 write of their sum in `prec`
+ *   HB_PROBE_STREAM81_BITS the same traffic combined with XOR (no FP work)
+ *   HB_PROBE_COPY          16-byte vector copy
+ *   HB_PROBE_FMA           independent FMA chains in `prec` */
+enum { HB_PROBE_STREAM81_FP = 0, HB_PROBE_STREAM81_BITS = 1, HB_PROBE_COPY = 2, HB_PROBE_FMA = 3 };
+hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int reps, double *rate);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *hb_last_error(void);
 

@@ -229,9 +229,85 @@ static int make_numbering(or_mesh *m)
     return 0;
 }
 
-/* Geometric factors from the analytic Jacobian of the trilinear map
- * x(r,s,t) = sum_{abc} V_abc phi_a(r) phi_b(s) phi_c(t), phi_0 = (1-r)/2,
- * phi_1 = (1+r)/2, evaluated at each GLL node. */
+/* The 8 vertices of element (ex,ey,ez), with the same perturbation rule as
+ * make_vertices, computed directly. */
+static void element_vertices(int Ex, int Ey, int Ez, double rho, uint64_t seed, int ex, int ey, int ez,
+                             double Ve[2][2][2][3])
+{
+    double h[3] = {1.0 / Ex, 1.0 / Ey, 1.0 / Ez};
+    for (int c = 0; c < 2; c++)
+        for (int b = 0; b < 2; b++)
+            for (int a = 0; a < 2; a++) {
+                int A = ex + a, B = ey + b, Cc = ez + c;
+                int64_t v = ((int64_t)Cc * (Ey + 1) + B) * (Ex + 1) + A;
+                double X[3] = {(double)A / Ex, (double)B / Ey, (double)Cc / Ez};
+                int inside = A > 0 && A < Ex && B > 0 && B < Ey && Cc > 0 && Cc < Ez;
+                for (int ax = 0; ax < 3; ax++) {
+                    double off = 0.0;
+                    if (inside) off = (2.0 * or_u01(seed, 1, (uint64_t)(3 * v + ax)) - 1.0) * rho * h[ax];
+                    Ve[c][b][a][ax] = X[ax] + off;
+                }
+            }
+}
+
+/* Geometric factors of one element from the analytic Jacobian of the
+ * trilinear map x(r,s,t) = sum_{abc} V_abc phi_a(r) phi_b(s) phi_c(t),
+ * phi_0 = (1-r)/2, phi_1 = (1+r)/2, at each GLL node. G: [n^3][6], Jw: [n^3],
+ * X: [n^3][3] (may be NULL). Returns the smallest det J. */
+static double element_geometry(int N, const double *xi, const double *w, double Ve[2][2][2][3], double *G,
+                               double *Jw, double *Xout)
+{
+    int n = N + 1;
+    double mind = INFINITY;
+    for (int k = 0; k < n; k++)
+        for (int j = 0; j < n; j++)
+            for (int i = 0; i < n; i++) {
+                double r = xi[i], s = xi[j], t = xi[k];
+                double ph[3][2] = {{0.5 * (1 - r), 0.5 * (1 + r)},
+                                   {0.5 * (1 - s), 0.5 * (1 + s)},
+                                   {0.5 * (1 - t), 0.5 * (1 + t)}};
+                double dph[2] = {-0.5, 0.5};
+                double J[3][3] = {{0}}, X[3] = {0};
+                for (int c = 0; c < 2; c++)
+                    for (int b = 0; b < 2; b++)
+                        for (int a = 0; a < 2; a++)
+                            for (int ax = 0; ax < 3; ax++) {
+                                double v = Ve[c][b][a][ax];
+                                X[ax] += v * ph[0][a] * ph[1][b] * ph[2][c];
+                                J[ax][0] += v * dph[a] * ph[1][b] * ph[2][c];
+                                J[ax][1] += v * ph[0][a] * dph[b] * ph[2][c];
+                                J[ax][2] += v * ph[0][a] * ph[1][b] * dph[c];
+                            }
+                double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                             J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                             J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+                double Ji[3][3];
+                Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+                Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+                Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+                Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+                Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+                Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+                Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+                Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+                Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+                double wq = w[i] * w[j] * w[k] * det;
+                int q = (k * n + j) * n + i;
+                const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+                for (int f = 0; f < 6; f++) {
+                    double g = 0.0;
+                    for (int x = 0; x < 3; x++) g += Ji[pa[f]][x] * Ji[pb[f]][x];
+                    G[6 * q + f] = wq * g;
+                }
+                Jw[q] = wq;
+                if (Xout)
+                    for (int ax = 0; ax < 3; ax++) Xout[3 * q + ax] = X[ax];
+                if (det < mind) mind = det;
+            }
+    return mind;
+}
+
+/* Geometric factors of every element (element_geometry on the box's vertices). */
 static void make_geometry(or_mesh *m)
 {
     int n = m->n;
@@ -247,52 +323,9 @@ static void make_geometry(or_mesh *m)
                         for (int a = 0; a < 2; a++)
                             for (int ax = 0; ax < 3; ax++)
                                 Ve[c][b][a][ax] = m->V[3 * vidx(m, ex + a, ey + b, ez + c) + ax];
-                for (int k = 0; k < n; k++)
-                    for (int j = 0; j < n; j++)
-                        for (int i = 0; i < n; i++) {
-                            double r = m->xi[i], s = m->xi[j], t = m->xi[k];
-                            double ph[3][2] = {{0.5 * (1 - r), 0.5 * (1 + r)},
-                                               {0.5 * (1 - s), 0.5 * (1 + s)},
-                                               {0.5 * (1 - t), 0.5 * (1 + t)}};
-                            double dph[2] = {-0.5, 0.5};
-                            /* J[x][l] = d x_x / d r_l, l = r, s, t */
-                            double J[3][3] = {{0}}, X[3] = {0};
-                            for (int c = 0; c < 2; c++)
-                                for (int b = 0; b < 2; b++)
-                                    for (int a = 0; a < 2; a++)
-                                        for (int ax = 0; ax < 3; ax++) {
-                                            double v = Ve[c][b][a][ax];
-                                            X[ax] += v * ph[0][a] * ph[1][b] * ph[2][c];
-                                            J[ax][0] += v * dph[a] * ph[1][b] * ph[2][c];
-                                            J[ax][1] += v * ph[0][a] * dph[b] * ph[2][c];
-                                            J[ax][2] += v * ph[0][a] * ph[1][b] * dph[c];
-                                        }
-                            double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-                            /* inverse by cofactors: Ji[l][x] = d r_l / d x_x */
-                            double Ji[3][3];
-                            Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
-                            Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
-                            Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
-                            Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
-                            Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
-                            Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
-                            Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
-                            Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
-                            Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
-                            double wq = m->w[i] * m->w[j] * m->w[k] * det;
-                            int64_t q = e * n3 + (k * n + j) * n + i;
-                            const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
-                            for (int f = 0; f < 6; f++) {
-                                double g = 0.0;
-                                for (int x = 0; x < 3; x++) g += Ji[pa[f]][x] * Ji[pb[f]][x];
-                                m->G[6 * q + f] = wq * g;
-                            }
-                            m->Jw[q] = wq;
-                            for (int ax = 0; ax < 3; ax++) m->X[3 * q + ax] = X[ax];
-                            if (det < mind) mind = det;
-                        }
+                double d = element_geometry(m->N, m->xi, m->w, Ve, m->G + 6 * e * n3, m->Jw + e * n3,
+                                            m->X + 3 * e * n3);
+                if (d < mind) mind = d;
             }
     m->min_detJ = mind;
 }
@@ -366,14 +399,10 @@ void or_mesh_copy_ref(const or_mesh *m, double *xi, double *w, double *D)
 /* ------------------------------------------------------------------ */
 
 /* y_e = S_L^e u_e = Dbold^T G^e Dbold u_e for one element, with u_e = Z_e x. */
-static void local_stiffness(const or_mesh *m, int64_t e, const double *x, double *ye,
-                            double *u, double *ur, double *us, double *ut)
+static void local_stiffness_ptr(int n, const double *D, const int32_t *l2g, const double *G, const double *x,
+                                double *ye, double *u, double *ur, double *us, double *ut)
 {
-    int n = m->n;
     int64_t n3 = (int64_t)n * n * n;
-    const double *D = m->D;
-    const int32_t *l2g = m->l2g + e * n3;
-    const double *G = m->G + 6 * e * n3;
 #define IX(i, j, k) (((k) * n + (j)) * n + (i))
     /* u = Z_e x (a Dirichlet node carries 0) */
     for (int q = 0; q < n3; q++) u[q] = l2g[q] >= 0 ? x[l2g[q]] : 0.0;
@@ -412,6 +441,13 @@ static void local_stiffness(const or_mesh *m, int64_t e, const double *x, double
                 ye[IX(i, j, k)] = a + b + c;
             }
 #undef IX
+}
+
+static void local_stiffness(const or_mesh *m, int64_t e, const double *x, double *ye, double *u, double *ur,
+                            double *us, double *ut)
+{
+    int64_t n3 = (int64_t)m->n * m->n * m->n;
+    local_stiffness_ptr(m->n, m->D, m->l2g + e * n3, m->G + 6 * e * n3, x, ye, u, ur, us, ut);
 }
 
 /* y = A x = Z^T S_L Z x + lambda x (screen 0, Eq. poisson) or
@@ -556,4 +592,79 @@ int or_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Selected rows of A x without building the mesh                      */
+/* ------------------------------------------------------------------ */
+
+/* out[r] = (A x)[rows[r]] for the box (Ex,Ey,Ez,N,rho,seed,faces), computed
+ * element by element: for each requested DOF the elements that contain it
+ * (ascending element order, as or_apply_A sums them) get their vertices,
+ * geometric factors and local product S_L^e Z_e x built on the spot. The
+ * global id of a lattice node is its rank among the unmasked lattice nodes
+ * in lexicographic order (the numbering or_mesh_create enumerates).
+ * Returns 0, or 1 on a bad row or allocation failure. */
+int or_apply_A_rows(int Ex, int Ey, int Ez, int N, double rho, uint64_t seed, unsigned faces, int screen,
+                    double lambda, const double *x, int64_t nrows, const int64_t *rows, double *out)
+{
+    int n = N + 1;
+    int64_t n3 = (int64_t)n * n * n;
+    int64_t NX = (int64_t)N * Ex + 1, NY = (int64_t)N * Ey + 1, NZ = (int64_t)N * Ez + 1;
+    int x0 = faces & 1u ? 1 : 0, x1 = faces & 2u ? 1 : 0, y0 = faces & 4u ? 1 : 0, y1 = faces & 8u ? 1 : 0;
+    int z0 = faces & 16u ? 1 : 0, z1 = faces & 32u ? 1 : 0;
+    int64_t NXu = NX - x0 - x1, NYu = NY - y0 - y1, NZu = NZ - z0 - z1;
+    double *xi = malloc(sizeof(double) * n), *w = malloc(sizeof(double) * n), *D = malloc(sizeof(double) * n * n);
+    double *G = malloc(sizeof(double) * 6 * n3), *Jw = malloc(sizeof(double) * n3);
+    double *wk = malloc(sizeof(double) * 5 * n3);
+    int32_t *l2g = malloc(sizeof(int32_t) * n3);
+    int err = 0;
+    if (!xi || !w || !D || !G || !Jw || !wk || !l2g) err = 1;
+    if (!err) {
+        or_gll(N, xi, w);
+        or_deriv(N, xi, D);
+    }
+    for (int64_t r = 0; r < nrows && !err; r++) {
+        int64_t g = rows[r];
+        if (g < 0 || g >= NXu * NYu * NZu) { err = 1; break; }
+        int64_t I = g % NXu + x0, J = (g / NXu) % NYu + y0, K = g / (NXu * NYu) + z0;
+        int exs[2], eys[2], ezs[2], nx = 0, ny = 0, nz = 0;
+        /* elements containing lattice coordinate I along x, ascending */
+        if (I % N == 0 && I / N - 1 >= 0) exs[nx++] = (int)(I / N - 1);
+        if (I / N < Ex) exs[nx++] = (int)(I / N);
+        if (J % N == 0 && J / N - 1 >= 0) eys[ny++] = (int)(J / N - 1);
+        if (J / N < Ey) eys[ny++] = (int)(J / N);
+        if (K % N == 0 && K / N - 1 >= 0) ezs[nz++] = (int)(K / N - 1);
+        if (K / N < Ez) ezs[nz++] = (int)(K / N);
+        double y = 0.0, mt[8];
+        int nm = 0;
+        for (int cz = 0; cz < nz; cz++)
+            for (int cy = 0; cy < ny; cy++)
+                for (int cx = 0; cx < nx; cx++) {
+                    int ex = exs[cx], ey = eys[cy], ez = ezs[cz];
+                    double Ve[2][2][2][3];
+                    element_vertices(Ex, Ey, Ez, rho, seed, ex, ey, ez, Ve);
+                    element_geometry(N, xi, w, Ve, G, Jw, NULL);
+                    for (int k = 0; k < n; k++)
+                        for (int j = 0; j < n; j++)
+                            for (int i = 0; i < n; i++) {
+                                int64_t Il = (int64_t)N * ex + i, Jl = (int64_t)N * ey + j, Kl = (int64_t)N * ez + k;
+                                int masked = (x0 && Il == 0) || (x1 && Il == NX - 1) || (y0 && Jl == 0) ||
+                                             (y1 && Jl == NY - 1) || (z0 && Kl == 0) || (z1 && Kl == NZ - 1);
+                                l2g[(k * n + j) * n + i] =
+                                    masked ? -1 : (int32_t)((Il - x0) + NXu * ((Jl - y0) + NYu * (Kl - z0)));
+                            }
+                    local_stiffness_ptr(n, D, l2g, G, x, wk, wk + n3, wk + 2 * n3, wk + 3 * n3, wk + 4 * n3);
+                    int q = (int)(((K - (int64_t)N * ez) * n + (J - (int64_t)N * ey)) * n + (I - (int64_t)N * ex));
+                    y += wk[q];
+                    mt[nm++] = lambda * (Jw[q] * x[g]);
+                }
+        /* screening after all element sums, copy by copy, as or_apply_A adds it */
+        if (screen == 0) y += lambda * x[g];
+        else
+            for (int c = 0; c < nm; c++) y += mt[c];
+        out[r] = y;
+    }
+    free(xi); free(w); free(D); free(G); free(Jw); free(wk); free(l2g);
+    return err;
 }

@@ -66,6 +66,8 @@ def _load():
         lib.or_cg.argtypes = [P, C.c_int, C.c_double, P, P, C.c_double, C.c_int,
                               P, P, P]
         lib.or_num_threads.restype = C.c_int
+        lib.or_apply_A_rows.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint,
+                                        C.c_int, C.c_double, P, C.c_int64, P, P]
         _lib = lib
     return _lib
 
@@ -97,6 +99,18 @@ def deriv(N: int) -> np.ndarray:
     D = np.zeros((N + 1, N + 1))
     _load().or_deriv(N, _ptr(xi), _ptr(D))
     return D
+
+
+def apply_A_rows(dims, N, rho, seed, x, rows, lam, screen=0, faces=0x3F):
+    """(A x)[rows] for the box, built element by element for the requested DOFs
+    only (no full mesh): for checks at sizes the full oracle cannot hold."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros(len(rows))
+    if _load().or_apply_A_rows(dims[0], dims[1], dims[2], N, rho, seed, faces, screen, lam, _ptr(x),
+                               len(rows), _ptr(rows), _ptr(out)) != 0:
+        raise ValueError("bad row or allocation failure")
+    return out
 
 
 def num_threads() -> int:

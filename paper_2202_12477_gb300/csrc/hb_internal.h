@@ -33,6 +33,8 @@ void hb_clear_error();
 // Counts one kernel launch; with timing enabled also records a CUDA event pair
 // around it on its stream (see hb_profile_* in the C header).
 void hb_count_launch();
+void hb_count_launches(unsigned long long k);
+bool hb_profiling_on();
 struct hb_prof_scope {
     cudaStream_t stream;
     cudaEvent_t stop;
@@ -95,6 +97,17 @@ struct hb_mesh {
     int32_t *scols;     // [nnz_s] e * surf_count + surface index, ascending
     double *ax_partials;  // [max element-kernel blocks] per-block partials of x.y
     int64_t n_ax_partials;
+    // captured runs of CG iterations (replayed while the key matches)
+    cudaStream_t cg_stream;
+    cudaEvent_t cg_ev[2];
+    struct cg_graph {
+        cudaGraphExec_t exec;
+        const void *x, *r, *p, *Ap;
+        const hb_cg_state *st;
+        int prec, screen, count, variant;
+        double lambda;
+        unsigned long long launches;  // kernels per replay
+    } graphs[2];  // [0] FP64 runs, [1] FP32 inner runs
 };
 
 // Reference element data computed on the host for every degree 1..15 (GLL

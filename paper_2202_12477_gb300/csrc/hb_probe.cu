@@ -1,0 +1,136 @@
+// Hardware probes used to calibrate the roofline (hipBone, arXiv 2202.12477,
+// Sec. 4.1: the empirical streaming rate B of an 8-read / 1-write kernel).
+//
+// HB_PROBE_STREAM81_FP   each thread reads 8 values and writes their sum (the
+//                        paper's calibration kernel; in FP64 on GB300 the 7
+//                        adds per output cost more than the memory traffic)
+// HB_PROBE_STREAM81_BITS the same traffic, combining the 8 words with XOR
+//                        (integer pipe): the memory rate alone
+// HB_PROBE_COPY          16-byte vector copy (read + write bytes)
+// HB_PROBE_FMA           independent FMA chains: the arithmetic peak
+#include <vector>
+
+#include "hb_internal.h"
+
+namespace {
+
+template <typename T>
+__global__ void probe_stream81_fp(const T *__restrict__ in, T *__restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T s = in[i];
+#pragma unroll
+        for (int q = 1; q < 8; q++) s += in[i + q * n];
+        out[i] = s;
+    }
+}
+
+template <typename U>
+__global__ void probe_stream81_bits(const U *__restrict__ in, U *__restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        U s = in[i];
+#pragma unroll
+        for (int q = 1; q < 8; q++) s ^= in[i + q * n];
+        out[i] = s;
+    }
+}
+
+__global__ void probe_copy(const double2 *__restrict__ in, double2 *__restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i];
+}
+
+template <typename T>
+__global__ void probe_fma(T *out, int iters, T b, T c)
+{
+    T a[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) a[q] = (T)(threadIdx.x + q) * (T)1e-7;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) a[q] = fma(a[q], b, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) s += a[q];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int reps, double *rate)
+{
+    hb_clear_error();
+    if (!rate || reps < 1 || (prec != HB_F64 && prec != HB_F32)) { hb_set_error("bad argument"); return HB_ERR_ARG; }
+    int dev = 0, sms = 0;
+    HB_TRY_CUDA(cudaGetDevice(&dev));
+    HB_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = sms * 16, threads = 256;
+    const size_t esz = prec == HB_F64 ? 8 : 4;
+    void *buf = nullptr;
+    size_t alloc = bytes;
+    if (kind == HB_PROBE_FMA) alloc = (size_t)grid * threads * esz;
+    if (alloc < 4096) alloc = 4096;
+    HB_TRY_CUDA(cudaMalloc(&buf, alloc));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t e = cudaMemset(buf, 0, alloc);
+    double work = 0.0;  // bytes or flops per launch
+    auto launch = [&]() {
+        if (kind == HB_PROBE_STREAM81_FP || kind == HB_PROBE_STREAM81_BITS) {
+            const int64_t n = (int64_t)(alloc / (9 * esz));
+            work = 9.0 * n * esz;
+            if (kind == HB_PROBE_STREAM81_FP) {
+                if (prec == HB_F64)
+                    probe_stream81_fp<double><<<grid, threads>>>((const double *)buf, (double *)buf + 8 * n, n);
+                else
+                    probe_stream81_fp<float><<<grid, threads>>>((const float *)buf, (float *)buf + 8 * n, n);
+            } else {
+                if (prec == HB_F64)
+                    probe_stream81_bits<unsigned long long><<<grid, threads>>>(
+                        (const unsigned long long *)buf, (unsigned long long *)buf + 8 * n, n);
+                else
+                    probe_stream81_bits<unsigned><<<grid, threads>>>((const unsigned *)buf, (unsigned *)buf + 8 * n,
+                                                                   n);
+            }
+        } else if (kind == HB_PROBE_COPY) {
+            const int64_t n = (int64_t)(alloc / 32);  // double2 elements in each half
+            work = 2.0 * n * 16;
+            probe_copy<<<grid, threads>>>((const double2 *)buf, (double2 *)buf + n, n);
+        } else {
+            const int iters = 4096;
+            work = 2.0 * 8 * iters * (double)grid * threads;
+            if (prec == HB_F64)
+                probe_fma<double><<<grid, threads>>>((double *)buf, iters, 0.9999999, 1e-9);
+            else
+                probe_fma<float><<<grid, threads>>>((float *)buf, iters, 0.9999999f, 1e-9f);
+        }
+        hb_count_launch();
+    };
+    float best = 1e30f;
+    if (kind < HB_PROBE_STREAM81_FP || kind > HB_PROBE_FMA) {
+        hb_set_error("unknown probe kind %d", kind);
+        e = cudaErrorInvalidValue;
+    }
+    for (int r = 0; r < reps + 1 && e == cudaSuccess; r++) {
+        cudaEventRecord(e0);
+        launch();
+        cudaEventRecord(e1);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0 && ms < best) best = ms;  // first launch is a warm-up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        if (!hb_last_error()[0]) hb_set_error("probe: %s", cudaGetErrorString(e));
+        return e == cudaErrorInvalidValue ? HB_ERR_ARG : HB_ERR_CUDA;
+    }
+    *rate = work / (best * 1e-3) / 1e9;  // GB/s or GFLOP/s
+    return HB_OK;
+}

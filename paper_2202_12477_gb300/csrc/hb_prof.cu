@@ -40,6 +40,8 @@ std::pair<cudaEvent_t, cudaEvent_t> take_pair()
 }  // namespace
 
 void hb_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void hb_count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+bool hb_profiling_on() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
 
 hb_prof_scope::hb_prof_scope(const char *name, cudaStream_t s) : stream(s), stop(nullptr)
 {

@@ -617,6 +617,11 @@ extern "C" hb_status hb_mesh_destroy(hb_mesh *m)
     cudaFree(m->srowptr);
     cudaFree(m->scols);
     cudaFree(m->ax_partials);
+    for (auto &g : m->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (m->cg_stream) cudaStreamDestroy(m->cg_stream);
+    if (m->cg_ev[0]) cudaEventDestroy(m->cg_ev[0]);
+    if (m->cg_ev[1]) cudaEventDestroy(m->cg_ev[1]);
     if (m->state_host) cudaFreeHost(m->state_host);
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);

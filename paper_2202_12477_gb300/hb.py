@@ -97,6 +97,7 @@ _SIGS = [
     ("hb_get_kernel_variant", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     ("hb_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
                               C.POINTER(C.c_double), C.c_void_p]),
+    ("hb_probe", C.c_int, [C.c_int, C.c_int, C.c_size_t, C.c_int, C.POINTER(C.c_double)]),
     ("hb_kernel_launches", C.c_ulonglong, []),
     ("hb_profile_enable", C.c_int, [C.c_int]),
     ("hb_profile_reset", C.c_int, []),
@@ -207,6 +208,16 @@ def hb_autotune(h, prec, screen=HB_SCREEN_IDENTITY, lam=0.1, reps=5, stream=None
     ms = (C.c_double * 8)(*([-1.0] * 8))
     _check(lib().hb_autotune(h, prec, screen, lam, reps, C.byref(best), ms, _stream_ptr(stream)))
     return best.value, {v: ms[v] for v in VARIANTS if ms[v] >= 0}
+
+
+HB_PROBE_STREAM81_FP, HB_PROBE_STREAM81_BITS, HB_PROBE_COPY, HB_PROBE_FMA = 0, 1, 2, 3
+
+
+def hb_probe(kind, prec=HB_F64, nbytes=4 << 30, reps=5) -> float:
+    """Best rate of a calibration probe: GB/s (stream, copy) or GFLOP/s (FMA)."""
+    r = C.c_double(0.0)
+    _check(lib().hb_probe(kind, prec, nbytes, reps, C.byref(r)))
+    return r.value
 
 
 def hb_kernel_launches() -> int:

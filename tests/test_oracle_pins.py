@@ -415,3 +415,18 @@ def test_manufactured_solution_algebraic_rate():
         errs.append(np.abs(x[l2g[mask]] - u).max())
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert (rates > 2.5).all(), (errs, rates)
+
+
+@pytest.mark.parametrize("dims,N,rho,lam,screen,faces", [((3, 2, 2), 3, 0.2, 0.1, 0, 0x3F),
+                                                         ((2, 3, 2), 5, 0.25, 0.7, 1, 0x3F),
+                                                         ((2, 2, 2), 2, 0.1, 0.0, 0, 0x15),
+                                                         ((3, 1, 2), 7, 0.1, 0.3, 1, 0x00)])
+def test_sampled_rows_equal_full_operator(dims, N, rho, lam, screen, faces):
+    """The row-by-row evaluation (used at sizes the full oracle cannot hold)
+    gives exactly the full oracle's rows: same elements, same summation order."""
+    m = orc.Mesh(*dims, N, rho=rho, seed=6, faces=faces)
+    x = np.random.default_rng(3).standard_normal(m.n_global)
+    y = m.apply_A(x, lam, screen)
+    rows = np.arange(m.n_global)
+    yr = orc.apply_A_rows(dims, N, rho, 6, x, rows, lam, screen, faces)
+    np.testing.assert_array_equal(yr, y)
