@@ -262,6 +262,11 @@ def run_gb300(args, rank, world, local):
 
     pk = peaks()
     ax = kern["ax_local"]
+    # DRAM bytes per local node of this kernel from one ncu capture of the same
+    # kernel on a smaller box (profiles/ax_pencil_f64_N7_32x32x30_ncu.md:
+    # 928.6 MB read + 89.5 MB written for 15,728,640 local nodes), scaled to
+    # this launch by local nodes; only valid for the kernel that was captured.
+    traffic = 64.73 * NL if (N == 7 and variant == 3) else None
     ax_flops = acc.op_local_flops(E, N)
     ax_bytes = acc.ax_local_bytes(NG, NL, 8)
     achieved_tf = ax_flops / (ax["ms_avg"] * 1e-3) / 1e12
@@ -289,7 +294,8 @@ def run_gb300(args, rank, world, local):
                      "peak": pk["fp64_tflops"], "unit": "TFLOP/s", "frac": achieved_tf / pk["fp64_tflops"],
                      "peak_src": "derived: 2 FP64 FMA/clk/SM (measured probe) x 152 SMs x 2070 MHz",
                      "flops_per_launch": ax_flops, "ms_per_launch": ax["ms_avg"],
-                     "traffic": None,
+                     "traffic": traffic,
+                     "traffic_note": "ncu dram bytes (read+write) per launch, scaled from a 32x32x30 capture",
                      "hbm_view": {"algorithmic_bytes_per_launch": ax_bytes,
                                   "achieved_gbs": ax_bytes / (ax["ms_avg"] * 1e-3) / 1e9,
                                   "peak_gbs": pk["hbm_gbs"], "peak_src": pk["hbm_src"],
