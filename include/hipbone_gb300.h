@@ -181,6 +181,8 @@ typedef struct {
     int max_it;            /* iteration cap (inner iterations in HB_MIXED) */
     double inner_rtol;     /* HB_MIXED: inner FP32 CG reduces its residual by this */
     int max_outer;         /* HB_MIXED: cap on FP64 defect-correction steps */
+    int precond;           /* 0: none (Algorithm 1, the paper's hipBone); 1: Jacobi,
+                              M = diag(A) (NekBone's diagonal preconditioner, Sec. 3) */
 } hb_cg_opts;
 
 typedef struct {
@@ -191,12 +193,21 @@ typedef struct {
     hb_status status;
 } hb_cg_result;
 
+/* diag(A) for the given screening (the Jacobi preconditioner's M): the sum over
+ * each DOF's copies of the element-matrix diagonal of Dbold^T G^e Dbold, plus
+ * lambda (identity) or lambda M_gg (mass). Written to a HOST buffer of
+ * n_global doubles; synchronises `stream`. */
+hb_status hb_diag_A(hb_mesh *mesh, hb_screen screen, double lambda, double *host_diag, void *stream);
+
 /* Solves A x = b with Algorithm 1 (x holds x0 on entry, the solution on exit;
  * both FP64 device vectors of length n_global). HB_F64 runs Algorithm 1 in FP64.
  * HB_MIXED runs FP64 defect correction: r = b - A x in FP64, an FP32 CG on
  * A d = r to inner_rtol (FP64 dot accumulation), x += d in FP64, until
- * ||b - A x|| <= rtol ||b||. The p.Ap and r.r reductions are fused into the
- * kernels that produce their operands (Sec. 3.5). Synchronises `stream`.
+ * ||b - A x|| <= rtol ||b||. precond = 1 applies the Jacobi preconditioner
+ * diag(A) (z = M^-1 r, alpha = r.z / p.Ap, beta from successive r.z, p = z + beta p;
+ * in HB_MIXED to the inner FP32 CG); the stopping test stays on ||r||. The p.Ap
+ * and r.r reductions are fused into the kernels that produce their operands
+ * (Sec. 3.5). Synchronises `stream`.
  * Returns HB_ERR_BREAKDOWN, HB_ERR_NOT_CONVERGED (rtol > 0 only) or HB_OK;
  * res (may be NULL) receives the counts, residual and device time. */
 hb_status hb_cg_solve(const hb_mesh *mesh, const hb_cg_opts *opts, const double *b,
@@ -214,7 +225,8 @@ hb_status hb_cg_solve(const hb_mesh *mesh, const hb_cg_opts *opts, const double 
  * rounds and queued ones admitted. Every slot runs on fixed grids with its own
  * reductions: a request's result does not depend on which others share the
  * GPU. The right-hand side is hb_fill_rhs kind 0 with the request's seed and
- * x0 = 0. Degrees N = 1..11; opts.prec must be HB_MIXED and opts.rtol > 0. */
+ * x0 = 0. Degrees N = 1..11; opts.prec must be HB_MIXED, opts.rtol > 0 and
+ * opts.precond = 0. */
 typedef struct hb_server hb_server;
 typedef struct {
     size_t mem_budget_bytes;   /* device memory the resident solves may hold */
@@ -257,18 +269,20 @@ double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx);
  *   HB_VARIANT_EVEN_ODD   (with PENCIL) even-odd split of the centro-antisymmetric D:
  *                         n^2/2 + 2n operations per line instead of n^2
  *   HB_VARIANT_EB2        (with PENCIL, N <= 10) two element groups per thread block
+ *   HB_VARIANT_ONE        (with PENCIL | EVEN_ODD) one element per thread block,
+ *                         which spreads small meshes over more SMs
  * The default is PENCIL | EVEN_ODD; hb_autotune measures and picks per mesh. */
-enum { HB_VARIANT_PENCIL = 1, HB_VARIANT_EVEN_ODD = 2, HB_VARIANT_EB2 = 4 };
+enum { HB_VARIANT_PENCIL = 1, HB_VARIANT_EVEN_ODD = 2, HB_VARIANT_EB2 = 4, HB_VARIANT_ONE = 8 };
 hb_status hb_set_kernel_variant(hb_mesh *mesh, hb_precision prec, int variant);
 hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *variant);
 
 /* Autotuner (the paper makes its 3-D / 2-D kernel switch a configurable choice
  * made from measurements, Sec. 3.2; here every variant is timed on the mesh
  * itself). Runs one untimed and `reps` timed applications of A for each
- * variant (0, PENCIL, PENCIL|EVEN_ODD, PENCIL|EB2, PENCIL|EVEN_ODD|EB2) on
- * `stream`, keeps the fastest for `prec` on this mesh and returns it in
- * *best_variant. ms_per_variant (may be NULL) has 8 slots indexed by variant
- * and receives the mean time of each. Allocates two scratch vectors for the
+ * variant (0, PENCIL, PENCIL|EVEN_ODD, PENCIL|EB2, PENCIL|EVEN_ODD|EB2,
+ * PENCIL|EVEN_ODD|ONE) on `stream`, keeps the fastest for `prec` on this mesh
+ * and returns it in *best_variant. ms_per_variant (may be NULL) has 16 slots
+ * indexed by variant and receives the mean time of each. Allocates two scratch vectors for the
  * duration of the call; synchronises `stream`. */
 hb_status hb_autotune(hb_mesh *mesh, hb_precision prec, hb_screen screen, double lambda, int reps,
                       int *best_variant, double *ms_per_variant, void *stream);

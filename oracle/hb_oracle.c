@@ -495,6 +495,51 @@ int or_apply_A(or_mesh *m, int screen, double lambda, const double *x, double *y
     return 0;
 }
 
+/* diag(A): for each DOF the sum over its copies of the element-matrix
+ * diagonal (Dbold^T G^e Dbold)_qq, written out term by term:
+ *   sum_m D[m][i]^2 G_rr(m,j,k) + sum_m D[m][j]^2 G_ss(i,m,k)
+ *   + sum_m D[m][k]^2 G_tt(i,j,m)
+ *   + 2 D[i][i] D[j][j] G_rs + 2 D[i][i] D[k][k] G_rt + 2 D[j][j] D[k][k] G_st,
+ * summed in element order, then + lambda (identity screening) or
+ * + lambda * sum Jw (mass screening). */
+int or_diag_A(const or_mesh *m, int screen, double lambda, double *d)
+{
+    int n = m->n;
+    int64_t n3 = (int64_t)n * n * n;
+    const double *D = m->D;
+    for (int64_t g = 0; g < m->n_global; g++) d[g] = 0.0;
+    for (int64_t e = 0; e < m->E; e++) {
+        const double *G = m->G + 6 * e * n3;
+        for (int k = 0; k < n; k++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) {
+                    int64_t q = e * n3 + (k * n + j) * n + i;
+                    int32_t g = m->l2g[q];
+                    if (g < 0) continue;
+                    double a = 0.0;
+                    for (int p = 0; p < n; p++) {
+                        a += D[p * n + i] * D[p * n + i] * G[6 * ((k * n + j) * n + p) + 0];
+                        a += D[p * n + j] * D[p * n + j] * G[6 * ((k * n + p) * n + i) + 3];
+                        a += D[p * n + k] * D[p * n + k] * G[6 * ((p * n + j) * n + i) + 5];
+                    }
+                    const double *gq = G + 6 * ((k * n + j) * n + i);
+                    a += 2.0 * D[i * n + i] * D[j * n + j] * gq[1];
+                    a += 2.0 * D[i * n + i] * D[k * n + k] * gq[2];
+                    a += 2.0 * D[j * n + j] * D[k * n + k] * gq[4];
+                    d[g] += a;
+                }
+    }
+    if (screen == 0) {
+        for (int64_t g = 0; g < m->n_global; g++) d[g] += lambda;
+    } else {
+        for (int64_t q = 0; q < m->n_local; q++) {
+            int32_t g = m->l2g[q];
+            if (g >= 0) d[g] += lambda * m->Jw[q];
+        }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Right-hand sides                                                    */
 /* ------------------------------------------------------------------ */
@@ -546,21 +591,26 @@ static double dot(int64_t n, const double *a, const double *b)
  * and the solution on exit. Stops when r.r <= rtol^2 b.b (rtol > 0) or after
  * max_it iterations. hist (may be NULL) receives r_j.r_j for j = 0..iters.
  * Returns 0 (done), 2 on breakdown (p.Ap <= 0 or not finite), 1 on no memory. */
-int or_cg(or_mesh *m, int screen, double lambda, const double *b, double *x,
-          double rtol, int max_it, int *iters, double *rel_res, double *hist)
+int or_pcg(or_mesh *m, int screen, double lambda, const double *b, double *x, double rtol, int max_it,
+           int precond, int *iters, double *rel_res, double *hist)
 {
     int64_t ng = m->n_global;
     double *r = (double *)malloc(sizeof(double) * ng);
     double *p = (double *)malloc(sizeof(double) * ng);
     double *Ap = (double *)malloc(sizeof(double) * ng);
-    if (!r || !p || !Ap) { free(r); free(p); free(Ap); return 1; }
+    double *z = (double *)malloc(sizeof(double) * ng);
+    double *dg = precond ? (double *)malloc(sizeof(double) * ng) : NULL;
+    if (!r || !p || !Ap || !z || (precond && !dg)) { free(r); free(p); free(Ap); free(z); free(dg); return 1; }
     int status = 0;
-    /* r_0 = b - A x, p = r */
+    if (precond) or_diag_A(m, screen, lambda, dg);
+    /* r_0 = b - A x, z_0 = M^-1 r_0 (M = diag(A), or I), p = z_0 */
     or_apply_A(m, screen, lambda, x, Ap);
     for (int64_t i = 0; i < ng; i++) r[i] = b[i] - Ap[i];
-    for (int64_t i = 0; i < ng; i++) p[i] = r[i];
+    for (int64_t i = 0; i < ng; i++) z[i] = precond ? r[i] / dg[i] : r[i];
+    for (int64_t i = 0; i < ng; i++) p[i] = z[i];
     double bb = dot(ng, b, b);
     double rr = dot(ng, r, r);
+    double rz = dot(ng, r, z);
     double tol2 = rtol * rtol * bb;
     if (hist) hist[0] = rr;
     int j = 0;
@@ -568,20 +618,29 @@ int or_cg(or_mesh *m, int screen, double lambda, const double *b, double *x,
         or_apply_A(m, screen, lambda, p, Ap);
         double pAp = dot(ng, p, Ap);
         if (!(pAp > 0.0) || !isfinite(pAp)) { status = 2; break; }
-        double alpha = rr / pAp;
+        double alpha = rz / pAp;
         for (int64_t i = 0; i < ng; i++) x[i] = x[i] + alpha * p[i];
         for (int64_t i = 0; i < ng; i++) r[i] = r[i] - alpha * Ap[i];
-        double rr_new = dot(ng, r, r);
-        double beta = rr_new / rr;
-        for (int64_t i = 0; i < ng; i++) p[i] = r[i] + beta * p[i];
-        rr = rr_new;
+        for (int64_t i = 0; i < ng; i++) z[i] = precond ? r[i] / dg[i] : r[i];
+        double rz_new = dot(ng, r, z);
+        double beta = rz_new / rz;
+        for (int64_t i = 0; i < ng; i++) p[i] = z[i] + beta * p[i];
+        rz = rz_new;
+        rr = dot(ng, r, r);
         j++;
         if (hist) hist[j] = rr;
     }
     *iters = j;
     *rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-    free(r); free(p); free(Ap);
+    free(r); free(p); free(Ap); free(z); free(dg);
     return status;
+}
+
+/* Algorithm 1 (no preconditioner). */
+int or_cg(or_mesh *m, int screen, double lambda, const double *b, double *x,
+          double rtol, int max_it, int *iters, double *rel_res, double *hist)
+{
+    return or_pcg(m, screen, lambda, b, x, rtol, max_it, 0, iters, rel_res, hist);
 }
 
 /* Number of threads the parallel element loop uses (1 without OpenMP). */

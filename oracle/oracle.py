@@ -66,6 +66,8 @@ def _load():
         lib.or_cg.argtypes = [P, C.c_int, C.c_double, P, P, C.c_double, C.c_int,
                               P, P, P]
         lib.or_num_threads.restype = C.c_int
+        lib.or_diag_A.argtypes = [P, C.c_int, C.c_double, P]
+        lib.or_pcg.argtypes = [P, C.c_int, C.c_double, P, P, C.c_double, C.c_int, C.c_int, P, P, P]
         lib.or_apply_A_rows.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint,
                                         C.c_int, C.c_double, P, C.c_int64, P, P]
         _lib = lib
@@ -193,15 +195,21 @@ class Mesh:
         _load().or_rhs(self._h, kind, seed, lam, _ptr(b))
         return b
 
-    def cg(self, b, lam, rtol=0.0, max_it=100, screen=0, x0=None, history=False):
-        """Algorithm 1. Returns (x, iters, rel_res, status[, r.r history])."""
+    def diag_A(self, lam: float, screen: int = 0) -> np.ndarray:
+        d = np.zeros(self.n_global)
+        _load().or_diag_A(self._h, screen, lam, _ptr(d))
+        return d
+
+    def cg(self, b, lam, rtol=0.0, max_it=100, screen=0, x0=None, history=False, precond=0):
+        """Algorithm 1 (precond=1: with the Jacobi preconditioner diag(A)).
+        Returns (x, iters, rel_res, status[, r.r history])."""
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros(self.n_global) if x0 is None else np.array(x0, dtype=np.float64)
         it = C.c_int(0)
         rel = C.c_double(0.0)
         hist = np.zeros(max_it + 1)
-        st = _load().or_cg(self._h, screen, lam, _ptr(b), _ptr(x), rtol, max_it,
-                           C.byref(it), C.byref(rel), _ptr(hist))
+        st = _load().or_pcg(self._h, screen, lam, _ptr(b), _ptr(x), rtol, max_it, precond,
+                            C.byref(it), C.byref(rel), _ptr(hist))
         if st == 1:
             raise MemoryError("oracle cg failed")
         out = (x, it.value, rel.value, st)

@@ -349,16 +349,18 @@ namespace hb2 {
 // translation unit), so nothing in it may share a symbol name across units.
 namespace {
 
+// eb_mode: 1 = about 256 threads per block, 2 = twice that many elements
+// (N <= 10), 0 = one element per block (spreads small meshes over more SMs).
 template <int N, bool EO>
-hb_status launch(const pencil_args &A, int eb_mult, cudaStream_t s, int64_t *nblocks_out)
+hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nblocks_out)
 {
     constexpr int n = N + 1, n2 = n * n;
     constexpr int EB1 = n2 >= 256 ? 1 : 256 / n2;
     if (A.E <= 0) return HB_OK;
-    static int attr_set[2][32] = {{0}};
+    static int attr_set[3][32] = {{0}};
     int dev = 0;
     HB_TRY_CUDA(cudaGetDevice(&dev));
-    const int which = eb_mult == 2 && n2 <= 128 ? 1 : 0;
+    const int which = (eb_mode == 2 && n2 <= 128) ? 1 : (eb_mode == 0 ? 2 : 0);
     auto go = [&](auto kern, int EB) -> hb_status {
         const size_t smem = sizeof(T) * 4 * (size_t)EB * pad<N>::size;
         if (dev >= 0 && dev < 32 && !attr_set[which][dev]) {
@@ -374,6 +376,9 @@ hb_status launch(const pencil_args &A, int eb_mult, cudaStream_t s, int64_t *nbl
     };
     if constexpr (n2 <= 128) {
         if (which == 1) return go(ax_pencil_kernel<N, EO, EB1 * 2>, EB1 * 2);
+    }
+    if constexpr (EO && EB1 > 1) {
+        if (which == 2) return go(ax_pencil_kernel<N, EO, 1>, 1);
     }
     return go(ax_pencil_kernel<N, EO, EB1>, EB1);
 }

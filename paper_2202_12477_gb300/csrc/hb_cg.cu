@@ -61,18 +61,18 @@ __global__ void __launch_bounds__(HB_RED_THREADS)
 
 __global__ void __launch_bounds__(HB_RED_THREADS)
     cg_init_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
-                   double *__restrict__ p, int64_t n, double rtol, int max_it, double *partials, unsigned *counter,
-                   hb_cg_state *st)
+                   double *__restrict__ p, const double *__restrict__ inv_d, int64_t n, double rtol, int max_it,
+                   double *partials, unsigned *counter, hb_cg_state *st)
 {
-    cg_init_body(b, Ax, r, p, n, rtol, max_it, partials, counter, st);
+    cg_init_body(b, Ax, r, p, inv_d, n, rtol, max_it, partials, counter, st);
 }
 
-template <typename T>
+template <typename T, bool PREC>
 __global__ void __launch_bounds__(HB_RED_THREADS)
-    cg_update_r_kernel(T *__restrict__ r, const T *__restrict__ Ap, int64_t n, double *partials, unsigned *counter,
-                       hb_cg_state *st)
+    cg_update_r_kernel(T *__restrict__ r, const T *__restrict__ Ap, T *__restrict__ z, const T *__restrict__ inv_d,
+                       int64_t n, double *partials, unsigned *counter, hb_cg_state *st)
 {
-    cg_update_r_body<T>(r, Ap, n, partials, counter, st);
+    cg_update_r_body<T, PREC>(r, Ap, z, inv_d, n, partials, counter, st);
 }
 
 template <typename T>
@@ -92,10 +92,10 @@ __global__ void __launch_bounds__(HB_RED_THREADS)
 
 __global__ void __launch_bounds__(HB_RED_THREADS)
     inner_init_kernel(const double *__restrict__ r, float *__restrict__ r32, float *__restrict__ p32,
-                      float *__restrict__ d32, int64_t n, double rtol_in, int max_it, double *partials,
-                      unsigned *counter, const hb_cg_state *outer, hb_cg_state *st)
+                      float *__restrict__ d32, const float *__restrict__ inv_d, int64_t n, double rtol_in,
+                      int max_it, double *partials, unsigned *counter, const hb_cg_state *outer, hb_cg_state *st)
 {
-    inner_init_body(r, r32, p32, d32, n, rtol_in, max_it, partials, counter, outer, st);
+    inner_init_body(r, r32, p32, d32, inv_d, n, rtol_in, max_it, partials, counter, outer, st);
 }
 
 __global__ void update_x_kernel(double *__restrict__ x, const float *__restrict__ d32, int64_t n,
@@ -187,7 +187,7 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
         return HB_ERR_ARG;
     }
     const int v = m->variant[prec == HB_F64 ? 0 : 1];
-    const int eo = (v & HB_VAR_EO) ? 1 : 0, ebm = (v & HB_VAR_EB2) ? 2 : 1;
+    const int eo = (v & HB_VAR_EO) ? 1 : 0, ebm = (v & HB_VAR_ONE) ? 0 : ((v & HB_VAR_EB2) ? 2 : 1);
     hb_status r;
     if (!(v & HB_VAR_PENCIL)) {
         if (prec == HB_F64) {
@@ -245,7 +245,7 @@ extern "C" hb_status hb_set_kernel_variant(hb_mesh *m, hb_precision prec, int va
     hb_clear_error();
     if (!m) { hb_set_error("null mesh"); return HB_ERR_ARG; }
     if (prec != HB_F64 && prec != HB_F32) { hb_set_error("variant precision must be HB_F64 or HB_F32"); return HB_ERR_ARG; }
-    if (variant < 0 || variant > HB_VAR_MAX || (!(variant & HB_VAR_PENCIL) && variant != 0)) {
+    if (!hb_valid_variant(variant)) {
         hb_set_error("invalid kernel variant %d", variant);
         return HB_ERR_ARG;
     }
@@ -331,7 +331,7 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
         return HB_ERR_NOMEM;
     }
     const int candidates[] = {0, HB_VAR_PENCIL, HB_VAR_PENCIL | HB_VAR_EO, HB_VAR_PENCIL | HB_VAR_EB2,
-                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_EB2};
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_EB2, HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE};
     const int saved = m->variant[pi];
     int best = saved;
     float best_ms = 1e30f;
@@ -373,7 +373,7 @@ static inline int64_t cg_stride(int64_t n) { return (n + 63) / 64 * 64; }
 // Workspace vectors for the solvers, grown on demand (FP64 r, p, Ap; FP32 r, p, Ap, d).
 static hb_status cg_workspace(hb_mesh *m)
 {
-    const size_t need = (size_t)cg_stride(m->n_global) * (3 * sizeof(double) + 4 * sizeof(float)) + 256;
+    const size_t need = (size_t)cg_stride(m->n_global) * (4 * sizeof(double) + 5 * sizeof(float)) + 256;
     if (m->cg_vec_bytes >= need) return HB_OK;
     if (m->cg_vec) cudaFree(m->cg_vec);
     m->cg_vec = nullptr;
@@ -383,10 +383,11 @@ static hb_status cg_workspace(hb_mesh *m)
     return HB_OK;
 }
 
-// Enqueues `count` iterations of Algorithm 1 on the vectors (x, r, p, Ap).
+// Enqueues `count` iterations of Algorithm 1 on the vectors (x, r, p, Ap);
+// with inv_d (the Jacobi preconditioner) z = M^-1 r is kept in z.
 template <typename T>
 static hb_status cg_iterations(const hb_mesh *m, hb_precision prec, int screen, double lambda, T *x, T *r, T *p,
-                               T *Ap, hb_cg_state *st, int count, cudaStream_t s)
+                               T *Ap, T *z, const T *inv_d, hb_cg_state *st, int count, cudaStream_t s)
 {
     const int64_t n = m->n_global;
     const int grid = red_grid(n);
@@ -395,12 +396,17 @@ static hb_status cg_iterations(const hb_mesh *m, hb_precision prec, int screen, 
         if (rs != HB_OK) return rs;
         {
             hb_prof_scope prof("cg_update_r", s);
-            cg_update_r_kernel<T><<<grid, HB_RED_THREADS, 0, s>>>(r, Ap, n, m->partials, m->counters + 2, st);
+            if (inv_d)
+                cg_update_r_kernel<T, true><<<grid, HB_RED_THREADS, 0, s>>>(r, Ap, z, inv_d, n, m->partials,
+                                                                            m->counters + 2, st);
+            else
+                cg_update_r_kernel<T, false><<<grid, HB_RED_THREADS, 0, s>>>(r, Ap, nullptr, nullptr, n, m->partials,
+                                                                             m->counters + 2, st);
             HB_CHECK_LAUNCH();
         }
         {
             hb_prof_scope prof("cg_update_xp", s);
-            cg_update_xp_kernel<T><<<grid, HB_RED_THREADS, 0, s>>>(x, p, r, n, m->counters + 3, st);
+            cg_update_xp_kernel<T><<<grid, HB_RED_THREADS, 0, s>>>(x, p, inv_d ? z : r, n, m->counters + 3, st);
             HB_CHECK_LAUNCH();
         }
     }
@@ -414,7 +420,7 @@ static hb_status cg_iterations(const hb_mesh *m, hb_precision prec, int screen, 
 // per-kernel timing is on (its event pairs are not captured).
 template <typename T>
 static hb_status cg_iterations_graph(const hb_mesh *mc, hb_precision prec, int screen, double lambda, T *x, T *r,
-                                     T *p, T *Ap, hb_cg_state *st, int count, cudaStream_t s)
+                                     T *p, T *Ap, T *z, const T *inv_d, hb_cg_state *st, int count, cudaStream_t s)
 {
     hb_mesh *m = const_cast<hb_mesh *>(mc);
     const int gi = prec == HB_F64 ? 0 : 1;
@@ -425,14 +431,15 @@ static hb_status cg_iterations_graph(const hb_mesh *mc, hb_precision prec, int s
         HB_TRY_CUDA(cudaEventCreateWithFlags(&m->cg_ev[0], cudaEventDisableTiming));
         HB_TRY_CUDA(cudaEventCreateWithFlags(&m->cg_ev[1], cudaEventDisableTiming));
     }
-    const bool hit = G.exec && G.x == x && G.r == r && G.p == p && G.Ap == Ap && G.st == st && G.prec == prec &&
+    const bool hit = G.exec && G.x == x && G.r == r && G.p == p && G.Ap == Ap && G.z == z && G.inv_d == inv_d &&
+                     G.st == st && G.prec == prec &&
                      G.screen == screen && G.count == count && G.variant == variant && G.lambda == lambda;
     if (!hit) {
         if (G.exec) cudaGraphExecDestroy(G.exec);
         G.exec = nullptr;
         const unsigned long long before = hb_kernel_launches();
         HB_TRY_CUDA(cudaStreamBeginCapture(m->cg_stream, cudaStreamCaptureModeThreadLocal));
-        hb_status rs = cg_iterations<T>(m, prec, screen, lambda, x, r, p, Ap, st, count, m->cg_stream);
+        hb_status rs = cg_iterations<T>(m, prec, screen, lambda, x, r, p, Ap, z, inv_d, st, count, m->cg_stream);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(m->cg_stream, &g);
         if (rs != HB_OK) {
@@ -446,7 +453,7 @@ static hb_status cg_iterations_graph(const hb_mesh *mc, hb_precision prec, int s
             return HB_ERR_CUDA;
         }
         G.launches = hb_kernel_launches() - before;
-        G.x = x; G.r = r; G.p = p; G.Ap = Ap; G.st = st;
+        G.x = x; G.r = r; G.p = p; G.Ap = Ap; G.z = z; G.inv_d = inv_d; G.st = st;
         G.prec = prec; G.screen = screen; G.count = count; G.variant = variant; G.lambda = lambda;
         // the captured launches were counted once at capture, for this first replay
     } else {
@@ -463,7 +470,7 @@ static hb_status cg_iterations_graph(const hb_mesh *mc, hb_precision prec, int s
 // Runs iterations until the device state says stop; returns the final state.
 template <typename T>
 static hb_status cg_drive(const hb_mesh *m, hb_precision prec, int screen, double lambda, T *x, T *r, T *p, T *Ap,
-                          hb_cg_state *st, int max_it, cudaStream_t s, hb_cg_state *out)
+                          T *z, const T *inv_d, hb_cg_state *st, int max_it, cudaStream_t s, hb_cg_state *out)
 {
     int done = 0;
     const int chunk_first = 25;
@@ -472,8 +479,9 @@ static hb_status cg_drive(const hb_mesh *m, hb_precision prec, int screen, doubl
     while (m->state_host->run && done < max_it) {
         int count = max_it - done;
         if (count > chunk_first && m->state_host->tol2 > 0.0) count = chunk_first;
-        hb_status rs = hb_profiling_on() ? cg_iterations<T>(m, prec, screen, lambda, x, r, p, Ap, st, count, s)
-                                         : cg_iterations_graph<T>(m, prec, screen, lambda, x, r, p, Ap, st, count, s);
+        hb_status rs = hb_profiling_on()
+                           ? cg_iterations<T>(m, prec, screen, lambda, x, r, p, Ap, z, inv_d, st, count, s)
+                           : cg_iterations_graph<T>(m, prec, screen, lambda, x, r, p, Ap, z, inv_d, st, count, s);
         if (rs != HB_OK) return rs;
         done += count;
         HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
@@ -492,6 +500,7 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
     if (!valid_screen(o->screen)) { hb_set_error("bad screen mode"); return HB_ERR_ARG; }
     if (o->prec != HB_F64 && o->prec != HB_MIXED) { hb_set_error("hb_cg_solve takes HB_F64 or HB_MIXED"); return HB_ERR_ARG; }
     if (o->max_it < 0 || !(o->rtol >= 0.0)) { hb_set_error("bad max_it or rtol"); return HB_ERR_ARG; }
+    if (o->precond != 0 && o->precond != 1) { hb_set_error("precond must be 0 or 1"); return HB_ERR_ARG; }
     if (o->prec == HB_MIXED && (!m->geo32 || !m->mdiag32)) { hb_set_error("HB_MIXED needs keep_fp32_copy"); return HB_ERR_ARG; }
     hb_device_guard dg(m->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -505,8 +514,14 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
     hb_status rs = cg_workspace(m);
     if (rs != HB_OK) return rs;
     const int64_t ns = cg_stride(n);
-    double *r = (double *)m->cg_vec, *p = r + ns, *Ap = p + ns;
-    float *r32 = (float *)(Ap + ns), *p32 = r32 + ns, *Ap32 = p32 + ns, *d32 = Ap32 + ns;
+    double *r = (double *)m->cg_vec, *p = r + ns, *Ap = p + ns, *z = Ap + ns;
+    float *r32 = (float *)(z + ns), *p32 = r32 + ns, *Ap32 = p32 + ns, *d32 = Ap32 + ns, *z32 = d32 + ns;
+    if (o->precond) {
+        rs = hb_mesh_inv_diag(m, o->screen, o->lambda, s);
+        if (rs != HB_OK) return rs;
+    }
+    const double *inv_d = o->precond ? m->inv_diag : nullptr;
+    const float *inv_d32 = o->precond ? m->inv_diag32 : nullptr;
     const int grid = red_grid(n);
     hb_cg_state *st = m->state, *st_in = m->state + 1;
     HB_TRY_CUDA(cudaEventRecord(m->ev0, s));
@@ -516,15 +531,15 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
         rs = hb_apply_A_impl(m, HB_F64, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
         if (rs != HB_OK) return rs;
         hb_count_launch();
-        cg_init_kernel<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, p, n, o->rtol, o->max_it, m->partials,
+        cg_init_kernel<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, p, inv_d, n, o->rtol, o->max_it, m->partials,
                                                        m->counters + 2, st);
         HB_CHECK_LAUNCH();
-        rs = cg_drive<double>(m, HB_F64, o->screen, o->lambda, x, r, p, Ap, st, o->max_it, s, &fin);
+        rs = cg_drive<double>(m, HB_F64, o->screen, o->lambda, x, r, p, Ap, z, inv_d, st, o->max_it, s, &fin);
         if (rs != HB_OK) return rs;
         R.iters = fin.it;
-        R.rel_res = fin.bb > 0.0 ? sqrt(fin.rr / fin.bb) : 0.0;
+        R.rel_res = fin.bb > 0.0 ? sqrt(fin.res2 / fin.bb) : 0.0;
         if (fin.status == HB_ERR_BREAKDOWN) R.status = HB_ERR_BREAKDOWN;
-        else if (o->rtol > 0.0 && fin.rr > fin.tol2) R.status = HB_ERR_NOT_CONVERGED;
+        else if (o->rtol > 0.0 && fin.res2 > fin.tol2) R.status = HB_ERR_NOT_CONVERGED;
     } else {
         const double rtol_in = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-4;
         const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
@@ -544,11 +559,12 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
             if (bb == 0.0 || rr <= o->rtol * o->rtol * bb) break;
             if (outer >= max_outer || used >= o->max_it) { R.status = HB_ERR_NOT_CONVERGED; break; }
             hb_count_launch();
-            inner_init_kernel<<<grid, HB_RED_THREADS, 0, s>>>(r, r32, p32, d32, n, rtol_in, o->max_it - used,
-                                                              m->partials, m->counters + 2, st, st_in);
+            inner_init_kernel<<<grid, HB_RED_THREADS, 0, s>>>(r, r32, p32, d32, inv_d32, n, rtol_in,
+                                                              o->max_it - used, m->partials, m->counters + 2, st,
+                                                              st_in);
             HB_CHECK_LAUNCH();
-            rs = cg_drive<float>(m, HB_F32, o->screen, o->lambda, d32, r32, p32, Ap32, st_in, o->max_it - used, s,
-                                 &fin);
+            rs = cg_drive<float>(m, HB_F32, o->screen, o->lambda, d32, r32, p32, Ap32, z32, inv_d32, st_in,
+                                 o->max_it - used, s, &fin);
             if (rs != HB_OK) return rs;
             used += fin.it;
             outer++;

@@ -11,6 +11,7 @@
 
 #define HB_MAX_N 15
 #define HB_RED_BLOCKS 1216  // fixed grid of every reduction kernel (8 x 152 SMs)
+#define HB_RED_MAXV 4       // values one grid reduction may carry (rows of the partials buffer)
 #define HB_RED_THREADS 256
 
 // ---------------------------------------------------------------- errors
@@ -48,8 +49,9 @@ struct hb_prof_scope {
 // host. `run` says whether the current iteration does any work; kernels of a
 // finished solve return at once, so a captured run of iterations may overshoot.
 struct hb_cg_state {
-    double rr;        // r_j . r_j
-    double rr_new;    // r_{j+1} . r_{j+1}
+    double rr;        // r_j . z_j (z = M^-1 r; r_j . r_j without a preconditioner): alpha's numerator
+    double rr_new;    // r_{j+1} . z_{j+1}
+    double res2;      // r_j . r_j, for the stopping test
     double pAp;       // p . A p
     double alpha, beta;
     double tol2;      // rtol^2 b.b
@@ -79,7 +81,7 @@ struct hb_mesh {
     float *mdiag32;
     void *yL;           // [n_local] doubles: element-local operator output
     // workspace for reductions and CG
-    double *partials;   // [2 * HB_RED_BLOCKS]
+    double *partials;   // [HB_RED_MAXV * HB_RED_BLOCKS]
     unsigned *counters; // [4]
     hb_cg_state *state; // device CG states [4]: 0 outer/FP64, 1 inner/dot
     hb_cg_state *state_host;  // pinned mirror
@@ -89,6 +91,12 @@ struct hb_mesh {
     size_t device_bytes;
     cudaEvent_t ev0, ev1;
     int variant[2];     // element-kernel variant per precision (HB_F64, HB_F32)
+    // Jacobi preconditioner: 1 / diag(A) for the (screen, lambda) it was built for
+    double *inv_diag;
+    float *inv_diag32;
+    int diag_screen;
+    double diag_lambda;
+    int diag_valid;
     // Z^T restricted to DOFs with a copy on an element surface (the pencil
     // kernels finish element-interior DOFs themselves)
     int64_t nsr, nnz_s;
@@ -102,7 +110,7 @@ struct hb_mesh {
     cudaEvent_t cg_ev[2];
     struct cg_graph {
         cudaGraphExec_t exec;
-        const void *x, *r, *p, *Ap;
+        const void *x, *r, *p, *Ap, *z, *inv_d;
         const hb_cg_state *st;
         int prec, screen, count, variant;
         double lambda;
@@ -136,8 +144,16 @@ hb_status hb_ax2_upload_f64(const double *D_all);
 hb_status hb_ax2_upload_f32(const double *D_all);
 
 // Element-kernel variants (bit flags): v1 = 0; HB_VAR_PENCIL = pencil kernel;
-// HB_VAR_EO = even-odd split (pencil only); HB_VAR_EB2 = two element groups per block.
-enum { HB_VAR_PENCIL = 1, HB_VAR_EO = 2, HB_VAR_EB2 = 4, HB_VAR_MAX = 7 };
+// HB_VAR_EO = even-odd split (pencil only); HB_VAR_EB2 = two element groups per
+// block; HB_VAR_ONE = one element per block (with PENCIL | EO only).
+enum { HB_VAR_PENCIL = 1, HB_VAR_EO = 2, HB_VAR_EB2 = 4, HB_VAR_ONE = 8, HB_VAR_MAX = 15 };
+static inline bool hb_valid_variant(int v)
+{
+    if (v == 0) return true;
+    if (v < 0 || v > HB_VAR_MAX || !(v & HB_VAR_PENCIL)) return false;
+    if (v & HB_VAR_ONE) return (v & HB_VAR_EO) && !(v & HB_VAR_EB2);
+    return true;
+}
 
 
 // y = Z^T y_L + lambda (x or M x); optional fused x.y into st->pAp (and the
@@ -151,6 +167,10 @@ hb_status hb_launch_assemble_f32(const hb_mesh *m, const float *yL, const float 
 
 hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, double lambda,
                           const void *x, void *y, hb_cg_state *st, int dot_mode, cudaStream_t s);
+
+// 1 / diag(A) in FP64 and FP32 for (screen, lambda), built on first use and
+// kept while (screen, lambda) stay the same.
+hb_status hb_mesh_inv_diag(hb_mesh *m, int screen, double lambda, cudaStream_t s);
 
 // a.b in FP64 into *out (device).
 hb_status hb_launch_dot_f64(const hb_mesh *m, const double *a, const double *b, int64_t n,

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(HB_SERVE_THREADS) serve_inner_init_kernel(cons
 {
     const hb_slot_desc &d = *D;
     if (!d.active || S->phase != HB_SLOT_OUTER) return;
-    inner_init_body(d.r, d.r32, d.p32, d.d32, d.n_global, d.inner_rtol, d.max_it - S->inner_total, d.partials,
+    inner_init_body(d.r, d.r32, d.p32, d.d32, nullptr, d.n_global, d.inner_rtol, d.max_it - S->inner_total, d.partials,
                     d.counters + 2, &S->outer, &S->inner);
 }
 
@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(HB_SERVE_THREADS) serve_update_r_kernel(const 
 {
     const hb_slot_desc &d = *D;
     if (!d.active) return;
-    cg_update_r_body<float>(d.r32, d.Ap32, d.n_global, d.partials, d.counters + 2, &S->inner);
+    cg_update_r_body<float, false>(d.r32, d.Ap32, nullptr, nullptr, d.n_global, d.partials, d.counters + 2,
+                                   &S->inner);
 }
 
 __global__ void __launch_bounds__(HB_SERVE_THREADS) serve_update_xp_kernel(const hb_slot_desc *D, hb_slot_state *S)
@@ -281,7 +282,7 @@ static hb_status admit(hb_server *S, int si, const request &rq)
     const int64_t n = m->n_global;
     const size_t ns = vec_stride(n);
     const size_t bytes = ns * (4 * sizeof(double) + 4 * sizeof(float)) +
-                         sizeof(double) * (2 * HB_RED_BLOCKS + HB_SERVE_GRID) + 64 * sizeof(unsigned);
+                         sizeof(double) * (HB_RED_MAXV * HB_RED_BLOCKS + HB_SERVE_GRID) + 64 * sizeof(unsigned);
     void *mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, bytes);
     if (e != cudaSuccess) {
@@ -292,7 +293,7 @@ static hb_status admit(hb_server *S, int si, const request &rq)
     double *b = (double *)mem, *x = b + ns, *r = x + ns, *Ap = r + ns;
     float *r32 = (float *)(Ap + ns), *p32 = r32 + ns, *Ap32 = p32 + ns, *d32 = Ap32 + ns;
     double *partials = (double *)(d32 + ns);
-    double *axp = partials + 2 * HB_RED_BLOCKS;
+    double *axp = partials + HB_RED_MAXV * HB_RED_BLOCKS;
     unsigned *ctr = (unsigned *)(axp + HB_SERVE_GRID);
     hb_slot_desc d{};
     d.active = 1;
@@ -526,6 +527,7 @@ extern "C" hb_status hb_server_submit(hb_server *S, const hb_mesh_desc *d, const
         return HB_ERR_ARG;
     }
     if (o->prec != HB_MIXED) { hb_set_error("the server runs HB_MIXED solves"); return HB_ERR_ARG; }
+    if (o->precond != 0) { hb_set_error("the server runs unpreconditioned solves (precond = 0)"); return HB_ERR_ARG; }
     if (o->screen != HB_SCREEN_IDENTITY && o->screen != HB_SCREEN_MASS) { hb_set_error("bad screen"); return HB_ERR_ARG; }
     if (!(o->rtol > 0.0) || o->max_it < 1) { hb_set_error("the server needs rtol > 0 and max_it >= 1"); return HB_ERR_ARG; }
     std::lock_guard<std::mutex> lk(S->mu);

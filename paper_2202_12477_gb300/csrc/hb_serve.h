@@ -28,7 +28,7 @@ struct hb_slot_desc {
     double *x, *r, *Ap;           // FP64 solution, residual, A x
     float *r32, *p32, *Ap32, *d32;  // FP32 inner CG
     double lambda, rtol, inner_rtol;
-    double *partials;             // [2 * HB_RED_BLOCKS]
+    double *partials;             // [HB_RED_MAXV * HB_RED_BLOCKS]
     double *ax_partials;          // [HB_SERVE_GRID]
     unsigned *counters;           // [8]
 };

@@ -617,6 +617,8 @@ extern "C" hb_status hb_mesh_destroy(hb_mesh *m)
     cudaFree(m->srowptr);
     cudaFree(m->scols);
     cudaFree(m->ax_partials);
+    cudaFree(m->inv_diag);
+    cudaFree(m->inv_diag32);
     for (auto &g : m->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (m->cg_stream) cudaStreamDestroy(m->cg_stream);
@@ -694,7 +696,7 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     HB_TRY_MESH(alloc((void **)&m->mdiag, sizeof(double) * (ng + 1)));
     if (d->keep_fp32_copy) HB_TRY_MESH(alloc((void **)&m->mdiag32, sizeof(float) * (ng + 1)));
     HB_TRY_MESH(alloc((void **)&m->yL, sizeof(double) * n_local));
-    HB_TRY_MESH(alloc((void **)&m->partials, sizeof(double) * 2 * HB_RED_BLOCKS));
+    HB_TRY_MESH(alloc((void **)&m->partials, sizeof(double) * HB_RED_MAXV * HB_RED_BLOCKS));
     HB_TRY_MESH(alloc((void **)&m->counters, sizeof(unsigned) * 8));
     HB_TRY_MESH(alloc((void **)&m->state, sizeof(hb_cg_state) * 4));
     HB_TRY_MESH(cudaMallocHost((void **)&m->state_host, sizeof(hb_cg_state)));
@@ -765,8 +767,8 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
         hb_status sst = build_surface_csr(m, s);
         if (sst != HB_OK) { hb_mesh_destroy(m); return sst; }
         // one partial per element-kernel block (at most one block per element)
-        const int EB1 = n * n >= 256 ? 1 : 256 / (n * n);
-        m->n_ax_partials = (E + EB1 - 1) / EB1 + 1;
+        // one partial per element-kernel block: at most one block per element
+        m->n_ax_partials = E + 1;
         cudaError_t ae = cudaMalloc((void **)&m->ax_partials, sizeof(double) * m->n_ax_partials);
         if (ae != cudaSuccess) {
             hb_set_error("ax partials: %s", cudaGetErrorString(ae));
@@ -815,6 +817,90 @@ extern "C" hb_status hb_mesh_copy_geo(const hb_mesh *m, double *host)
     if (!m || !host) { hb_set_error("null argument"); return HB_ERR_ARG; }
     hb_device_guard dg(m->device);
     HB_TRY_CUDA(cudaMemcpy(host, m->geo, sizeof(double) * 7 * m->n_local, cudaMemcpyDeviceToHost));
+    return HB_OK;
+}
+
+// ---------------------------------------------------------------- Jacobi preconditioner
+
+// Diagonal of the element matrix Dbold^T G^e Dbold at every local node:
+//   sum_m D[m][i]^2 G_rr(m,j,k) + sum_m D[m][j]^2 G_ss(i,m,k) + sum_m D[m][k]^2 G_tt(i,j,m)
+//   + 2 D_ii D_jj G_rs + 2 D_ii D_kk G_rt + 2 D_jj D_kk G_st.
+__global__ void k_elem_diag(const double *__restrict__ geo, const double *__restrict__ D, int N, int64_t n_local,
+                            double *__restrict__ out)
+{
+    const int n = N + 1, n2 = n * n;
+    const int64_t n3 = (int64_t)n2 * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_local;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = q / n3;
+        const int node = (int)(q - e * n3);
+        const int i = node % n, j = (node / n) % n, k = node / n2;
+        auto G = [&](int c, int ii, int jj, int kk) { return geo[((e * n + kk) * 7 + c) * (int64_t)n2 + jj * n + ii]; };
+        double a = 0.0;
+        for (int p = 0; p < n; p++) {
+            a += D[p * n + i] * D[p * n + i] * G(0, p, j, k);
+            a += D[p * n + j] * D[p * n + j] * G(3, i, p, k);
+            a += D[p * n + k] * D[p * n + k] * G(5, i, j, p);
+        }
+        a += 2.0 * D[i * n + i] * D[j * n + j] * G(1, i, j, k);
+        a += 2.0 * D[i * n + i] * D[k * n + k] * G(2, i, j, k);
+        a += 2.0 * D[j * n + j] * D[k * n + k] * G(4, i, j, k);
+        out[q] = a;
+    }
+}
+
+// diag(A)_g = sum of the copies (CSR order = element order) + screening; stores 1/diag.
+__global__ void k_diag_assemble(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ cols,
+                                const double *__restrict__ dl, const double *__restrict__ mdiag, int screen,
+                                double lambda, int64_t ng, double *__restrict__ inv64, float *__restrict__ inv32)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int p = rowptr[g]; p < rowptr[g + 1]; p++) s += dl[cols[p]];
+        s += screen ? lambda * mdiag[g] : lambda;
+        const double inv = 1.0 / s;
+        inv64[g] = inv;
+        inv32[g] = (float)inv;
+    }
+}
+
+hb_status hb_mesh_inv_diag(hb_mesh *m, int screen, double lambda, cudaStream_t s)
+{
+    if (m->diag_valid && m->diag_screen == screen && m->diag_lambda == lambda) return HB_OK;
+    const int64_t ng = m->n_global;
+    if (!m->inv_diag) {
+        HB_TRY_CUDA(cudaMalloc((void **)&m->inv_diag, sizeof(double) * (ng + 1)));
+        HB_TRY_CUDA(cudaMalloc((void **)&m->inv_diag32, sizeof(float) * (ng + 1)));
+        m->device_bytes += 12 * (size_t)(ng + 1);
+    }
+    hb_count_launch();
+    k_elem_diag<<<grid_for(m->n_local, 256), 256, 0, s>>>(m->geo, hb_dev_D64(m->N), m->N, m->n_local,
+                                                         (double *)m->yL);
+    HB_CHECK_LAUNCH();
+    hb_count_launch();
+    k_diag_assemble<<<grid_for(ng, 256), 256, 0, s>>>(m->rowptr, m->cols, (const double *)m->yL, m->mdiag, screen,
+                                                     lambda, ng, m->inv_diag, m->inv_diag32);
+    HB_CHECK_LAUNCH();
+    m->diag_valid = 1;
+    m->diag_screen = screen;
+    m->diag_lambda = lambda;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_diag_A(hb_mesh *m, hb_screen screen, double lambda, double *host_diag, void *stream)
+{
+    hb_clear_error();
+    if (!m || (!host_diag && m->n_global)) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (screen != HB_SCREEN_IDENTITY && screen != HB_SCREEN_MASS) { hb_set_error("bad screen"); return HB_ERR_ARG; }
+    hb_device_guard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m->n_global == 0) return HB_OK;
+    hb_status st = hb_mesh_inv_diag(m, screen, lambda, s);
+    if (st != HB_OK) return st;
+    std::vector<double> inv((size_t)m->n_global);
+    HB_TRY_CUDA(cudaMemcpyAsync(inv.data(), m->inv_diag, sizeof(double) * m->n_global, cudaMemcpyDeviceToHost, s));
+    HB_TRY_CUDA(cudaStreamSynchronize(s));
+    for (int64_t g = 0; g < m->n_global; g++) host_diag[g] = 1.0 / inv[(size_t)g];
     return HB_OK;
 }
 

@@ -18,6 +18,7 @@ using hbacc::dot_acc;
 template <int NV>
 __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned *counter, double (&tot)[NV])
 {
+    static_assert(NV >= 1 && NV <= HB_RED_MAXV, "partials buffers hold HB_RED_MAXV rows");
     __shared__ double sh[NV][32];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -77,14 +78,40 @@ __device__ __forceinline__ void assemble_body(const T *__restrict__ yL, const in
     if (DOT == HB_DOT_CG_PAP && st->run == 0) return;
     const T lam = (T)lambda;
     dot_acc<T> acc;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
-        const int a = __ldg(rowptr + g), z = __ldg(rowptr + g + 1);
-        T s = T(0);
-        for (int p = a; p < z; p++) s += __ldcs(yL + __ldcs(cols + p));
-        const T xv = x[g];
-        s += SCREEN ? lam * (mdiag[g] * xv) : lam * xv;
-        y[g] = s;
-        if (DOT) acc.add(xv, s);
+    // four independent rows per pass (see assemble_surf_body)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g0 < ng; g0 += 4 * stride) {
+        int a[4], z[4], c0[4], c1[4];
+        T xv[4], s[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t g = g0 + u * stride;
+            a[u] = g < ng ? __ldg(rowptr + g) : 0;
+            z[u] = g < ng ? __ldg(rowptr + g + 1) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t g = g0 + u * stride;
+            c0[u] = a[u] < z[u] ? __ldcs(cols + a[u]) : -1;
+            c1[u] = a[u] + 1 < z[u] ? __ldcs(cols + a[u] + 1) : -1;
+            xv[u] = g < ng ? x[g] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const T v0 = c0[u] >= 0 ? __ldcs(yL + c0[u]) : T(0);
+            const T v1 = c1[u] >= 0 ? __ldcs(yL + c1[u]) : T(0);
+            s[u] = v0 + v1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t g = g0 + u * stride;
+            if (g >= ng) continue;
+            T t = s[u];
+            for (int p = a[u] + 2; p < z[u]; p++) t += __ldcs(yL + __ldcs(cols + p));
+            t += SCREEN ? lam * (mdiag[g] * xv[u]) : lam * xv[u];
+            y[g] = t;
+            if (DOT) acc.add(xv[u], t);
+        }
     }
     if (DOT) {
         double v[1] = {acc.value()}, tot[1];
@@ -207,50 +234,59 @@ __device__ __forceinline__ void dot_body(const T *__restrict__ a, const T *__res
 
 // ---------------------------------------------------------------- CG kernels
 
-// r = b - Ax; p = r; r.r and b.b; state set up for Algorithm 1.
-__device__ __forceinline__ void cg_init_body(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
-                   double *__restrict__ p, int64_t n, double rtol, int max_it, double *partials,
-                   unsigned *counter, hb_cg_state *st)
+// r = b - Ax; z = M^-1 r (M = diag(A) when inv_d is given, else z = r);
+// p = z; r.z, r.r and b.b; state set up for Algorithm 1 (preconditioned).
+__device__ __forceinline__ void cg_init_body(const double *__restrict__ b, const double *__restrict__ Ax,
+                                             double *__restrict__ r, double *__restrict__ p,
+                                             const double *__restrict__ inv_d, int64_t n, double rtol, int max_it,
+                                             double *partials, unsigned *counter, hb_cg_state *st)
 {
-    dot_acc<double> rr, bb;
+    dot_acc<double> rz, rr, bb;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double bi = b[i];
         const double ri = bi - Ax[i];
+        const double zi = inv_d ? ri * inv_d[i] : ri;
         r[i] = ri;
-        p[i] = ri;
+        p[i] = zi;
+        rz.add(ri, zi);
         rr.add(ri, ri);
         bb.add(bi, bi);
     }
-    double v[2] = {rr.value(), bb.value()}, tot[2];
-    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+    double v[3] = {rz.value(), rr.value(), bb.value()}, tot[3];
+    if (grid_sum<3>(v, partials, counter, tot) && threadIdx.x == 0) {
         st->rr = tot[0];
-        st->bb = tot[1];
-        st->tol2 = rtol * rtol * tot[1];
+        st->res2 = tot[1];
+        st->bb = tot[2];
+        st->tol2 = rtol * rtol * tot[2];
         st->it = 0;
         st->max_it = max_it;
         st->status = HB_OK;
         st->alpha = st->beta = st->pAp = 0.0;
-        st->run = (max_it > 0 && tot[0] > st->tol2) ? 1 : 0;
+        st->run = (max_it > 0 && tot[1] > st->tol2) ? 1 : 0;
         st->next_run = st->run;
     }
 }
 
-// Algorithm 1, line 9 and the r.r of line 10: r -= alpha Ap.
-template <typename T>
-__device__ __forceinline__ void cg_update_r_body(T *__restrict__ r, const T *__restrict__ Ap, int64_t n, double *partials,
-                       unsigned *counter, hb_cg_state *st)
+// Algorithm 1, line 9 and the dot of line 10: r -= alpha Ap. With the
+// preconditioner (PREC) also z = M^-1 r, the new r.z (for beta) and r.r (for
+// the stopping test); without it r.r serves both.
+template <typename T, bool PREC>
+__device__ __forceinline__ void cg_update_r_body(T *__restrict__ r, const T *__restrict__ Ap, T *__restrict__ z,
+                                                 const T *__restrict__ inv_d, int64_t n, double *partials,
+                                                 unsigned *counter, hb_cg_state *st)
 {
     if (st->run == 0) return;
     const T alpha = (T)st->alpha;
-    dot_acc<T> acc;
+    dot_acc<T> acc, acc2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
-        T rv[4], av[4];
+        T rv[4], av[4], dv[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const int64_t i = i0 + u * stride;
             rv[u] = i < n ? r[i] : T(0);
             av[u] = i < n ? __ldcs(Ap + i) : T(0);
+            if (PREC) dv[u] = i < n ? inv_d[i] : T(0);
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
@@ -258,18 +294,37 @@ __device__ __forceinline__ void cg_update_r_body(T *__restrict__ r, const T *__r
             if (i < n) {
                 const T ri = rv[u] - alpha * av[u];
                 r[i] = ri;
-                acc.add(ri, ri);
+                if (PREC) {
+                    const T zi = ri * dv[u];
+                    z[i] = zi;
+                    acc.add(ri, zi);
+                    acc2.add(ri, ri);
+                } else {
+                    acc.add(ri, ri);
+                }
             }
         }
     }
-    double v[1] = {acc.value()}, tot[1];
-    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-        const double rr_new = tot[0];
-        st->rr_new = rr_new;
-        st->beta = rr_new / st->rr;
-        st->rr = rr_new;
-        st->it += 1;
-        st->next_run = (st->it < st->max_it && rr_new > st->tol2) ? 1 : 0;
+    if (PREC) {
+        double v[2] = {acc.value(), acc2.value()}, tot[2];
+        if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+            st->rr_new = tot[0];
+            st->beta = tot[0] / st->rr;
+            st->rr = tot[0];
+            st->res2 = tot[1];
+            st->it += 1;
+            st->next_run = (st->it < st->max_it && tot[1] > st->tol2) ? 1 : 0;
+        }
+    } else {
+        double v[1] = {acc.value()}, tot[1];
+        if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+            st->rr_new = tot[0];
+            st->beta = tot[0] / st->rr;
+            st->rr = tot[0];
+            st->res2 = tot[0];
+            st->it += 1;
+            st->next_run = (st->it < st->max_it && tot[0] > st->tol2) ? 1 : 0;
+        }
     }
 }
 
@@ -335,30 +390,36 @@ __device__ __forceinline__ void residual_body(const double *__restrict__ b, cons
 }
 
 // Inner start: r32 = r / ||r|| (so the inner system is well scaled in FP32),
-// p32 = r32, d32 = 0; inner state for A d = r32 with relative target rtol_in.
-__device__ __forceinline__ void inner_init_body(const double *__restrict__ r, float *__restrict__ r32, float *__restrict__ p32,
-                      float *__restrict__ d32, int64_t n, double rtol_in, int max_it, double *partials,
-                      unsigned *counter, const hb_cg_state *outer, hb_cg_state *st)
+// z32 = M^-1 r32 when inv_d is given, p32 = z32, d32 = 0; inner state for
+// A d = r32 with relative target rtol_in.
+__device__ __forceinline__ void inner_init_body(const double *__restrict__ r, float *__restrict__ r32,
+                                                float *__restrict__ p32, float *__restrict__ d32,
+                                                const float *__restrict__ inv_d, int64_t n, double rtol_in,
+                                                int max_it, double *partials, unsigned *counter,
+                                                const hb_cg_state *outer, hb_cg_state *st)
 {
     const double scale = 1.0 / sqrt(outer->rr);
-    dot_acc<float> acc;
+    dot_acc<float> rz, rr;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float v = (float)(r[i] * scale);
+        const float zi = inv_d ? v * inv_d[i] : v;
         r32[i] = v;
-        p32[i] = v;
+        p32[i] = zi;
         d32[i] = 0.0f;
-        acc.add(v, v);
+        rz.add(v, zi);
+        rr.add(v, v);
     }
-    double v[1] = {acc.value()}, tot[1];
-    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+    double v[2] = {rz.value(), rr.value()}, tot[2];
+    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
         st->rr = tot[0];
-        st->bb = tot[0];
-        st->tol2 = rtol_in * rtol_in * tot[0];
+        st->res2 = tot[1];
+        st->bb = tot[1];
+        st->tol2 = rtol_in * rtol_in * tot[1];
         st->it = 0;
         st->max_it = max_it;
         st->status = HB_OK;
         st->alpha = st->beta = st->pAp = 0.0;
-        st->run = (max_it > 0 && tot[0] > st->tol2) ? 1 : 0;
+        st->run = (max_it > 0 && tot[1] > st->tol2) ? 1 : 0;
         st->next_run = st->run;
     }
 }

@@ -44,7 +44,7 @@ class hb_mesh_info_t(C.Structure):
 
 class hb_cg_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("screen", C.c_int), ("lambda_", C.c_double), ("rtol", C.c_double),
-                ("max_it", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int)]
+                ("max_it", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int), ("precond", C.c_int)]
 
 
 class hb_cg_result(C.Structure):
@@ -83,6 +83,7 @@ _SIGS = [
     ("hb_dot_noalloc", C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                  C.POINTER(C.c_double), C.c_void_p]),
     ("hb_fill_rhs", C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_double, C.c_void_p, C.c_void_p]),
+    ("hb_diag_A", C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
     ("hb_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
                               C.POINTER(hb_cg_result), C.c_void_p]),
     ("hb_u01", C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64]),
@@ -187,8 +188,8 @@ def hb_u01(seed, stream, idx) -> float:
     return lib().hb_u01(seed, stream, idx)
 
 
-HB_VARIANT_PENCIL, HB_VARIANT_EVEN_ODD, HB_VARIANT_EB2 = 1, 2, 4
-VARIANTS = [0, 1, 3, 5, 7]  # every valid combination
+HB_VARIANT_PENCIL, HB_VARIANT_EVEN_ODD, HB_VARIANT_EB2, HB_VARIANT_ONE = 1, 2, 4, 8
+VARIANTS = [0, 1, 3, 5, 7, 11]  # every valid combination
 
 
 def hb_set_kernel_variant(h, prec, variant) -> None:
@@ -205,7 +206,7 @@ def hb_autotune(h, prec, screen=HB_SCREEN_IDENTITY, lam=0.1, reps=5, stream=None
     """Times every kernel variant on this mesh, keeps the fastest; returns
     (best variant, {variant: ms})."""
     best = C.c_int(-1)
-    ms = (C.c_double * 8)(*([-1.0] * 8))
+    ms = (C.c_double * 16)(*([-1.0] * 16))
     _check(lib().hb_autotune(h, prec, screen, lam, reps, C.byref(best), ms, _stream_ptr(stream)))
     return best.value, {v: ms[v] for v in VARIANTS if ms[v] >= 0}
 
@@ -289,12 +290,18 @@ class Mesh:
         return b
 
     def cg(self, b, x=None, lam=0.0, rtol=0.0, max_it=100, prec=HB_F64, screen=HB_SCREEN_IDENTITY,
-           inner_rtol=1e-4, max_outer=30, stream=None):
+           inner_rtol=1e-4, max_outer=30, precond=0, stream=None):
         if x is None:
             x = self.vec()
-        opts = hb_cg_opts(prec, screen, lam, rtol, max_it, inner_rtol, max_outer)
+        opts = hb_cg_opts(prec, screen, lam, rtol, max_it, inner_rtol, max_outer, precond)
         res = hb_cg_solve(self.handle, opts, b.data_ptr(), x.data_ptr(), stream)
         return x, res
+
+    def diag_A(self, lam=0.0, screen=HB_SCREEN_IDENTITY, stream=None):
+        import numpy as np
+        out = np.zeros(self.n_global)
+        _check(lib().hb_diag_A(self.handle, screen, lam, out.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
+        return out
 
     def l2g(self):
         import numpy as np
@@ -323,7 +330,7 @@ class Server:
     def submit(self, ex, ey, ez, N, perturb=0.1, seed=0, rhs_seed=0, lam=0.1, rtol=1e-8, max_it=100000,
                inner_rtol=1e-4, max_outer=30, screen=HB_SCREEN_IDENTITY, faces=ALL_FACES, keep_x=False) -> int:
         d = hb_mesh_desc(ex, ey, ez, N, perturb, seed, faces, 1)
-        o = hb_cg_opts(HB_MIXED, screen, lam, rtol, max_it, inner_rtol, max_outer)
+        o = hb_cg_opts(HB_MIXED, screen, lam, rtol, max_it, inner_rtol, max_outer, 0)
         t = C.c_int64(0)
         _check(lib().hb_server_submit(self.handle, C.byref(d), C.byref(o), rhs_seed, 1 if keep_x else 0,
                                       C.byref(t)))

@@ -278,3 +278,37 @@ def test_autotune_keeps_parity(tmp_path):
     assert again == chosen
     x = inputs.random_vector(m.n_global, seed=5)
     assert _rel(m.apply_A(_to_dev(x), lam=0.1).cpu().numpy(), o.apply_A(x, 0.1)) <= 1e-12
+
+
+# ---------------------------------------------------------------- Jacobi preconditioner
+
+@pytest.mark.parametrize("dims,N,rho,lam,screen", [((3, 2, 2), 3, 0.2, 0.1, 0), ((2, 2, 3), 6, 0.25, 0.7, 1),
+                                                   ((2, 2, 2), 9, 0.1, 0.0, 0)])
+def test_diagonal_matches_oracle(dims, N, rho, lam, screen):
+    m, o = _pair(dims, N, rho=rho, seed=N)
+    d = m.diag_A(lam=lam, screen=screen)
+    d_or = o.diag_A(lam, screen)
+    assert np.abs(d - d_or).max() <= 1e-13 * np.abs(d_or).max()
+
+
+def test_pcg_fixed_iterations_match_oracle():
+    m, o = _pair((3, 3, 3), 5, rho=0.25, seed=3)
+    b = m.rhs(kind=0, seed=5)
+    x_or, it_or, rel_or, st_or = o.cg(b.cpu().numpy(), 0.1, rtol=0.0, max_it=30, precond=1)
+    x, res = m.cg(b, lam=0.1, rtol=0.0, max_it=30, precond=1)
+    assert res.iters == 30 and it_or == 30 and res.status == hb.HB_OK
+    assert _rel(x.cpu().numpy(), x_or) <= 1e-12
+    assert abs(res.rel_res - rel_or) <= 1e-9 * rel_or
+
+
+@pytest.mark.parametrize("prec", [hb.HB_F64, hb.HB_MIXED])
+def test_pcg_converges_with_fewer_iterations(prec):
+    m, o = _pair((4, 3, 3), 7, rho=0.2, seed=6)
+    b = m.rhs(kind=0, seed=6)
+    x0, r0 = m.cg(b, lam=0.0, rtol=1e-10, max_it=20000, prec=prec, precond=0)
+    x1, r1 = m.cg(b, lam=0.0, rtol=1e-10, max_it=20000, prec=prec, precond=1)
+    assert r0.status == hb.HB_OK and r1.status == hb.HB_OK
+    assert r1.iters < r0.iters
+    bn = b.cpu().numpy()
+    r = bn - o.apply_A(x1.cpu().numpy(), 0.0)
+    assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(bn)

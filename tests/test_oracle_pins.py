@@ -430,3 +430,23 @@ def test_sampled_rows_equal_full_operator(dims, N, rho, lam, screen, faces):
     rows = np.arange(m.n_global)
     yr = orc.apply_A_rows(dims, N, rho, 6, x, rows, lam, screen, faces)
     np.testing.assert_array_equal(yr, y)
+
+
+@pytest.mark.parametrize("dims,N,rho,lam,screen", [((2, 2, 2), 3, 0.2, 0.1, 0), ((2, 1, 2), 5, 0.3, 0.7, 1),
+                                                   ((1, 2, 2), 2, 0.0, 0.0, 0)])
+def test_diagonal_equals_dense_diagonal(dims, N, rho, lam, screen):
+    m = orc.Mesh(*dims, N, rho=rho, seed=5)
+    A = _dense_bruteforce(m, lam, screen)
+    np.testing.assert_allclose(m.diag_A(lam, screen), np.diag(A), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("N,lam", [(3, 0.1), (5, 0.0)])
+def test_jacobi_pcg_matches_dense_solve(N, lam):
+    m = orc.Mesh(2, 2, 2, N, rho=0.25, seed=2)
+    b = m.rhs(kind=0, seed=4)
+    xs = np.linalg.solve(_dense_bruteforce(m, lam), b)
+    x, it, rel, st = m.cg(b, lam, rtol=1e-12, max_it=5000, precond=1)
+    assert st == 0 and rel <= 1e-12
+    assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+    x0, it0, *_ = m.cg(b, lam, rtol=1e-12, max_it=5000, precond=0)
+    assert it <= it0  # diagonal scaling never hurts on these meshes
