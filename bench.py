@@ -372,16 +372,18 @@ def run_sweep(args, rank, world, local):
         for prec in args.precisions.split(","):
             dims = c2_dims(N, args.local_nodes)
             m = hb.Mesh(*dims, N, perturb=0.1, seed=0, fp32=(prec == "f32"))
-            hbprec = hb.HB_F64 if prec == "f64" else hb.HB_F32
-            dt = torch.float64 if prec == "f64" else torch.float32
+            hbprec = {"f64": hb.HB_F64, "f32": hb.HB_F32, "f64x": hb.HB_F64X}[prec]
+            # the double-float kernel takes its block shape from the FP64 variant
+            varprec = hb.HB_F32 if prec == "f32" else hb.HB_F64
+            dt = torch.float32 if prec == "f32" else torch.float64
             x = torch.from_numpy(inputs.random_vector(m.n_global, 1)).to("cuda", dt)
             y = torch.empty_like(x)
             for var in variants:
                 if var is not None:
-                    hb.hb_set_kernel_variant(m.handle, hbprec, var)
-                var = hb.hb_get_kernel_variant(m.handle, hbprec)
+                    hb.hb_set_kernel_variant(m.handle, varprec, var)
+                var = hb.hb_get_kernel_variant(m.handle, varprec)
                 for _ in range(3):
-                    m.apply_A(x, y, lam=0.1)
+                    m.apply_A(x, y, lam=0.1, prec=hbprec)
                 torch.cuda.synchronize()
                 hb.hb_profile_reset()
                 hb.hb_profile_enable(True)
@@ -389,14 +391,14 @@ def run_sweep(args, rank, world, local):
                 e0.record()
                 reps = args.reps
                 for _ in range(reps):
-                    m.apply_A(x, y, lam=0.1)
+                    m.apply_A(x, y, lam=0.1, prec=hbprec)
                 e1.record()
                 torch.cuda.synchronize()
                 hb.hb_profile_enable(False)
                 t = e0.elapsed_time(e1) / reps
                 axm, axn = hb.hb_profile_read("ax_local")
                 asm, asn = hb.hb_profile_read("assemble")
-                esz = 8 if prec == "f64" else 4
+                esz = 4 if prec == "f32" else 8
                 fl = acc.op_flops(m.E, N)
                 rec = {"workload": "operator sweep", "N": N, "prec": prec, "variant": var, "elements": list(dims),
                        "n_local": m.n_local, "n_global": m.n_global, "ms": t,
@@ -409,6 +411,9 @@ def run_sweep(args, rank, world, local):
                 rec["hbm_frac_method_min"] = rec["eff_gbs_method_min"] / pk["hbm_gbs"]
                 rec["alu_frac"] = (acc.op_local_flops(m.E, N) / (axm / axn * 1e-3) / 1e12
                                    / (pk["fp64_tflops"] if prec == "f64" else pk["fp32_tflops"]))
+                if prec == "f64x":
+                    # a double-float flop costs several FP32 instructions: no single ALU roof
+                    rec["alu_frac"] = None
                 print(json.dumps(rec), flush=True)
             m.close()
             del x, y
@@ -430,7 +435,7 @@ def _solve_report(m, b, lam, prec, rtol, screen=0, max_it=200000, inner_rtol=1e-
     # FP64 residual of the returned solution, recomputed with the FP64 operator
     r = b - m.apply_A(x, lam=lam, screen=screen)
     rel = float(torch.linalg.norm(r) / torch.linalg.norm(b))
-    return x, {"prec": {hb.HB_F64: "f64", hb.HB_MIXED: "mixed"}[prec], "precond": ["none", "jacobi"][precond],
+    return x, {"prec": {hb.HB_F64: "f64", hb.HB_MIXED: "mixed", hb.HB_F64X: "f64x"}[prec], "precond": ["none", "jacobi"][precond],
                "time_s": e0.elapsed_time(e1) / 1e3,
                "iters": res.iters, "outer_iters": res.outer_iters, "status": hb.STATUS_NAMES[res.status],
                "rel_res_fp64": rel}
@@ -458,6 +463,10 @@ def run_c3(args, rank, world, local):
     for prec in (hb.HB_F64, hb.HB_MIXED):  # with the Jacobi preconditioner
         _, rec = _solve_report(m, b, 0.0, prec, 1e-10, precond=1)
         out["results"].append(rec)
+    # FP64 CG with the double-float element kernel
+    x, rec = _solve_report(m, b, 0.0, hb.HB_F64X, 1e-10)
+    out["results"].append(rec)
+    out["f64x_vs_fp64_rel_err"] = float(torch.linalg.norm(x - xs[hb.HB_F64]) / torch.linalg.norm(xs[hb.HB_F64]))
     d = xs[hb.HB_MIXED] - xs[hb.HB_F64]
     out["mixed_vs_fp64_rel_err"] = float(torch.linalg.norm(d) / torch.linalg.norm(xs[hb.HB_F64]))
     out["speedup_mixed_over_fp64"] = out["results"][0]["time_s"] / out["results"][1]["time_s"]

@@ -54,7 +54,12 @@ typedef enum {
 typedef enum {
     HB_F64 = 0,    /* IEEE FP64 storage and arithmetic */
     HB_F32 = 1,    /* FP32 storage and arithmetic, FP64 dot accumulation */
-    HB_MIXED = 2   /* CG only: FP32 inner CG inside an FP64 defect-correction loop */
+    HB_MIXED = 2,  /* CG only: FP32 inner CG inside an FP64 defect-correction loop */
+    HB_F64X = 3    /* FP64 storage (x, y, geometric factors); the element kernel
+                      computes in double-float (pairs of FP32 with error-free
+                      transformations, ~47-bit significand) on the FP32 pipes,
+                      gather and vector stage in FP64. Agrees with HB_F64 to
+                      ~1e-14 relative; not IEEE FP64 arithmetic. */
 } hb_precision;
 
 typedef enum {
@@ -126,8 +131,8 @@ hb_status hb_mesh_copy_geo(const hb_mesh *mesh, double *host_geo);
  * derivatives with the geometric factors), sums back with Z^T in a fixed order
  * (no atomics: results are bitwise reproducible), and adds lambda x
  * (identity screening) or lambda M x (mass screening).
- * prec HB_F64: x, y are double*; HB_F32: float* (needs keep_fp32_copy).
- * x and y must not overlap. */
+ * prec HB_F64 or HB_F64X: x, y are double*; HB_F32: float* (needs
+ * keep_fp32_copy). x and y must not overlap. */
 hb_status hb_apply_A(const hb_mesh *mesh, hb_precision prec, hb_screen screen,
                      double lambda, const void *x, void *y, void *stream);
 
@@ -200,7 +205,8 @@ typedef struct {
 hb_status hb_diag_A(hb_mesh *mesh, hb_screen screen, double lambda, double *host_diag, void *stream);
 
 /* Solves A x = b with Algorithm 1 (x holds x0 on entry, the solution on exit;
- * both FP64 device vectors of length n_global). HB_F64 runs Algorithm 1 in FP64.
+ * both FP64 device vectors of length n_global). HB_F64 runs Algorithm 1 in FP64;
+ * HB_F64X the same with the double-float element kernel.
  * HB_MIXED runs FP64 defect correction: r = b - A x in FP64, an FP32 CG on
  * A d = r to inner_rtol (FP64 dot accumulation), x += d in FP64, until
  * ||b - A x|| <= rtol ||b||. precond = 1 applies the Jacobi preconditioner

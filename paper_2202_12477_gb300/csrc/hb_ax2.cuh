@@ -25,15 +25,46 @@
 #include "hb_acc.cuh"
 
 #ifndef HB_AX2_T
-#error "define HB_AX2_T (double or float) before including hb_ax2.cuh"
+#error "define HB_AX2_T (the compute type: double, float or df) before including hb_ax2.cuh"
 #endif
+#ifndef HB_AX2_S
+#define HB_AX2_S HB_AX2_T
+#endif
+
+#include <type_traits>
+
+#include "hb_df.cuh"
 
 namespace hb2 {
 // Internal linkage: this header is compiled once per precision (T differs by
 // translation unit), so nothing in it may share a symbol name across units.
 namespace {
 
-using T = HB_AX2_T;
+using T = HB_AX2_T;  // arithmetic of the element kernel
+using S = HB_AX2_S;  // storage of x, y and the geometric factors
+
+// Conversions between storage and compute types (identity unless the kernel
+// computes in double-float on FP64 data).
+template <typename TT, typename SS>
+struct conv {
+    static __device__ __forceinline__ TT c(SS v) { return v; }
+    static __device__ __forceinline__ SS s(TT v) { return v; }
+    static TT table(double v) { return (TT)v; }
+};
+template <>
+struct conv<df, double> {
+    static __device__ __forceinline__ df c(double v) { return df_from_double(v); }
+    static __device__ __forceinline__ double s(df v) { return df_to_double(v); }
+    static df table(double v)
+    {
+        const float h = (float)v;
+        return df(h, (float)(v - (double)h));
+    }
+};
+__device__ __forceinline__ T to_c(S v) { return conv<T, S>::c(v); }
+__device__ __forceinline__ S to_s(T v) { return conv<T, S>::s(v); }
+// Host: a table entry of the compute type from an FP64 value.
+static inline T table_value(double v) { return conv<T, S>::table(v); }
 
 // ------------------------------------------------------------ constant tables
 // Per degree N (n = N+1, h = ceil(n/2)): D and D^T at offset off(N) =
@@ -68,8 +99,8 @@ static inline hb_status upload_tables(const double *D_all)
         const double *D = D_all + o;
         for (int i = 0; i < n; i++)
             for (int m = 0; m < n; m++) {
-                hD[o + i * n + m] = (T)D[i * n + m];
-                hDt[o + i * n + m] = (T)D[m * n + i];
+                hD[o + i * n + m] = table_value(D[i * n + m]);
+                hDt[o + i * n + m] = table_value(D[m * n + i]);
             }
         for (int i = 0; i < h; i++)
             for (int m = 0; m < h; m++) {
@@ -86,10 +117,10 @@ static inline hb_status upload_tables(const double *D_all)
                     et = 0.5 * (D[m * n + i] + D[mm * n + i]);
                     ot = 0.5 * (D[m * n + i] - D[mm * n + i]);
                 }
-                hE[oh + i * h + m] = (T)e;
-                hO[oh + i * h + m] = (T)od;
-                hEt[oh + i * h + m] = (T)et;
-                hOt[oh + i * h + m] = (T)ot;
+                hE[oh + i * h + m] = table_value(e);
+                hO[oh + i * h + m] = table_value(od);
+                hEt[oh + i * h + m] = table_value(et);
+                hOt[oh + i * h + m] = table_value(ot);
             }
     }
     HB_TRY_CUDA(cudaMemcpyToSymbol(c_D, hD, sizeof hD));
@@ -168,14 +199,14 @@ struct shape {
 // (partials[blockIdx.x], if partials is not null). Surface nodes go to ysurf
 // in the per-element surface order of surf_index() for the Z^T gather.
 struct pencil_args {
-    const T *x;
+    const S *x;
     const int32_t *l2g;
-    const T *geo;
-    T *ysurf;
-    T *y;
+    const S *geo;
+    S *ysurf;
+    S *y;
     int64_t E;
     const int *run;
-    T lambda;
+    S lambda;
     int screen;
     double *partials;
 };
@@ -222,13 +253,13 @@ __host__ __device__ constexpr int pencil_min_blocks()
 // (it synchronises the block).
 template <int N, bool EO, int EB>
 __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, T *sm,
-                                             hbacc::dot_acc<T> &acc)
+                                             hbacc::dot_acc<S> &acc)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     using P = pad<N>;
-    const T *__restrict__ x = A.x;
+    const S *__restrict__ x = A.x;
     const int32_t *__restrict__ l2g = A.l2g;
-    const T *__restrict__ geo = A.geo;
+    const S *__restrict__ geo = A.geo;
     const int64_t E = A.E;
     const int tid = threadIdx.x;
     const int el = tid / n2;
@@ -248,7 +279,7 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
         for (int k = 0; k < n; k++) {
             const int g = __ldcs(lg + k * n2);
             gl[k] = g;
-            U[P::at(p0, p1, k)] = g >= 0 ? __ldg(x + g) : T(0);
+            U[P::at(p0, p1, k)] = g >= 0 ? to_c(__ldg(x + g)) : T(0);
         }
     }
     __syncthreads();
@@ -270,17 +301,17 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
     __syncthreads();
     if (active) {
         // metric factors at the t-line's nodes (coalesced rows of n^2 per factor)
-        const T *ge = geo + e * 7 * n3 + a;
+        const S *ge = geo + e * 7 * n3 + a;
 #pragma unroll
         for (int k = 0; k < n; k++) {
-            const T *g = ge + k * 7 * n2;
-            const T grr = __ldcs(g), grs = __ldcs(g + n2), grt = __ldcs(g + 2 * n2);
-            const T gss = __ldcs(g + 3 * n2), gst = __ldcs(g + 4 * n2), gtt = __ldcs(g + 5 * n2);
+            const S *g = ge + k * 7 * n2;
+            const T grr = to_c(__ldcs(g)), grs = to_c(__ldcs(g + n2)), grt = to_c(__ldcs(g + 2 * n2));
+            const T gss = to_c(__ldcs(g + 3 * n2)), gst = to_c(__ldcs(g + 4 * n2)), gtt = to_c(__ldcs(g + 5 * n2));
             const int q = P::at(p0, p1, k);
             const T ur = B1[q], us = B2[q], ut = B3[q];
-            B1[q] = grr * ur + grs * us + grt * ut;
-            B2[q] = grs * ur + gss * us + gst * ut;
-            B3[q] = grt * ur + gst * us + gtt * ut;
+            B1[q] = fma(grt, ut, fma(grs, us, grr * ur));
+            B2[q] = fma(gst, ut, fma(gss, us, grs * ur));
+            B3[q] = fma(gtt, ut, fma(gst, us, grt * ur));
         }
     }
     __syncthreads();
@@ -301,23 +332,25 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
     __syncthreads();
     if (active) {
         constexpr int NS = surf_count<N>();
-        T *ys = A.ysurf + e * NS;
+        S *ys = A.ysurf + e * NS;
         const bool ring = p0 == 0 || p0 == N || p1 == 0 || p1 == N;
         const int r = ring ? ring_index<N>(p0, p1) : 0;
 #pragma unroll
         for (int k = 0; k < n; k++) {
             const int q = P::at(p0, p1, k);
-            T y = B1[q] + B2[q] + B3[q];
+            const T yc = B1[q] + B2[q] + B3[q];
             if (k == 0) {
-                ys[a] = y;
+                ys[a] = to_s(yc);
             } else if (k == N) {
-                ys[n2 + a] = y;
+                ys[n2 + a] = to_s(yc);
             } else if (ring) {
-                ys[2 * n2 + (k - 1) * 4 * N + r] = y;
+                ys[2 * n2 + (k - 1) * 4 * N + r] = to_s(yc);
             } else {
                 // element-interior node: its DOF has no other copy (never masked)
-                const T xv = U[q];
-                const T jw = A.screen ? __ldg(geo + (e * n + k) * 7 * n2 + 6 * n2 + a) : T(1);
+                // (the double-float copy in U holds 47 bits of x: reload the value itself)
+                const S xv = std::is_same<T, S>::value ? to_s(U[q]) : __ldg(x + gl[k]);
+                const S jw = A.screen ? __ldg(geo + (e * n + k) * 7 * n2 + 6 * n2 + a) : S(1);
+                S y = to_s(yc);
                 y += A.lambda * (jw * xv);
                 A.y[gl[k]] = y;
                 acc.add(xv, y);
@@ -333,7 +366,7 @@ __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, E
 {
     if (A.run && *A.run == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    hbacc::dot_acc<T> acc;
+    hbacc::dot_acc<S> acc;
     pencil_group<N, EO, EB>(A, blockIdx.x, reinterpret_cast<T *>(smem_raw), acc);
     if (A.partials) {
         const double v = hbacc::block_sum(acc.value());

@@ -72,7 +72,7 @@ constexpr size_t serve_smem_max()
 }
 
 template <int N>
-__device__ __forceinline__ void serve_groups(const pencil_args &A, T *sm, hbacc::dot_acc<T> &acc)
+__device__ __forceinline__ void serve_groups(const pencil_args &A, T *sm, hbacc::dot_acc<S> &acc)
 {
     constexpr int EB = serve_eb<N>();
     const int64_t ngroups = (A.E + EB - 1) / EB;
@@ -82,15 +82,15 @@ __device__ __forceinline__ void serve_groups(const pencil_args &A, T *sm, hbacc:
 // One slot's element kernel on a fixed grid: the degree is read from the
 // slot descriptor, each block walks element groups grid-stride.
 __global__ void __launch_bounds__(HB_SERVE_THREADS, 1)
-    serve_ax_kernel(const hb_slot_desc *__restrict__ D, const hb_slot_state *__restrict__ S)
+    serve_ax_kernel(const hb_slot_desc *__restrict__ D, const hb_slot_state *__restrict__ St)
 {
     const hb_slot_desc &d = *D;
-    if (!d.active || S->phase != HB_SLOT_OUTER) return;
+    if (!d.active || St->phase != HB_SLOT_OUTER) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     pencil_args A{(const T *)d.x, d.l2g, d.geo, (T *)d.ysurf, (T *)d.Ap, d.E, nullptr, (T)d.lambda,
                   d.screen, nullptr};
-    hbacc::dot_acc<T> acc;
+    hbacc::dot_acc<S> acc;
     switch (d.N) {
     case 1: serve_groups<1>(A, sm, acc); break;
     case 2: serve_groups<2>(A, sm, acc); break;

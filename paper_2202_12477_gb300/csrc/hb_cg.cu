@@ -182,9 +182,21 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
                           hb_cg_state *st, int dot_mode, cudaStream_t s)
 {
     const int *run = (dot_mode == HB_DOT_CG_PAP && st) ? &st->run : nullptr;
-    if (prec != HB_F64 && prec != HB_F32) {
+    if (prec != HB_F64 && prec != HB_F32 && prec != HB_F64X) {
         hb_set_error("precision %d not valid for the operator", (int)prec);
         return HB_ERR_ARG;
+    }
+    if (prec == HB_F64X) {
+        // double-float element kernel (pencil, even-odd); block shape from the FP64 variant
+        const int v64 = m->variant[0];
+        const int ebm = (v64 & HB_VAR_ONE) ? 0 : ((v64 & HB_VAR_EB2) ? 2 : 1);
+        double *partials = dot_mode != HB_DOT_NONE ? m->ax_partials : nullptr;
+        int64_t nblk = 0;
+        hb_status r = hb_launch_ax2_f64x(m, (const double *)x, (double *)m->yL, (double *)y, lambda, screen,
+                                         partials, run, ebm, s, &nblk);
+        if (r != HB_OK) return r;
+        return launch_assemble_surf<double>(m, (const double *)m->yL, (const double *)x, (double *)y, m->mdiag,
+                                            screen, lambda, partials ? nblk : 0, st, dot_mode, s);
     }
     const int v = m->variant[prec == HB_F64 ? 0 : 1];
     const int eo = (v & HB_VAR_EO) ? 1 : 0, ebm = (v & HB_VAR_ONE) ? 0 : ((v & HB_VAR_EB2) ? 2 : 1);
@@ -267,9 +279,12 @@ extern "C" hb_status hb_apply_A(const hb_mesh *m, hb_precision prec, hb_screen s
     hb_clear_error();
     if (!m || (!x && m->n_global) || (!y && m->n_global)) { hb_set_error("null argument"); return HB_ERR_ARG; }
     if (!valid_screen(screen)) { hb_set_error("bad screen mode %d", (int)screen); return HB_ERR_ARG; }
-    if (prec != HB_F64 && prec != HB_F32) { hb_set_error("hb_apply_A takes HB_F64 or HB_F32"); return HB_ERR_ARG; }
+    if (prec != HB_F64 && prec != HB_F32 && prec != HB_F64X) {
+        hb_set_error("hb_apply_A takes HB_F64, HB_F32 or HB_F64X");
+        return HB_ERR_ARG;
+    }
     if (m->n_global == 0) return HB_OK;
-    const size_t esz = prec == HB_F64 ? 8 : 4;
+    const size_t esz = prec == HB_F32 ? 4 : 8;
     const char *xa = (const char *)x, *ya = (const char *)y;
     if (xa < ya + esz * m->n_global && ya < xa + esz * m->n_global) { hb_set_error("x and y overlap"); return HB_ERR_ARG; }
     hb_device_guard dg(m->device);
@@ -423,7 +438,7 @@ static hb_status cg_iterations_graph(const hb_mesh *mc, hb_precision prec, int s
                                      T *p, T *Ap, T *z, const T *inv_d, hb_cg_state *st, int count, cudaStream_t s)
 {
     hb_mesh *m = const_cast<hb_mesh *>(mc);
-    const int gi = prec == HB_F64 ? 0 : 1;
+    const int gi = prec == HB_F32 ? 1 : 0;
     hb_mesh::cg_graph &G = m->graphs[gi];
     const int variant = m->variant[gi];
     if (!m->cg_stream) {
@@ -498,7 +513,10 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
     hb_mesh *m = const_cast<hb_mesh *>(mc);
     if (!m || !o || ((!b || !x) && m->n_global)) { hb_set_error("null argument"); return HB_ERR_ARG; }
     if (!valid_screen(o->screen)) { hb_set_error("bad screen mode"); return HB_ERR_ARG; }
-    if (o->prec != HB_F64 && o->prec != HB_MIXED) { hb_set_error("hb_cg_solve takes HB_F64 or HB_MIXED"); return HB_ERR_ARG; }
+    if (o->prec != HB_F64 && o->prec != HB_MIXED && o->prec != HB_F64X) {
+        hb_set_error("hb_cg_solve takes HB_F64, HB_F64X or HB_MIXED");
+        return HB_ERR_ARG;
+    }
     if (o->max_it < 0 || !(o->rtol >= 0.0)) { hb_set_error("bad max_it or rtol"); return HB_ERR_ARG; }
     if (o->precond != 0 && o->precond != 1) { hb_set_error("precond must be 0 or 1"); return HB_ERR_ARG; }
     if (o->prec == HB_MIXED && (!m->geo32 || !m->mdiag32)) { hb_set_error("HB_MIXED needs keep_fp32_copy"); return HB_ERR_ARG; }
@@ -526,15 +544,15 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
     hb_cg_state *st = m->state, *st_in = m->state + 1;
     HB_TRY_CUDA(cudaEventRecord(m->ev0, s));
     hb_cg_state fin{};
-    if (o->prec == HB_F64) {
+    if (o->prec == HB_F64 || o->prec == HB_F64X) {
         // r0 = b - A x0, p = r0 (Algorithm 1, lines 4-5)
-        rs = hb_apply_A_impl(m, HB_F64, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
+        rs = hb_apply_A_impl(m, o->prec, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
         if (rs != HB_OK) return rs;
         hb_count_launch();
         cg_init_kernel<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, p, inv_d, n, o->rtol, o->max_it, m->partials,
                                                        m->counters + 2, st);
         HB_CHECK_LAUNCH();
-        rs = cg_drive<double>(m, HB_F64, o->screen, o->lambda, x, r, p, Ap, z, inv_d, st, o->max_it, s, &fin);
+        rs = cg_drive<double>(m, o->prec, o->screen, o->lambda, x, r, p, Ap, z, inv_d, st, o->max_it, s, &fin);
         if (rs != HB_OK) return rs;
         R.iters = fin.it;
         R.rel_res = fin.bb > 0.0 ? sqrt(fin.res2 / fin.bb) : 0.0;

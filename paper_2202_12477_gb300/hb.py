@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_NOMEM", 3: "HB_ERR_CUDA"
                 5: "HB_ERR_BREAKDOWN", 6: "HB_ERR_NOT_CONVERGED", 7: "HB_ERR_TIMEOUT", 8: "HB_ERR_BUSY",
                 9: "HB_ERR_NOT_FOUND"}
 # hb_precision
-HB_F64, HB_F32, HB_MIXED = 0, 1, 2
+HB_F64, HB_F32, HB_MIXED, HB_F64X = 0, 1, 2, 3
 # hb_screen
 HB_SCREEN_IDENTITY, HB_SCREEN_MASS = 0, 1
 ALL_FACES = 0x3F
@@ -270,9 +270,13 @@ class Mesh:
         import torch
         return torch.zeros(self.n_global, dtype=dtype or torch.float64, device="cuda")
 
-    def apply_A(self, x, y=None, lam=0.0, screen=HB_SCREEN_IDENTITY, stream=None):
+    def apply_A(self, x, y=None, lam=0.0, screen=HB_SCREEN_IDENTITY, stream=None, prec=None):
+        """y = A x. The precision follows x's dtype (float64: HB_F64, float32:
+        HB_F32) unless `prec` is given (HB_F64X takes float64 vectors)."""
         import torch
-        prec = HB_F64 if x.dtype == torch.float64 else HB_F32
+        if prec is None:
+            prec = HB_F64 if x.dtype == torch.float64 else HB_F32
+        assert x.dtype == (torch.float32 if prec == HB_F32 else torch.float64)
         if y is None:
             y = torch.empty_like(x)
         assert x.is_cuda and x.is_contiguous() and x.numel() == self.n_global

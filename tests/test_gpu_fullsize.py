@@ -55,6 +55,12 @@ def test_full_size_apply_sampled_rows(N):
         y = m.apply_A(xd, lam=0.1).cpu().numpy()
         err = np.abs(y[rows] - ref).max()
         assert err <= 1e-12 * scale, (variant, err / scale)
+    # double-float element kernel on the same FP64 data
+    for variant in (3, 11):
+        hb.hb_set_kernel_variant(m.handle, hb.HB_F64, variant)
+        y = m.apply_A(xd, lam=0.1, prec=hb.HB_F64X).cpu().numpy()
+        err = np.abs(y[rows] - ref).max()
+        assert err <= 1e-12 * scale, ("f64x", variant, err / scale)
     # FP32 operator (the mixed-precision inner product) on the same rows
     x32 = x.astype(np.float32)
     ref32 = orc.apply_A_rows(dims, N, 0.1, 0, x32.astype(np.float64), rows, 0.1)

@@ -126,6 +126,53 @@ def test_apply_A_fp32(dims, N):
     assert _rel(y, y_or) <= 2e-5
 
 
+@pytest.mark.parametrize("dims,N", OP_CASES)
+@pytest.mark.parametrize("variant", [3, 11])
+def test_apply_A_double_float(dims, N, variant):
+    """HB_F64X: FP64 data, element kernel in double-float arithmetic
+    (~47-bit significand): same 1e-12 bar as the FP64 operator."""
+    m, o = _pair(dims, N, rho=0.2, seed=N + 5)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, variant)
+    x = inputs.random_vector(m.n_global, seed=500 + N)
+    for screen, lam in [(0, 0.1), (1, 0.7)]:
+        y_or = o.apply_A(x, lam, screen)
+        y = m.apply_A(_to_dev(x), lam=lam, screen=screen, prec=hb.HB_F64X).cpu().numpy()
+        assert _rel(y, y_or) <= 1e-12
+        assert np.abs(y - y_or).max() <= 1e-12 * np.abs(y_or).max()
+
+
+def test_double_float_split_edge_values():
+    """Inputs whose magnitudes leave the float range of the split (tiny,
+    huge, zero, negative zero) still give the FP64 operator's result."""
+    m, o = _pair((2, 2, 2), 4, rho=0.1, seed=2)
+    x = inputs.random_vector(m.n_global, seed=9)
+    x[0], x[1], x[2], x[3] = 0.0, -0.0, 1e-300, -3e-41
+    x[4], x[5] = 2.0 ** -126, -(2.0 ** -127)
+    x *= 1.0
+    y_or = o.apply_A(x, 0.1, 0)
+    y = m.apply_A(_to_dev(x), lam=0.1, prec=hb.HB_F64X).cpu().numpy()
+    assert np.abs(y - y_or).max() <= 1e-12 * np.abs(y_or).max()
+    big = x * 1e30
+    y_or = o.apply_A(big, 0.1, 0)
+    y = m.apply_A(_to_dev(big), lam=0.1, prec=hb.HB_F64X).cpu().numpy()
+    assert np.abs(y - y_or).max() <= 1e-12 * np.abs(y_or).max()
+
+
+def test_cg_double_float_matches_oracle():
+    """CG (Algorithm 1) with the double-float operator: 50 fixed iterations
+    agree with the oracle's iterates as closely as the FP64 path does."""
+    m, o = _pair((4, 3, 3), 5, rho=0.15, seed=4)
+    b = m.rhs(kind=0, seed=4)
+    x_or, it_or, rel_or, st_or = o.cg(b.cpu().numpy(), 0.1, rtol=0.0, max_it=50)
+    x, res = m.cg(b, lam=0.1, rtol=0.0, max_it=50, prec=hb.HB_F64X)
+    assert res.status == hb.HB_OK and res.iters == 50
+    assert _rel(x.cpu().numpy(), x_or) <= 1e-9
+    x2, res2 = m.cg(b, lam=0.1, rtol=1e-10, max_it=5000, prec=hb.HB_F64X)
+    assert res2.status == hb.HB_OK and res2.rel_res <= 1e-10
+    r = b - m.apply_A(x2, lam=0.1)
+    assert float(torch.linalg.norm(r) / torch.linalg.norm(b)) <= 1e-9
+
+
 def test_apply_A_reproducible_and_linear():
     m, o = _pair((4, 4, 3), 5, rho=0.2, seed=3)
     x = _to_dev(inputs.random_vector(m.n_global, seed=1))
