@@ -609,6 +609,74 @@ def run_c5(args, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+def run_split(args, rank, world, local):
+    """Split operator with the halo / gather exchanges overlapped (Sec. 3.3),
+    ranks emulated on one GPU: per rank grid, mean of `reps` back-to-back
+    applications of the partitioned A against the one-mesh A (same pencil
+    kernel, variant 3), the halo exchange alone, and the sum of the per-kernel
+    device times over all ranks (above the wall time when ranks overlap)."""
+    import time
+
+    import torch
+
+    from paper_2202_12477_gb300 import hb, inputs
+    torch.cuda.set_device(local)
+    N = args.N
+    dims = c2_dims(N, args.local_nodes)
+    m = hb.Mesh(*dims, N, perturb=0.1, seed=0, fp32=False)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, 3)
+    x_lex = inputs.random_vector(m.n_global, 1)
+    reps = args.reps
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    xd = torch.from_numpy(x_lex).cuda()
+    yd = torch.empty_like(xd)
+    ms_fused = timed(lambda: m.apply_A(xd, yd, lam=0.1))
+    grids = [tuple(int(v) for v in g.split("x")) for g in args.split_grids.split(",")]
+    for grid in grids:
+        t0 = time.time()
+        part = hb.Part(m, *grid, seed=0)
+        t_build = time.time() - t0
+        xp = torch.from_numpy(x_lex[part.perm]).cuda()
+        yp = torch.empty_like(xp)
+        ms_split = timed(lambda: part.apply_A(xp, yp, lam=0.1))
+        ms_exch = timed(lambda: part.halo_exchange(xp))
+        # per-kernel device times over all ranks (one pass, events on each rank's stream)
+        torch.cuda.synchronize()
+        hb.hb_profile_reset()
+        hb.hb_profile_enable(True)
+        part.apply_A(xp, yp, lam=0.1)
+        torch.cuda.synchronize()
+        hb.hb_profile_enable(False)
+        kern = {}
+        for name in ("ax_local", "part_pack", "part_halo_gather", "part_local_gather", "part_final"):
+            t, c = hb.hb_profile_read(name)
+            kern[name] = {"ms": t, "launches": c}
+        err = float(torch.max(torch.abs(yp - yd[torch.from_numpy(part.perm.astype('int64')).cuda()]))
+                    / torch.max(torch.abs(yd)))
+        print(json.dumps({"workload": "split operator, virtual ranks on one GPU", "N": N, "elements": list(dims),
+                          "n_global": m.n_global, "ranks": list(grid), "n_shared": part.info.n_shared,
+                          "exchange_values": part.info.exchange_values, "build_s": t_build,
+                          "ms_fused": ms_fused, "ms_split": ms_split, "split_over_fused": ms_split / ms_fused,
+                          "ms_halo_exchange_alone": ms_exch, "kernels_one_apply": kern,
+                          "kernel_sum_ms": sum(v["ms"] for v in kern.values()),
+                          "max_rel_diff_vs_fused": err, "reps": reps}), flush=True)
+        part.close()
+        del xp, yp
+        torch.cuda.empty_cache()
+
+
 def run_c1(args, rank, world, local):
     """Small latency-bound solve: 4^3 elements, N=7, perturb 0.1h, lambda 0.1,
     uniform rhs, exactly 100 FP64 CG iterations (runs replayed as CUDA graphs)."""
@@ -664,7 +732,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "sweep", "c1", "c3", "c4", "c5", "probe"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "sweep", "c1", "c3", "c4", "c5", "probe", "split"])
+    ap.add_argument("--split-grids", default="1x1x1,2x1x1,2x2x2,4x4x2")
     ap.add_argument("--c5-requests", type=int, default=200)
     ap.add_argument("--c5-emax", type=int, default=32)
     ap.add_argument("--c5-slots", type=int, default=32)
@@ -692,6 +761,8 @@ def main():
         run_sweep(args, rank, world, local)
     elif args.workload == "c1":
         run_c1(args, rank, world, local)
+    elif args.workload == "split":
+        run_split(args, rank, world, local)
     elif args.workload == "probe":
         run_probe(args, rank, world, local)
     elif args.workload == "c3":

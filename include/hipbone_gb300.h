@@ -219,6 +219,68 @@ hb_status hb_diag_A(hb_mesh *mesh, hb_screen screen, double lambda, double *host
 hb_status hb_cg_solve(const hb_mesh *mesh, const hb_cg_opts *opts, const double *b,
                       double *x, hb_cg_result *res, void *stream);
 
+/* ---------------------------------------------------------------- partitioned operator
+ * The operator split the way a distributed run applies it (Sec. 3.3,
+ * "Overlapping halo and gather communication", and its operator timeline
+ * figure), with the ranks emulated on one GPU: the element box is cut into
+ * px x py x pz blocks of elements, one virtual rank each, every rank with its
+ * own CUDA streams, element data and exchange buffers in device memory.
+ *  - A node shared by elements of several ranks is a halo node; an element
+ *    holding one is a halo element, the others are interior elements.
+ *  - Each assembled DOF has one owner: a DOF of one rank's elements belongs to
+ *    it; a halo DOF goes to one of the ranks that hold it, picked at random
+ *    but fairly (uniformly among them, by u01(seed, 3, g), g its lexicographic
+ *    global id).
+ *  - Vectors are in partition order: rank 0's owned DOFs, then rank 1's, ...,
+ *    each rank's in lexicographic order (hb_part_copy_perm gives the map).
+ * y = A x runs per rank as: pack the owned values other ranks need; element
+ * kernel on the first half of the interior elements while the halo values are
+ * copied into the receivers' halo buffers; element kernel on the halo
+ * elements; gather their partial sums at halo nodes into send buffers; element
+ * kernel on the other half of the interior elements and the rank-local gather
+ * Z^T while those partial sums are copied to the owners; the owners add them
+ * in rank order. The result equals hb_apply_A's up to the order of the sums.
+ * Precision FP64; the element kernel is the mesh's FP64 pencil variant
+ * (variant 0 runs as variant 3). */
+typedef struct hb_part hb_part;
+typedef struct {
+    int n_ranks;
+    int64_t n_global;
+    int64_t n_shared;        /* DOFs held by more than one rank */
+    int64_t exchange_values; /* values each halo exchange moves (= each gather exchange) */
+} hb_part_info_t;
+typedef struct {
+    int64_t n_owned, offset;          /* owned DOFs and their start in partition order */
+    int64_t n_halo;                   /* DOFs other ranks own that this rank's elements hold */
+    int64_t n_send;                   /* owned values sent per halo exchange */
+    int64_t n_elem_interior1, n_elem_halo, n_elem_interior2;
+} hb_part_rank_info_t;
+
+/* Builds the partition of `mesh` (which must outlive it) on the mesh's device;
+ * 1 <= px <= ex (same for y, z), px*py*pz <= 64. Host work O(n_local);
+ * synchronises `stream`. */
+hb_status hb_part_create(const hb_mesh *mesh, int px, int py, int pz, uint64_t seed, void *stream,
+                         hb_part **out);
+hb_status hb_part_destroy(hb_part *part);
+hb_status hb_part_info(const hb_part *part, hb_part_info_t *out);
+hb_status hb_part_rank_info(const hb_part *part, int rank, hb_part_rank_info_t *out);
+/* perm_host[i] = the mesh's (lexicographic) global id of partition-order DOF i;
+ * n_global int32 values; synchronous. */
+hb_status hb_part_copy_perm(const hb_part *part, int32_t *perm_host);
+/* y = A x with x, y FP64 device vectors of n_global values in partition order
+ * (x and y must not overlap). Ordered after and before `stream`. */
+hb_status hb_part_apply_A(const hb_part *part, hb_screen screen, double lambda, const double *x, double *y,
+                          void *stream);
+/* The halo exchange alone: fills every rank's halo buffer from x (partition
+ * order); with halo_host != NULL also copies rank `rank`'s halo buffer
+ * (n_halo doubles) there and synchronises. */
+hb_status hb_part_halo_exchange(const hb_part *part, const double *x, int rank, double *halo_host, void *stream);
+/* hb_cg_solve (HB_F64, no preconditioner) with the partitioned operator; b and x
+ * in partition order. Dot products run over the concatenated owned segments
+ * (the sum over ranks in rank order of each rank's part). */
+hb_status hb_part_cg_solve(const hb_part *part, const hb_cg_opts *opts, const double *b, double *x,
+                           hb_cg_result *res, void *stream);
+
 /* ---------------------------------------------------------------- serving
  * A CG server with continuous batching on one GPU (the paper runs one solve at
  * a time; the server applies Algorithm 1 in the FP32-inner / FP64

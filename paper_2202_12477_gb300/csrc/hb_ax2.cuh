@@ -209,6 +209,9 @@ struct pencil_args {
     S lambda;
     int screen;
     double *partials;
+    // l2g entries g <= -2 read halo[-2 - g] (values of DOFs another partition
+    // owns, filled by a halo exchange); -1 is a masked node
+    const S *halo;
 };
 
 // Position of surface node (i,j,k) in its element's surface block:
@@ -279,7 +282,10 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
         for (int k = 0; k < n; k++) {
             const int g = __ldcs(lg + k * n2);
             gl[k] = g;
-            U[P::at(p0, p1, k)] = g >= 0 ? to_c(__ldg(x + g)) : T(0);
+            S v = S(0);
+            if (g >= 0) v = __ldg(x + g);
+            else if (g < -1) v = __ldg(A.halo + (-2 - g));
+            U[P::at(p0, p1, k)] = to_c(v);
         }
     }
     __syncthreads();

@@ -39,6 +39,24 @@ hb_status hb_launch_ax2_f64(const hb_mesh *m, const double *x, double *ysurf, do
     }
 }
 
+// Pencil kernel on a contiguous range of E elements given by its own arrays
+// (l2g, geo and ysurf start at the range's first element); l2g entries <= -2
+// read halo values. Used by the partitioned operator.
+hb_status hb_launch_ax2_f64_range(int N, int64_t E, const double *x, const double *halo, const int32_t *l2g,
+                                  const double *geo, double *ysurf, double *y, double lambda, int screen,
+                                  const int *run, int eo, int eb_mult, cudaStream_t s)
+{
+    hb2::pencil_args A{x, l2g, geo, ysurf, y, E, run, lambda, screen, nullptr, halo};
+    switch (N) {
+#define HB_CASE(NN) \
+    case NN: return eo ? hb2::launch<NN, true>(A, eb_mult, s, nullptr) : hb2::launch<NN, false>(A, eb_mult, s, nullptr);
+        HB_CASE(1) HB_CASE(2) HB_CASE(3) HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8)
+        HB_CASE(9) HB_CASE(10) HB_CASE(11) HB_CASE(12) HB_CASE(13) HB_CASE(14) HB_CASE(15)
+#undef HB_CASE
+    default: hb_set_error("unsupported N=%d", N); return HB_ERR_ARG;
+    }
+}
+
 int hb_surf_count(int N) { return 2 * (N + 1) * (N + 1) + 4 * N * (N - 1); }
 
 // ---------------------------------------------------------------- serving

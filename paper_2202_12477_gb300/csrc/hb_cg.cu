@@ -545,7 +545,7 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
     HB_TRY_CUDA(cudaEventRecord(m->ev0, s));
     hb_cg_state fin{};
     if (o->prec == HB_F64 || o->prec == HB_F64X) {
-        // r0 = b - A x0, p = r0 (Algorithm 1, lines 4-5)
+        // r0 = b - A x0, p = r0 (the start of Algorithm 1)
         rs = hb_apply_A_impl(m, o->prec, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
         if (rs != HB_OK) return rs;
         hb_count_launch();

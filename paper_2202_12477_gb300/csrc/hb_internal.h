@@ -140,6 +140,9 @@ hb_status hb_launch_ax2_f32(const hb_mesh *m, const float *x, float *ysurf, floa
                             double *partials, const int *run, int eo, int eb_mult, cudaStream_t s,
                             int64_t *nblocks);
 int hb_surf_count(int N);  // surface nodes of one element: 2 n^2 + 4 N (N-1)
+hb_status hb_launch_ax2_f64_range(int N, int64_t E, const double *x, const double *halo, const int32_t *l2g,
+                                  const double *geo, double *ysurf, double *y, double lambda, int screen,
+                                  const int *run, int eo, int eb_mult, cudaStream_t s);
 hb_status hb_launch_ax2_f64x(const hb_mesh *m, const double *x, double *ysurf, double *y, double lambda, int screen,
                              double *partials, const int *run, int eb_mode, cudaStream_t s, int64_t *nblocks);
 hb_status hb_ax2_upload_f64x(const double *D_all);

@@ -267,7 +267,7 @@ __device__ __forceinline__ void cg_init_body(const double *__restrict__ b, const
     }
 }
 
-// Algorithm 1, line 9 and the dot of line 10: r -= alpha Ap. With the
+// Algorithm 1: r -= alpha Ap and the new r.r. With the
 // preconditioner (PREC) also z = M^-1 r, the new r.z (for beta) and r.r (for
 // the stopping test); without it r.r serves both.
 template <typename T, bool PREC>
@@ -328,7 +328,7 @@ __device__ __forceinline__ void cg_update_r_body(T *__restrict__ r, const T *__r
     }
 }
 
-// Algorithm 1, lines 8 and 11 (x += alpha p with the old p, then p = r + beta p).
+// Algorithm 1: x += alpha p with the old p, then p = r + beta p.
 // The block that finishes last ends the iteration: run <- next_run.
 template <typename T>
 __device__ __forceinline__ void cg_update_xp_body(T *__restrict__ x, T *__restrict__ p, const T *__restrict__ r, int64_t n,

@@ -62,6 +62,16 @@ class hb_server_stats_t(C.Structure):
                 ("mem_used", C.c_size_t)]
 
 
+class hb_part_info_t(C.Structure):
+    _fields_ = [("n_ranks", C.c_int), ("n_global", C.c_int64), ("n_shared", C.c_int64),
+                ("exchange_values", C.c_int64)]
+
+
+class hb_part_rank_info_t(C.Structure):
+    _fields_ = [("n_owned", C.c_int64), ("offset", C.c_int64), ("n_halo", C.c_int64), ("n_send", C.c_int64),
+                ("n_elem_interior1", C.c_int64), ("n_elem_halo", C.c_int64), ("n_elem_interior2", C.c_int64)]
+
+
 class HBError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -87,6 +97,16 @@ _SIGS = [
     ("hb_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
                               C.POINTER(hb_cg_result), C.c_void_p]),
     ("hb_u01", C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64]),
+    ("hb_part_create", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_void_p,
+                                 C.POINTER(C.c_void_p)]),
+    ("hb_part_destroy", C.c_int, [C.c_void_p]),
+    ("hb_part_info", C.c_int, [C.c_void_p, C.POINTER(hb_part_info_t)]),
+    ("hb_part_rank_info", C.c_int, [C.c_void_p, C.c_int, C.POINTER(hb_part_rank_info_t)]),
+    ("hb_part_copy_perm", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("hb_part_apply_A", C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("hb_part_halo_exchange", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("hb_part_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
+                                   C.POINTER(hb_cg_result), C.c_void_p]),
     ("hb_server_create", C.c_int, [C.POINTER(hb_server_opts), C.POINTER(C.c_void_p)]),
     ("hb_server_submit", C.c_int, [C.c_void_p, C.POINTER(hb_mesh_desc), C.POINTER(hb_cg_opts), C.c_uint64,
                                    C.c_int, C.POINTER(C.c_int64)]),
@@ -318,6 +338,81 @@ class Mesh:
         out = np.zeros(7 * self.n_local, dtype=np.float64)
         _check(lib().hb_mesh_copy_geo(self.handle, out.ctypes.data_as(C.c_void_p)))
         return out
+
+
+# ---------------------------------------------------------------- partitioned operator
+
+class Part:
+    """Owns one hb_part: the operator split over px*py*pz virtual ranks of
+    `mesh` (which must stay open). Vectors are FP64 torch CUDA tensors in
+    partition order; `perm[i]` is the mesh's global id of entry i."""
+
+    def __init__(self, mesh, px, py, pz, seed=0, stream=None):
+        import numpy as np
+        self.mesh = mesh
+        h = C.c_void_p()
+        _check(lib().hb_part_create(mesh.handle, px, py, pz, seed, _stream_ptr(stream), C.byref(h)))
+        self.handle = h
+        info = hb_part_info_t()
+        _check(lib().hb_part_info(h, C.byref(info)))
+        self.info = info
+        self.n_ranks = info.n_ranks
+        self.n_global = info.n_global
+        self.perm = np.empty(self.n_global, dtype=np.int32)
+        _check(lib().hb_part_copy_perm(h, self.perm.ctypes.data_as(C.c_void_p)))
+
+    def rank_info(self, rank) -> hb_part_rank_info_t:
+        out = hb_part_rank_info_t()
+        _check(lib().hb_part_rank_info(self.handle, rank, C.byref(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().hb_part_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vec(self):
+        import torch
+        return torch.zeros(self.n_global, dtype=torch.float64, device="cuda")
+
+    def apply_A(self, x, y=None, lam=0.0, screen=HB_SCREEN_IDENTITY, stream=None):
+        import torch
+        assert x.is_cuda and x.dtype == torch.float64 and x.numel() == self.n_global
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().hb_part_apply_A(self.handle, screen, lam, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                     _stream_ptr(stream)))
+        return y
+
+    def halo_exchange(self, x, rank=-1, stream=None):
+        """Fills every rank's halo buffer from x; returns rank `rank`'s buffer
+        as a numpy array (None for rank < 0)."""
+        import numpy as np
+        if rank < 0:
+            _check(lib().hb_part_halo_exchange(self.handle, C.c_void_p(x.data_ptr()), -1, None,
+                                               _stream_ptr(stream)))
+            return None
+        out = np.empty(self.rank_info(rank).n_halo, dtype=np.float64)
+        _check(lib().hb_part_halo_exchange(self.handle, C.c_void_p(x.data_ptr()), rank,
+                                           out.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
+        return out
+
+    def cg(self, b, x=None, lam=0.0, rtol=0.0, max_it=100, screen=HB_SCREEN_IDENTITY, stream=None):
+        if x is None:
+            x = self.vec()
+        opts = hb_cg_opts(HB_F64, screen, lam, rtol, max_it, 0.0, 0, 0)
+        res = hb_cg_result()
+        st = lib().hb_part_cg_solve(self.handle, C.byref(opts), C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
+                                    C.byref(res), _stream_ptr(stream))
+        if st not in (HB_OK, HB_ERR_NOT_CONVERGED, HB_ERR_BREAKDOWN):
+            _check(st)
+        return x, res
 
 
 # ---------------------------------------------------------------- server
