@@ -222,32 +222,36 @@ def run_gb300(args, rank, world, local):
     b = m.rhs(kind=0, seed=0)
     x = m.vec()
 
-    # warm-up: W iterations
-    m.cg(b, x=x.zero_(), lam=lam, rtol=0.0, max_it=args.warmup)
+    # one stepwise solve of W + K iterations: its start (r0 = b - A x0) and the
+    # W warm-up iterations run before the timed region, which holds exactly
+    # the K timed iterations
+    x.zero_()
+    m.cg_begin(b, x, lam=lam, rtol=0.0, max_it=args.warmup + args.steps)
+    m.cg_iterate(args.warmup)
     torch.cuda.synchronize()
 
     hb.hb_profile_reset()
     hb.hb_profile_enable(True)
     launches0 = hb.hb_kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    x.zero_()
     with ClockSampler(gpu_uuid()) as clk:
         dist.barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
-        _, res = m.cg(b, x=x, lam=lam, rtol=0.0, max_it=args.steps)
+        m.cg_iterate(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
         dist.barrier()
     launches = hb.hb_kernel_launches() - launches0
     hb.hb_profile_enable(False)
+    res = m.cg_finish()
     t_ms = ev0.elapsed_time(ev1)
     t_max = dist.max(t_ms)
     kern = {}
     for name in ("ax_local", "assemble", "cg_update_r", "cg_update_xp"):
         ms, cnt = hb.hb_profile_read(name)
         kern[name] = {"ms_total": ms, "launches": cnt, "ms_avg": ms / cnt if cnt else None}
-    assert res.iters == args.steps, (res.iters, args.steps)
+    assert res.iters == args.warmup + args.steps, (res.iters, args.warmup, args.steps)
 
     # end to end: pinned host b in, solve through the C ABI, x back to pinned host
     b_host = b.cpu().pin_memory()
@@ -677,6 +681,54 @@ def run_split(args, rank, world, local):
         torch.cuda.empty_cache()
 
 
+def run_scat(args, rank, world, local):
+    """Assembled against scattered (NekBone) storage: FP64 CG time per
+    iteration over `steps` fixed iterations on the degree-sweep mesh (same
+    pencil element kernel, variant 3), with each scheme's algorithmic bytes
+    per iteration (Sec. 3.1's claim that assembled storage moves fewer)."""
+    import torch
+
+    from paper_2202_12477_gb300 import accounting as acc
+    from paper_2202_12477_gb300 import hb
+    torch.cuda.set_device(local)
+    pk = peaks()
+    Ns = [int(v) for v in args.degrees.split(",")] if args.degrees else [args.N]
+    K = max(args.steps, 10)
+    for N in Ns:
+        dims = c2_dims(N, args.local_nodes)
+        m = hb.Mesh(*dims, N, perturb=0.1, seed=0, fp32=False)
+        hb.hb_set_kernel_variant(m.handle, hb.HB_F64, 3)
+        sc = hb.Scat(m)
+        b = m.rhs(kind=0, seed=0)
+        bL = sc.scatter(b)
+        out = {"workload": "assembled vs scattered storage, FP64 CG", "N": N, "elements": list(dims),
+               "n_global": m.n_global, "n_local": m.n_local, "iterations": K}
+        for name, solve in (("assembled", lambda: m.cg(b, lam=0.1, rtol=0.0, max_it=K)),
+                            ("scattered", lambda: sc.cg(bL, lam=0.1, rtol=0.0, max_it=K))):
+            solve()  # warm-up (graph capture on the assembled path)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, res = solve()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            nb = (acc.assembled_cg_min_bytes(m.n_global, m.n_local) if name == "assembled"
+                  else acc.scattered_cg_min_bytes(m.n_local))
+            out[name] = {"ms_per_iter": ms, "gdofs": m.n_global / (ms * 1e-3) / 1e9, "iters": res.iters,
+                         "rel_res": res.rel_res, "min_bytes_per_iter": nb,
+                         "bytes_time_at_hbm_peak_ms": nb / (pk["hbm_gbs"] * 1e9) * 1e3}
+        out["scattered_over_assembled_time"] = out["scattered"]["ms_per_iter"] / out["assembled"]["ms_per_iter"]
+        out["scattered_over_assembled_bytes"] = (out["scattered"]["min_bytes_per_iter"]
+                                                 / out["assembled"]["min_bytes_per_iter"])
+        out["residual_rel_diff"] = abs(out["scattered"]["rel_res"] - out["assembled"]["rel_res"]) / max(
+            out["assembled"]["rel_res"], 1e-300)
+        print(json.dumps(out), flush=True)
+        sc.close()
+        m.close()
+        torch.cuda.empty_cache()
+
+
 def run_c1(args, rank, world, local):
     """Small latency-bound solve: 4^3 elements, N=7, perturb 0.1h, lambda 0.1,
     uniform rhs, exactly 100 FP64 CG iterations (runs replayed as CUDA graphs)."""
@@ -732,7 +784,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "sweep", "c1", "c3", "c4", "c5", "probe", "split"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "sweep", "c1", "c3", "c4", "c5", "probe", "split", "scat"])
     ap.add_argument("--split-grids", default="1x1x1,2x1x1,2x2x2,4x4x2")
     ap.add_argument("--c5-requests", type=int, default=200)
     ap.add_argument("--c5-emax", type=int, default=32)
@@ -763,6 +815,8 @@ def main():
         run_c1(args, rank, world, local)
     elif args.workload == "split":
         run_split(args, rank, world, local)
+    elif args.workload == "scat":
+        run_scat(args, rank, world, local)
     elif args.workload == "probe":
         run_probe(args, rank, world, local)
     elif args.workload == "c3":

@@ -219,6 +219,19 @@ hb_status hb_diag_A(hb_mesh *mesh, hb_screen screen, double lambda, double *host
 hb_status hb_cg_solve(const hb_mesh *mesh, const hb_cg_opts *opts, const double *b,
                       double *x, hb_cg_result *res, void *stream);
 
+/* Stepwise form of hb_cg_solve for HB_F64 / HB_F64X (with or without the
+ * Jacobi preconditioner), for callers that time or interleave iterations:
+ * hb_cg_begin computes r0 = b - A x0 and the solver state (enqueued on
+ * `stream`, no host wait); hb_cg_iterate enqueues up to `count` more
+ * iterations (never past opts->max_it; kernels of a solve that has met rtol
+ * return at once) without waiting for the host; hb_cg_finish waits and fills
+ * res (time_ms = 0) with the status rules of hb_cg_solve. One stepwise solve
+ * per mesh at a time; b and x must stay valid until hb_cg_finish, and the
+ * mesh's other solver calls must not run in between. */
+hb_status hb_cg_begin(hb_mesh *mesh, const hb_cg_opts *opts, const double *b, double *x, void *stream);
+hb_status hb_cg_iterate(hb_mesh *mesh, int count, void *stream);
+hb_status hb_cg_finish(hb_mesh *mesh, hb_cg_result *res, void *stream);
+
 /* ---------------------------------------------------------------- partitioned operator
  * The operator split the way a distributed run applies it (Sec. 3.3,
  * "Overlapping halo and gather communication", and its operator timeline
@@ -279,6 +292,37 @@ hb_status hb_part_halo_exchange(const hb_part *part, const double *x, int rank, 
  * in partition order. Dot products run over the concatenated owned segments
  * (the sum over ranks in rank order of each rank's part). */
 hb_status hb_part_cg_solve(const hb_part *part, const hb_cg_opts *opts, const double *b, double *x,
+                           hb_cg_result *res, void *stream);
+
+/* ---------------------------------------------------------------- scattered storage
+ * NekBone's storage of the DOF vectors (Sec. 2, the scattered form, and
+ * Sec. 3.1 "DOF Storage"): vectors have n_local entries x_L = Z x_G, one per
+ * element node (element e's node q at e (N+1)^3 + q, q = i + n (j + n k)), and
+ * the operator is b_L = (Z Z^T S_L + lambda I) x_L: the element-local S_L on
+ * x_L, then the gather-scatter Z Z^T, which sums the copies of each DOF and
+ * writes the sum back to every copy. Masked (Dirichlet) nodes hold 0. Inner
+ * products are weighted by the inverse multiplicity c_L = 1 / (Z^T Z)_gg (0 at
+ * masked nodes), so (a_L, b_L)_c = a_G . b_G. The library offers it to measure
+ * the paper's claim that assembled storage moves fewer bytes per CG iteration;
+ * results equal the assembled path's up to rounding. FP64 only. */
+typedef struct hb_scat hb_scat;
+/* Builds the weights, the masked-node list and the copy map of `mesh` (which
+ * must outlive it); synchronises `stream`. */
+hb_status hb_scat_create(const hb_mesh *mesh, void *stream, hb_scat **out);
+hb_status hb_scat_destroy(hb_scat *sc);
+/* x_L = Z x_G (x_G: n_global doubles; x_L: n_local doubles; device). */
+hb_status hb_scat_scatter(const hb_scat *sc, const double *xG, double *xL, void *stream);
+/* y_L = (Z Z^T S_L + lambda I) x_L (identity screening) or with lambda M_gg
+ * x_g at every copy (mass screening); x_L, y_L device, n_local doubles, must
+ * not overlap. */
+hb_status hb_scat_apply_A(const hb_scat *sc, hb_screen screen, double lambda, const double *xL, double *yL,
+                          void *stream);
+/* Weighted inner product sum_q c_q a_q b_q (fixed-order FP64 reduction) into
+ * *out_host; synchronises `stream`. */
+hb_status hb_scat_dot(const hb_scat *sc, const double *aL, const double *bL, double *out_host, void *stream);
+/* Algorithm 1 on scattered vectors with weighted inner products (HB_F64, no
+ * preconditioner); b_L and x_L (x0 in, solution out) device, n_local doubles. */
+hb_status hb_scat_cg_solve(const hb_scat *sc, const hb_cg_opts *opts, const double *bL, double *xL,
                            hb_cg_result *res, void *stream);
 
 /* ---------------------------------------------------------------- serving

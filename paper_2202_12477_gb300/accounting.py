@@ -72,6 +72,23 @@ def assemble_bytes(NG: int, nnz: int, esz: int) -> int:
     return (esz + 4) * nnz + (4 + 2 * esz) * NG
 
 
+def assembled_cg_min_bytes(NG: int, NL: int) -> int:
+    """Least bytes of one CG iteration on assembled vectors with p.Ap and r.r
+    fused into the kernels that produce their operands: A p (16 N_G + 52 N_L),
+    r -= alpha Ap (read r, Ap; write r: 24 N_G), x += alpha p and
+    p = r + beta p (read x, p, r; write x, p: 40 N_G) = 80 N_G + 52 N_L."""
+    return 80 * NG + 52 * NL
+
+
+def scattered_cg_min_bytes(NL: int) -> int:
+    """The same iteration on scattered vectors (Sec. 2, Sec. 3.1): A p reads
+    p_L and the six factors and writes y_L (64 N_L, no node map); the weighted
+    p.Ap, fused, still reads the weights (8 N_L); r -= alpha Ap with the
+    weighted r.r reads r, Ap, c and writes r (32 N_L); the x, p update moves
+    40 N_L: 144 N_L."""
+    return 144 * NL
+
+
 def box_dofs(N: int, Ex: int, Ey: int, Ez: int) -> int:
     """Global DOFs of a box with Dirichlet nodes on all six faces."""
     return (N * Ex - 1) * (N * Ey - 1) * (N * Ez - 1)

@@ -277,10 +277,13 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
 
     int gl[n];  // node ids of this thread's t-line (i,j) = (p0,p1)
     if (active) {
-        const int32_t *lg = l2g + e * n3 + a;
+        // l2g == nullptr: x and y are scattered (length n_local) vectors, node q
+        // of element e at e n^3 + q
+        const int32_t *lg = l2g ? l2g + e * n3 + a : nullptr;
+        const int lbase = (int)(e * n3 + a);
 #pragma unroll
         for (int k = 0; k < n; k++) {
-            const int g = __ldcs(lg + k * n2);
+            const int g = lg ? __ldcs(lg + k * n2) : lbase + k * n2;
             gl[k] = g;
             S v = S(0);
             if (g >= 0) v = __ldg(x + g);

@@ -57,6 +57,24 @@ hb_status hb_launch_ax2_f64_range(int N, int64_t E, const double *x, const doubl
     }
 }
 
+// Pencil kernel on scattered vectors (x_L, y_L of length n_local, no l2g):
+// interior nodes of every element get y_L = (S_L x_L) + lambda term, surface
+// nodes go to ysurf for the gather-scatter.
+hb_status hb_launch_ax2_f64_scat(const hb_mesh *m, const double *xL, double *ysurf, double *yL, double lambda,
+                                 int screen, const int *run, int eo, int eb_mult, cudaStream_t s)
+{
+    if (!m->geo) { hb_set_error("mesh has no double geometric factors"); return HB_ERR_ARG; }
+    hb2::pencil_args A{xL, nullptr, m->geo, ysurf, yL, m->E, run, lambda, screen, nullptr, nullptr};
+    switch (m->N) {
+#define HB_CASE(NN) \
+    case NN: return eo ? hb2::launch<NN, true>(A, eb_mult, s, nullptr) : hb2::launch<NN, false>(A, eb_mult, s, nullptr);
+        HB_CASE(1) HB_CASE(2) HB_CASE(3) HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8)
+        HB_CASE(9) HB_CASE(10) HB_CASE(11) HB_CASE(12) HB_CASE(13) HB_CASE(14) HB_CASE(15)
+#undef HB_CASE
+    default: hb_set_error("unsupported N=%d", m->N); return HB_ERR_ARG;
+    }
+}
+
 int hb_surf_count(int N) { return 2 * (N + 1) * (N + 1) + 4 * N * (N - 1); }
 
 // ---------------------------------------------------------------- serving

@@ -604,6 +604,93 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
     return R.status;
 }
 
+// ---------------------------------------------------------------- stepwise solve
+
+extern "C" hb_status hb_cg_begin(hb_mesh *m, const hb_cg_opts *o, const double *b, double *x, void *stream)
+{
+    hb_clear_error();
+    if (!m || !o || ((!b || !x) && m->n_global)) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (!valid_screen(o->screen)) { hb_set_error("bad screen mode"); return HB_ERR_ARG; }
+    if (o->prec != HB_F64 && o->prec != HB_F64X) { hb_set_error("hb_cg_begin takes HB_F64 or HB_F64X"); return HB_ERR_ARG; }
+    if (o->max_it < 0 || !(o->rtol >= 0.0)) { hb_set_error("bad max_it or rtol"); return HB_ERR_ARG; }
+    if (o->precond != 0 && o->precond != 1) { hb_set_error("precond must be 0 or 1"); return HB_ERR_ARG; }
+    hb_device_guard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    m->step.active = 0;
+    const int64_t n = m->n_global;
+    hb_status rs = cg_workspace(m);
+    if (rs != HB_OK) return rs;
+    if (o->precond) {
+        rs = hb_mesh_inv_diag(m, o->screen, o->lambda, s);
+        if (rs != HB_OK) return rs;
+    }
+    if (n > 0) {
+        const int64_t ns = cg_stride(n);
+        double *r = (double *)m->cg_vec, *p = r + ns, *Ap = p + ns;
+        rs = hb_apply_A_impl(m, o->prec, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
+        if (rs != HB_OK) return rs;
+        hb_count_launch();
+        cg_init_kernel<<<red_grid(n), HB_RED_THREADS, 0, s>>>(b, Ap, r, p, o->precond ? m->inv_diag : nullptr, n,
+                                                              o->rtol, o->max_it, m->partials, m->counters + 2,
+                                                              m->state);
+        HB_CHECK_LAUNCH();
+    }
+    m->step.active = 1;
+    m->step.o = *o;
+    m->step.b = b;
+    m->step.x = x;
+    m->step.done = 0;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_cg_iterate(hb_mesh *m, int count, void *stream)
+{
+    hb_clear_error();
+    if (!m) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (!m->step.active) { hb_set_error("no stepwise solve begun on this mesh"); return HB_ERR_ARG; }
+    if (count < 0) { hb_set_error("count < 0"); return HB_ERR_ARG; }
+    const hb_cg_opts &o = m->step.o;
+    count = std::min(count, o.max_it - m->step.done);
+    if (count <= 0 || m->n_global == 0) return HB_OK;
+    hb_device_guard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t ns = cg_stride(m->n_global);
+    double *r = (double *)m->cg_vec, *p = r + ns, *Ap = p + ns, *z = Ap + ns;
+    const double *inv_d = o.precond ? m->inv_diag : nullptr;
+    double *x = m->step.x;
+    hb_status rs = hb_profiling_on()
+                       ? cg_iterations<double>(m, o.prec, o.screen, o.lambda, x, r, p, Ap, z, inv_d, m->state, count,
+                                               s)
+                       : cg_iterations_graph<double>(m, o.prec, o.screen, o.lambda, x, r, p, Ap, z, inv_d, m->state,
+                                                     count, s);
+    if (rs != HB_OK) return rs;
+    m->step.done += count;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_cg_finish(hb_mesh *m, hb_cg_result *res, void *stream)
+{
+    hb_clear_error();
+    if (!m) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (!m->step.active) { hb_set_error("no stepwise solve begun on this mesh"); return HB_ERR_ARG; }
+    hb_device_guard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    m->step.active = 0;
+    hb_cg_result R{};
+    R.status = HB_OK;
+    if (m->n_global > 0) {
+        HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, m->state, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
+        HB_TRY_CUDA(cudaStreamSynchronize(s));
+        const hb_cg_state fin = *m->state_host;
+        R.iters = fin.it;
+        R.rel_res = fin.bb > 0.0 ? sqrt(fin.res2 / fin.bb) : 0.0;
+        if (fin.status == HB_ERR_BREAKDOWN) R.status = HB_ERR_BREAKDOWN;
+        else if (m->step.o.rtol > 0.0 && fin.res2 > fin.tol2) R.status = HB_ERR_NOT_CONVERGED;
+    }
+    if (res) *res = R;
+    return R.status;
+}
+
 // ---------------------------------------------------------------- dot without any allocation
 //
 // hb_dot needs a mesh, and a mesh holds device memory the library allocated.

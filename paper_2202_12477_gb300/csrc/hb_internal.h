@@ -105,6 +105,14 @@ struct hb_mesh {
     int32_t *scols;     // [nnz_s] e * surf_count + surface index, ascending
     double *ax_partials;  // [max element-kernel blocks] per-block partials of x.y
     int64_t n_ax_partials;
+    // stepwise solve (hb_cg_begin / hb_cg_iterate / hb_cg_finish)
+    struct cg_step {
+        int active;
+        hb_cg_opts o;
+        const double *b;
+        double *x;
+        int done;
+    } step;
     // captured runs of CG iterations (replayed while the key matches)
     cudaStream_t cg_stream;
     cudaEvent_t cg_ev[2];
@@ -140,6 +148,9 @@ hb_status hb_launch_ax2_f32(const hb_mesh *m, const float *x, float *ysurf, floa
                             double *partials, const int *run, int eo, int eb_mult, cudaStream_t s,
                             int64_t *nblocks);
 int hb_surf_count(int N);  // surface nodes of one element: 2 n^2 + 4 N (N-1)
+int hb_surf_pos(int N, int i, int j, int k);  // node's place in the surface block; -1 inside
+hb_status hb_launch_ax2_f64_scat(const hb_mesh *m, const double *xL, double *ysurf, double *yL, double lambda,
+                                 int screen, const int *run, int eo, int eb_mult, cudaStream_t s);
 hb_status hb_launch_ax2_f64_range(int N, int64_t E, const double *x, const double *halo, const int32_t *l2g,
                                   const double *geo, double *ysurf, double *y, double lambda, int screen,
                                   const int *run, int eo, int eb_mult, cudaStream_t s);

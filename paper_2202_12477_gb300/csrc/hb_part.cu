@@ -225,11 +225,13 @@ hb_status alloc(hb_part *P, size_t count, T **d)
     return HB_OK;
 }
 
+}  // namespace
+
 // Surface position of node (i,j,k) in its element's surface block (the order
 // the pencil kernel writes: k = 0 face, k = N face, then per slab k = 1..N-1
 // the ring j = 0 row, j = N row, then i = 0 / i = N for j = 1..N-1); -1 for an
 // element-interior node.
-int surf_pos(int N, int i, int j, int k)
+int hb_surf_pos(int N, int i, int j, int k)
 {
     const int n = N + 1, n2 = n * n;
     if (k == 0) return j * n + i;
@@ -239,6 +241,8 @@ int surf_pos(int N, int i, int j, int k)
     const int r = j == 0 ? i : (j == N ? N + 1 + i : 2 * (N + 1) + 2 * (j - 1) + (i == N ? 1 : 0));
     return 2 * n2 + (k - 1) * 4 * N + r;
 }
+
+namespace {
 
 // CSR from (row, col) pairs: rows 0..nrows-1, columns ascending per row.
 void build_csr(int64_t nrows, std::vector<std::pair<int32_t, int32_t>> &rc, std::vector<int32_t> &rowptr,
@@ -420,7 +424,7 @@ hb_status build(hb_part *P, cudaStream_t s)
             for (int k = 0; k < n; k++)
                 for (int j = 0; j < n; j++)
                     for (int i = 0; i < n; i++) {
-                        const int sp = surf_pos(N, i, j, k);
+                        const int sp = hb_surf_pos(N, i, j, k);
                         if (sp < 0) continue;
                         const int32_t c = lc[(size_t)el * n3 + (k * n + j) * n + i];
                         if (c == -1) continue;

@@ -97,6 +97,16 @@ _SIGS = [
     ("hb_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
                               C.POINTER(hb_cg_result), C.c_void_p]),
     ("hb_u01", C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64]),
+    ("hb_cg_begin", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("hb_cg_iterate", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    ("hb_cg_finish", C.c_int, [C.c_void_p, C.POINTER(hb_cg_result), C.c_void_p]),
+    ("hb_scat_create", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("hb_scat_destroy", C.c_int, [C.c_void_p]),
+    ("hb_scat_scatter", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("hb_scat_apply_A", C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("hb_scat_dot", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    ("hb_scat_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
+                                   C.POINTER(hb_cg_result), C.c_void_p]),
     ("hb_part_create", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_void_p,
                                  C.POINTER(C.c_void_p)]),
     ("hb_part_destroy", C.c_int, [C.c_void_p]),
@@ -321,6 +331,23 @@ class Mesh:
         res = hb_cg_solve(self.handle, opts, b.data_ptr(), x.data_ptr(), stream)
         return x, res
 
+    def cg_begin(self, b, x, lam=0.0, rtol=0.0, max_it=100, prec=HB_F64, screen=HB_SCREEN_IDENTITY, precond=0,
+                 stream=None):
+        """Stepwise solve: r0 and the state (see hb_cg_begin); b and x must stay alive until cg_finish."""
+        opts = hb_cg_opts(prec, screen, lam, rtol, max_it, 0.0, 0, precond)
+        _check(lib().hb_cg_begin(self.handle, C.byref(opts), C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
+                                 _stream_ptr(stream)))
+
+    def cg_iterate(self, count, stream=None):
+        _check(lib().hb_cg_iterate(self.handle, count, _stream_ptr(stream)))
+
+    def cg_finish(self, stream=None) -> hb_cg_result:
+        res = hb_cg_result()
+        st = lib().hb_cg_finish(self.handle, C.byref(res), _stream_ptr(stream))
+        if st not in (HB_OK, HB_ERR_NOT_CONVERGED, HB_ERR_BREAKDOWN):
+            _check(st)
+        return res
+
     def diag_A(self, lam=0.0, screen=HB_SCREEN_IDENTITY, stream=None):
         import numpy as np
         out = np.zeros(self.n_global)
@@ -413,6 +440,68 @@ class Part:
         if st not in (HB_OK, HB_ERR_NOT_CONVERGED, HB_ERR_BREAKDOWN):
             _check(st)
         return x, res
+
+
+# ---------------------------------------------------------------- scattered storage
+
+class Scat:
+    """Owns one hb_scat: NekBone's scattered (n_local) vectors of `mesh`
+    (which must stay open). Vectors are FP64 torch CUDA tensors of n_local."""
+
+    def __init__(self, mesh, stream=None):
+        self.mesh = mesh
+        h = C.c_void_p()
+        _check(lib().hb_scat_create(mesh.handle, _stream_ptr(stream), C.byref(h)))
+        self.handle = h
+        self.n_local = mesh.n_local
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().hb_scat_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vec(self):
+        import torch
+        return torch.zeros(self.n_local, dtype=torch.float64, device="cuda")
+
+    def scatter(self, xG, xL=None, stream=None):
+        if xL is None:
+            xL = self.vec()
+        _check(lib().hb_scat_scatter(self.handle, C.c_void_p(xG.data_ptr()), C.c_void_p(xL.data_ptr()),
+                                     _stream_ptr(stream)))
+        return xL
+
+    def apply_A(self, xL, yL=None, lam=0.0, screen=HB_SCREEN_IDENTITY, stream=None):
+        import torch
+        assert xL.is_cuda and xL.dtype == torch.float64 and xL.numel() == self.n_local
+        if yL is None:
+            yL = torch.empty_like(xL)
+        _check(lib().hb_scat_apply_A(self.handle, screen, lam, C.c_void_p(xL.data_ptr()), C.c_void_p(yL.data_ptr()),
+                                     _stream_ptr(stream)))
+        return yL
+
+    def dot(self, a, b, stream=None) -> float:
+        out = C.c_double()
+        _check(lib().hb_scat_dot(self.handle, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), C.byref(out),
+                                 _stream_ptr(stream)))
+        return out.value
+
+    def cg(self, bL, xL=None, lam=0.0, rtol=0.0, max_it=100, screen=HB_SCREEN_IDENTITY, stream=None):
+        if xL is None:
+            xL = self.vec()
+        opts = hb_cg_opts(HB_F64, screen, lam, rtol, max_it, 0.0, 0, 0)
+        res = hb_cg_result()
+        st = lib().hb_scat_cg_solve(self.handle, C.byref(opts), C.c_void_p(bL.data_ptr()),
+                                    C.c_void_p(xL.data_ptr()), C.byref(res), _stream_ptr(stream))
+        if st not in (HB_OK, HB_ERR_NOT_CONVERGED, HB_ERR_BREAKDOWN):
+            _check(st)
+        return xL, res
 
 
 # ---------------------------------------------------------------- server

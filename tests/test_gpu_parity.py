@@ -303,6 +303,27 @@ def test_cg_mixed_precision_reaches_fp64_residual(N, lam):
     assert err <= 1e-6
 
 
+@pytest.mark.parametrize("prec,precond", [(hb.HB_F64, 0), (hb.HB_F64, 1), (hb.HB_F64X, 0)])
+def test_stepwise_cg_equals_one_call(prec, precond):
+    """hb_cg_begin + hb_cg_iterate (in pieces) + hb_cg_finish gives the same
+    iterate, bit for bit, as hb_cg_solve with the same iteration count; the
+    iteration count never passes max_it."""
+    m, o = _pair((3, 3, 2), 5, rho=0.1, seed=8)
+    b = m.rhs(kind=0, seed=8)
+    x1, r1 = m.cg(b, lam=0.1, rtol=0.0, max_it=20, prec=prec, precond=precond)
+    x2 = m.vec()
+    m.cg_begin(b, x2, lam=0.1, rtol=0.0, max_it=20, prec=prec, precond=precond)
+    m.cg_iterate(7)
+    m.cg_iterate(5)
+    m.cg_iterate(50)
+    r2 = m.cg_finish()
+    assert r2.iters == 20 and r2.status == hb.HB_OK
+    assert torch.equal(x1, x2)
+    assert r2.rel_res == r1.rel_res
+    with pytest.raises(hb.HBError):
+        m.cg_iterate(1)  # finished: no solve begun
+
+
 def test_cg_zero_rhs_and_breakdown():
     m = hb.Mesh(2, 2, 2, 3)
     b = m.vec()
