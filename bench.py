@@ -392,12 +392,13 @@ def run_sweep(args, rank, world, local):
                 hb.hb_profile_reset()
                 hb.hb_profile_enable(True)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
                 reps = args.reps
-                for _ in range(reps):
-                    m.apply_A(x, y, lam=0.1, prec=hbprec)
-                e1.record()
-                torch.cuda.synchronize()
+                with ClockSampler(gpu_uuid()) as clk:
+                    e0.record()
+                    for _ in range(reps):
+                        m.apply_A(x, y, lam=0.1, prec=hbprec)
+                    e1.record()
+                    torch.cuda.synchronize()
                 hb.hb_profile_enable(False)
                 t = e0.elapsed_time(e1) / reps
                 axm, axn = hb.hb_profile_read("ax_local")
@@ -411,7 +412,7 @@ def run_sweep(args, rank, world, local):
                        "eff_gbs_method_min": acc.ax_min_bytes(m.n_global, m.n_local, esz) / (t * 1e-3) / 1e9,
                        "ax_local_gbs": acc.ax_local_bytes(m.n_global, m.n_local, esz) / (axm / axn * 1e-3) / 1e9,
                        "assemble_gbs": acc.assemble_bytes(m.n_global, m.info.nnz, esz) / (asm / asn * 1e-3) / 1e9,
-                       "hbm_peak_gbs": pk["hbm_gbs"]}
+                       "hbm_peak_gbs": pk["hbm_gbs"], "clocks": clk.summary()}
                 rec["hbm_frac_method_min"] = rec["eff_gbs_method_min"] / pk["hbm_gbs"]
                 rec["alu_frac"] = (acc.op_local_flops(m.E, N) / (axm / axn * 1e-3) / 1e12
                                    / (pk["fp64_tflops"] if prec == "f64" else pk["fp32_tflops"]))

@@ -214,6 +214,22 @@ struct pencil_args {
     const S *halo;
 };
 
+// ------------------------------------------------------------ L2 prefetch
+// One thread asks the memory system to bring a block's geometric factors
+// (contiguous in memory) into L2 with a bulk prefetch, so their DRAM reads
+// overlap the x gather and the first contractions. Only the 16-byte-aligned
+// interior of the range is named; nothing is waited for.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uintptr_t lo = (a + 15) & ~uintptr_t(15), hi = (a + bytes) & ~uintptr_t(15);
+    for (uintptr_t q = lo; q < hi;) {
+        const uintptr_t chunk = hi - q < (uintptr_t(1) << 20) ? hi - q : (uintptr_t(1) << 20);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"((unsigned)chunk) : "memory");
+        q += chunk;
+    }
+}
+
 // Position of surface node (i,j,k) in its element's surface block:
 // the k = 0 face, the k = N face, then for k = 1..N-1 the ring of 4N nodes of
 // that slab (j = 0 row, j = N row, then i = 0 / i = N for j = 1..N-1).
@@ -254,7 +270,13 @@ __host__ __device__ constexpr int pencil_min_blocks()
 // threads of the block; further threads only join the barriers. Adds the
 // group's interior-node x.y to `acc`. Every thread of the block must call it
 // (it synchronises the block).
-template <int N, bool EO, int EB>
+// Gather modes: GM_L2G reads x through l2g (-1 = masked); GM_HALO also reads
+// halo[-2 - g] for l2g entries g <= -2 (partitioned operator); GM_SCAT reads
+// scattered vectors, node q of element e at e n^3 + q (no l2g). A template
+// parameter, so the common kernel carries no branch for the other two.
+enum { GM_L2G = 0, GM_HALO = 1, GM_SCAT = 2 };
+
+template <int N, bool EO, int EB, int GM = GM_L2G>
 __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, T *sm,
                                              hbacc::dot_acc<S> &acc)
 {
@@ -277,18 +299,28 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
 
     int gl[n];  // node ids of this thread's t-line (i,j) = (p0,p1)
     if (active) {
-        // l2g == nullptr: x and y are scattered (length n_local) vectors, node q
-        // of element e at e n^3 + q
-        const int32_t *lg = l2g ? l2g + e * n3 + a : nullptr;
-        const int lbase = (int)(e * n3 + a);
+        if constexpr (GM == GM_SCAT) {
+            const int lbase = (int)(e * n3 + a);
 #pragma unroll
-        for (int k = 0; k < n; k++) {
-            const int g = lg ? __ldcs(lg + k * n2) : lbase + k * n2;
-            gl[k] = g;
-            S v = S(0);
-            if (g >= 0) v = __ldg(x + g);
-            else if (g < -1) v = __ldg(A.halo + (-2 - g));
-            U[P::at(p0, p1, k)] = to_c(v);
+            for (int k = 0; k < n; k++) {
+                gl[k] = lbase + k * n2;
+                U[P::at(p0, p1, k)] = to_c(__ldg(x + gl[k]));
+            }
+        } else {
+            const int32_t *lg = l2g + e * n3 + a;
+#pragma unroll
+            for (int k = 0; k < n; k++) {
+                const int g = __ldcs(lg + k * n2);
+                gl[k] = g;
+                if constexpr (GM == GM_HALO) {
+                    S v = S(0);
+                    if (g >= 0) v = __ldg(x + g);
+                    else if (g < -1) v = __ldg(A.halo + (-2 - g));
+                    U[P::at(p0, p1, k)] = to_c(v);
+                } else {
+                    U[P::at(p0, p1, k)] = g >= 0 ? to_c(__ldg(x + g)) : T(0);
+                }
+            }
         }
     }
     __syncthreads();
@@ -369,14 +401,22 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
     __syncthreads();  // the block's buffers are reused by the next group
 }
 
-template <int N, bool EO, int EB>
+template <int N, bool EO, int EB, bool PF = false, int GM = GM_L2G>
 __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, EB>()))
     ax_pencil_kernel(const pencil_args A)
 {
     if (A.run && *A.run == 0) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     hbacc::dot_acc<S> acc;
-    pencil_group<N, EO, EB>(A, blockIdx.x, reinterpret_cast<T *>(smem_raw), acc);
+    if constexpr (PF) {
+        if (threadIdx.x == 0) {
+            constexpr int64_t n3 = (N + 1) * (N + 1) * (N + 1);
+            const int64_t e0 = (int64_t)blockIdx.x * EB;
+            const int64_t cnt = A.E - e0 < EB ? A.E - e0 : EB;
+            prefetch_l2(A.geo + e0 * 7 * n3, (size_t)(cnt * 7 * n3) * sizeof(S));
+        }
+    }
+    pencil_group<N, EO, EB, GM>(A, blockIdx.x, reinterpret_cast<T *>(smem_raw), acc);
     if (A.partials) {
         const double v = hbacc::block_sum(acc.value());
         if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
@@ -392,17 +432,19 @@ namespace hb2 {
 namespace {
 
 // eb_mode: 1 = about 256 threads per block, 2 = twice that many elements
-// (N <= 10), 0 = one element per block (spreads small meshes over more SMs).
-template <int N, bool EO>
+// (N <= 10), 0 = one element per block (spreads small meshes over more SMs),
+// 3 = as 1 with a bulk L2 prefetch of the block's geometric factors at the
+// start (even-odd only).
+template <int N, bool EO, int GM = GM_L2G>
 hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nblocks_out)
 {
     constexpr int n = N + 1, n2 = n * n;
     constexpr int EB1 = n2 >= 256 ? 1 : 256 / n2;
     if (A.E <= 0) return HB_OK;
-    static int attr_set[3][32] = {{0}};
+    static int attr_set[4][32] = {{0}};
     int dev = 0;
     HB_TRY_CUDA(cudaGetDevice(&dev));
-    const int which = (eb_mode == 2 && n2 <= 128) ? 1 : (eb_mode == 0 ? 2 : 0);
+    const int which = (eb_mode == 2 && n2 <= 128) ? 1 : (eb_mode == 0 ? 2 : (eb_mode == 3 ? 3 : 0));
     auto go = [&](auto kern, int EB) -> hb_status {
         const size_t smem = sizeof(T) * 4 * (size_t)EB * pad<N>::size;
         if (dev >= 0 && dev < 32 && !attr_set[which][dev]) {
@@ -416,13 +458,21 @@ hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nbl
         HB_CHECK_LAUNCH();
         return HB_OK;
     };
-    if constexpr (n2 <= 128) {
-        if (which == 1) return go(ax_pencil_kernel<N, EO, EB1 * 2>, EB1 * 2);
+    if constexpr (GM != GM_L2G) {
+        // partitioned and scattered operators: the base block shape only
+        return go(ax_pencil_kernel<N, EO, EB1, false, GM>, EB1);
+    } else {
+        if constexpr (n2 <= 128) {
+            if (which == 1) return go(ax_pencil_kernel<N, EO, EB1 * 2>, EB1 * 2);
+        }
+        if constexpr (EO && EB1 > 1) {
+            if (which == 2) return go(ax_pencil_kernel<N, EO, 1>, 1);
+        }
+        if constexpr (EO) {
+            if (which == 3) return go(ax_pencil_kernel<N, EO, EB1, true>, EB1);
+        }
+        return go(ax_pencil_kernel<N, EO, EB1>, EB1);
     }
-    if constexpr (EO && EB1 > 1) {
-        if (which == 2) return go(ax_pencil_kernel<N, EO, 1>, 1);
-    }
-    return go(ax_pencil_kernel<N, EO, EB1>, EB1);
 }
 
 }  // namespace

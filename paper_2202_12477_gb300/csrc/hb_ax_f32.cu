@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(HB_SERVE_THREADS, 1)
 {
     const hb_slot_desc &d = *D;
     if (!d.active || St->inner.run == 0) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     pencil_args A{(const T *)d.p32, d.l2g, d.geo32, (T *)d.ysurf, (T *)d.Ap32, d.E, nullptr, (T)d.lambda,
                   d.screen, d.ax_partials};

@@ -39,17 +39,20 @@ hb_status hb_launch_ax2_f64(const hb_mesh *m, const double *x, double *ysurf, do
     }
 }
 
-// Pencil kernel on a contiguous range of E elements given by its own arrays
-// (l2g, geo and ysurf start at the range's first element); l2g entries <= -2
-// read halo values. Used by the partitioned operator.
+// Pencil kernel (even-odd, base block shape) on a contiguous range of E
+// elements given by its own arrays (l2g, geo and ysurf start at the range's
+// first element); l2g entries <= -2 read halo values. Used by the partitioned
+// operator; eo and eb_mult are accepted for symmetry and not used.
 hb_status hb_launch_ax2_f64_range(int N, int64_t E, const double *x, const double *halo, const int32_t *l2g,
                                   const double *geo, double *ysurf, double *y, double lambda, int screen,
                                   const int *run, int eo, int eb_mult, cudaStream_t s)
 {
+    (void)eo;
+    (void)eb_mult;
     hb2::pencil_args A{x, l2g, geo, ysurf, y, E, run, lambda, screen, nullptr, halo};
     switch (N) {
 #define HB_CASE(NN) \
-    case NN: return eo ? hb2::launch<NN, true>(A, eb_mult, s, nullptr) : hb2::launch<NN, false>(A, eb_mult, s, nullptr);
+    case NN: return hb2::launch<NN, true, hb2::GM_HALO>(A, 1, s, nullptr);
         HB_CASE(1) HB_CASE(2) HB_CASE(3) HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8)
         HB_CASE(9) HB_CASE(10) HB_CASE(11) HB_CASE(12) HB_CASE(13) HB_CASE(14) HB_CASE(15)
 #undef HB_CASE
@@ -57,17 +60,20 @@ hb_status hb_launch_ax2_f64_range(int N, int64_t E, const double *x, const doubl
     }
 }
 
-// Pencil kernel on scattered vectors (x_L, y_L of length n_local, no l2g):
-// interior nodes of every element get y_L = (S_L x_L) + lambda term, surface
-// nodes go to ysurf for the gather-scatter.
+// Pencil kernel (even-odd, base block shape) on scattered vectors (x_L, y_L
+// of length n_local, no l2g): interior nodes of every element get
+// y_L = (S_L x_L) + lambda term, surface nodes go to ysurf for the
+// gather-scatter; eo and eb_mult are accepted for symmetry and not used.
 hb_status hb_launch_ax2_f64_scat(const hb_mesh *m, const double *xL, double *ysurf, double *yL, double lambda,
                                  int screen, const int *run, int eo, int eb_mult, cudaStream_t s)
 {
     if (!m->geo) { hb_set_error("mesh has no double geometric factors"); return HB_ERR_ARG; }
+    (void)eo;
+    (void)eb_mult;
     hb2::pencil_args A{xL, nullptr, m->geo, ysurf, yL, m->E, run, lambda, screen, nullptr, nullptr};
     switch (m->N) {
 #define HB_CASE(NN) \
-    case NN: return eo ? hb2::launch<NN, true>(A, eb_mult, s, nullptr) : hb2::launch<NN, false>(A, eb_mult, s, nullptr);
+    case NN: return hb2::launch<NN, true, hb2::GM_SCAT>(A, 1, s, nullptr);
         HB_CASE(1) HB_CASE(2) HB_CASE(3) HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8)
         HB_CASE(9) HB_CASE(10) HB_CASE(11) HB_CASE(12) HB_CASE(13) HB_CASE(14) HB_CASE(15)
 #undef HB_CASE
@@ -122,7 +128,7 @@ __global__ void __launch_bounds__(HB_SERVE_THREADS, 1)
 {
     const hb_slot_desc &d = *D;
     if (!d.active || St->phase != HB_SLOT_OUTER) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     pencil_args A{(const T *)d.x, d.l2g, d.geo, (T *)d.ysurf, (T *)d.Ap, d.E, nullptr, (T)d.lambda,
                   d.screen, nullptr};

@@ -189,7 +189,7 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
     if (prec == HB_F64X) {
         // double-float element kernel (pencil, even-odd); block shape from the FP64 variant
         const int v64 = m->variant[0];
-        const int ebm = (v64 & HB_VAR_ONE) ? 0 : ((v64 & HB_VAR_EB2) ? 2 : 1);
+        const int ebm = hb_variant_eb_mode(v64);
         double *partials = dot_mode != HB_DOT_NONE ? m->ax_partials : nullptr;
         int64_t nblk = 0;
         hb_status r = hb_launch_ax2_f64x(m, (const double *)x, (double *)m->yL, (double *)y, lambda, screen,
@@ -199,7 +199,7 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
                                             screen, lambda, partials ? nblk : 0, st, dot_mode, s);
     }
     const int v = m->variant[prec == HB_F64 ? 0 : 1];
-    const int eo = (v & HB_VAR_EO) ? 1 : 0, ebm = (v & HB_VAR_ONE) ? 0 : ((v & HB_VAR_EB2) ? 2 : 1);
+    const int eo = (v & HB_VAR_EO) ? 1 : 0, ebm = hb_variant_eb_mode(v);
     hb_status r;
     if (!(v & HB_VAR_PENCIL)) {
         if (prec == HB_F64) {
@@ -346,7 +346,8 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
         return HB_ERR_NOMEM;
     }
     const int candidates[] = {0, HB_VAR_PENCIL, HB_VAR_PENCIL | HB_VAR_EO, HB_VAR_PENCIL | HB_VAR_EB2,
-                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_EB2, HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE};
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_EB2, HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE,
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_TMA};
     const int saved = m->variant[pi];
     int best = saved;
     float best_ms = 1e30f;

@@ -162,14 +162,22 @@ hb_status hb_ax2_upload_f32(const double *D_all);
 
 // Element-kernel variants (bit flags): v1 = 0; HB_VAR_PENCIL = pencil kernel;
 // HB_VAR_EO = even-odd split (pencil only); HB_VAR_EB2 = two element groups per
-// block; HB_VAR_ONE = one element per block (with PENCIL | EO only).
-enum { HB_VAR_PENCIL = 1, HB_VAR_EO = 2, HB_VAR_EB2 = 4, HB_VAR_ONE = 8, HB_VAR_MAX = 15 };
+// block; HB_VAR_ONE = one element per block (with PENCIL | EO only);
+// HB_VAR_TMA = bulk L2 prefetch of each block's geometric factors at its
+// start (with PENCIL | EO only).
+enum { HB_VAR_PENCIL = 1, HB_VAR_EO = 2, HB_VAR_EB2 = 4, HB_VAR_ONE = 8, HB_VAR_TMA = 16, HB_VAR_MAX = 31 };
 static inline bool hb_valid_variant(int v)
 {
     if (v == 0) return true;
     if (v < 0 || v > HB_VAR_MAX || !(v & HB_VAR_PENCIL)) return false;
-    if (v & HB_VAR_ONE) return (v & HB_VAR_EO) && !(v & HB_VAR_EB2);
+    if ((v & HB_VAR_ONE) && (v & HB_VAR_TMA)) return false;
+    if (v & (HB_VAR_ONE | HB_VAR_TMA)) return (v & HB_VAR_EO) && !(v & HB_VAR_EB2);
     return true;
+}
+// eb_mode of the pencil launchers for a variant
+static inline int hb_variant_eb_mode(int v)
+{
+    return (v & HB_VAR_ONE) ? 0 : (v & HB_VAR_TMA) ? 3 : (v & HB_VAR_EB2) ? 2 : 1;
 }
 
 
