@@ -387,9 +387,18 @@ double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx);
  *                         bulk L2 prefetch (cp.async.bulk.prefetch) of the block's
  *                         geometric factors at its start, so their DRAM reads
  *                         overlap the x gather and the first contractions.
+ *   HB_VARIANT_WS         (with PENCIL | EVEN_ODD; HB_F32, odd N) persistent
+ *                         warp-specialised kernel: a producer warp stages each
+ *                         element group's node map and geometric factors in shared
+ *                         memory with cp.async.bulk (mbarrier-tracked) while the
+ *                         other warps compute the previous group. Other precisions
+ *                         and even N run PENCIL | EVEN_ODD. Its waits are bounded:
+ *                         one that gives up makes the next hb_cg_solve,
+ *                         hb_cg_finish or hb_autotune on the mesh return
+ *                         HB_ERR_TIMEOUT.
  * The default is PENCIL | EVEN_ODD; hb_autotune measures and picks per mesh. */
 enum { HB_VARIANT_PENCIL = 1, HB_VARIANT_EVEN_ODD = 2, HB_VARIANT_EB2 = 4, HB_VARIANT_ONE = 8,
-       HB_VARIANT_TMA = 16 };
+       HB_VARIANT_TMA = 16, HB_VARIANT_WS = 32 };
 hb_status hb_set_kernel_variant(hb_mesh *mesh, hb_precision prec, int variant);
 hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *variant);
 
@@ -397,8 +406,9 @@ hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *var
  * made from measurements, Sec. 3.2; here every variant is timed on the mesh
  * itself). Runs one untimed and `reps` timed applications of A for each
  * variant (0, PENCIL, PENCIL|EVEN_ODD, PENCIL|EB2, PENCIL|EVEN_ODD|EB2,
- * PENCIL|EVEN_ODD|ONE, PENCIL|EVEN_ODD|TMA) on `stream`, keeps the fastest for
- * `prec` on this mesh and returns it in *best_variant. ms_per_variant (may be NULL) has 32 slots
+ * PENCIL|EVEN_ODD|ONE, PENCIL|EVEN_ODD|TMA, PENCIL|EVEN_ODD|WS) on `stream`, keeps
+ * the fastest for `prec` on this mesh and returns it in *best_variant.
+ * ms_per_variant (may be NULL) has 64 slots
  * indexed by variant and receives the mean time of each. Allocates two scratch vectors for the
  * duration of the call; synchronises `stream`. */
 hb_status hb_autotune(hb_mesh *mesh, hb_precision prec, hb_screen screen, double lambda, int reps,

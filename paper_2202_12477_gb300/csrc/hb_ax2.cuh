@@ -132,6 +132,70 @@ static inline hb_status upload_tables(const double *D_all)
     return HB_OK;
 }
 
+// ------------------------------------------------------------ staged pipeline
+// The warp-specialised variant (WS): a producer warp copies each element
+// group's node map and geometric factors (contiguous in memory) into shared
+// memory with cp.async.bulk; mbarriers count the bytes in ("full") and the
+// consumer warps' releases ("empty"). Every wait is bounded: after kWaitTries
+// polls it records bit 0 in the kernel's error word and carries on, so no
+// thread ever leaves the common control flow (the results are then wrong and
+// the error is reported by the host).
+constexpr unsigned kWaitTries = 1u << 24;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Announces `bytes` on the barrier and starts the copy (addresses and size
+// multiples of 16 bytes).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Waits (bounded) for phase `parity` of the barrier to complete.
+__device__ __forceinline__ void mbar_wait(uint64_t *bar, unsigned parity, unsigned *err)
+{
+    const unsigned a = smem_u32(bar);
+    for (unsigned t = 0; t < kWaitTries; t++) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return;
+    }
+    if (err) atomicOr(err, 1u);
+}
+
+// Shared state of one WS block for the group being computed.
+struct ws_ctx {
+    const int32_t *lsm;  // staged node map of the group
+    const void *gsm;     // staged geometric factors of the group (S)
+    uint64_t *full_l, *empty_l, *full_g, *empty_g;
+    unsigned parity;     // phase parity of this group's barriers
+    unsigned *err;
+};
+
 // ------------------------------------------------------------ line contractions
 
 // Applies M = D (TR = false) or D^T (TR = true) to one line held in `in`
@@ -212,6 +276,7 @@ struct pencil_args {
     // l2g entries g <= -2 read halo[-2 - g] (values of DOFs another partition
     // owns, filled by a halo exchange); -1 is a masked node
     const S *halo;
+    unsigned *err;  // WS kernels: bit 0 set when a bounded wait gave up
 };
 
 // ------------------------------------------------------------ L2 prefetch
@@ -276,11 +341,25 @@ __host__ __device__ constexpr int pencil_min_blocks()
 // parameter, so the common kernel carries no branch for the other two.
 enum { GM_L2G = 0, GM_HALO = 1, GM_SCAT = 2 };
 
-template <int N, bool EO, int EB, int GM = GM_L2G>
+// Barrier of the threads computing a group: the whole block, or (WS) the
+// consumer warps only (named barrier 1), the producer warp running apart.
+template <bool WS, int NC>
+__device__ __forceinline__ void group_sync()
+{
+    if constexpr (WS) asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory");
+    else __syncthreads();
+}
+
+template <int N, int EB>
+__host__ __device__ constexpr int ws_consumers() { return (EB * (N + 1) * (N + 1) + 31) / 32 * 32; }
+
+template <int N, bool EO, int EB, int GM = GM_L2G, bool WS = false>
 __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, T *sm,
-                                             hbacc::dot_acc<S> &acc)
+                                             hbacc::dot_acc<S> &acc, const ws_ctx *w = nullptr)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    constexpr int NC = ws_consumers<N, EB>();
+    static_assert(!WS || GM == GM_L2G, "the staged pipeline reads x through l2g");
     using P = pad<N>;
     const S *__restrict__ x = A.x;
     const int32_t *__restrict__ l2g = A.l2g;
@@ -307,10 +386,11 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
                 U[P::at(p0, p1, k)] = to_c(__ldg(x + gl[k]));
             }
         } else {
-            const int32_t *lg = l2g + e * n3 + a;
+            const int32_t *lg = WS ? w->lsm + el * n3 + a : l2g + e * n3 + a;
+            if constexpr (WS) mbar_wait(w->full_l, w->parity, w->err);
 #pragma unroll
             for (int k = 0; k < n; k++) {
-                const int g = __ldcs(lg + k * n2);
+                const int g = WS ? lg[k * n2] : __ldcs(lg + k * n2);
                 gl[k] = g;
                 if constexpr (GM == GM_HALO) {
                     S v = S(0);
@@ -322,8 +402,15 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
                 }
             }
         }
+    } else if constexpr (WS) {
+        mbar_wait(w->full_l, w->parity, w->err);  // keep every thread's phase in step
     }
-    __syncthreads();
+    if constexpr (WS) {
+        // this warp is done with the staged node map
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(w->empty_l);
+    }
+    group_sync<WS, NC>();
     if (active) {
         T in[n];
         // r-line (j,k) = (p0,p1)
@@ -339,15 +426,22 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
         for (int m = 0; m < n; m++) in[m] = U[P::at(p0, p1, m)];
         line_st<N, false, EO>(in, [&](int m, T v) { B3[P::at(p0, p1, m)] = v; });
     }
-    __syncthreads();
+    group_sync<WS, NC>();
+    if constexpr (WS) mbar_wait(w->full_g, w->parity, w->err);
     if (active) {
         // metric factors at the t-line's nodes (coalesced rows of n^2 per factor)
-        const S *ge = geo + e * 7 * n3 + a;
+        const S *ge = WS ? static_cast<const S *>(w->gsm) + el * 7 * n3 + a : geo + e * 7 * n3 + a;
 #pragma unroll
         for (int k = 0; k < n; k++) {
             const S *g = ge + k * 7 * n2;
-            const T grr = to_c(__ldcs(g)), grs = to_c(__ldcs(g + n2)), grt = to_c(__ldcs(g + 2 * n2));
-            const T gss = to_c(__ldcs(g + 3 * n2)), gst = to_c(__ldcs(g + 4 * n2)), gtt = to_c(__ldcs(g + 5 * n2));
+            T grr, grs, grt, gss, gst, gtt;
+            if constexpr (WS) {
+                grr = to_c(g[0]), grs = to_c(g[n2]), grt = to_c(g[2 * n2]);
+                gss = to_c(g[3 * n2]), gst = to_c(g[4 * n2]), gtt = to_c(g[5 * n2]);
+            } else {
+                grr = to_c(__ldcs(g)), grs = to_c(__ldcs(g + n2)), grt = to_c(__ldcs(g + 2 * n2));
+                gss = to_c(__ldcs(g + 3 * n2)), gst = to_c(__ldcs(g + 4 * n2)), gtt = to_c(__ldcs(g + 5 * n2));
+            }
             const int q = P::at(p0, p1, k);
             const T ur = B1[q], us = B2[q], ut = B3[q];
             B1[q] = fma(grt, ut, fma(grs, us, grr * ur));
@@ -355,7 +449,12 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
             B3[q] = fma(gtt, ut, fma(gst, us, grt * ur));
         }
     }
-    __syncthreads();
+    if constexpr (WS) {
+        // this warp is done with the staged factors
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(w->empty_g);
+    }
+    group_sync<WS, NC>();
     if (active) {
         // D^T along each direction, in place (the whole line is in registers
         // before any output of it is stored)
@@ -370,7 +469,7 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
         for (int m = 0; m < n; m++) in[m] = B3[P::at(p0, p1, m)];
         line_st<N, true, EO>(in, [&](int m, T v) { B3[P::at(p0, p1, m)] = v; });
     }
-    __syncthreads();
+    group_sync<WS, NC>();
     if (active) {
         constexpr int NS = surf_count<N>();
         S *ys = A.ysurf + e * NS;
@@ -398,7 +497,7 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
             }
         }
     }
-    __syncthreads();  // the block's buffers are reused by the next group
+    group_sync<WS, NC>();  // the buffers are reused by the next group
 }
 
 template <int N, bool EO, int EB, bool PF = false, int GM = GM_L2G>
@@ -423,6 +522,83 @@ __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, E
     }
 }
 
+// ------------------------------------------------------------ WS kernel
+// Shared memory of a WS block: the four element buffers (T), then from
+// 128-byte boundaries the staged factors (S) and node map of one group.
+template <int N, int EB>
+__host__ __device__ constexpr int ws_off_g() { return ((int)sizeof(T) * 4 * EB * pad<N>::size + 127) / 128 * 128; }
+template <int N, int EB>
+__host__ __device__ constexpr int ws_off_l()
+{
+    return (ws_off_g<N, EB>() + (int)sizeof(S) * 7 * EB * (N + 1) * (N + 1) * (N + 1) + 127) / 128 * 128;
+}
+template <int N, int EB>
+__host__ __device__ constexpr int ws_smem() { return ws_off_l<N, EB>() + 4 * EB * (N + 1) * (N + 1) * (N + 1); }
+template <int N, int EB>
+__host__ __device__ constexpr int ws_min_blocks()
+{
+    constexpr int by_smem = (228 * 1024) / (ws_smem<N, EB>() + 1024);
+    constexpr int by_threads = 2048 / (ws_consumers<N, EB>() + 32);
+    constexpr int b = by_smem < by_threads ? by_smem : by_threads;
+    return b < 1 ? 1 : (b > 4 ? 4 : b);
+}
+// Bulk copies need whole elements in 16-byte multiples (n even) and room.
+template <int N, int EB>
+__host__ __device__ constexpr bool ws_ok()
+{
+    return (N + 1) % 2 == 0 && ws_smem<N, EB>() <= 200 * 1024;
+}
+
+// Persistent: block b computes groups b, b + gridDim.x, ...; the last warp
+// stages the next group's node map as soon as the consumers have read the
+// current one, and its factors as soon as they have applied the current ones,
+// so the DRAM reads of group i+1 overlap the computation of group i.
+template <int N, int EB>
+__global__ void __launch_bounds__(ws_consumers<N, EB>() + 32, (ws_min_blocks<N, EB>()))
+    ax_pencil_ws_kernel(const pencil_args A)
+{
+    if (A.run && *A.run == 0) return;
+    constexpr int n3 = (N + 1) * (N + 1) * (N + 1), NC = ws_consumers<N, EB>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t bars[4];  // full_l, empty_l, full_g, empty_g
+    T *bufs = reinterpret_cast<T *>(smem_raw);
+    S *gsm = reinterpret_cast<S *>(smem_raw + ws_off_g<N, EB>());
+    int32_t *lsm = reinterpret_cast<int32_t *>(smem_raw + ws_off_l<N, EB>());
+    const int64_t ngroups = (A.E + EB - 1) / EB;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], NC / 32);
+        mbar_init(&bars[2], 1);
+        mbar_init(&bars[3], NC / 32);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    hbacc::dot_acc<S> acc;
+    if (threadIdx.x >= NC) {
+        if (threadIdx.x == NC) {  // producer (one lane of the last warp)
+            unsigned i = 0;
+            for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, i++) {
+                const int64_t e0 = g * EB, cnt = A.E - e0 < EB ? A.E - e0 : EB;
+                if (i > 0) mbar_wait(&bars[1], (i - 1) & 1, A.err);
+                bulk_g2s(lsm, A.l2g + e0 * n3, (unsigned)(cnt * n3 * 4), &bars[0]);
+                if (i > 0) mbar_wait(&bars[3], (i - 1) & 1, A.err);
+                bulk_g2s(gsm, A.geo + e0 * 7 * n3, (unsigned)(cnt * 7 * n3 * sizeof(S)), &bars[2]);
+            }
+        }
+        __syncwarp();  // the producer warp reconverges before the block-wide barrier below
+    } else {
+        unsigned i = 0;
+        for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, i++) {
+            const ws_ctx w{lsm, gsm, &bars[0], &bars[1], &bars[2], &bars[3], i & 1u, A.err};
+            pencil_group<N, true, EB, GM_L2G, true>(A, g, bufs, acc, &w);
+        }
+    }
+    if (A.partials) {
+        const double v = hbacc::block_sum(acc.value());
+        if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
+    }
+}
+
 }  // namespace
 }  // namespace hb2
 
@@ -434,17 +610,18 @@ namespace {
 // eb_mode: 1 = about 256 threads per block, 2 = twice that many elements
 // (N <= 10), 0 = one element per block (spreads small meshes over more SMs),
 // 3 = as 1 with a bulk L2 prefetch of the block's geometric factors at the
-// start (even-odd only).
+// start (even-odd only), 4 = the persistent warp-specialised kernel (even-odd,
+// odd N, units that define HB_AX2_WS; else as 1).
 template <int N, bool EO, int GM = GM_L2G>
 hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nblocks_out)
 {
     constexpr int n = N + 1, n2 = n * n;
     constexpr int EB1 = n2 >= 256 ? 1 : 256 / n2;
     if (A.E <= 0) return HB_OK;
-    static int attr_set[4][32] = {{0}};
+    static int attr_set[5][32] = {{0}};
     int dev = 0;
     HB_TRY_CUDA(cudaGetDevice(&dev));
-    const int which = (eb_mode == 2 && n2 <= 128) ? 1 : (eb_mode == 0 ? 2 : (eb_mode == 3 ? 3 : 0));
+    const int which = (eb_mode == 2 && n2 <= 128) ? 1 : (eb_mode == 0 ? 2 : (eb_mode == 3 ? 3 : (eb_mode == 4 ? 4 : 0)));
     auto go = [&](auto kern, int EB) -> hb_status {
         const size_t smem = sizeof(T) * 4 * (size_t)EB * pad<N>::size;
         if (dev >= 0 && dev < 32 && !attr_set[which][dev]) {
@@ -471,6 +648,35 @@ hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nbl
         if constexpr (EO) {
             if (which == 3) return go(ax_pencil_kernel<N, EO, EB1, true>, EB1);
         }
+#ifdef HB_AX2_WS
+        if constexpr (EO && ws_ok<N, EB1>()) {
+            if (which == 4) {
+                // persistent grid: the blocks that fit on every SM at once
+                constexpr int smem = ws_smem<N, EB1>();
+                auto kern = ax_pencil_ws_kernel<N, EB1>;
+                if (dev >= 0 && dev < 32 && !attr_set[4][dev]) {
+                    HB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                    attr_set[4][dev] = 1;
+                }
+                static int grid_of[32] = {0};
+                if (dev < 0 || dev >= 32) dev = 0;
+                if (!grid_of[dev]) {
+                    int per_sm = 0, sms = 0;
+                    HB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
+                                                                              ws_consumers<N, EB1>() + 32, smem));
+                    HB_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+                    grid_of[dev] = (per_sm > 0 ? per_sm : 1) * sms;
+                }
+                const int64_t ngroups = (A.E + EB1 - 1) / EB1;
+                const int64_t blocks = ngroups < grid_of[dev] ? ngroups : grid_of[dev];
+                if (nblocks_out) *nblocks_out = blocks;
+                hb_prof_scope prof("ax_local", s);
+                kern<<<(unsigned)blocks, ws_consumers<N, EB1>() + 32, smem, s>>>(A);
+                HB_CHECK_LAUNCH();
+                return HB_OK;
+            }
+        }
+#endif
         return go(ax_pencil_kernel<N, EO, EB1>, EB1);
     }
 }

@@ -1,6 +1,7 @@
 // Instantiations of the element-local operator for T = float, N = 1..15.
 #include "hb_ax.cuh"
 #define HB_AX2_T float
+#define HB_AX2_WS 1
 #include "hb_ax2.cuh"
 
 hb_status hb_launch_ax_local_f32(const hb_mesh *m, const float *x, float *yL, const int *run, cudaStream_t s)
@@ -28,7 +29,8 @@ hb_status hb_launch_ax2_f32(const hb_mesh *m, const float *x, float *ysurf, floa
                             int64_t *nblocks)
 {
     if (!m->geo32) { hb_set_error("mesh has no float geometric factors"); return HB_ERR_ARG; }
-    hb2::pencil_args A{x, m->l2g, m->geo32, ysurf, y, m->E, run, (float)lambda, screen, partials};
+    hb2::pencil_args A{x, m->l2g, m->geo32, ysurf, y, m->E, run, (float)lambda, screen, partials, nullptr,
+                       m->counters + 7};
     switch (m->N) {
 #define HB_CASE(NN) \
     case NN: return eo ? hb2::launch<NN, true>(A, eb_mult, s, nblocks) : hb2::launch<NN, false>(A, eb_mult, s, nblocks);

@@ -315,6 +315,21 @@ extern "C" hb_status hb_dot(const hb_mesh *m, hb_precision prec, const void *a, 
     return HB_OK;
 }
 
+// Error word the element kernels set when a bounded wait gave up (bit 0: a
+// staged-pipeline wait); read and cleared at the solvers' sync points.
+static hb_status check_dev_err(hb_mesh *m, cudaStream_t s)
+{
+    unsigned v = 0;
+    HB_TRY_CUDA(cudaMemcpyAsync(&v, m->counters + 7, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HB_TRY_CUDA(cudaStreamSynchronize(s));
+    if (v) {
+        HB_TRY_CUDA(cudaMemsetAsync(m->counters + 7, 0, sizeof(unsigned), s));
+        hb_set_error("an element kernel gave up waiting for staged data");
+        return HB_ERR_TIMEOUT;
+    }
+    return HB_OK;
+}
+
 // ---------------------------------------------------------------- autotuner
 
 extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen, double lambda, int reps,
@@ -347,7 +362,7 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
     }
     const int candidates[] = {0, HB_VAR_PENCIL, HB_VAR_PENCIL | HB_VAR_EO, HB_VAR_PENCIL | HB_VAR_EB2,
                               HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_EB2, HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE,
-                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_TMA};
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_TMA, HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_WS};
     const int saved = m->variant[pi];
     int best = saved;
     float best_ms = 1e30f;
@@ -378,6 +393,7 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
         hb_set_error("autotune: %s", cudaGetErrorString(e));
         st = HB_ERR_CUDA;
     }
+    if (st == HB_OK) st = check_dev_err(m, s);
     m->variant[pi] = st == HB_OK ? best : saved;
     if (best_variant) *best_variant = m->variant[pi];
     return st;
@@ -601,6 +617,10 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
     float ms = 0.f;
     HB_TRY_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
     R.time_ms = ms;
+    {
+        const hb_status de = check_dev_err(m, s);
+        if (de != HB_OK) R.status = de;
+    }
     if (res) *res = R;
     return R.status;
 }
@@ -687,6 +707,8 @@ extern "C" hb_status hb_cg_finish(hb_mesh *m, hb_cg_result *res, void *stream)
         R.rel_res = fin.bb > 0.0 ? sqrt(fin.res2 / fin.bb) : 0.0;
         if (fin.status == HB_ERR_BREAKDOWN) R.status = HB_ERR_BREAKDOWN;
         else if (m->step.o.rtol > 0.0 && fin.res2 > fin.tol2) R.status = HB_ERR_NOT_CONVERGED;
+        const hb_status de = check_dev_err(m, s);
+        if (de != HB_OK) R.status = de;
     }
     if (res) *res = R;
     return R.status;

@@ -164,20 +164,24 @@ hb_status hb_ax2_upload_f32(const double *D_all);
 // HB_VAR_EO = even-odd split (pencil only); HB_VAR_EB2 = two element groups per
 // block; HB_VAR_ONE = one element per block (with PENCIL | EO only);
 // HB_VAR_TMA = bulk L2 prefetch of each block's geometric factors at its
-// start (with PENCIL | EO only).
-enum { HB_VAR_PENCIL = 1, HB_VAR_EO = 2, HB_VAR_EB2 = 4, HB_VAR_ONE = 8, HB_VAR_TMA = 16, HB_VAR_MAX = 31 };
+// start (with PENCIL | EO only); HB_VAR_WS = persistent warp-specialised
+// kernel staging node map and factors through shared memory (with
+// PENCIL | EO only; FP32 and odd N, else the PENCIL | EO kernel runs).
+enum { HB_VAR_PENCIL = 1, HB_VAR_EO = 2, HB_VAR_EB2 = 4, HB_VAR_ONE = 8, HB_VAR_TMA = 16, HB_VAR_WS = 32,
+       HB_VAR_MAX = 63 };
 static inline bool hb_valid_variant(int v)
 {
     if (v == 0) return true;
     if (v < 0 || v > HB_VAR_MAX || !(v & HB_VAR_PENCIL)) return false;
-    if ((v & HB_VAR_ONE) && (v & HB_VAR_TMA)) return false;
-    if (v & (HB_VAR_ONE | HB_VAR_TMA)) return (v & HB_VAR_EO) && !(v & HB_VAR_EB2);
+    const int extra = v & (HB_VAR_ONE | HB_VAR_TMA | HB_VAR_WS | HB_VAR_EB2);
+    if (extra & (HB_VAR_ONE | HB_VAR_TMA | HB_VAR_WS))
+        return (v & HB_VAR_EO) && (extra == HB_VAR_ONE || extra == HB_VAR_TMA || extra == HB_VAR_WS);
     return true;
 }
 // eb_mode of the pencil launchers for a variant
 static inline int hb_variant_eb_mode(int v)
 {
-    return (v & HB_VAR_ONE) ? 0 : (v & HB_VAR_TMA) ? 3 : (v & HB_VAR_EB2) ? 2 : 1;
+    return (v & HB_VAR_ONE) ? 0 : (v & HB_VAR_TMA) ? 3 : (v & HB_VAR_WS) ? 4 : (v & HB_VAR_EB2) ? 2 : 1;
 }
 
 
