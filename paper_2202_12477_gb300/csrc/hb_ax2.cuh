@@ -326,8 +326,9 @@ __host__ __device__ constexpr int pencil_min_blocks()
     // FP64 is bound by the FP64 pipe: no register cap (a cap only adds spills).
     // FP32 is bound by memory: ask for the resident blocks shared memory
     // allows, up to 4 (2 for the large degrees, whose lines need registers).
-    if constexpr (sizeof(T) == 8) return 1;
-    constexpr int cap = (N + 1) * (N + 1) > 128 ? 2 : 4;
+    if constexpr (std::is_same<T, double>::value) return 1;
+    // double-float: bound by the FP32 issue rate, so residency matters too
+    constexpr int cap = (N + 1) * (N + 1) > 128 ? 2 : (sizeof(T) == 8 ? 3 : 4);
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
 

@@ -74,8 +74,11 @@ __device__ __forceinline__ df fma(const df &a, const df &b, const df &c)
 
 // double -> (h, l) by taking the bit fields apart: h holds the top 24 bits
 // of the significand (truncated), l the next 23, so |x - (h + l)| < 2^-46 |x|.
-// No FP64 instruction is used. Values below 2^-126 or above the float range
-// fall back to a conversion.
+// Integer and FP32 instructions only (no FP64 conversion anywhere, so the
+// FP64 pipe stays free): magnitudes below 2^-126 become a signed zero and
+// magnitudes at or above 2^128 (and infinities, NaN) a signed infinity; l is
+// dropped where it would fall below the FP32 normal range (|x| < 2^-103,
+// where the split keeps 24 bits).
 __device__ __forceinline__ df df_from_double(double v)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
@@ -83,18 +86,14 @@ __device__ __forceinline__ df df_from_double(double v)
     const unsigned sign = hi & 0x80000000u;
     const int e = (int)((hi >> 20) & 0x7FFu);
     const int ef = e - 896;  // float biased exponent
-    if (ef <= 0 || ef >= 255) {
-        const float h = (float)v;
-        return df(h, (float)(v - (double)h));
-    }
     const unsigned m23 = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-    const float h = __uint_as_float(sign | ((unsigned)ef << 23) | m23);
+    const unsigned hbits = ef <= 0 ? sign : (ef >= 255 ? (sign | 0x7F800000u) : (sign | ((unsigned)ef << 23) | m23));
     // the remaining 29 significand bits, top 23 of them as a float in [0,1)
     const float f1 = __uint_as_float(0x3F800000u | ((lo & 0x1FFFFFFFu) >> 6)) - 1.0f;
     const int es = e - 919;  // 2^(e - 1046) as a float exponent
-    const float scale = es > 0 ? __uint_as_float((unsigned)es << 23) : 0.0f;
+    const float scale = (es > 0 && ef > 0 && ef < 255) ? __uint_as_float((unsigned)es << 23) : 0.0f;
     const float l = f1 * scale;
-    return df(h, sign ? -l : l);
+    return df(__uint_as_float(hbits), sign ? -l : l);
 }
 
 // float -> double exactly, by bit fields (zero and subnormals give 0).
