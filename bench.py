@@ -270,13 +270,30 @@ def run_gb300(args, rank, world, local):
     torch.cuda.synchronize()
     e2e_ms = dist.max(e0.elapsed_time(e1))
 
+    # the same iterations with the double-float element kernel (HB_F64X: FP64
+    # data, FP32-pair arithmetic, 1e-12 parity with the FP64 oracle)
+    x.zero_()
+    m.cg_begin(b, x, lam=lam, rtol=0.0, max_it=args.warmup + args.steps, prec=hb.HB_F64X)
+    m.cg_iterate(args.warmup)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    f0.record(stream)
+    m.cg_iterate(args.steps)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    m.cg_finish()
+    f64x_ms = dist.max(f0.elapsed_time(f1))
+
     pk = peaks()
     ax = kern["ax_local"]
     # DRAM bytes per local node of this kernel from one ncu capture of the same
-    # kernel on a smaller box (profiles/ax_pencil_f64_N7_32x32x30_ncu.md:
-    # 928.6 MB read + 89.5 MB written for 15,728,640 local nodes), scaled to
-    # this launch by local nodes; only valid for the kernel that was captured.
-    traffic = 64.73 * NL if (N == 7 and variant == 3) else None
+    # kernel on a smaller box (profiles/ax_pencil_f64_N7_32x32x30_ncu.md, 32x32x30
+    # hexahedra, 15,728,640 local nodes), scaled to this launch by local nodes;
+    # only for the captured (degree, variant) pairs.
+    per_node = {(7, 3): 64.77, (7, 11): 64.66}.get((N, variant))
+    traffic = per_node * NL if per_node else None
     ax_flops = acc.op_local_flops(E, N)
     ax_bytes = acc.ax_local_bytes(NG, NL, 8)
     achieved_tf = ax_flops / (ax["ms_avg"] * 1e-3) / 1e12
@@ -316,6 +333,10 @@ def run_gb300(args, rank, world, local):
         "e2e": {"value": world * NG * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
                 "h2d_bytes_per_step": 8 * NG / args.steps, "d2h_bytes_per_step": 8 * NG / args.steps,
                 "note": f"one hb_cg_solve of {args.steps} iterations per host round trip"},
+        "f64x": {"value": aggregate_rate(world, NG * args.steps, f64x_ms) / 1e9, "unit": "GDOF/s",
+                 "ms_per_step": f64x_ms / args.steps,
+                 "note": "same CG iterations with the double-float element kernel (FP64 storage, gather "
+                         "and vector stage; FP32-pair contractions; A x within 1e-12 of the FP64 oracle)"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
@@ -775,7 +796,9 @@ def run_probe(args, rank, world, local):
            "stream81_bits64_gbs": hb.hb_probe(hb.HB_PROBE_STREAM81_BITS, hb.HB_F64, nb),
            "copy_gbs": hb.hb_probe(hb.HB_PROBE_COPY, hb.HB_F64, nb),
            "fma_fp64_gflops": hb.hb_probe(hb.HB_PROBE_FMA, hb.HB_F64, 0),
-           "fma_fp32_gflops": hb.hb_probe(hb.HB_PROBE_FMA, hb.HB_F32, 0)}
+           "fma_fp32_gflops": hb.hb_probe(hb.HB_PROBE_FMA, hb.HB_F32, 0),
+           "dmma_fp64_gflops": hb.hb_probe(hb.HB_PROBE_DMMA, hb.HB_F64, 0),
+           "dmma_plus_fma_fp64_gflops": hb.hb_probe(hb.HB_PROBE_DMMA_FMA, hb.HB_F64, 0)}
     print(json.dumps(out), flush=True)
 
 

@@ -439,8 +439,11 @@ hb_status hb_profile_read(const char *name, double *total_ms, long long *launche
  *   HB_PROBE_STREAM81_FP   8 reads, 1 write of their sum in `prec`
  *   HB_PROBE_STREAM81_BITS the same traffic combined with XOR (no FP work)
  *   HB_PROBE_COPY          16-byte vector copy
- *   HB_PROBE_FMA           independent FMA chains in `prec` */
-enum { HB_PROBE_STREAM81_FP = 0, HB_PROBE_STREAM81_BITS = 1, HB_PROBE_COPY = 2, HB_PROBE_FMA = 3 };
+ *   HB_PROBE_FMA           independent FMA chains in `prec`
+ *   HB_PROBE_DMMA          FP64 warp matrix multiply-accumulate (mma.sync m8n8k4)
+ *   HB_PROBE_DMMA_FMA      the two above interleaved in one loop (prec ignored) */
+enum { HB_PROBE_STREAM81_FP = 0, HB_PROBE_STREAM81_BITS = 1, HB_PROBE_COPY = 2, HB_PROBE_FMA = 3,
+       HB_PROBE_DMMA = 4, HB_PROBE_DMMA_FMA = 5 };
 hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int reps, double *rate);
 
 /* Message for the last failed call on this thread ("" if none). */

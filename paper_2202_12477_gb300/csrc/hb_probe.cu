@@ -58,6 +58,33 @@ __global__ void probe_fma(T *out, int iters, T b, T c)
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// FP64 warp-level matrix multiply-accumulate (mma.sync m8n8k4, 512 flops per
+// warp and instruction): four independent accumulator tiles per warp.
+// With `with_fma`, every thread also runs four independent FP64 FMA chains
+// in the same loop, to see whether the two paths share one pipe.
+template <bool with_fma>
+__global__ void probe_dmma(double *out, int iters)
+{
+    const double a = 1e-7 * (threadIdx.x + 1), b = 0.9999999;
+    double c[4][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+    double f[4] = {a, 2 * a, 3 * a, 4 * a};
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                         : "+d"(c[q][0]), "+d"(c[q][1])
+                         : "d"(a), "d"(b));
+        if (with_fma) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) f[q] = fma(f[q], b, 1e-9);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) s += c[q][0] + c[q][1] + f[q];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 
 extern "C" hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int reps, double *rate)
@@ -71,7 +98,7 @@ extern "C" hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int rep
     const size_t esz = prec == HB_F64 ? 8 : 4;
     void *buf = nullptr;
     size_t alloc = bytes;
-    if (kind == HB_PROBE_FMA) alloc = (size_t)grid * threads * esz;
+    if (kind == HB_PROBE_FMA || kind == HB_PROBE_DMMA || kind == HB_PROBE_DMMA_FMA) alloc = (size_t)grid * threads * 8;
     if (alloc < 4096) alloc = 4096;
     HB_TRY_CUDA(cudaMalloc(&buf, alloc));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -100,6 +127,16 @@ extern "C" hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int rep
             const int64_t n = (int64_t)(alloc / 32);  // double2 elements in each half
             work = 2.0 * n * 16;
             probe_copy<<<grid, threads>>>((const double2 *)buf, (double2 *)buf + n, n);
+        } else if (kind == HB_PROBE_DMMA || kind == HB_PROBE_DMMA_FMA) {
+            const int iters = 2048;
+            const double warps = (double)grid * threads / 32;
+            // counted: the matrix flops (4 x 512 per warp and iteration), plus
+            // with FMA the 4 x 2 flops per thread and iteration
+            work = warps * iters * 4 * 512.0 + (kind == HB_PROBE_DMMA_FMA ? 8.0 * iters * (double)grid * threads : 0.0);
+            if (kind == HB_PROBE_DMMA)
+                probe_dmma<false><<<grid, threads>>>((double *)buf, iters);
+            else
+                probe_dmma<true><<<grid, threads>>>((double *)buf, iters);
         } else {
             const int iters = 4096;
             work = 2.0 * 8 * iters * (double)grid * threads;
@@ -111,7 +148,7 @@ extern "C" hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int rep
         hb_count_launch();
     };
     float best = 1e30f;
-    if (kind < HB_PROBE_STREAM81_FP || kind > HB_PROBE_FMA) {
+    if (kind < HB_PROBE_STREAM81_FP || kind > HB_PROBE_DMMA_FMA) {
         hb_set_error("unknown probe kind %d", kind);
         e = cudaErrorInvalidValue;
     }

@@ -243,6 +243,7 @@ def hb_autotune(h, prec, screen=HB_SCREEN_IDENTITY, lam=0.1, reps=5, stream=None
 
 
 HB_PROBE_STREAM81_FP, HB_PROBE_STREAM81_BITS, HB_PROBE_COPY, HB_PROBE_FMA = 0, 1, 2, 3
+HB_PROBE_DMMA, HB_PROBE_DMMA_FMA = 4, 5
 
 
 def hb_probe(kind, prec=HB_F64, nbytes=4 << 30, reps=5) -> float:
