@@ -80,36 +80,64 @@ __device__ __forceinline__ void serve_groups(const pencil_args &A, T *sm, hbacc:
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) pencil_group<N, true, EB>(A, g, sm, acc);
 }
 
-// One slot's element kernel on a fixed grid: the degree is read from the
-// slot descriptor, each block walks element groups grid-stride.
-__global__ void __launch_bounds__(HB_SERVE_THREADS, 1)
+// Degree dispatch over [NN, HI] (only these degrees are instantiated).
+template <int NN, int HI>
+__device__ __forceinline__ void serve_dispatch(int N, const pencil_args &A, T *sm, hbacc::dot_acc<S> &acc)
+{
+    if (N == NN) serve_groups<NN>(A, sm, acc);
+    else if constexpr (NN < HI) serve_dispatch<NN + 1, HI>(N, A, sm, acc);
+}
+
+template <int LO, int HI>
+constexpr size_t serve_smem_range()
+{
+    if constexpr (LO == HI) return serve_smem_of<LO>();
+    else return serve_smem_of<LO>() > serve_smem_range<LO + 1, HI>() ? serve_smem_of<LO>() : serve_smem_range<LO + 1, HI>();
+}
+
+// One slot's FP32 element kernel for the degrees [LO, HI] (the slot's degree
+// is read from its descriptor; a kernel whose range does not hold it returns
+// at once). Two degree classes with their own register budgets keep the
+// small degrees at four resident blocks per SM; one kernel for every degree
+// took the register count of the largest and ran one block per SM. Each
+// block walks element groups grid-stride and writes one partial of p.Ap.
+template <int LO, int HI, int MINB>
+__global__ void __launch_bounds__(HB_SERVE_THREADS, MINB)
     serve_ax_kernel(const hb_slot_desc *__restrict__ D, const hb_slot_state *__restrict__ St)
 {
     const hb_slot_desc &d = *D;
-    if (!d.active || St->inner.run == 0) return;
+    if (!d.active || St->inner.run == 0 || d.N < LO || d.N > HI) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     pencil_args A{(const T *)d.p32, d.l2g, d.geo32, (T *)d.ysurf, (T *)d.Ap32, d.E, nullptr, (T)d.lambda,
                   d.screen, d.ax_partials};
     hbacc::dot_acc<S> acc;
-    switch (d.N) {
-    case 1: serve_groups<1>(A, sm, acc); break;
-    case 2: serve_groups<2>(A, sm, acc); break;
-    case 3: serve_groups<3>(A, sm, acc); break;
-    case 4: serve_groups<4>(A, sm, acc); break;
-    case 5: serve_groups<5>(A, sm, acc); break;
-    case 6: serve_groups<6>(A, sm, acc); break;
-    case 7: serve_groups<7>(A, sm, acc); break;
-    case 8: serve_groups<8>(A, sm, acc); break;
-    case 9: serve_groups<9>(A, sm, acc); break;
-    case 10: serve_groups<10>(A, sm, acc); break;
-    case 11: serve_groups<11>(A, sm, acc); break;
-    default: break;
+    serve_dispatch<LO, HI>(d.N, A, sm, acc);
+    const double v = hbacc::block_sum(acc.value());
+    if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
+}
+
+template <int LO, int HI, int MINB>
+hb_status serve_launch_class(const hb_slot_desc *d, const hb_slot_state *st, cudaStream_t s)
+{
+    static int attr_set[32] = {0};
+    static int grid_of[32] = {0};
+    int dev = 0;
+    HB_TRY_CUDA(cudaGetDevice(&dev));
+    const size_t smem = serve_smem_range<LO, HI>();
+    auto kern = serve_ax_kernel<LO, HI, MINB>;
+    if (dev < 0 || dev >= 32) dev = 0;
+    if (!attr_set[dev]) {
+        HB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int sms = 0;
+        HB_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        grid_of[dev] = MINB * sms < HB_SERVE_AXP ? MINB * sms : HB_SERVE_AXP;
+        attr_set[dev] = 1;
     }
-    if (A.partials) {
-        const double v = hbacc::block_sum(acc.value());
-        if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
-    }
+    hb_count_launch();
+    kern<<<grid_of[dev], HB_SERVE_THREADS, smem, s>>>(d, st);
+    HB_CHECK_LAUNCH();
+    return HB_OK;
 }
 
 }  // namespace
@@ -117,19 +145,11 @@ __global__ void __launch_bounds__(HB_SERVE_THREADS, 1)
 
 size_t hb_serve_ax_smem_f32() { return hb2::serve_smem_max(); }
 
+// Both degree classes are launched; the one that does not hold the slot's
+// degree returns at once (the round graph is captured before slots are filled).
 hb_status hb_serve_launch_ax_f32(const hb_slot_desc *d, const hb_slot_state *st, cudaStream_t s)
 {
-    static int attr_set[32] = {0};
-    int dev = 0;
-    HB_TRY_CUDA(cudaGetDevice(&dev));
-    const size_t smem = hb2::serve_smem_max();
-    if (dev >= 0 && dev < 32 && !attr_set[dev]) {
-        HB_TRY_CUDA(cudaFuncSetAttribute(hb2::serve_ax_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        attr_set[dev] = 1;
-    }
-    hb_count_launch();
-    hb2::serve_ax_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, smem, s>>>(d, st);
-    HB_CHECK_LAUNCH();
-    return HB_OK;
+    hb_status r = hb2::serve_launch_class<1, 7, 4>(d, st, s);
+    if (r != HB_OK) return r;
+    return hb2::serve_launch_class<8, HB_SERVE_MAX_N, 2>(d, st, s);
 }

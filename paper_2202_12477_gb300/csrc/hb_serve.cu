@@ -125,11 +125,11 @@ __global__ void __launch_bounds__(HB_SERVE_THREADS) serve_asm32_kernel(const hb_
     if (d.screen)
         assemble_surf_body<float, 1, HB_DOT_CG_PAP>((const float *)d.ysurf, d.srow_g, d.srowptr, d.scols, d.p32,
                                                     d.mdiag32, d.lambda, d.Ap32, d.nsr, d.ax_partials,
-                                                    HB_SERVE_GRID, d.partials, d.counters, &S->inner);
+                                                    HB_SERVE_AXP, d.partials, d.counters, &S->inner);
     else
         assemble_surf_body<float, 0, HB_DOT_CG_PAP>((const float *)d.ysurf, d.srow_g, d.srowptr, d.scols, d.p32,
                                                     d.mdiag32, d.lambda, d.Ap32, d.nsr, d.ax_partials,
-                                                    HB_SERVE_GRID, d.partials, d.counters, &S->inner);
+                                                    HB_SERVE_AXP, d.partials, d.counters, &S->inner);
 }
 
 __global__ void __launch_bounds__(HB_SERVE_THREADS) serve_update_r_kernel(const hb_slot_desc *D, hb_slot_state *S)
@@ -282,7 +282,7 @@ static hb_status admit(hb_server *S, int si, const request &rq)
     const int64_t n = m->n_global;
     const size_t ns = vec_stride(n);
     const size_t bytes = ns * (4 * sizeof(double) + 4 * sizeof(float)) +
-                         sizeof(double) * (HB_RED_MAXV * HB_RED_BLOCKS + HB_SERVE_GRID) + 64 * sizeof(unsigned);
+                         sizeof(double) * (HB_RED_MAXV * HB_RED_BLOCKS + HB_SERVE_AXP) + 64 * sizeof(unsigned);
     void *mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, bytes);
     if (e != cudaSuccess) {
@@ -294,7 +294,7 @@ static hb_status admit(hb_server *S, int si, const request &rq)
     float *r32 = (float *)(Ap + ns), *p32 = r32 + ns, *Ap32 = p32 + ns, *d32 = Ap32 + ns;
     double *partials = (double *)(d32 + ns);
     double *axp = partials + HB_RED_MAXV * HB_RED_BLOCKS;
-    unsigned *ctr = (unsigned *)(axp + HB_SERVE_GRID);
+    unsigned *ctr = (unsigned *)(axp + HB_SERVE_AXP);
     hb_slot_desc d{};
     d.active = 1;
     d.N = m->N;
@@ -333,6 +333,7 @@ static hb_status admit(hb_server *S, int si, const request &rq)
     ss.status = HB_OK;
     e = cudaMemsetAsync(x, 0, sizeof(double) * ns, S->s_main);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 64 * sizeof(unsigned), S->s_main);
+    if (e == cudaSuccess) e = cudaMemsetAsync(axp, 0, HB_SERVE_AXP * sizeof(double), S->s_main);
     if (e == cudaSuccess) st = hb_fill_rhs(m, 0, rq.seed, 0.0, b, S->s_main);
     if (e == cudaSuccess && st == HB_OK) {
         S->h_desc[si] = d;

@@ -5,7 +5,8 @@
 #include "hb_internal.h"
 
 #define HB_SERVE_MAX_N 11     // degrees the server accepts
-#define HB_SERVE_GRID 304     // fixed grid of every serving kernel (2 x 152 SMs)
+#define HB_SERVE_GRID 304     // fixed grid of the serving vector kernels (2 x 152 SMs)
+#define HB_SERVE_AXP 1024     // room for the FP32 element kernels' block partials (their grids are smaller)
 #define HB_SERVE_THREADS 256
 
 enum { HB_SLOT_EMPTY = 0, HB_SLOT_OUTER = 1, HB_SLOT_INNER = 2, HB_SLOT_DONE = 3 };
@@ -29,7 +30,7 @@ struct hb_slot_desc {
     float *r32, *p32, *Ap32, *d32;  // FP32 inner CG
     double lambda, rtol, inner_rtol;
     double *partials;             // [HB_RED_MAXV * HB_RED_BLOCKS]
-    double *ax_partials;          // [HB_SERVE_GRID]
+    double *ax_partials;          // [HB_SERVE_AXP], zero past the element kernel's grid
     unsigned *counters;           // [8]
 };
 
