@@ -275,6 +275,16 @@ typedef struct {
 hb_status hb_part_create(const hb_mesh *mesh, int px, int py, int pz, uint64_t seed, void *stream,
                          hb_part **out);
 hb_status hb_part_destroy(hb_part *part);
+/* The same partition planned on the host alone (no device work; what
+ * hb_part_create does before it uploads): l2g_host is the mesh's node map
+ * (ex*ey*ez*(N+1)^3 int32, -1 on masked nodes, e.g. from hb_mesh_copy_l2g).
+ * Writes perm_host (n_global int32, as hb_part_copy_perm) and counts_host
+ * (2 + 8*px*py*pz int64): n_shared, exchange_values, then per rank n_owned,
+ * offset, n_halo, n_send, n_elem_interior1, n_elem_halo, n_elem_interior2 and
+ * the number of owned DOFs other ranks hold. HB_ERR_ARG for bad sizes or a
+ * node map that is out of range or leaves a DOF without an element. */
+hb_status hb_part_plan(const int32_t *l2g_host, int ex, int ey, int ez, int N, int64_t n_global, int px, int py,
+                       int pz, uint64_t seed, int32_t *perm_host, int64_t *counts_host);
 hb_status hb_part_info(const hb_part *part, hb_part_info_t *out);
 hb_status hb_part_rank_info(const hb_part *part, int rank, hb_part_rank_info_t *out);
 /* perm_host[i] = the mesh's (lexicographic) global id of partition-order DOF i;

@@ -274,47 +274,62 @@ void free_part(hb_part *P)
     delete P;
 }
 
-hb_status build(hb_part *P, cudaStream_t s)
-{
-    const hb_mesh *m = P->m;
-    const int N = m->N, n = N + 1, n3 = n * n * n;
-    const int Ex = m->desc.ex, Ey = m->desc.ey, Ez = m->desc.ez;
-    const int64_t E = m->E, NG = m->n_global;
-    const int Pn = P->P;
-    P->N = N;
-    P->n = n;
-    P->NS = hb_surf_count(N);
-    P->n_global = NG;
+// Host plan of one rank: everything build() uploads.
+struct rank_plan {
+    int64_t off = 0, n_owned = 0, n_halo = 0, n_send = 0, n_oshared = 0, nlr = 0;
+    int64_t e_int1 = 0, e_halo = 0, e_int2 = 0;
+    std::vector<int32_t> order;  // global element ids in local order
+    std::vector<int32_t> lc;     // local codes of the rank's elements
+    std::vector<int32_t> send;   // partition ids sent, by destination
+    std::vector<int64_t> send_off, recv_off;
+    std::vector<int32_t> hrowptr, hcols, lrows, lrowptr, lcols, oshared, frowptr, fcols;
+};
 
-    std::vector<int32_t> l2g((size_t)E * n3);
-    HB_TRY_CUDA(cudaMemcpyAsync(l2g.data(), m->l2g, l2g.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    HB_TRY_CUDA(cudaStreamSynchronize(s));
+struct part_plan {
+    int64_t n_shared = 0, exchange_values = 0;
+    std::vector<int32_t> perm;  // partition id -> lexicographic id
+    std::vector<rank_plan> R;
+};
+
+// Plans the partition of a box mesh from its host node map (no device work):
+// element ranks, DOF owners, partition order, per-rank element order, local
+// codes, halo lists, send lists and the three CSRs; then checks that every
+// index the kernels and copies will follow stays inside its buffer.
+hb_status plan_partition(const int32_t *l2g, int Ex, int Ey, int Ez, int N, int64_t NG, int px, int py, int pz,
+                         uint64_t seed, part_plan &PL)
+{
+    const int n = N + 1, n3 = n * n * n, NS = hb_surf_count(N);
+    const int64_t E = (int64_t)Ex * Ey * Ez;
+    const int Pn = px * py * pz;
 
     // rank of every element: block (ex * px / Ex, ...) of the element box
     std::vector<int8_t> erank((size_t)E);
     for (int64_t e = 0; e < E; e++) {
         const int64_t ex = e % Ex, ey = (e / Ex) % Ey, ez = e / ((int64_t)Ex * Ey);
-        const int rx = (int)(ex * P->px / Ex), ry = (int)(ey * P->py / Ey), rz = (int)(ez * P->pz / Ez);
-        erank[e] = (int8_t)(rx + P->px * (ry + P->py * rz));
+        const int rx = (int)(ex * px / Ex), ry = (int)(ey * py / Ey), rz = (int)(ez * pz / Ez);
+        erank[e] = (int8_t)(rx + px * (ry + py * rz));
     }
     // ranks holding each DOF, then its owner (one of them, uniformly at random)
     std::vector<uint64_t> held((size_t)NG, 0);
     for (int64_t e = 0; e < E; e++) {
         const uint64_t bit = 1ull << erank[e];
         const int32_t *lg = &l2g[(size_t)e * n3];
-        for (int q = 0; q < n3; q++)
+        for (int q = 0; q < n3; q++) {
+            if (lg[q] >= NG) { hb_set_error("node map entry %d out of range", lg[q]); return HB_ERR_ARG; }
             if (lg[q] >= 0) held[lg[q]] |= bit;
+        }
     }
     std::vector<int8_t> owner((size_t)NG);
     std::vector<int64_t> cnt(Pn, 0);
     int64_t n_shared = 0;
     for (int64_t g = 0; g < NG; g++) {
         const uint64_t h = held[g];
+        if (!h) { hb_set_error("DOF %lld held by no element", (long long)g); return HB_ERR_ARG; }
         const int c = __builtin_popcountll(h);
         int pick = 0;
         if (c > 1) {
             n_shared++;
-            pick = (int)(hb_u01(P->seed, 3, (uint64_t)g) * c);
+            pick = (int)(hb_u01(seed, 3, (uint64_t)g) * c);
             if (pick >= c) pick = c - 1;
         }
         uint64_t hh = h;
@@ -322,22 +337,22 @@ hb_status build(hb_part *P, cudaStream_t s)
         owner[g] = (int8_t)__builtin_ctzll(hh);
         cnt[owner[g]]++;
     }
-    P->n_shared = n_shared;
+    PL.n_shared = n_shared;
     // partition order: by owner, then lexicographic
     std::vector<int64_t> off(Pn + 1, 0);
     for (int p = 0; p < Pn; p++) off[p + 1] = off[p] + cnt[p];
     std::vector<int32_t> newid((size_t)NG);
-    P->perm.assign((size_t)NG, 0);
+    PL.perm.assign((size_t)NG, 0);
     {
         std::vector<int64_t> next(off.begin(), off.end() - 1);
         for (int64_t g = 0; g < NG; g++) {
             const int64_t id = next[owner[g]]++;
             newid[g] = (int32_t)id;
-            P->perm[id] = (int32_t)g;
+            PL.perm[id] = (int32_t)g;
         }
     }
+    PL.R.assign(Pn, rank_plan());
     // elements per rank, halo elements (holding a shared DOF) apart
-    std::vector<std::vector<int32_t>> order(Pn);
     {
         std::vector<std::vector<int32_t>> inter(Pn), halo(Pn);
         for (int64_t e = 0; e < E; e++) {
@@ -346,23 +361,22 @@ hb_status build(hb_part *P, cudaStream_t s)
             for (int q = 0; q < n3 && !h; q++) h = lg[q] >= 0 && __builtin_popcountll(held[lg[q]]) > 1;
             (h ? halo : inter)[erank[e]].push_back((int32_t)e);
         }
-        P->R.resize(Pn);
         for (int p = 0; p < Pn; p++) {
-            part_rank &R = P->R[p];
+            rank_plan &R = PL.R[p];
             const size_t half = inter[p].size() / 2;
             R.e_int1 = (int64_t)half;
             R.e_halo = (int64_t)halo[p].size();
             R.e_int2 = (int64_t)(inter[p].size() - half);
-            order[p].insert(order[p].end(), inter[p].begin(), inter[p].begin() + half);
-            order[p].insert(order[p].end(), halo[p].begin(), halo[p].end());
-            order[p].insert(order[p].end(), inter[p].begin() + half, inter[p].end());
+            R.order.insert(R.order.end(), inter[p].begin(), inter[p].begin() + half);
+            R.order.insert(R.order.end(), halo[p].begin(), halo[p].end());
+            R.order.insert(R.order.end(), inter[p].begin() + half, inter[p].end());
         }
     }
     // halo DOFs of each rank, in partition order (so grouped by owner)
     std::vector<std::vector<int32_t>> halo_ids(Pn);  // partition ids
     for (int p = 0; p < Pn; p++) {
         std::vector<int32_t> &H = halo_ids[p];
-        for (int32_t e : order[p]) {
+        for (int32_t e : PL.R[p].order) {
             const int32_t *lg = &l2g[(size_t)e * n3];
             for (int q = 0; q < n3; q++)
                 if (lg[q] >= 0 && owner[lg[q]] != p) H.push_back(newid[lg[q]]);
@@ -376,7 +390,7 @@ hb_status build(hb_part *P, cudaStream_t s)
     std::vector<int32_t> slot((size_t)NG, -1);  // scratch: partition id -> row index
     int64_t exch = 0;
     for (int p = 0; p < Pn; p++) {
-        part_rank &R = P->R[p];
+        rank_plan &R = PL.R[p];
         R.off = off[p];
         R.n_owned = cnt[p];
         R.n_halo = (int64_t)halo_ids[p].size();
@@ -386,30 +400,29 @@ hb_status build(hb_part *P, cudaStream_t s)
         for (int32_t id : halo_ids[p]) R.recv_off[owner_of_id(id) + 1]++;
         for (int q = 0; q < Pn; q++) R.recv_off[q + 1] += R.recv_off[q];
     }
-    P->exchange_values = exch;
+    PL.exchange_values = exch;
     for (int p = 0; p < Pn; p++) {
-        part_rank &R = P->R[p];
+        rank_plan &R = PL.R[p];
         // send list: for each destination q, q's halo segment owned by p
-        std::vector<int32_t> send;
         R.send_off.assign(Pn + 1, 0);
         for (int q = 0; q < Pn; q++) {
-            const part_rank &Q = P->R[q];
-            for (int64_t t = Q.recv_off[p]; t < Q.recv_off[p + 1]; t++) send.push_back(halo_ids[q][t]);
-            R.send_off[q + 1] = (int64_t)send.size();
+            const rank_plan &Q = PL.R[q];
+            for (int64_t t = Q.recv_off[p]; t < Q.recv_off[p + 1]; t++) R.send.push_back(halo_ids[q][t]);
+            R.send_off[q + 1] = (int64_t)R.send.size();
         }
-        R.n_send = (int64_t)send.size();
+        R.n_send = (int64_t)R.send.size();
         // owned halo DOFs (shared, owned by p), ascending
-        std::vector<int32_t> oshared(send.begin(), send.end());
-        std::sort(oshared.begin(), oshared.end());
-        oshared.erase(std::unique(oshared.begin(), oshared.end()), oshared.end());
-        R.n_oshared = (int64_t)oshared.size();
+        R.oshared.assign(R.send.begin(), R.send.end());
+        std::sort(R.oshared.begin(), R.oshared.end());
+        R.oshared.erase(std::unique(R.oshared.begin(), R.oshared.end()), R.oshared.end());
+        R.n_oshared = (int64_t)R.oshared.size();
         // local codes of the rank's elements
         for (int64_t t = 0; t < R.n_halo; t++) slot[halo_ids[p][t]] = (int32_t)t;
-        const int64_t Ep = (int64_t)order[p].size();
-        std::vector<int32_t> lc((size_t)Ep * n3);
+        const int64_t Ep = (int64_t)R.order.size();
+        R.lc.assign((size_t)Ep * n3, 0);
         for (int64_t el = 0; el < Ep; el++) {
-            const int32_t *lg = &l2g[(size_t)order[p][el] * n3];
-            int32_t *o = &lc[(size_t)el * n3];
+            const int32_t *lg = &l2g[(size_t)R.order[el] * n3];
+            int32_t *o = &R.lc[(size_t)el * n3];
             for (int q = 0; q < n3; q++) {
                 const int32_t g = lg[q];
                 o[q] = g < 0 ? -1 : (owner[g] == p ? newid[g] : -2 - slot[newid[g]]);
@@ -417,81 +430,113 @@ hb_status build(hb_part *P, cudaStream_t s)
         }
         for (int64_t t = 0; t < R.n_halo; t++) slot[halo_ids[p][t]] = -1;
         // surface rows: halo rows (halo order, then owned halo DOFs) and local rows
-        for (int64_t t = 0; t < R.n_oshared; t++) slot[oshared[t]] = (int32_t)(R.n_halo + t);
+        for (int64_t t = 0; t < R.n_oshared; t++) slot[R.oshared[t]] = (int32_t)(R.n_halo + t);
         std::vector<std::pair<int32_t, int32_t>> hrc, lrc;
-        std::vector<int32_t> lrows;
         for (int64_t el = 0; el < Ep; el++)
             for (int k = 0; k < n; k++)
                 for (int j = 0; j < n; j++)
                     for (int i = 0; i < n; i++) {
                         const int sp = hb_surf_pos(N, i, j, k);
                         if (sp < 0) continue;
-                        const int32_t c = lc[(size_t)el * n3 + (k * n + j) * n + i];
+                        const int32_t c = R.lc[(size_t)el * n3 + (k * n + j) * n + i];
                         if (c == -1) continue;
-                        const int32_t col = (int32_t)(el * P->NS + sp);
+                        const int32_t col = (int32_t)(el * NS + sp);
                         if (c <= -2) hrc.push_back({-2 - c, col});
                         else if (slot[c] >= 0) hrc.push_back({slot[c], col});
                         else lrc.push_back({c, col});
                     }
         // local rows: compact the partition ids
-        {
-            for (auto &pr : lrc) lrows.push_back(pr.first);
-            std::sort(lrows.begin(), lrows.end());
-            lrows.erase(std::unique(lrows.begin(), lrows.end()), lrows.end());
-            for (auto &pr : lrc) pr.first = (int32_t)(std::lower_bound(lrows.begin(), lrows.end(), pr.first) -
-                                                      lrows.begin());
-            R.nlr = (int64_t)lrows.size();
-        }
-        std::vector<int32_t> hrowptr, hcols, lrowptr, lcols;
-        build_csr(R.n_halo + R.n_oshared, hrc, hrowptr, hcols);
-        build_csr(R.nlr, lrc, lrowptr, lcols);
-        for (int64_t t = 0; t < R.n_oshared; t++) slot[oshared[t]] = -1;
+        for (auto &pr : lrc) R.lrows.push_back(pr.first);
+        std::sort(R.lrows.begin(), R.lrows.end());
+        R.lrows.erase(std::unique(R.lrows.begin(), R.lrows.end()), R.lrows.end());
+        for (auto &pr : lrc)
+            pr.first = (int32_t)(std::lower_bound(R.lrows.begin(), R.lrows.end(), pr.first) - R.lrows.begin());
+        R.nlr = (int64_t)R.lrows.size();
+        build_csr(R.n_halo + R.n_oshared, hrc, R.hrowptr, R.hcols);
+        build_csr(R.nlr, lrc, R.lrowptr, R.lcols);
+        for (int64_t t = 0; t < R.n_oshared; t++) slot[R.oshared[t]] = -1;
         // finalize rows: owned halo DOF -> its positions in the send list (= grecv)
         std::vector<std::pair<int32_t, int32_t>> frc;
-        for (int64_t t = 0; t < R.n_oshared; t++) slot[oshared[t]] = (int32_t)t;
-        for (int64_t q = 0; q < R.n_send; q++) frc.push_back({slot[send[q]], (int32_t)q});
-        for (int64_t t = 0; t < R.n_oshared; t++) slot[oshared[t]] = -1;
-        std::vector<int32_t> frowptr, fcols;
-        build_csr(R.n_oshared, frc, frowptr, fcols);
+        for (int64_t t = 0; t < R.n_oshared; t++) slot[R.oshared[t]] = (int32_t)t;
+        for (int64_t q = 0; q < R.n_send; q++) frc.push_back({slot[R.send[q]], (int32_t)q});
+        for (int64_t t = 0; t < R.n_oshared; t++) slot[R.oshared[t]] = -1;
+        build_csr(R.n_oshared, frc, R.frowptr, R.fcols);
 
         // every index the kernels and copies will follow stays inside its buffer
-        {
-            const int64_t lo = off[p], hi = off[p] + cnt[p], nsurf = Ep * P->NS;
-            bool ok = true;
-            for (int32_t c : lc) ok = ok && (c == -1 || (c >= lo && c < hi) || (c <= -2 && -2 - (int64_t)c < R.n_halo));
-            // element-interior nodes are written to y directly: they must be owned
-            for (int64_t el = 0; el < Ep && ok; el++)
-                for (int k = 1; k < N; k++)
-                    for (int j = 1; j < N; j++)
-                        for (int i = 1; i < N; i++) ok = ok && lc[(size_t)el * n3 + (k * n + j) * n + i] >= lo;
-            for (int32_t c : send) ok = ok && c >= lo && c < hi;
-            for (int32_t c : lrows) ok = ok && c >= lo && c < hi;
-            for (int32_t c : oshared) ok = ok && c >= lo && c < hi;
-            for (int32_t c : hcols) ok = ok && c >= 0 && c < nsurf;
-            for (int32_t c : lcols) ok = ok && c >= 0 && c < nsurf;
-            for (int32_t c : fcols) ok = ok && c >= 0 && c < R.n_send;
-            ok = ok && (int64_t)hrowptr.back() == (int64_t)hcols.size() && (int64_t)lrowptr.back() == (int64_t)lcols.size() &&
-                 (int64_t)frowptr.back() == (int64_t)fcols.size();
-            for (int64_t t = 0; t < R.n_oshared && ok; t++) ok = frowptr[t + 1] > frowptr[t];  // sent to someone
-            for (int q = 0; q < Pn && ok; q++)
-                ok = P->R[q].recv_off[p + 1] - P->R[q].recv_off[p] == R.send_off[q + 1] - R.send_off[q];
-            if (!ok) {
-                hb_set_error("partition of rank %d is inconsistent", p);
-                return HB_ERR_ARG;
-            }
+        const int64_t lo = off[p], hi = off[p] + cnt[p], nsurf = Ep * NS;
+        bool ok = true;
+        for (int32_t c : R.lc) ok = ok && (c == -1 || (c >= lo && c < hi) || (c <= -2 && -2 - (int64_t)c < R.n_halo));
+        // element-interior nodes are written to y directly: they must be owned
+        for (int64_t el = 0; el < Ep && ok; el++)
+            for (int k = 1; k < N; k++)
+                for (int j = 1; j < N; j++)
+                    for (int i = 1; i < N; i++) ok = ok && R.lc[(size_t)el * n3 + (k * n + j) * n + i] >= lo;
+        for (int32_t c : R.send) ok = ok && c >= lo && c < hi;
+        for (int32_t c : R.lrows) ok = ok && c >= lo && c < hi;
+        for (int32_t c : R.oshared) ok = ok && c >= lo && c < hi;
+        for (int32_t c : R.hcols) ok = ok && c >= 0 && c < nsurf;
+        for (int32_t c : R.lcols) ok = ok && c >= 0 && c < nsurf;
+        for (int32_t c : R.fcols) ok = ok && c >= 0 && c < R.n_send;
+        ok = ok && (int64_t)R.hrowptr.back() == (int64_t)R.hcols.size() &&
+             (int64_t)R.lrowptr.back() == (int64_t)R.lcols.size() && (int64_t)R.frowptr.back() == (int64_t)R.fcols.size();
+        for (int64_t t = 0; t < R.n_oshared && ok; t++) ok = R.frowptr[t + 1] > R.frowptr[t];  // sent to someone
+        for (int q = 0; q < Pn && ok; q++)
+            ok = PL.R[q].recv_off[p + 1] - PL.R[q].recv_off[p] == R.send_off[q + 1] - R.send_off[q];
+        if (!ok) {
+            hb_set_error("partition of rank %d is inconsistent", p);
+            return HB_ERR_ARG;
         }
-        // device data of the rank
-        hb_status st;
-        if ((st = upload(P, lc, &R.l2g)) != HB_OK) return st;
-        if ((st = upload(P, send, &R.send_idx)) != HB_OK) return st;
-        if ((st = upload(P, hrowptr, &R.hrowptr)) != HB_OK) return st;
-        if ((st = upload(P, hcols, &R.hcols)) != HB_OK) return st;
-        if ((st = upload(P, lrows, &R.lrow_g)) != HB_OK) return st;
-        if ((st = upload(P, lrowptr, &R.lrowptr)) != HB_OK) return st;
-        if ((st = upload(P, lcols, &R.lcols)) != HB_OK) return st;
-        if ((st = upload(P, oshared, &R.frow_g)) != HB_OK) return st;
-        if ((st = upload(P, frowptr, &R.frowptr)) != HB_OK) return st;
-        if ((st = upload(P, fcols, &R.fcols)) != HB_OK) return st;
+    }
+    return HB_OK;
+}
+
+hb_status build(hb_part *P, cudaStream_t s)
+{
+    const hb_mesh *m = P->m;
+    const int N = m->N, n = N + 1, n3 = n * n * n;
+    const int64_t E = m->E, NG = m->n_global;
+    const int Pn = P->P;
+    P->N = N;
+    P->n = n;
+    P->NS = hb_surf_count(N);
+    P->n_global = NG;
+
+    std::vector<int32_t> l2g((size_t)E * n3);
+    HB_TRY_CUDA(cudaMemcpyAsync(l2g.data(), m->l2g, l2g.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HB_TRY_CUDA(cudaStreamSynchronize(s));
+    part_plan PL;
+    hb_status st = plan_partition(l2g.data(), m->desc.ex, m->desc.ey, m->desc.ez, N, NG, P->px, P->py, P->pz,
+                                  P->seed, PL);
+    if (st != HB_OK) return st;
+    P->n_shared = PL.n_shared;
+    P->exchange_values = PL.exchange_values;
+    P->perm = PL.perm;
+    P->R.resize(Pn);
+    for (int p = 0; p < Pn; p++) {
+        const rank_plan &Q = PL.R[p];
+        part_rank &R = P->R[p];
+        R.off = Q.off;
+        R.n_owned = Q.n_owned;
+        R.n_halo = Q.n_halo;
+        R.n_send = Q.n_send;
+        R.n_oshared = Q.n_oshared;
+        R.nlr = Q.nlr;
+        R.e_int1 = Q.e_int1;
+        R.e_halo = Q.e_halo;
+        R.e_int2 = Q.e_int2;
+        R.send_off = Q.send_off;
+        R.recv_off = Q.recv_off;
+        const int64_t Ep = (int64_t)Q.order.size();
+        if ((st = upload(P, Q.lc, &R.l2g)) != HB_OK) return st;
+        if ((st = upload(P, Q.send, &R.send_idx)) != HB_OK) return st;
+        if ((st = upload(P, Q.hrowptr, &R.hrowptr)) != HB_OK) return st;
+        if ((st = upload(P, Q.hcols, &R.hcols)) != HB_OK) return st;
+        if ((st = upload(P, Q.lrows, &R.lrow_g)) != HB_OK) return st;
+        if ((st = upload(P, Q.lrowptr, &R.lrowptr)) != HB_OK) return st;
+        if ((st = upload(P, Q.lcols, &R.lcols)) != HB_OK) return st;
+        if ((st = upload(P, Q.oshared, &R.frow_g)) != HB_OK) return st;
+        if ((st = upload(P, Q.frowptr, &R.frowptr)) != HB_OK) return st;
+        if ((st = upload(P, Q.fcols, &R.fcols)) != HB_OK) return st;
         if ((st = alloc(P, (size_t)Ep * 7 * n3, &R.geo)) != HB_OK) return st;
         if ((st = alloc(P, (size_t)Ep * P->NS, &R.ysurf)) != HB_OK) return st;
         if ((st = alloc(P, (size_t)R.n_halo, &R.halo)) != HB_OK) return st;
@@ -500,7 +545,7 @@ hb_status build(hb_part *P, cudaStream_t s)
         if ((st = alloc(P, (size_t)R.n_send, &R.grecv)) != HB_OK) return st;
         if (Ep > 0) {
             int32_t *d_el = nullptr;
-            if ((st = upload(P, order[p], &d_el)) != HB_OK) return st;
+            if ((st = upload(P, Q.order, &d_el)) != HB_OK) return st;
             hb_count_launch();
             k_gather_geo<<<grid_for(Ep * 7 * n3), kThreads, 0, s>>>(m->geo, d_el, Ep, (int64_t)7 * n3, R.geo);
             HB_CHECK_LAUNCH();
@@ -513,7 +558,6 @@ hb_status build(hb_part *P, cudaStream_t s)
     // lumped mass in partition order
     {
         int32_t *d_perm = nullptr;
-        hb_status st;
         if ((st = upload(P, P->perm, &d_perm)) != HB_OK) return st;
         if ((st = alloc(P, (size_t)NG, &P->mdiag)) != HB_OK) return st;
         if (NG > 0) {
@@ -525,14 +569,11 @@ hb_status build(hb_part *P, cudaStream_t s)
     HB_TRY_CUDA(cudaEventCreateWithFlags(&P->ev_start, cudaEventDisableTiming));
     HB_TRY_CUDA(cudaEventCreate(&P->ev0));
     HB_TRY_CUDA(cudaEventCreate(&P->ev1));
-    {
-        hb_status st;
-        if ((st = alloc(P, (size_t)HB_RED_MAXV * HB_RED_BLOCKS, &P->partials)) != HB_OK) return st;
-        if ((st = alloc(P, 8, &P->counters)) != HB_OK) return st;
-        if ((st = alloc(P, 2, &P->state)) != HB_OK) return st;
-        HB_TRY_CUDA(cudaMemsetAsync(P->counters, 0, 8 * sizeof(unsigned), s));
-        HB_TRY_CUDA(cudaMallocHost((void **)&P->state_host, sizeof(hb_cg_state)));
-    }
+    if ((st = alloc(P, (size_t)HB_RED_MAXV * HB_RED_BLOCKS, &P->partials)) != HB_OK) return st;
+    if ((st = alloc(P, 8, &P->counters)) != HB_OK) return st;
+    if ((st = alloc(P, 2, &P->state)) != HB_OK) return st;
+    HB_TRY_CUDA(cudaMemsetAsync(P->counters, 0, 8 * sizeof(unsigned), s));
+    HB_TRY_CUDA(cudaMallocHost((void **)&P->state_host, sizeof(hb_cg_state)));
     HB_TRY_CUDA(cudaStreamSynchronize(s));
     return HB_OK;
 }
@@ -704,6 +745,38 @@ extern "C" hb_status hb_part_create(const hb_mesh *mesh, int px, int py, int pz,
         return st;
     }
     *out = P;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_part_plan(const int32_t *l2g_host, int ex, int ey, int ez, int N, int64_t n_global,
+                                  int px, int py, int pz, uint64_t seed, int32_t *perm_host, int64_t *counts_host)
+{
+    hb_clear_error();
+    if (!l2g_host || !perm_host || !counts_host) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (ex < 1 || ey < 1 || ez < 1 || N < 1 || N > HB_MAX_N || n_global < 0) { hb_set_error("bad mesh sizes"); return HB_ERR_ARG; }
+    if (px < 1 || py < 1 || pz < 1 || px > ex || py > ey || pz > ez || px * py * pz > 64) {
+        hb_set_error("rank grid %dx%dx%d does not fit %dx%dx%d elements (at most 64 ranks)", px, py, pz, ex, ey, ez);
+        return HB_ERR_ARG;
+    }
+    part_plan PL;
+    hb_status st = plan_partition(l2g_host, ex, ey, ez, N, n_global, px, py, pz, seed, PL);
+    if (st != HB_OK) return st;
+    if (!PL.perm.empty()) std::memcpy(perm_host, PL.perm.data(), PL.perm.size() * sizeof(int32_t));
+    const int Pn = px * py * pz;
+    counts_host[0] = PL.n_shared;
+    counts_host[1] = PL.exchange_values;
+    for (int p = 0; p < Pn; p++) {
+        const rank_plan &R = PL.R[p];
+        int64_t *c = counts_host + 2 + 8 * p;
+        c[0] = R.n_owned;
+        c[1] = R.off;
+        c[2] = R.n_halo;
+        c[3] = R.n_send;
+        c[4] = R.e_int1;
+        c[5] = R.e_halo;
+        c[6] = R.e_int2;
+        c[7] = R.n_oshared;
+    }
     return HB_OK;
 }
 

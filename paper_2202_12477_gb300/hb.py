@@ -110,6 +110,8 @@ _SIGS = [
     ("hb_part_create", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_void_p,
                                  C.POINTER(C.c_void_p)]),
     ("hb_part_destroy", C.c_int, [C.c_void_p]),
+    ("hb_part_plan", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int, C.c_int,
+                               C.c_int, C.c_uint64, C.c_void_p, C.c_void_p]),
     ("hb_part_info", C.c_int, [C.c_void_p, C.POINTER(hb_part_info_t)]),
     ("hb_part_rank_info", C.c_int, [C.c_void_p, C.c_int, C.POINTER(hb_part_rank_info_t)]),
     ("hb_part_copy_perm", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -370,6 +372,22 @@ class Mesh:
 
 
 # ---------------------------------------------------------------- partitioned operator
+
+def hb_part_plan(l2g, dims, N, n_global, grid, seed=0):
+    """Host-only partition plan of a box mesh from its node map (numpy int32,
+    E*(N+1)^3 values). Returns (perm, n_shared, exchange_values, per-rank
+    counts as an int64 array [P][8]: n_owned, offset, n_halo, n_send,
+    n_elem_interior1, n_elem_halo, n_elem_interior2, n_owned_shared)."""
+    import numpy as np
+    l2g = np.ascontiguousarray(l2g, dtype=np.int32)
+    P = grid[0] * grid[1] * grid[2]
+    perm = np.empty(n_global, dtype=np.int32)
+    counts = np.zeros(2 + 8 * P, dtype=np.int64)
+    _check(lib().hb_part_plan(l2g.ctypes.data_as(C.c_void_p), dims[0], dims[1], dims[2], N, n_global, grid[0],
+                              grid[1], grid[2], seed, perm.ctypes.data_as(C.c_void_p),
+                              counts.ctypes.data_as(C.c_void_p)))
+    return perm, int(counts[0]), int(counts[1]), counts[2:].reshape(P, 8)
+
 
 class Part:
     """Owns one hb_part: the operator split over px*py*pz virtual ranks of
