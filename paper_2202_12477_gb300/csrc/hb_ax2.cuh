@@ -316,6 +316,19 @@ struct pad {
 
 // Blocks per SM that shared memory allows (228 KB per SM, 1 KB reserved per
 // block); the register budget is set to match so occupancy is not lost to it.
+// Degrees whose kernel reads its node ids again for the interior-node
+// epilogue rather than holding n of them in registers through every phase:
+// where that buys a third resident block (FP32 N = 12..14: 8-17% faster,
+// measured; double-float N = 11: 1.44x). Elsewhere the extra loads cost more
+// than the residency gains, or shared memory is the limit.
+template <int N>
+__host__ __device__ constexpr bool reload_ids()
+{
+    if constexpr (sizeof(S) == 4) return N >= 12 && N <= 14;
+    else if constexpr (!std::is_same<T, S>::value) return N == 11;
+    else return false;
+}
+
 template <int N, int EB>
 __host__ __device__ constexpr int pencil_min_blocks()
 {
@@ -326,11 +339,10 @@ __host__ __device__ constexpr int pencil_min_blocks()
     // FP64 is bound by the FP64 pipe: no register cap (a cap only adds spills).
     // FP32 is bound by memory: ask for the resident blocks shared memory
     // allows, up to 4 (2 for the large degrees, whose lines need registers;
-    // 3 for N = 12..14, which reload their node ids).
+    // 3 where the node ids are reloaded).
     if constexpr (std::is_same<T, double>::value) return 1;
     // double-float: bound by the FP32 issue rate, so residency matters too
-    constexpr int cap = (N + 1) * (N + 1) > 128 ? (sizeof(T) == 4 && N >= 12 && N <= 14 ? 3 : 2)
-                                                : (sizeof(T) == 8 ? 3 : 4);
+    constexpr int cap = (N + 1) * (N + 1) > 128 ? (reload_ids<N>() ? 3 : 2) : (sizeof(T) == 8 ? 3 : 4);
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
@@ -363,11 +375,7 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     constexpr int NC = ws_consumers<N, EB>();
     static_assert(!WS || GM == GM_L2G, "the staged pipeline reads x through l2g");
-    // FP32, N = 12..14: the node ids are read again for the interior-node
-    // epilogue rather than held in n registers through every phase, which buys
-    // a third resident block (8-17% faster, measured); at other degrees the
-    // extra loads cost more than the residency gains.
-    constexpr bool kReloadIds = sizeof(S) == 4 && GM != GM_SCAT && N >= 12 && N <= 14;
+    constexpr bool kReloadIds = GM != GM_SCAT && reload_ids<N>();
     using P = pad<N>;
     const S *__restrict__ x = A.x;
     const int32_t *__restrict__ l2g = A.l2g;
@@ -496,11 +504,12 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
             } else {
                 // element-interior node: its DOF has no other copy (never masked)
                 // (the double-float copy in U holds 47 bits of x: reload the value itself)
-                const S xv = std::is_same<T, S>::value ? to_s(U[q]) : __ldg(x + gl[k]);
+                const int gk = kReloadIds ? __ldg(l2g + e * n3 + a + k * n2) : gl[k];
+                const S xv = std::is_same<T, S>::value ? to_s(U[q]) : __ldg(x + gk);
                 const S jw = A.screen ? __ldg(geo + (e * n + k) * 7 * n2 + 6 * n2 + a) : S(1);
                 S y = to_s(yc);
                 y += A.lambda * (jw * xv);
-                A.y[kReloadIds ? __ldg(l2g + e * n3 + a + k * n2) : gl[k]] = y;
+                A.y[gk] = y;
                 acc.add(xv, y);
             }
         }
