@@ -406,9 +406,14 @@ double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx);
  *                         one that gives up makes the next hb_cg_solve,
  *                         hb_cg_finish or hb_autotune on the mesh return
  *                         HB_ERR_TIMEOUT.
+ *   HB_VARIANT_CSR        (with PENCIL | EVEN_ODD, alone or with ONE) the element
+ *                         kernel writes each surface value straight to its place
+ *                         in the surface CSR order, so Z^T reads contiguous runs
+ *                         instead of scattered copies. Needs an int32 per surface
+ *                         copy, built when the variant is first set.
  * The default is PENCIL | EVEN_ODD; hb_autotune measures and picks per mesh. */
 enum { HB_VARIANT_PENCIL = 1, HB_VARIANT_EVEN_ODD = 2, HB_VARIANT_EB2 = 4, HB_VARIANT_ONE = 8,
-       HB_VARIANT_TMA = 16, HB_VARIANT_WS = 32 };
+       HB_VARIANT_TMA = 16, HB_VARIANT_WS = 32, HB_VARIANT_CSR = 64 };
 hb_status hb_set_kernel_variant(hb_mesh *mesh, hb_precision prec, int variant);
 hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *variant);
 
@@ -416,9 +421,9 @@ hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *var
  * made from measurements, Sec. 3.2; here every variant is timed on the mesh
  * itself). Runs one untimed and `reps` timed applications of A for each
  * variant (0, PENCIL, PENCIL|EVEN_ODD, PENCIL|EB2, PENCIL|EVEN_ODD|EB2,
- * PENCIL|EVEN_ODD|ONE, PENCIL|EVEN_ODD|TMA, PENCIL|EVEN_ODD|WS) on `stream`, keeps
- * the fastest for `prec` on this mesh and returns it in *best_variant.
- * ms_per_variant (may be NULL) has 64 slots
+ * PENCIL|EVEN_ODD|ONE, PENCIL|EVEN_ODD|TMA, PENCIL|EVEN_ODD|WS, PENCIL|EVEN_ODD|CSR,
+ * PENCIL|EVEN_ODD|ONE|CSR) on `stream`, keeps the fastest for `prec` on this mesh
+ * and returns it in *best_variant. ms_per_variant (may be NULL) has 128 slots
  * indexed by variant and receives the mean time of each. Allocates two scratch vectors for the
  * duration of the call; synchronises `stream`. */
 hb_status hb_autotune(hb_mesh *mesh, hb_precision prec, hb_screen screen, double lambda, int reps,

@@ -277,6 +277,9 @@ struct pencil_args {
     // owns, filled by a halo exchange); -1 is a masked node
     const S *halo;
     unsigned *err;  // WS kernels: bit 0 set when a bounded wait gave up
+    // SP kernels: CSR position of every surface copy (e * surface nodes +
+    // surface index; -1 masked); ysurf is then indexed by CSR position
+    const int32_t *spos;
 };
 
 // ------------------------------------------------------------ L2 prefetch
@@ -368,7 +371,7 @@ __device__ __forceinline__ void group_sync()
 template <int N, int EB>
 __host__ __device__ constexpr int ws_consumers() { return (EB * (N + 1) * (N + 1) + 31) / 32 * 32; }
 
-template <int N, bool EO, int EB, int GM = GM_L2G, bool WS = false>
+template <int N, bool EO, int EB, int GM = GM_L2G, bool WS = false, bool SP = false>
 __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, T *sm,
                                              hbacc::dot_acc<S> &acc, const ws_ctx *w = nullptr)
 {
@@ -495,7 +498,12 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
         for (int k = 0; k < n; k++) {
             const int q = P::at(p0, p1, k);
             const T yc = B1[q] + B2[q] + B3[q];
-            if (k == 0) {
+            if (SP && (k == 0 || k == N || ring)) {
+                // straight to the copy's CSR position (the gather reads contiguous runs)
+                const int sidx = k == 0 ? a : (k == N ? n2 + a : 2 * n2 + (k - 1) * 4 * N + r);
+                const int pos = __ldg(A.spos + e * NS + sidx);
+                if (pos >= 0) A.ysurf[pos] = to_s(yc);
+            } else if (k == 0) {
                 ys[a] = to_s(yc);
             } else if (k == N) {
                 ys[n2 + a] = to_s(yc);
@@ -517,7 +525,7 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
     group_sync<WS, NC>();  // the buffers are reused by the next group
 }
 
-template <int N, bool EO, int EB, bool PF = false, int GM = GM_L2G>
+template <int N, bool EO, int EB, bool PF = false, int GM = GM_L2G, bool SP = false>
 __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, EB>()))
     ax_pencil_kernel(const pencil_args A)
 {
@@ -532,7 +540,7 @@ __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, E
             prefetch_l2(A.geo + e0 * 7 * n3, (size_t)(cnt * 7 * n3) * sizeof(S));
         }
     }
-    pencil_group<N, EO, EB, GM>(A, blockIdx.x, reinterpret_cast<T *>(smem_raw), acc);
+    pencil_group<N, EO, EB, GM, false, SP>(A, blockIdx.x, reinterpret_cast<T *>(smem_raw), acc);
     if (A.partials) {
         const double v = hbacc::block_sum(acc.value());
         if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
@@ -628,17 +636,21 @@ namespace {
 // (N <= 10), 0 = one element per block (spreads small meshes over more SMs),
 // 3 = as 1 with a bulk L2 prefetch of the block's geometric factors at the
 // start (even-odd only), 4 = the persistent warp-specialised kernel (even-odd,
-// odd N, units that define HB_AX2_WS; else as 1).
+// odd N, units that define HB_AX2_WS; else as 1). With bit 8 (modes 0 and 1,
+// even-odd) surface values go to their CSR positions (A.spos).
 template <int N, bool EO, int GM = GM_L2G>
 hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nblocks_out)
 {
     constexpr int n = N + 1, n2 = n * n;
     constexpr int EB1 = n2 >= 256 ? 1 : 256 / n2;
     if (A.E <= 0) return HB_OK;
-    static int attr_set[5][32] = {{0}};
+    static int attr_set[7][32] = {{0}};
     int dev = 0;
     HB_TRY_CUDA(cudaGetDevice(&dev));
-    const int which = (eb_mode == 2 && n2 <= 128) ? 1 : (eb_mode == 0 ? 2 : (eb_mode == 3 ? 3 : (eb_mode == 4 ? 4 : 0)));
+    const bool sp = (eb_mode & 8) != 0;  // CSR-position surface store
+    eb_mode &= 7;
+    const int which = sp ? (eb_mode == 0 ? 6 : 5)
+                         : (eb_mode == 2 && n2 <= 128) ? 1 : (eb_mode == 0 ? 2 : (eb_mode == 3 ? 3 : (eb_mode == 4 ? 4 : 0)));
     auto go = [&](auto kern, int EB) -> hb_status {
         const size_t smem = sizeof(T) * 4 * (size_t)EB * pad<N>::size;
         if (dev >= 0 && dev < 32 && !attr_set[which][dev]) {
@@ -656,6 +668,10 @@ hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nbl
         // partitioned and scattered operators: the base block shape only
         return go(ax_pencil_kernel<N, EO, EB1, false, GM>, EB1);
     } else {
+        if constexpr (EO) {
+            if (which == 6) return go(ax_pencil_kernel<N, EO, 1, false, GM_L2G, true>, 1);
+            if (which == 5) return go(ax_pencil_kernel<N, EO, EB1, false, GM_L2G, true>, EB1);
+        }
         if constexpr (n2 <= 128) {
             if (which == 1) return go(ax_pencil_kernel<N, EO, EB1 * 2>, EB1 * 2);
         }

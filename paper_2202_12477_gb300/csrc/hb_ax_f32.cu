@@ -30,7 +30,7 @@ hb_status hb_launch_ax2_f32(const hb_mesh *m, const float *x, float *ysurf, floa
 {
     if (!m->geo32) { hb_set_error("mesh has no float geometric factors"); return HB_ERR_ARG; }
     hb2::pencil_args A{x, m->l2g, m->geo32, ysurf, y, m->E, run, (float)lambda, screen, partials, nullptr,
-                       m->counters + 7};
+                       m->counters + 7, (eb_mult & 8) ? m->spos : nullptr};
     switch (m->N) {
 #define HB_CASE(NN) \
     case NN: return eo ? hb2::launch<NN, true>(A, eb_mult, s, nblocks) : hb2::launch<NN, false>(A, eb_mult, s, nblocks);

@@ -28,7 +28,8 @@ hb_status hb_launch_ax2_f64(const hb_mesh *m, const double *x, double *ysurf, do
                             int64_t *nblocks)
 {
     if (!m->geo) { hb_set_error("mesh has no double geometric factors"); return HB_ERR_ARG; }
-    hb2::pencil_args A{x, m->l2g, m->geo, ysurf, y, m->E, run, (double)lambda, screen, partials};
+    hb2::pencil_args A{x, m->l2g, m->geo, ysurf, y, m->E, run, (double)lambda, screen, partials, nullptr, nullptr,
+                       (eb_mult & 8) ? m->spos : nullptr};
     switch (m->N) {
 #define HB_CASE(NN) \
     case NN: return eo ? hb2::launch<NN, true>(A, eb_mult, s, nblocks) : hb2::launch<NN, false>(A, eb_mult, s, nblocks);

@@ -12,7 +12,8 @@ hb_status hb_launch_ax2_f64x(const hb_mesh *m, const double *x, double *ysurf, d
                              double *partials, const int *run, int eb_mode, cudaStream_t s, int64_t *nblocks)
 {
     if (!m->geo) { hb_set_error("mesh has no FP64 geometric factors"); return HB_ERR_ARG; }
-    hb2::pencil_args A{x, m->l2g, m->geo, ysurf, y, m->E, run, lambda, screen, partials};
+    hb2::pencil_args A{x, m->l2g, m->geo, ysurf, y, m->E, run, lambda, screen, partials, nullptr, nullptr,
+                       (eb_mode & 8) ? m->spos : nullptr};
     switch (m->N) {
 #define HB_CASE(NN) \
     case NN: return hb2::launch<NN, true>(A, eb_mode, s, nblocks);

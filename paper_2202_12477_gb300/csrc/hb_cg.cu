@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(HB_RED_THREADS)
     assemble_body<T, SCREEN, DOT>(yL, rowptr, cols, x, mdiag, lambda, y, ng, partials, counter, st);
 }
 
-template <typename T, int SCREEN, int DOT>
+template <typename T, int SCREEN, int DOT, bool CONTIG>
 __global__ void __launch_bounds__(HB_RED_THREADS)
     assemble_surf_kernel(const T *__restrict__ ys, const int32_t *__restrict__ srow_g,
                          const int32_t *__restrict__ rowptr, const int32_t *__restrict__ cols,
@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(HB_RED_THREADS)
                          int64_t nrows, const double *__restrict__ ax_partials, int64_t n_axp, double *partials,
                          unsigned *counter, hb_cg_state *st)
 {
-    assemble_surf_body<T, SCREEN, DOT>(ys, srow_g, rowptr, cols, x, mdiag, lambda, y, nrows, ax_partials, n_axp,
-                                       partials, counter, st);
+    assemble_surf_body<T, SCREEN, DOT, CONTIG>(ys, srow_g, rowptr, cols, x, mdiag, lambda, y, nrows, ax_partials,
+                                               n_axp, partials, counter, st);
 }
 
 template <typename T>
@@ -130,18 +130,23 @@ hb_status launch_assemble(const hb_mesh *m, const T *yL, const T *x, T *y, const
     return HB_OK;
 }
 
+// contig: the element kernel wrote the surface values at their CSR positions.
 template <typename T>
 hb_status launch_assemble_surf(const hb_mesh *m, const T *ys, const T *x, T *y, const T *mdiag, int screen,
-                               double lambda, int64_t n_axp, hb_cg_state *st, int dot_mode, cudaStream_t s)
+                               double lambda, int64_t n_axp, hb_cg_state *st, int dot_mode, cudaStream_t s,
+                               bool contig = false)
 {
     const int64_t nr = m->nsr;
     const int grid = red_grid(nr > 0 ? nr : 1);
     unsigned *ctr = m->counters + 0;
     hb_prof_scope prof("assemble", s);
-#define HB_ASM(SC, DM)                                                                                      \
-    assemble_surf_kernel<T, SC, DM><<<grid, HB_RED_THREADS, 0, s>>>(ys, m->srow_g, m->srowptr, m->scols, x,  \
-                                                                    mdiag, lambda, y, nr, m->ax_partials,    \
-                                                                    n_axp, m->partials, ctr, st)
+#define HB_ASM(SC, DM)                                                                                          \
+    (contig ? assemble_surf_kernel<T, SC, DM, true><<<grid, HB_RED_THREADS, 0, s>>>(                           \
+                  ys, m->srow_g, m->srowptr, nullptr, x, mdiag, lambda, y, nr, m->ax_partials, n_axp,          \
+                  m->partials, ctr, st)                                                                         \
+            : assemble_surf_kernel<T, SC, DM, false><<<grid, HB_RED_THREADS, 0, s>>>(                          \
+                  ys, m->srow_g, m->srowptr, m->scols, x, mdiag, lambda, y, nr, m->ax_partials, n_axp,         \
+                  m->partials, ctr, st))
     if (screen == 0) {
         if (dot_mode == HB_DOT_NONE) HB_ASM(0, HB_DOT_NONE);
         else if (dot_mode == HB_DOT_TO_TMP) HB_ASM(0, HB_DOT_TO_TMP);
@@ -190,16 +195,18 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
         // double-float element kernel (pencil, even-odd); block shape from the FP64 variant
         const int v64 = m->variant[0];
         const int ebm = hb_variant_eb_mode(v64);
+        if ((ebm & 8) && !m->spos) { hb_set_error("surface positions missing for variant %d", v64); return HB_ERR_ARG; }
         double *partials = dot_mode != HB_DOT_NONE ? m->ax_partials : nullptr;
         int64_t nblk = 0;
         hb_status r = hb_launch_ax2_f64x(m, (const double *)x, (double *)m->yL, (double *)y, lambda, screen,
                                          partials, run, ebm, s, &nblk);
         if (r != HB_OK) return r;
         return launch_assemble_surf<double>(m, (const double *)m->yL, (const double *)x, (double *)y, m->mdiag,
-                                            screen, lambda, partials ? nblk : 0, st, dot_mode, s);
+                                            screen, lambda, partials ? nblk : 0, st, dot_mode, s, (ebm & 8) != 0);
     }
     const int v = m->variant[prec == HB_F64 ? 0 : 1];
     const int eo = (v & HB_VAR_EO) ? 1 : 0, ebm = hb_variant_eb_mode(v);
+    if ((ebm & 8) && !m->spos) { hb_set_error("surface positions missing for variant %d", v); return HB_ERR_ARG; }
     hb_status r;
     if (!(v & HB_VAR_PENCIL)) {
         if (prec == HB_F64) {
@@ -220,14 +227,14 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
                               ebm, s, &nblk);
         if (r != HB_OK) return r;
         return launch_assemble_surf<double>(m, (const double *)m->yL, (const double *)x, (double *)y, m->mdiag,
-                                            screen, lambda, partials ? nblk : 0, st, dot_mode, s);
+                                            screen, lambda, partials ? nblk : 0, st, dot_mode, s, (ebm & 8) != 0);
     }
     if (!m->mdiag32) { hb_set_error("mesh has no FP32 data (keep_fp32_copy = 0)"); return HB_ERR_ARG; }
     r = hb_launch_ax2_f32(m, (const float *)x, (float *)m->yL, (float *)y, lambda, screen, partials, run, eo, ebm, s,
                           &nblk);
     if (r != HB_OK) return r;
     return launch_assemble_surf<float>(m, (const float *)m->yL, (const float *)x, (float *)y, m->mdiag32, screen,
-                                       lambda, partials ? nblk : 0, st, dot_mode, s);
+                                       lambda, partials ? nblk : 0, st, dot_mode, s, (ebm & 8) != 0);
 }
 
 hb_status hb_launch_dot_f64(const hb_mesh *m, const double *a, const double *b, int64_t n, double *out,
@@ -260,6 +267,11 @@ extern "C" hb_status hb_set_kernel_variant(hb_mesh *m, hb_precision prec, int va
     if (!hb_valid_variant(variant)) {
         hb_set_error("invalid kernel variant %d", variant);
         return HB_ERR_ARG;
+    }
+    if (variant & HB_VAR_CSR) {
+        hb_device_guard dg(m->device);
+        hb_status st = hb_mesh_ensure_spos(m, nullptr);
+        if (st != HB_OK) return st;
     }
     m->variant[prec == HB_F64 ? 0 : 1] = variant;
     return HB_OK;
@@ -362,7 +374,17 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
     }
     const int candidates[] = {0, HB_VAR_PENCIL, HB_VAR_PENCIL | HB_VAR_EO, HB_VAR_PENCIL | HB_VAR_EB2,
                               HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_EB2, HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE,
-                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_TMA, HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_WS};
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_TMA, HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_WS,
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_CSR,
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE | HB_VAR_CSR};
+    {
+        hb_status sp = hb_mesh_ensure_spos(m, s);
+        if (sp != HB_OK) {
+            cudaFree(x);
+            cudaFree(y);
+            return sp;
+        }
+    }
     const int saved = m->variant[pi];
     int best = saved;
     float best_ms = 1e30f;

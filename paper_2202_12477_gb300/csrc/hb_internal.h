@@ -103,6 +103,7 @@ struct hb_mesh {
     int32_t *srow_g;    // [nsr] global id of each surface row (ascending)
     int32_t *srowptr;   // [nsr + 1]
     int32_t *scols;     // [nnz_s] e * surf_count + surface index, ascending
+    int32_t *spos;      // [E * surface nodes] CSR position of each surface copy (-1 masked); built on demand
     double *ax_partials;  // [max element-kernel blocks] per-block partials of x.y
     int64_t n_ax_partials;
     // stepwise solve (hb_cg_begin / hb_cg_iterate / hb_cg_finish)
@@ -167,22 +168,28 @@ hb_status hb_ax2_upload_f32(const double *D_all);
 // start (with PENCIL | EO only); HB_VAR_WS = persistent warp-specialised
 // kernel staging node map and factors through shared memory (with
 // PENCIL | EO only; FP32 and odd N, else the PENCIL | EO kernel runs).
+// HB_VAR_CSR = surface values written straight to their CSR positions, so the
+// surface gather reads contiguous runs (with PENCIL | EO, alone or with ONE).
 enum { HB_VAR_PENCIL = 1, HB_VAR_EO = 2, HB_VAR_EB2 = 4, HB_VAR_ONE = 8, HB_VAR_TMA = 16, HB_VAR_WS = 32,
-       HB_VAR_MAX = 63 };
+       HB_VAR_CSR = 64, HB_VAR_MAX = 127 };
 static inline bool hb_valid_variant(int v)
 {
     if (v == 0) return true;
     if (v < 0 || v > HB_VAR_MAX || !(v & HB_VAR_PENCIL)) return false;
     const int extra = v & (HB_VAR_ONE | HB_VAR_TMA | HB_VAR_WS | HB_VAR_EB2);
+    if (v & HB_VAR_CSR) return (v & HB_VAR_EO) && (extra == 0 || extra == HB_VAR_ONE);
     if (extra & (HB_VAR_ONE | HB_VAR_TMA | HB_VAR_WS))
         return (v & HB_VAR_EO) && (extra == HB_VAR_ONE || extra == HB_VAR_TMA || extra == HB_VAR_WS);
     return true;
 }
-// eb_mode of the pencil launchers for a variant
+// eb_mode of the pencil launchers for a variant (bit 8: CSR-position surface store)
 static inline int hb_variant_eb_mode(int v)
 {
-    return (v & HB_VAR_ONE) ? 0 : (v & HB_VAR_TMA) ? 3 : (v & HB_VAR_WS) ? 4 : (v & HB_VAR_EB2) ? 2 : 1;
+    const int b = (v & HB_VAR_ONE) ? 0 : (v & HB_VAR_TMA) ? 3 : (v & HB_VAR_WS) ? 4 : (v & HB_VAR_EB2) ? 2 : 1;
+    return b | ((v & HB_VAR_CSR) ? 8 : 0);
 }
+// Builds mesh->spos if it is missing (synchronises s).
+hb_status hb_mesh_ensure_spos(hb_mesh *m, cudaStream_t s);
 
 
 // y = Z^T y_L + lambda (x or M x); optional fused x.y into st->pAp (and the

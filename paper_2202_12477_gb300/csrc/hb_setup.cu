@@ -595,6 +595,37 @@ done:
     return st;
 }
 
+__global__ void k_spos(const int32_t *__restrict__ scols, int64_t nnz, int32_t *__restrict__ spos)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x)
+        spos[scols[q]] = (int32_t)q;
+}
+
+// CSR position of every surface copy (the inverse of scols), -1 for masked
+// surface nodes; built the first time a variant that writes it is chosen.
+hb_status hb_mesh_ensure_spos(hb_mesh *m, cudaStream_t s)
+{
+    if (m->spos) return HB_OK;
+    const int64_t total = m->E * (int64_t)hb_surf_count(m->N);
+    int32_t *p = nullptr;
+    HB_TRY_CUDA(cudaMalloc((void **)&p, sizeof(int32_t) * (total > 0 ? total : 1)));
+    cudaError_t e = cudaMemsetAsync(p, 0xFF, sizeof(int32_t) * (total > 0 ? total : 1), s);
+    if (e == cudaSuccess && m->nnz_s > 0) {
+        hb_count_launch();
+        k_spos<<<grid_for(m->nnz_s, 256), 256, 0, s>>>(m->scols, m->nnz_s, p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        hb_set_error("surface positions: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;
+    }
+    m->spos = p;
+    m->device_bytes += sizeof(int32_t) * (size_t)total;
+    return HB_OK;
+}
+
 // ---------------------------------------------------------------- mesh lifetime
 
 
@@ -617,6 +648,7 @@ extern "C" hb_status hb_mesh_destroy(hb_mesh *m)
     cudaFree(m->srow_g);
     cudaFree(m->srowptr);
     cudaFree(m->scols);
+    cudaFree(m->spos);
     cudaFree(m->ax_partials);
     cudaFree(m->inv_diag);
     cudaFree(m->inv_diag32);

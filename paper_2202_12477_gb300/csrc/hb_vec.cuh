@@ -138,7 +138,9 @@ __device__ __forceinline__ void assemble_body(const T *__restrict__ yL, const in
 // copies of ysurf (ascending: element order) + lambda (x_g | M_gg x_g).
 // With a dot mode, x.y over these rows plus the element kernel's per-block
 // partials (interior DOFs) is reduced on the fixed grid.
-template <typename T, int SCREEN, int DOT>
+// CONTIG: the copies of row r are ys[rowptr[r] .. rowptr[r+1]) (the element
+// kernel wrote them at their CSR positions); cols is not read.
+template <typename T, int SCREEN, int DOT, bool CONTIG = false>
 __device__ __forceinline__ void assemble_surf_body(const T *__restrict__ ys, const int32_t *__restrict__ srow_g,
                          const int32_t *__restrict__ rowptr, const int32_t *__restrict__ cols,
                          const T *__restrict__ x, const T *__restrict__ mdiag, double lambda, T *__restrict__ y,
@@ -165,8 +167,13 @@ __device__ __forceinline__ void assemble_surf_body(const T *__restrict__ ys, con
         }
 #pragma unroll
         for (int u = 0; u < U4; u++) {
-            c0[u] = a[u] < z[u] ? __ldcs(cols + a[u]) : -1;
-            c1[u] = a[u] + 1 < z[u] ? __ldcs(cols + a[u] + 1) : -1;
+            if constexpr (CONTIG) {
+                c0[u] = a[u] < z[u] ? a[u] : -1;
+                c1[u] = a[u] + 1 < z[u] ? a[u] + 1 : -1;
+            } else {
+                c0[u] = a[u] < z[u] ? __ldcs(cols + a[u]) : -1;
+                c1[u] = a[u] + 1 < z[u] ? __ldcs(cols + a[u] + 1) : -1;
+            }
             xv[u] = g[u] >= 0 ? x[g[u]] : T(0);
         }
 #pragma unroll
@@ -179,7 +186,7 @@ __device__ __forceinline__ void assemble_surf_body(const T *__restrict__ ys, con
         for (int u = 0; u < U4; u++) {
             if (g[u] < 0) continue;
             T t = s[u];
-            for (int p = a[u] + 2; p < z[u]; p++) t += __ldcs(ys + __ldcs(cols + p));
+            for (int p = a[u] + 2; p < z[u]; p++) t += __ldcs(ys + (CONTIG ? p : __ldcs(cols + p)));
             t += SCREEN ? lam * (mdiag[g[u]] * xv[u]) : lam * xv[u];
             y[g[u]] = t;
             if (DOT) acc.add(xv[u], t);
