@@ -292,7 +292,7 @@ def run_gb300(args, rank, world, local):
     # kernel on a smaller box (profiles/ax_pencil_f64_N7_32x32x30_ncu.md, 32x32x30
     # hexahedra, 15,728,640 local nodes), scaled to this launch by local nodes;
     # only for the captured (degree, variant) pairs.
-    per_node = {(7, 3): 64.77, (7, 11): 64.66}.get((N, variant))
+    per_node = {(7, 3): 64.77, (7, 11): 64.66, (7, 67): 67.53, (7, 75): 67.42}.get((N, variant))
     traffic = per_node * NL if per_node else None
     ax_flops = acc.op_local_flops(E, N)
     ax_bytes = acc.ax_local_bytes(NG, NL, 8)
