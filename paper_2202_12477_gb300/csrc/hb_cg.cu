@@ -418,6 +418,13 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
     if (st == HB_OK) st = check_dev_err(m, s);
     m->variant[pi] = st == HB_OK ? best : saved;
     if (best_variant) *best_variant = m->variant[pi];
+    // the surface positions were built for the timing; keep them only if used
+    if (m->spos && !(m->variant[0] & HB_VAR_CSR) && !(m->variant[1] & HB_VAR_CSR)) {
+        cudaStreamSynchronize(s);
+        cudaFree(m->spos);
+        m->spos = nullptr;
+        m->device_bytes -= sizeof(int32_t) * (size_t)(m->E * (int64_t)hb_surf_count(m->N));
+    }
     return st;
 }
 
