@@ -421,6 +421,7 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
     // the surface positions were built for the timing; keep them only if used
     if (m->spos && !(m->variant[0] & HB_VAR_CSR) && !(m->variant[1] & HB_VAR_CSR)) {
         cudaStreamSynchronize(s);
+        hb_mesh_drop_graphs(m);
         cudaFree(m->spos);
         m->spos = nullptr;
         m->device_bytes -= sizeof(int32_t) * (size_t)(m->E * (int64_t)hb_surf_count(m->N));

@@ -190,6 +190,8 @@ static inline int hb_variant_eb_mode(int v)
 }
 // Builds mesh->spos if it is missing (synchronises s).
 hb_status hb_mesh_ensure_spos(hb_mesh *m, cudaStream_t s);
+// Destroys the mesh's captured CG runs (before an array they use is replaced).
+void hb_mesh_drop_graphs(hb_mesh *m);
 
 
 // y = Z^T y_L + lambda (x or M x); optional fused x.y into st->pAp (and the

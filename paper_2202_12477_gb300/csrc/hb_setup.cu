@@ -621,9 +621,19 @@ hb_status hb_mesh_ensure_spos(hb_mesh *m, cudaStream_t s)
         hb_set_error("surface positions: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;
     }
+    hb_mesh_drop_graphs(m);  // captured runs hold the array pointer of the time
     m->spos = p;
     m->device_bytes += sizeof(int32_t) * (size_t)total;
     return HB_OK;
+}
+
+void hb_mesh_drop_graphs(hb_mesh *m)
+{
+    for (auto &g : m->graphs)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
 }
 
 // ---------------------------------------------------------------- mesh lifetime

@@ -348,6 +348,25 @@ def test_autotune_keeps_parity(tmp_path):
     assert _rel(m.apply_A(_to_dev(x), lam=0.1).cpu().numpy(), o.apply_A(x, 0.1)) <= 1e-12
 
 
+def test_csr_store_variant_survives_rebuilds():
+    """The CSR-position store's array is built when the variant is set and
+    freed by the autotuner when unused; captured CG runs that used it are
+    dropped, so CG after set -> autotune -> set again stays correct."""
+    m, o = _pair((3, 3, 3), 5, rho=0.15, seed=12)
+    b = m.rhs(kind=0, seed=12)
+    x_or, *_ = o.cg(b.cpu().numpy(), 0.1, rtol=0.0, max_it=20)
+    for variant in (67, 75):
+        hb.hb_set_kernel_variant(m.handle, hb.HB_F64, variant)
+        x, r = m.cg(b, lam=0.1, rtol=0.0, max_it=20)
+        assert _rel(x.cpu().numpy(), x_or) <= 1e-11
+        hb.hb_autotune(m.handle, hb.HB_F64, reps=1)
+        hb.hb_set_kernel_variant(m.handle, hb.HB_F64, 3)
+        hb.hb_autotune(m.handle, hb.HB_F32, reps=1)
+        hb.hb_set_kernel_variant(m.handle, hb.HB_F64, variant)
+        x2, r2 = m.cg(b, lam=0.1, rtol=0.0, max_it=20)
+        assert torch.equal(x, x2)
+
+
 # ---------------------------------------------------------------- Jacobi preconditioner
 
 @pytest.mark.parametrize("dims,N,rho,lam,screen", [((3, 2, 2), 3, 0.2, 0.1, 0), ((2, 2, 3), 6, 0.25, 0.7, 1),
