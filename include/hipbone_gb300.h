@@ -219,6 +219,16 @@ hb_status hb_diag_A(hb_mesh *mesh, hb_screen screen, double lambda, double *host
 hb_status hb_cg_solve(const hb_mesh *mesh, const hb_cg_opts *opts, const double *b,
                       double *x, hb_cg_result *res, void *stream);
 
+/* How hb_cg_solve runs HB_F64 without a preconditioner: mode 0 (default) runs
+ * every iteration inside one cooperative kernel (the phases of an iteration
+ * separated by grid-wide barriers instead of launches, one block per element
+ * with its three line directions contracted at once) when the mesh has at
+ * most 300 elements and one block per element fits on the GPU at once;
+ * mode 1 never does; mode 2 does whenever they fit. The fused run computes the same
+ * Algorithm 1 with its own fixed-order reductions (results agree with the
+ * launched kernels to rounding, not bitwise). */
+hb_status hb_set_cg_fused(hb_mesh *mesh, int mode);
+
 /* Stepwise form of hb_cg_solve for HB_F64 / HB_F64X (with or without the
  * Jacobi preconditioner), for callers that time or interleave iterations:
  * hb_cg_begin computes r0 = b - A x0 and the solver state (enqueued on

@@ -357,7 +357,10 @@ __host__ __device__ constexpr int pencil_min_blocks()
 // halo[-2 - g] for l2g entries g <= -2 (partitioned operator); GM_SCAT reads
 // scattered vectors, node q of element e at e n^3 + q (no l2g). A template
 // parameter, so the common kernel carries no branch for the other two.
-enum { GM_L2G = 0, GM_HALO = 1, GM_SCAT = 2 };
+// GM_L2G_CG is GM_L2G for kernels that write x themselves between element
+// passes (the fused CG): x is read through L2 (ld.global.cg), never through
+// the non-coherent read-only path.
+enum { GM_L2G = 0, GM_HALO = 1, GM_SCAT = 2, GM_L2G_CG = 3 };
 
 // Barrier of the threads computing a group: the whole block, or (WS) the
 // consumer warps only (named barrier 1), the producer warp running apart.
@@ -378,6 +381,7 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     constexpr int NC = ws_consumers<N, EB>();
     static_assert(!WS || GM == GM_L2G, "the staged pipeline reads x through l2g");
+    static_assert(GM != GM_L2G_CG || std::is_same<T, S>::value, "the fused path is FP32 or FP64");
     constexpr bool kReloadIds = GM != GM_SCAT && reload_ids<N>();
     using P = pad<N>;
     const S *__restrict__ x = A.x;
@@ -416,6 +420,8 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
                     if (g >= 0) v = __ldg(x + g);
                     else if (g < -1) v = __ldg(A.halo + (-2 - g));
                     U[P::at(p0, p1, k)] = to_c(v);
+                } else if constexpr (GM == GM_L2G_CG) {
+                    U[P::at(p0, p1, k)] = g >= 0 ? to_c(__ldcg(x + g)) : T(0);
                 } else {
                     U[P::at(p0, p1, k)] = g >= 0 ? to_c(__ldg(x + g)) : T(0);
                 }
@@ -545,6 +551,99 @@ __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, E
         const double v = hbacc::block_sum(acc.value());
         if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
     }
+}
+
+// ------------------------------------------------------------ three-group element
+// One element per block on 3 (N+1)^2 threads: group d = 0, 1, 2 of n^2
+// threads contracts the r-, s- or t-lines respectively (the three directions
+// at once), and the gather, metric and epilogue phases split each t-line's
+// k range over the groups (k = d, d + 3, ...). For a small mesh, where the
+// element's own latency sets the time, this keeps all four FP64 units of an
+// SM busy instead of the two that n^2 threads reach. Same arithmetic as
+// pencil_group per node. Every thread of the block must call it.
+template <int N, int GM = GM_L2G>
+__device__ __forceinline__ void pencil_element3(const pencil_args &A, int64_t e, T *sm, hbacc::dot_acc<S> &acc)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    constexpr int NS = surf_count<N>();
+    using P = pad<N>;
+    const S *__restrict__ x = A.x;
+    const int32_t *__restrict__ l2g = A.l2g;
+    const S *__restrict__ geo = A.geo;
+    const int tid = threadIdx.x;
+    const int d = tid / n2;            // 0 r, 1 s, 2 t; 3+ idle
+    const int a = tid - d * n2;
+    const int p0 = a % n, p1 = a / n;
+    const bool active = d < 3 && e < A.E;
+    T *U = sm;
+    T *B1 = U + P::size, *B2 = B1 + P::size, *B3 = B2 + P::size;
+    T *Bd = d == 0 ? B1 : (d == 1 ? B2 : B3);
+    if (active) {
+        const int32_t *lg = l2g + e * n3 + a;
+        for (int k = d; k < n; k += 3) {
+            const int g = __ldcs(lg + k * n2);
+            S v = S(0);
+            if (g >= 0) v = GM == GM_L2G_CG ? __ldcg(x + g) : __ldg(x + g);
+            U[P::at(p0, p1, k)] = to_c(v);
+        }
+    }
+    __syncthreads();
+    // the line this thread owns in its direction: node m of it at
+    // r: (m, p0, p1), s: (p0, m, p1), t: (p0, p1, m)
+    auto at_line = [&](int m) { return d == 0 ? P::at(m, p0, p1) : (d == 1 ? P::at(p0, m, p1) : P::at(p0, p1, m)); };
+    if (active) {
+        T in[n];
+#pragma unroll
+        for (int m = 0; m < n; m++) in[m] = U[at_line(m)];
+        line_st<N, false, true>(in, [&](int m, T v) { Bd[at_line(m)] = v; });
+    }
+    __syncthreads();
+    if (active) {
+        const S *ge = geo + e * 7 * n3 + a;
+        for (int k = d; k < n; k += 3) {
+            const S *g = ge + k * 7 * n2;
+            const T grr = to_c(__ldcs(g)), grs = to_c(__ldcs(g + n2)), grt = to_c(__ldcs(g + 2 * n2));
+            const T gss = to_c(__ldcs(g + 3 * n2)), gst = to_c(__ldcs(g + 4 * n2)), gtt = to_c(__ldcs(g + 5 * n2));
+            const int q = P::at(p0, p1, k);
+            const T ur = B1[q], us = B2[q], ut = B3[q];
+            B1[q] = fma(grt, ut, fma(grs, us, grr * ur));
+            B2[q] = fma(gst, ut, fma(gss, us, grs * ur));
+            B3[q] = fma(gtt, ut, fma(gst, us, grt * ur));
+        }
+    }
+    __syncthreads();
+    if (active) {
+        T in[n];
+#pragma unroll
+        for (int m = 0; m < n; m++) in[m] = Bd[at_line(m)];
+        line_st<N, true, true>(in, [&](int m, T v) { Bd[at_line(m)] = v; });
+    }
+    __syncthreads();
+    if (active) {
+        S *ys = A.ysurf + e * NS;
+        const bool ring = p0 == 0 || p0 == N || p1 == 0 || p1 == N;
+        const int r = ring ? ring_index<N>(p0, p1) : 0;
+        for (int k = d; k < n; k += 3) {
+            const int q = P::at(p0, p1, k);
+            const T yc = B1[q] + B2[q] + B3[q];
+            if (k == 0) {
+                ys[a] = to_s(yc);
+            } else if (k == N) {
+                ys[n2 + a] = to_s(yc);
+            } else if (ring) {
+                ys[2 * n2 + (k - 1) * 4 * N + r] = to_s(yc);
+            } else {
+                const int gk = __ldg(l2g + e * n3 + a + k * n2);
+                const S xv = std::is_same<T, S>::value ? to_s(U[q]) : __ldg(x + gk);
+                const S jw = A.screen ? __ldg(geo + (e * n + k) * 7 * n2 + 6 * n2 + a) : S(1);
+                S y = to_s(yc);
+                y += A.lambda * (jw * xv);
+                A.y[gk] = y;
+                acc.add(xv, y);
+            }
+        }
+    }
+    __syncthreads();  // the buffers are reused by the next element
 }
 
 // ------------------------------------------------------------ WS kernel

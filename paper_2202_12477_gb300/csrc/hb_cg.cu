@@ -553,6 +553,19 @@ static hb_status cg_drive(const hb_mesh *m, hb_precision prec, int screen, doubl
     return HB_OK;
 }
 
+// Fused CG: FP64 without a preconditioner, when every element of the mesh
+// fits in one cooperative launch (one per block; mode 0: and the mesh is
+// small enough that latency sets the time, at most 300 elements, where it
+// measured faster than the launched kernels; mode 2: whenever it fits).
+static bool use_fused_cg(const hb_mesh *m, const hb_cg_opts *o)
+{
+    if (o->prec != HB_F64 || o->precond || m->fused_mode == 1) return false;
+    const int64_t groups = m->E;  // one element per block
+    const int cap = hb_cg_fused_capacity(m->N);
+    if (cap <= 0 || groups > cap) return false;
+    return m->fused_mode == 2 || groups <= 300;
+}
+
 extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const double *b, double *x,
                                  hb_cg_result *res, void *stream)
 {
@@ -599,8 +612,16 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
         cg_init_kernel<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, p, inv_d, n, o->rtol, o->max_it, m->partials,
                                                        m->counters + 2, st);
         HB_CHECK_LAUNCH();
-        rs = cg_drive<double>(m, o->prec, o->screen, o->lambda, x, r, p, Ap, z, inv_d, st, o->max_it, s, &fin);
-        if (rs != HB_OK) return rs;
+        if (use_fused_cg(m, o)) {
+            rs = hb_cg_fused_run(m, o->screen, o->lambda, x, r, p, Ap, st, s);
+            if (rs != HB_OK) return rs;
+            HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
+            HB_TRY_CUDA(cudaStreamSynchronize(s));
+            fin = *m->state_host;
+        } else {
+            rs = cg_drive<double>(m, o->prec, o->screen, o->lambda, x, r, p, Ap, z, inv_d, st, o->max_it, s, &fin);
+            if (rs != HB_OK) return rs;
+        }
         R.iters = fin.it;
         R.rel_res = fin.bb > 0.0 ? sqrt(fin.res2 / fin.bb) : 0.0;
         if (fin.status == HB_ERR_BREAKDOWN) R.status = HB_ERR_BREAKDOWN;
@@ -653,6 +674,15 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
     }
     if (res) *res = R;
     return R.status;
+}
+
+extern "C" hb_status hb_set_cg_fused(hb_mesh *m, int mode)
+{
+    hb_clear_error();
+    if (!m) { hb_set_error("null mesh"); return HB_ERR_ARG; }
+    if (mode < 0 || mode > 2) { hb_set_error("fused mode must be 0, 1 or 2"); return HB_ERR_ARG; }
+    m->fused_mode = mode;
+    return HB_OK;
 }
 
 // ---------------------------------------------------------------- stepwise solve

@@ -106,6 +106,7 @@ struct hb_mesh {
     int32_t *spos;      // [E * surface nodes] CSR position of each surface copy (-1 masked); built on demand
     double *ax_partials;  // [max element-kernel blocks] per-block partials of x.y
     int64_t n_ax_partials;
+    int fused_mode;     // hb_cg_solve in one cooperative kernel: 0 small meshes, 1 never, 2 whenever it fits
     // stepwise solve (hb_cg_begin / hb_cg_iterate / hb_cg_finish)
     struct cg_step {
         int active;
@@ -190,6 +191,12 @@ static inline int hb_variant_eb_mode(int v)
 }
 // Builds mesh->spos if it is missing (synchronises s).
 hb_status hb_mesh_ensure_spos(hb_mesh *m, cudaStream_t s);
+// Fused CG (one cooperative kernel for all iterations): element groups one
+// launch can keep resident for degree N (0: not available), and the run.
+int hb_cg_fused_capacity(int N);
+hb_status hb_cg_fused_upload(const double *D_all);
+hb_status hb_cg_fused_run(const hb_mesh *m, int screen, double lambda, double *x, double *r, double *p, double *Ap,
+                          hb_cg_state *st, cudaStream_t s);
 // Destroys the mesh's captured CG runs (before an array they use is replaced).
 void hb_mesh_drop_graphs(hb_mesh *m);
 

@@ -97,6 +97,7 @@ _SIGS = [
     ("hb_cg_solve", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p,
                               C.POINTER(hb_cg_result), C.c_void_p]),
     ("hb_u01", C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64]),
+    ("hb_set_cg_fused", C.c_int, [C.c_void_p, C.c_int]),
     ("hb_cg_begin", C.c_int, [C.c_void_p, C.POINTER(hb_cg_opts), C.c_void_p, C.c_void_p, C.c_void_p]),
     ("hb_cg_iterate", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     ("hb_cg_finish", C.c_int, [C.c_void_p, C.POINTER(hb_cg_result), C.c_void_p]),

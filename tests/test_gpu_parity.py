@@ -309,6 +309,7 @@ def test_stepwise_cg_equals_one_call(prec, precond):
     iterate, bit for bit, as hb_cg_solve with the same iteration count; the
     iteration count never passes max_it."""
     m, o = _pair((3, 3, 2), 5, rho=0.1, seed=8)
+    hb.lib().hb_set_cg_fused(m.handle, 1)  # the launched kernels (the stepwise form never fuses)
     b = m.rhs(kind=0, seed=8)
     x1, r1 = m.cg(b, lam=0.1, rtol=0.0, max_it=20, prec=prec, precond=precond)
     x2 = m.vec()
@@ -322,6 +323,41 @@ def test_stepwise_cg_equals_one_call(prec, precond):
     assert r2.rel_res == r1.rel_res
     with pytest.raises(hb.HBError):
         m.cg_iterate(1)  # finished: no solve begun
+
+
+@pytest.mark.parametrize("dims,N", [((12, 12, 12), 1), ((3, 2, 2), 3), ((4, 4, 4), 7), ((2, 2, 3), 10), ((2, 1, 2), 15)])
+def test_fused_cg_matches_oracle_and_launched_path(dims, N):
+    """The one-kernel CG (cooperative launch, grid-wide barriers) follows the
+    oracle's iterates and agrees with the launched kernels to rounding."""
+    m, o = _pair(dims, N, rho=0.15, seed=N + 20)
+    b = m.rhs(kind=0, seed=N)
+    x_or, *_ = o.cg(b.cpu().numpy(), 0.1, rtol=0.0, max_it=40)
+    hb.lib().hb_set_cg_fused(m.handle, 2)
+    x_f, r_f = m.cg(b, lam=0.1, rtol=0.0, max_it=40)
+    hb.lib().hb_set_cg_fused(m.handle, 1)
+    x_l, r_l = m.cg(b, lam=0.1, rtol=0.0, max_it=40)
+    assert (r_f.iters, r_f.status) == (r_l.iters, r_l.status) == (40, hb.HB_OK)
+    assert _rel(x_f.cpu().numpy(), x_or) <= 1e-11
+    assert _rel(x_f.cpu().numpy(), x_l.cpu().numpy()) <= 1e-12
+    assert abs(r_f.rel_res - r_l.rel_res) <= 1e-8 * r_l.rel_res
+    # converged solve and repeatability
+    hb.lib().hb_set_cg_fused(m.handle, 2)
+    x1, q1 = m.cg(b, lam=0.1, rtol=1e-10, max_it=5000)
+    x2, q2 = m.cg(b, lam=0.1, rtol=1e-10, max_it=5000)
+    assert q1.status == hb.HB_OK and q1.rel_res <= 1e-10 and torch.equal(x1, x2)
+    bn = b.cpu().numpy()
+    assert np.linalg.norm(bn - o.apply_A(x1.cpu().numpy(), 0.1)) <= 1.05e-10 * np.linalg.norm(bn)
+
+
+def test_fused_cg_breakdown_and_zero_rhs():
+    m, _ = _pair((2, 2, 2), 4, rho=0.1, seed=3)
+    hb.lib().hb_set_cg_fused(m.handle, 2)
+    x, res = m.cg(m.vec(), lam=0.1, rtol=1e-10, max_it=50)
+    assert res.iters == 0 and res.status == hb.HB_OK and float(torch.abs(x).max()) == 0.0
+    b = m.rhs(kind=0, seed=1)
+    x, res = m.cg(b, lam=-1e6, rtol=1e-10, max_it=50)
+    assert res.status == hb.HB_ERR_BREAKDOWN
+    assert hb.lib().hb_set_cg_fused(m.handle, 3) == hb.HB_ERR_ARG
 
 
 def test_cg_zero_rhs_and_breakdown():
