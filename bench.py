@@ -476,11 +476,11 @@ def run_c3(args, rank, world, local):
     torch.cuda.set_device(local)
     N, E1 = args.N if args.N != 7 else 7, args.c3_elems
     m = hb.Mesh(E1, E1, E1, N, perturb=0.1, seed=0, fp32=True)
-    autotune.tune_mesh(m, lam=0.0)
+    chosen = autotune.tune_mesh(m, lam=0.0)
     b = m.rhs(kind=1, lam=0.0)
     out = {"workload": f"single large solve N={N}, {E1}^3 elements, perturb 0.1h, manufactured rhs "
                        f"(u = sin sin sin), lambda 0, rtol 1e-10", "n_global": m.n_global, "n_local": m.n_local,
-           "results": []}
+           "kernel_variants": {"f64": chosen[hb.HB_F64], "f32": chosen[hb.HB_F32]}, "results": []}
     xs = {}
     for prec in (hb.HB_F64, hb.HB_MIXED):
         x, rec = _solve_report(m, b, 0.0, prec, 1e-10)
@@ -496,6 +496,19 @@ def run_c3(args, rank, world, local):
     d = xs[hb.HB_MIXED] - xs[hb.HB_F64]
     out["mixed_vs_fp64_rel_err"] = float(torch.linalg.norm(d) / torch.linalg.norm(xs[hb.HB_F64]))
     out["speedup_mixed_over_fp64"] = out["results"][0]["time_s"] / out["results"][1]["time_s"]
+    if args.c3_inner:
+        # the inner tolerance of the mixed solver (its one free parameter), with
+        # and without the Jacobi preconditioner on the inner CG
+        sweep = []
+        for tol in [float(v) for v in args.c3_inner.split(",")]:
+            for pc in (0, 1):
+                _, rec = _solve_report(m, b, 0.0, hb.HB_MIXED, 1e-10, inner_rtol=tol, precond=pc)
+                rec["inner_rtol"] = tol
+                sweep.append(rec)
+        out["mixed_inner_sweep"] = sweep
+        best = min(sweep, key=lambda r: r["time_s"] if r["rel_res_fp64"] <= 1e-10 else 1e30)
+        out["mixed_best"] = best
+        out["speedup_best_mixed_over_fp64"] = out["results"][0]["time_s"] / best["time_s"]
     print(json.dumps(out), flush=True)
 
 
@@ -827,6 +840,7 @@ def main():
     ap.add_argument("--c5-k", type=int, default=16)
     ap.add_argument("--c5-budget-gb", type=float, default=160.0)
     ap.add_argument("--c3-elems", type=int, default=80)
+    ap.add_argument("--c3-inner", default="", help="comma-separated inner tolerances to sweep in the mixed solver")
     ap.add_argument("--c4-elems", type=int, default=24)
     ap.add_argument("--N", type=int, default=7)
     ap.add_argument("--degrees", default="")
