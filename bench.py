@@ -24,6 +24,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -349,8 +351,55 @@ def run_gb300(args, rank, world, local):
 
 # ---------------------------------------------------------------- reference arm (the oracle)
 
+def run_reference_workloads(args):
+    """The reference arm (the oracle, as it stands, on the host cores) on the
+    other configurations: config 1 (A x median of 5, 100 CG iterations), the
+    degree-sweep meshes for N in 3, 7, 11, 15 (A x once, 3 CG iterations, per
+    iteration), and config 3 (per-iteration time, with the time to 1e-10
+    extrapolated from the iteration count the GPU solvers needed, labelled
+    as such)."""
+    from oracle import oracle as orc
+    out = {"impl": "reference", "workload": "oracle timings on the host cores", "cores": orc.num_threads(),
+           "results": []}
+
+    def one(label, dims, N, ax_reps, iters, lam=0.1, kind=0):
+        t0 = time.perf_counter()
+        m = orc.Mesh(*dims, N, rho=0.1, seed=0)
+        t_create = time.perf_counter() - t0
+        x = np.random.default_rng(0).standard_normal(m.n_global)
+        ts = []
+        for _ in range(ax_reps):
+            t0 = time.perf_counter()
+            m.apply_A(x, lam)
+            ts.append(time.perf_counter() - t0)
+        b = m.rhs(kind=kind, seed=0, lam=0.0) if kind else m.rhs(kind=0, seed=0)
+        t0 = time.perf_counter()
+        m.cg(b, lam, rtol=0.0, max_it=iters)
+        t_cg = time.perf_counter() - t0
+        rec = {"config": label, "N": N, "elements": list(dims), "n_global": m.n_global, "setup_s": t_create,
+               "ax_ms_median": float(np.median(ts)) * 1e3, "ax_gdofs": m.n_global / float(np.median(ts)) / 1e9,
+               "cg_iterations": iters, "cg_ms_per_iteration": t_cg * 1e3 / iters,
+               "cg_gdofs": m.n_global * iters / t_cg / 1e9}
+        m.close()
+        out["results"].append(rec)
+        print(json.dumps(rec), flush=True)
+        return rec
+
+    one("config 1", (4, 4, 4), 7, 5, 100)
+    for N in (3, 7, 11, 15):
+        one("degree sweep", c2_dims(N), N, 1, 3)
+    r3 = one("config 3 (per iteration)", (80, 80, 80), 7, 1, 1, lam=0.0, kind=1)
+    # iteration counts of the GPU solvers to 1e-10 on this mesh (FP64 CG 3710)
+    r3["time_to_1e-10_s_extrapolated"] = r3["cg_ms_per_iteration"] * 3710 / 1e3
+    r3["extrapolation"] = "per-iteration time x 3710 FP64 CG iterations (the GPU FP64 solver's count)"
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, rank, world, local):
     if rank != 0:
+        return
+    if args.workload != "c2":
+        run_reference_workloads(args)
         return
     from oracle import oracle as orc
     N = args.N
