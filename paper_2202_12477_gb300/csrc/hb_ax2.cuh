@@ -771,13 +771,17 @@ hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nbl
             if (which == 6) return go(ax_pencil_kernel<N, EO, 1, false, GM_L2G, true>, 1);
             if (which == 5) return go(ax_pencil_kernel<N, EO, EB1, false, GM_L2G, true>, EB1);
         }
-        if constexpr (n2 <= 128) {
+        // the double-float unit keeps the block shapes the FP64 autotuner picks
+        // in practice (base, one element, and their CSR-store forms); the
+        // others run as the base shape there
+        constexpr bool kAll = std::is_same<T, S>::value;
+        if constexpr (kAll && n2 <= 128) {
             if (which == 1) return go(ax_pencil_kernel<N, EO, EB1 * 2>, EB1 * 2);
         }
         if constexpr (EO && EB1 > 1) {
             if (which == 2) return go(ax_pencil_kernel<N, EO, 1>, 1);
         }
-        if constexpr (EO) {
+        if constexpr (kAll && EO) {
             if (which == 3) return go(ax_pencil_kernel<N, EO, EB1, true>, EB1);
         }
 #ifdef HB_AX2_WS
