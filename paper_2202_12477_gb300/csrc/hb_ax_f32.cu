@@ -49,11 +49,11 @@ hb_status hb_launch_ax2_f32(const hb_mesh *m, const float *x, float *ysurf, floa
 namespace hb2 {
 namespace {
 
-template <int N>
-__host__ __device__ constexpr int serve_eb() { return HB_SERVE_THREADS / ((N + 1) * (N + 1)); }
+template <int N, int TH = HB_SERVE_THREADS>
+__host__ __device__ constexpr int serve_eb() { return TH / ((N + 1) * (N + 1)); }
 
-template <int N>
-__host__ __device__ constexpr size_t serve_smem_of() { return sizeof(T) * 4 * serve_eb<N>() * pad<N>::size; }
+template <int N, int TH = HB_SERVE_THREADS>
+__host__ __device__ constexpr size_t serve_smem_of() { return sizeof(T) * 4 * serve_eb<N, TH>() * pad<N>::size; }
 
 constexpr size_t serve_smem_max()
 {
@@ -72,37 +72,40 @@ constexpr size_t serve_smem_max()
     return m;
 }
 
-template <int N>
+template <int N, int TH>
 __device__ __forceinline__ void serve_groups(const pencil_args &A, T *sm, hbacc::dot_acc<S> &acc)
 {
-    constexpr int EB = serve_eb<N>();
+    constexpr int EB = serve_eb<N, TH>();
     const int64_t ngroups = (A.E + EB - 1) / EB;
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) pencil_group<N, true, EB>(A, g, sm, acc);
 }
 
 // Degree dispatch over [NN, HI] (only these degrees are instantiated).
-template <int NN, int HI>
+template <int NN, int HI, int TH>
 __device__ __forceinline__ void serve_dispatch(int N, const pencil_args &A, T *sm, hbacc::dot_acc<S> &acc)
 {
-    if (N == NN) serve_groups<NN>(A, sm, acc);
-    else if constexpr (NN < HI) serve_dispatch<NN + 1, HI>(N, A, sm, acc);
+    if (N == NN) serve_groups<NN, TH>(A, sm, acc);
+    else if constexpr (NN < HI) serve_dispatch<NN + 1, HI, TH>(N, A, sm, acc);
 }
 
-template <int LO, int HI>
+template <int LO, int HI, int TH>
 constexpr size_t serve_smem_range()
 {
-    if constexpr (LO == HI) return serve_smem_of<LO>();
-    else return serve_smem_of<LO>() > serve_smem_range<LO + 1, HI>() ? serve_smem_of<LO>() : serve_smem_range<LO + 1, HI>();
+    if constexpr (LO == HI) return serve_smem_of<LO, TH>();
+    else return serve_smem_of<LO, TH>() > serve_smem_range<LO + 1, HI, TH>() ? serve_smem_of<LO, TH>()
+                                                                            : serve_smem_range<LO + 1, HI, TH>();
 }
 
-// One slot's FP32 element kernel for the degrees [LO, HI] (the slot's degree
-// is read from its descriptor; a kernel whose range does not hold it returns
-// at once). Two degree classes with their own register budgets keep the
-// small degrees at four resident blocks per SM; one kernel for every degree
-// took the register count of the largest and ran one block per SM. Each
-// block walks element groups grid-stride and writes one partial of p.Ap.
-template <int LO, int HI, int MINB>
-__global__ void __launch_bounds__(HB_SERVE_THREADS, MINB)
+// One slot's FP32 element kernel for the degrees [LO, HI] on TH-thread
+// blocks (the slot's degree is read from its descriptor; a kernel whose range
+// does not hold it returns at once). Degree classes with their own register
+// budgets and block sizes keep the small degrees at four resident blocks per
+// SM and give N = 11 blocks of exactly one element (144 threads); one kernel
+// for every degree took the register count of the largest and ran one block
+// per SM. Each block walks element groups grid-stride and writes one partial
+// of p.Ap.
+template <int LO, int HI, int MINB, int TH>
+__global__ void __launch_bounds__(TH, MINB)
     serve_ax_kernel(const hb_slot_desc *__restrict__ D, const hb_slot_state *__restrict__ St)
 {
     const hb_slot_desc &d = *D;
@@ -112,20 +115,20 @@ __global__ void __launch_bounds__(HB_SERVE_THREADS, MINB)
     pencil_args A{(const T *)d.p32, d.l2g, d.geo32, (T *)d.ysurf, (T *)d.Ap32, d.E, nullptr, (T)d.lambda,
                   d.screen, d.ax_partials};
     hbacc::dot_acc<S> acc;
-    serve_dispatch<LO, HI>(d.N, A, sm, acc);
+    serve_dispatch<LO, HI, TH>(d.N, A, sm, acc);
     const double v = hbacc::block_sum(acc.value());
     if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
 }
 
-template <int LO, int HI, int MINB>
+template <int LO, int HI, int MINB, int TH>
 hb_status serve_launch_class(const hb_slot_desc *d, const hb_slot_state *st, cudaStream_t s)
 {
     static int attr_set[32] = {0};
     static int grid_of[32] = {0};
     int dev = 0;
     HB_TRY_CUDA(cudaGetDevice(&dev));
-    const size_t smem = serve_smem_range<LO, HI>();
-    auto kern = serve_ax_kernel<LO, HI, MINB>;
+    const size_t smem = serve_smem_range<LO, HI, TH>();
+    auto kern = serve_ax_kernel<LO, HI, MINB, TH>;
     if (dev < 0 || dev >= 32) dev = 0;
     if (!attr_set[dev]) {
         HB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -135,7 +138,7 @@ hb_status serve_launch_class(const hb_slot_desc *d, const hb_slot_state *st, cud
         attr_set[dev] = 1;
     }
     hb_count_launch();
-    kern<<<grid_of[dev], HB_SERVE_THREADS, smem, s>>>(d, st);
+    kern<<<grid_of[dev], TH, smem, s>>>(d, st);
     HB_CHECK_LAUNCH();
     return HB_OK;
 }
@@ -145,11 +148,14 @@ hb_status serve_launch_class(const hb_slot_desc *d, const hb_slot_state *st, cud
 
 size_t hb_serve_ax_smem_f32() { return hb2::serve_smem_max(); }
 
-// Both degree classes are launched; the one that does not hold the slot's
-// degree returns at once (the round graph is captured before slots are filled).
+// Every degree class is launched; those that do not hold the slot's degree
+// return at once (the round graph is captured before slots are filled).
+static_assert(HB_SERVE_MAX_N == 11, "the serving degree classes cover N = 1..11");
 hb_status hb_serve_launch_ax_f32(const hb_slot_desc *d, const hb_slot_state *st, cudaStream_t s)
 {
-    hb_status r = hb2::serve_launch_class<1, 7, 4>(d, st, s);
+    hb_status r = hb2::serve_launch_class<1, 7, 4, 256>(d, st, s);
     if (r != HB_OK) return r;
-    return hb2::serve_launch_class<8, HB_SERVE_MAX_N, 2>(d, st, s);
+    r = hb2::serve_launch_class<8, 10, 2, 256>(d, st, s);
+    if (r != HB_OK) return r;
+    return hb2::serve_launch_class<11, 11, 3, 144>(d, st, s);
 }
