@@ -28,8 +28,11 @@ def device_key(name: str, sms: int) -> str:
     return f"{name.strip()}|{sms}SM"
 
 
+_PREC_NAME = {hb.HB_F64: "f64", hb.HB_F32: "f32", hb.HB_F64X: "f64x"}
+
+
 def entry_key(N: int, prec: int) -> str:
-    return f"N{N}|{'f64' if prec == hb.HB_F64 else 'f32'}"
+    return f"N{N}|{_PREC_NAME[prec]}"
 
 
 def load(path: str | None = None) -> dict:
@@ -53,7 +56,8 @@ def store(cache: dict, path: str | None = None) -> None:
 
 def lookup(cache: dict, dev: str, N: int, prec: int):
     e = cache.get(dev, {}).get(entry_key(N, prec))
-    if isinstance(e, dict) and e.get("variant") in hb.VARIANTS:
+    valid = hb.VARIANTS_F64X if prec == hb.HB_F64X else hb.VARIANTS
+    if isinstance(e, dict) and e.get("variant") in valid:
         return e["variant"]
     return None
 

@@ -192,8 +192,8 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
         return HB_ERR_ARG;
     }
     if (prec == HB_F64X) {
-        // double-float element kernel (pencil, even-odd); block shape from the FP64 variant
-        const int v64 = m->variant[0];
+        // double-float element kernel (pencil, even-odd) in its own variant's block shape
+        const int v64 = m->variant[2];
         const int ebm = hb_variant_eb_mode(v64);
         if ((ebm & 8) && !m->spos) { hb_set_error("surface positions missing for variant %d", v64); return HB_ERR_ARG; }
         double *partials = dot_mode != HB_DOT_NONE ? m->ax_partials : nullptr;
@@ -204,7 +204,7 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
         return launch_assemble_surf<double>(m, (const double *)m->yL, (const double *)x, (double *)y, m->mdiag,
                                             screen, lambda, partials ? nblk : 0, st, dot_mode, s, (ebm & 8) != 0);
     }
-    const int v = m->variant[prec == HB_F64 ? 0 : 1];
+    const int v = m->variant[hb_variant_slot(prec)];
     const int eo = (v & HB_VAR_EO) ? 1 : 0, ebm = hb_variant_eb_mode(v);
     if ((ebm & 8) && !m->spos) { hb_set_error("surface positions missing for variant %d", v); return HB_ERR_ARG; }
     hb_status r;
@@ -263,9 +263,10 @@ extern "C" hb_status hb_set_kernel_variant(hb_mesh *m, hb_precision prec, int va
 {
     hb_clear_error();
     if (!m) { hb_set_error("null mesh"); return HB_ERR_ARG; }
-    if (prec != HB_F64 && prec != HB_F32) { hb_set_error("variant precision must be HB_F64 or HB_F32"); return HB_ERR_ARG; }
-    if (!hb_valid_variant(variant)) {
-        hb_set_error("invalid kernel variant %d", variant);
+    const int slot = hb_variant_slot(prec);
+    if (slot < 0) { hb_set_error("variant precision must be HB_F64, HB_F32 or HB_F64X"); return HB_ERR_ARG; }
+    if (!hb_valid_variant(variant) || (prec == HB_F64X && !hb_valid_variant_f64x(variant))) {
+        hb_set_error("invalid kernel variant %d for precision %d", variant, (int)prec);
         return HB_ERR_ARG;
     }
     if (variant & HB_VAR_CSR) {
@@ -273,15 +274,16 @@ extern "C" hb_status hb_set_kernel_variant(hb_mesh *m, hb_precision prec, int va
         hb_status st = hb_mesh_ensure_spos(m, nullptr);
         if (st != HB_OK) return st;
     }
-    m->variant[prec == HB_F64 ? 0 : 1] = variant;
+    m->variant[slot] = variant;
     return HB_OK;
 }
 
 extern "C" hb_status hb_get_kernel_variant(const hb_mesh *m, hb_precision prec, int *variant)
 {
     if (!m || !variant) { hb_set_error("null argument"); return HB_ERR_ARG; }
-    if (prec != HB_F64 && prec != HB_F32) { hb_set_error("variant precision must be HB_F64 or HB_F32"); return HB_ERR_ARG; }
-    *variant = m->variant[prec == HB_F64 ? 0 : 1];
+    const int slot = hb_variant_slot(prec);
+    if (slot < 0) { hb_set_error("variant precision must be HB_F64, HB_F32 or HB_F64X"); return HB_ERR_ARG; }
+    *variant = m->variant[slot];
     return HB_OK;
 }
 
@@ -349,15 +351,15 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
 {
     hb_clear_error();
     if (!m) { hb_set_error("null mesh"); return HB_ERR_ARG; }
-    if (prec != HB_F64 && prec != HB_F32) { hb_set_error("hb_autotune takes HB_F64 or HB_F32"); return HB_ERR_ARG; }
+    if (hb_variant_slot(prec) < 0) { hb_set_error("hb_autotune takes HB_F64, HB_F32 or HB_F64X"); return HB_ERR_ARG; }
     if (prec == HB_F32 && !m->geo32) { hb_set_error("HB_F32 needs keep_fp32_copy"); return HB_ERR_ARG; }
     if (!valid_screen(screen)) { hb_set_error("bad screen mode"); return HB_ERR_ARG; }
     if (reps < 1) reps = 1;
     hb_device_guard dg(m->device);
     cudaStream_t s = (cudaStream_t)stream;
-    const int pi = prec == HB_F64 ? 0 : 1;
+    const int pi = hb_variant_slot(prec);
     const int64_t n = m->n_global;
-    const size_t esz = prec == HB_F64 ? 8 : 4;
+    const size_t esz = prec == HB_F32 ? 4 : 8;
     if (n == 0) {
         if (best_variant) *best_variant = m->variant[pi];
         return HB_OK;
@@ -390,6 +392,7 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
     float best_ms = 1e30f;
     hb_status st = HB_OK;
     for (int c : candidates) {
+        if (prec == HB_F64X && !hb_valid_variant_f64x(c)) continue;
         m->variant[pi] = c;
         // one untimed application (first launch, attribute setup), then `reps` timed ones
         st = hb_apply_A_impl(m, prec, screen, lambda, x, y, nullptr, HB_DOT_NONE, s);
@@ -419,7 +422,7 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
     m->variant[pi] = st == HB_OK ? best : saved;
     if (best_variant) *best_variant = m->variant[pi];
     // the surface positions were built for the timing; keep them only if used
-    if (m->spos && !(m->variant[0] & HB_VAR_CSR) && !(m->variant[1] & HB_VAR_CSR)) {
+    if (m->spos && !((m->variant[0] | m->variant[1] | m->variant[2]) & HB_VAR_CSR)) {
         cudaStreamSynchronize(s);
         hb_mesh_drop_graphs(m);
         cudaFree(m->spos);
@@ -487,7 +490,7 @@ static hb_status cg_iterations_graph(const hb_mesh *mc, hb_precision prec, int s
     hb_mesh *m = const_cast<hb_mesh *>(mc);
     const int gi = prec == HB_F32 ? 1 : 0;
     hb_mesh::cg_graph &G = m->graphs[gi];
-    const int variant = m->variant[gi];
+    const int variant = m->variant[hb_variant_slot(prec)];
     if (!m->cg_stream) {
         HB_TRY_CUDA(cudaStreamCreateWithFlags(&m->cg_stream, cudaStreamNonBlocking));
         HB_TRY_CUDA(cudaEventCreateWithFlags(&m->cg_ev[0], cudaEventDisableTiming));

@@ -90,7 +90,7 @@ struct hb_mesh {
     double min_detJ;
     size_t device_bytes;
     cudaEvent_t ev0, ev1;
-    int variant[2];     // element-kernel variant per precision (HB_F64, HB_F32)
+    int variant[3];     // element-kernel variant per precision (HB_F64, HB_F32, HB_F64X)
     // Jacobi preconditioner: 1 / diag(A) for the (screen, lambda) it was built for
     double *inv_diag;
     float *inv_diag32;
@@ -182,6 +182,18 @@ static inline bool hb_valid_variant(int v)
     if (extra & (HB_VAR_ONE | HB_VAR_TMA | HB_VAR_WS))
         return (v & HB_VAR_EO) && (extra == HB_VAR_ONE || extra == HB_VAR_TMA || extra == HB_VAR_WS);
     return true;
+}
+// The double-float unit instantiates the even-odd pencil kernel in its base
+// and one-element shapes and their CSR-store forms only.
+static inline bool hb_valid_variant_f64x(int v)
+{
+    const int base = HB_VAR_PENCIL | HB_VAR_EO;
+    return v == base || v == (base | HB_VAR_ONE) || v == (base | HB_VAR_CSR) || v == (base | HB_VAR_ONE | HB_VAR_CSR);
+}
+// Slot of hb_mesh::variant for a precision (-1: none).
+static inline int hb_variant_slot(int prec)
+{
+    return prec == HB_F64 ? 0 : prec == HB_F32 ? 1 : prec == HB_F64X ? 2 : -1;
 }
 // eb_mode of the pencil launchers for a variant (bit 8: CSR-position surface store)
 static inline int hb_variant_eb_mode(int v)

@@ -715,6 +715,7 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     m->desc = *d;
     m->variant[0] = HB_VAR_PENCIL | HB_VAR_EO;
     m->variant[1] = HB_VAR_PENCIL | HB_VAR_EO;
+    m->variant[2] = HB_VAR_PENCIL | HB_VAR_EO;
     m->N = N;
     m->n = n;
     m->E = E;

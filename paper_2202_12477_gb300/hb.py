@@ -225,6 +225,7 @@ HB_VARIANT_PENCIL, HB_VARIANT_EVEN_ODD, HB_VARIANT_EB2, HB_VARIANT_ONE, HB_VARIA
     1, 2, 4, 8, 16, 32
 HB_VARIANT_CSR = 64
 VARIANTS = [0, 1, 3, 5, 7, 11, 19, 35, 67, 75]  # every valid combination
+VARIANTS_F64X = [3, 11, 67, 75]  # the shapes the double-float kernel is built in
 
 
 def hb_set_kernel_variant(h, prec, variant) -> None:

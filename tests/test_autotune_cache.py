@@ -11,10 +11,12 @@ def test_cache_roundtrip(tmp_path):
     dev = at.device_key("NVIDIA GB300", 152)
     c = at.record({}, dev, 7, hb.HB_F64, 3, {0: 12.9, 3: 12.5})
     at.record(c, dev, 7, hb.HB_F32, 7, {3: 1.48, 7: 1.45})
+    at.record(c, dev, 7, hb.HB_F64X, 67, {3: 7.1, 67: 6.4})
     at.store(c, path)
     c2 = at.load(path)
     assert at.lookup(c2, dev, 7, hb.HB_F64) == 3
     assert at.lookup(c2, dev, 7, hb.HB_F32) == 7
+    assert at.lookup(c2, dev, 7, hb.HB_F64X) == 67
     assert at.lookup(c2, dev, 9, hb.HB_F64) is None
     assert at.lookup(c2, at.device_key("other", 80), 7, hb.HB_F64) is None
 
@@ -26,6 +28,9 @@ def test_cache_rejects_garbage(tmp_path):
     dev = at.device_key("g", 1)
     path.write_text(json.dumps({dev: {at.entry_key(3, hb.HB_F64): {"variant": 6}}}))
     assert at.lookup(at.load(str(path)), dev, 3, hb.HB_F64) is None  # 6 is not a valid variant
+    # the double-float kernel is not built in the EB2 shape
+    path.write_text(json.dumps({dev: {at.entry_key(3, hb.HB_F64X): {"variant": 7}}}))
+    assert at.lookup(at.load(str(path)), dev, 3, hb.HB_F64X) is None
 
 
 def test_env_override(monkeypatch, tmp_path):

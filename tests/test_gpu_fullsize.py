@@ -56,8 +56,8 @@ def test_full_size_apply_sampled_rows(N):
         err = np.abs(y[rows] - ref).max()
         assert err <= 1e-12 * scale, (variant, err / scale)
     # double-float element kernel on the same FP64 data
-    for variant in (3, 11):
-        hb.hb_set_kernel_variant(m.handle, hb.HB_F64, variant)
+    for variant in hb.VARIANTS_F64X:
+        hb.hb_set_kernel_variant(m.handle, hb.HB_F64X, variant)
         y = m.apply_A(xd, lam=0.1, prec=hb.HB_F64X).cpu().numpy()
         err = np.abs(y[rows] - ref).max()
         assert err <= 1e-12 * scale, ("f64x", variant, err / scale)

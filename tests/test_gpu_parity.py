@@ -127,18 +127,39 @@ def test_apply_A_fp32(dims, N):
 
 
 @pytest.mark.parametrize("dims,N", OP_CASES)
-@pytest.mark.parametrize("variant", [3, 11])
+@pytest.mark.parametrize("variant", hb.VARIANTS_F64X)
 def test_apply_A_double_float(dims, N, variant):
     """HB_F64X: FP64 data, element kernel in double-float arithmetic
-    (~47-bit significand): same 1e-12 bar as the FP64 operator."""
+    (~47-bit significand): same 1e-12 bar as the FP64 operator, in each
+    block shape the double-float kernel is built in."""
     m, o = _pair(dims, N, rho=0.2, seed=N + 5)
-    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, variant)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F64X, variant)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, 0)  # the FP64 slot does not steer HB_F64X
     x = inputs.random_vector(m.n_global, seed=500 + N)
     for screen, lam in [(0, 0.1), (1, 0.7)]:
         y_or = o.apply_A(x, lam, screen)
         y = m.apply_A(_to_dev(x), lam=lam, screen=screen, prec=hb.HB_F64X).cpu().numpy()
         assert _rel(y, y_or) <= 1e-12
         assert np.abs(y - y_or).max() <= 1e-12 * np.abs(y_or).max()
+
+
+def test_double_float_variant_slot():
+    """HB_F64X keeps its own variant: it takes only the shapes its kernel is
+    built in, and autotuning it leaves the FP64 choice alone."""
+    m, o = _pair((5, 4, 3), 7, rho=0.1, seed=3)
+    assert hb.hb_get_kernel_variant(m.handle, hb.HB_F64X) == 3
+    for bad in (0, 1, 5, 7, 19, 35):
+        with pytest.raises(hb.HBError):
+            hb.hb_set_kernel_variant(m.handle, hb.HB_F64X, bad)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, 7)
+    best, ms = hb.hb_autotune(m.handle, hb.HB_F64X, reps=2)
+    assert best in hb.VARIANTS_F64X and sorted(ms) == hb.VARIANTS_F64X
+    assert hb.hb_get_kernel_variant(m.handle, hb.HB_F64X) == best
+    assert hb.hb_get_kernel_variant(m.handle, hb.HB_F64) == 7
+    x = inputs.random_vector(m.n_global, seed=31)
+    y = m.apply_A(_to_dev(x), lam=0.1, prec=hb.HB_F64X).cpu().numpy()
+    y_or = o.apply_A(x, 0.1, 0)
+    assert np.abs(y - y_or).max() <= 1e-12 * np.abs(y_or).max()
 
 
 def test_double_float_split_edge_values():
