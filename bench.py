@@ -448,8 +448,7 @@ def run_sweep(args, rank, world, local):
             dims = c2_dims(N, args.local_nodes)
             m = hb.Mesh(*dims, N, perturb=0.1, seed=0, fp32=(prec == "f32"))
             hbprec = {"f64": hb.HB_F64, "f32": hb.HB_F32, "f64x": hb.HB_F64X}[prec]
-            # the double-float kernel takes its block shape from the FP64 variant
-            varprec = hb.HB_F32 if prec == "f32" else hb.HB_F64
+            varprec = hbprec  # each precision keeps its own kernel variant
             dt = torch.float32 if prec == "f32" else torch.float64
             x = torch.from_numpy(inputs.random_vector(m.n_global, 1)).to("cuda", dt)
             y = torch.empty_like(x)

@@ -321,15 +321,32 @@ struct pad {
 // block); the register budget is set to match so occupancy is not lost to it.
 // Degrees whose kernel reads its node ids again for the interior-node
 // epilogue rather than holding n of them in registers through every phase:
-// where that buys a third resident block (FP32 N = 12..14: 8-17% faster,
-// measured; double-float N = 11: 1.44x). Elsewhere the extra loads cost more
-// than the residency gains, or shared memory is the limit.
+// where that buys more resident blocks. Measured on the full-size operator
+// (about 128M local nodes): FP32 N = 3, 7, 9 and 11..13 gain 5-21% with the
+// resident-block counts of f32_blocks(); at N = 5, 8, 10 and 15 the extra
+// loads (and at N = 15 spills) cost more than the residency gains; at N = 14
+// shared memory is the limit either way. Double-float N = 11: 1.44x.
 template <int N>
 __host__ __device__ constexpr bool reload_ids()
 {
-    if constexpr (sizeof(S) == 4) return N >= 12 && N <= 14;
+    if constexpr (sizeof(S) == 4) return N == 3 || N == 7 || N == 9 || (N >= 11 && N <= 14);
     else if constexpr (!std::is_same<T, S>::value) return N == 11;
     else return false;
+}
+
+// Resident blocks per SM asked of the FP32 kernel (memory-bound: latency is
+// hidden by residency), per degree, from the same measurements: 4 (2 for
+// n^2 > 128, whose lines need registers) unless the node ids are reloaded.
+template <int N>
+__host__ __device__ constexpr int f32_blocks()
+{
+    switch (N) {
+    case 3: return 6;
+    case 7: case 9: case 12: return 5;
+    case 11: return 6;
+    case 13: case 14: return 4;
+    default: return (N + 1) * (N + 1) > 128 ? 2 : 4;
+    }
 }
 
 template <int N, int EB>
@@ -341,11 +358,12 @@ __host__ __device__ constexpr int pencil_min_blocks()
     constexpr int b = by_smem < by_threads ? by_smem : by_threads;
     // FP64 is bound by the FP64 pipe: no register cap (a cap only adds spills).
     // FP32 is bound by memory: ask for the resident blocks shared memory
-    // allows, up to 4 (2 for the large degrees, whose lines need registers;
-    // 3 where the node ids are reloaded).
+    // allows, up to f32_blocks().
     if constexpr (std::is_same<T, double>::value) return 1;
     // double-float: bound by the FP32 issue rate, so residency matters too
-    constexpr int cap = (N + 1) * (N + 1) > 128 ? (reload_ids<N>() ? 3 : 2) : (sizeof(T) == 8 ? 3 : 4);
+    // (up to 3; 2 for n^2 > 128 unless the node ids are reloaded)
+    constexpr int cap = sizeof(T) == 4 ? f32_blocks<N>()
+                                       : ((N + 1) * (N + 1) > 128 ? (reload_ids<N>() ? 3 : 2) : 3);
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
