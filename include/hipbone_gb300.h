@@ -476,6 +476,17 @@ enum { HB_PROBE_STREAM81_FP = 0, HB_PROBE_STREAM81_BITS = 1, HB_PROBE_COPY = 2, 
        HB_PROBE_DMMA = 4, HB_PROBE_DMMA_FMA = 5 };
 hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int reps, double *rate);
 
+/* Self-test of the bounded device waits (every wait in this library's
+ * kernels gives up after about one second of wall time, records the failure
+ * in an error word and lets the kernel finish; the call that started it then
+ * returns HB_ERR_TIMEOUT). which = 0 runs a kernel whose mbarrier wait (the
+ * staged pipeline of HB_VARIANT_WS) never completes; which = 1 a cooperative
+ * kernel whose grid barrier (the fused CG) waits for one block more than it
+ * launched. Neither faults or hangs: *status receives HB_ERR_TIMEOUT when the
+ * kernel gave up and reported it (the expected outcome), HB_OK if it reported
+ * nothing. Takes about a second; synchronises `stream`. */
+hb_status hb_selftest_wait(int which, hb_status *status, void *stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *hb_last_error(void);
 

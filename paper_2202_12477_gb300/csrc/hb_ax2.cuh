@@ -136,11 +136,19 @@ static inline hb_status upload_tables(const double *D_all)
 // The warp-specialised variant (WS): a producer warp copies each element
 // group's node map and geometric factors (contiguous in memory) into shared
 // memory with cp.async.bulk; mbarriers count the bytes in ("full") and the
-// consumer warps' releases ("empty"). Every wait is bounded: after kWaitTries
-// polls it records bit 0 in the kernel's error word and carries on, so no
-// thread ever leaves the common control flow (the results are then wrong and
-// the error is reported by the host).
-constexpr unsigned kWaitTries = 1u << 24;
+// consumer warps' releases ("empty"). Every wait is bounded: after about
+// kWaitNs of wall time it records bit 0 in the kernel's error word and carries
+// on, so no thread ever leaves the common control flow (the results are then
+// wrong and the error is reported by the host).
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+// Wall time in ns (the GPU's global timer), for bounded waits.
+__device__ __forceinline__ unsigned long long wall_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {
@@ -173,7 +181,8 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 __device__ __forceinline__ void mbar_wait(uint64_t *bar, unsigned parity, unsigned *err)
 {
     const unsigned a = smem_u32(bar);
-    for (unsigned t = 0; t < kWaitTries; t++) {
+    unsigned long long t0 = 0;
+    for (unsigned t = 0;; t++) {
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -183,6 +192,11 @@ __device__ __forceinline__ void mbar_wait(uint64_t *bar, unsigned parity, unsign
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return;
+        if ((t & 255u) == 0) {
+            const unsigned long long now = wall_ns();
+            if (t == 0) t0 = now;
+            else if (now - t0 > kWaitNs) break;
+        }
     }
     if (err) atomicOr(err, 1u);
 }
@@ -725,6 +739,13 @@ __global__ void __launch_bounds__(ws_consumers<N, EB>() + 32, (ws_min_blocks<N, 
                 bulk_g2s(lsm, A.l2g + e0 * n3, (unsigned)(cnt * n3 * 4), &bars[0]);
                 if (i > 0) mbar_wait(&bars[3], (i - 1) & 1, A.err);
                 bulk_g2s(gsm, A.geo + e0 * 7 * n3, (unsigned)(cnt * 7 * n3 * sizeof(S)), &bars[2]);
+            }
+            // no copy of this block may still be in flight when it exits (the
+            // consumers waited for every one; this matters only after a wait
+            // of theirs gave up)
+            if (i > 0) {
+                mbar_wait(&bars[0], (i - 1) & 1, A.err);
+                mbar_wait(&bars[2], (i - 1) & 1, A.err);
             }
         }
         __syncwarp();  // the producer warp reconverges before the block-wide barrier below

@@ -20,6 +20,30 @@ hb_status hb_launch_ax_local_f32(const hb_mesh *m, const float *x, float *yL, co
 
 hb_status hb_ax2_upload_f32(const double *D_all) { return hb2::upload_tables(D_all); }
 
+namespace hb2 {
+namespace {
+// Self-test of the staged pipeline's bounded wait: an mbarrier that nothing
+// arrives at, so every thread's wait gives up and sets bit 0 of *err.
+__global__ void mbar_timeout_kernel(unsigned *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    mbar_wait(&bar, 0, err);
+}
+}  // namespace
+}  // namespace hb2
+
+hb_status hb_selftest_mbar_timeout(unsigned *err, cudaStream_t s)
+{
+    hb2::mbar_timeout_kernel<<<1, 32, 0, s>>>(err);
+    HB_CHECK_LAUNCH();
+    return HB_OK;
+}
+
 // Pencil variant with the interior/surface split: eo selects the even-odd
 // split, eb_mult = 2 doubles the elements per block (N <= 10). Interior DOFs
 // are finished here (y, lambda term, partial of x.y); surface values go to

@@ -329,8 +329,9 @@ extern "C" hb_status hb_dot(const hb_mesh *m, hb_precision prec, const void *a, 
     return HB_OK;
 }
 
-// Error word the element kernels set when a bounded wait gave up (bit 0: a
-// staged-pipeline wait); read and cleared at the solvers' sync points.
+// Error word the kernels set when a bounded wait gave up (bit 0: a
+// staged-pipeline wait, bit 1: a fused-CG grid barrier); read and cleared at
+// the solvers' sync points.
 static hb_status check_dev_err(hb_mesh *m, cudaStream_t s)
 {
     unsigned v = 0;
@@ -338,7 +339,7 @@ static hb_status check_dev_err(hb_mesh *m, cudaStream_t s)
     HB_TRY_CUDA(cudaStreamSynchronize(s));
     if (v) {
         HB_TRY_CUDA(cudaMemsetAsync(m->counters + 7, 0, sizeof(unsigned), s));
-        hb_set_error("an element kernel gave up waiting for staged data");
+        hb_set_error("a kernel gave up waiting (%s)", (v & 2u) ? "fused CG grid barrier" : "staged data");
         return HB_ERR_TIMEOUT;
     }
     return HB_OK;

@@ -10,16 +10,57 @@
 //   | every block sums them -> beta, stopping test; x += alpha p, p = r + beta p
 // Every block computes alpha and beta itself from the same partials in the
 // same order, so all blocks take the same decisions (no broadcast needed).
-#include <cooperative_groups.h>
-
+// The barriers are bounded: a block that waits more than about a second
+// records bit 1 in the mesh's error word and every block then leaves the
+// iteration loop (the host reports HB_ERR_TIMEOUT).
 #include "hb_internal.h"
 #define HB_AX2_T double
 #include "hb_ax2.cuh"
 #include "hb_vec.cuh"
 
-namespace cgx = cooperative_groups;
-
 namespace {
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident at once)
+// on one counter word: block 0 adds 2^31 - (nb - 1) and every other block 1,
+// so the counter's top bit flips exactly when the last of the nb blocks has
+// arrived, once per barrier, with no reset. Thread 0 of each block arrives
+// after a fence (its block's writes are then visible to the others) and
+// polls until the top bit differs from the one its own atomic saw, for at
+// most hb2::kWaitNs of wall time. Returns true in every thread of the block
+// if this block gave up (the caller must then stop: the blocks still waiting
+// give up in turn, so the launch ends).
+__device__ bool grid_barrier(unsigned *bar, unsigned nb, unsigned *err)
+{
+    __shared__ int s_fail;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (nb - 1u) : 1u;
+        __threadfence();
+        const unsigned old = atomicAdd(bar, add);
+        if (((old ^ ld_acquire(bar)) & 0x80000000u) == 0) {
+            const unsigned long long t0 = hb2::wall_ns();
+            while (((old ^ ld_acquire(bar)) & 0x80000000u) == 0) {
+                if (hb2::wall_ns() - t0 > hb2::kWaitNs) {
+                    atomicOr(err, 2u);
+                    fail = 1;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_fail = fail;
+    }
+    __syncthreads();
+    return s_fail != 0;
+}
 
 struct fused_args {
     const int32_t *l2g;
@@ -33,6 +74,8 @@ struct fused_args {
     int screen;
     double *part_a, *part_b;  // [gridDim.x] block partials (two, alternating)
     hb_cg_state *st;          // in: rr, tol2, max_it, run; out: final state
+    unsigned *bar;            // grid barrier counter (zero at launch)
+    unsigned *err;            // error word (bit 1: a barrier wait gave up)
 };
 
 // Block size for degree N: the three thread groups of pencil_element3, at
@@ -71,7 +114,6 @@ __device__ __forceinline__ double sum_partials(const double *p, int nb)
 template <int N>
 __global__ void __launch_bounds__(fused_threads<N>()) cg_fused_kernel(const fused_args F)
 {
-    cgx::grid_group grid = cgx::this_grid();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double *sm = reinterpret_cast<double *>(smem_raw);
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,7 +139,10 @@ __global__ void __launch_bounds__(fused_threads<N>()) cg_fused_kernel(const fuse
         hbacc::dot_acc<double> acc;
         for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x)
             hb2::pencil_element3<N, hb2::GM_L2G_CG>(A, g, sm, acc);
-        grid.sync();
+        if (grid_barrier(F.bar, nb, F.err)) {
+            status = HB_ERR_TIMEOUT;
+            break;
+        }
         // Z^T on the surface DOFs
         // (data written by other blocks in this launch is read through L2)
         for (int64_t rI = gtid; rI < F.nsr; rI += gthreads) {
@@ -113,7 +158,10 @@ __global__ void __launch_bounds__(fused_threads<N>()) cg_fused_kernel(const fuse
             const double v = hbacc::block_sum(acc.value());
             if (threadIdx.x == 0) F.part_a[blockIdx.x] = v;
         }
-        grid.sync();
+        if (grid_barrier(F.bar, nb, F.err)) {
+            status = HB_ERR_TIMEOUT;
+            break;
+        }
         pAp = sum_partials(F.part_a, nb);
         if (!(pAp > 0.0) || !isfinite(pAp)) {
             status = HB_ERR_BREAKDOWN;
@@ -131,7 +179,10 @@ __global__ void __launch_bounds__(fused_threads<N>()) cg_fused_kernel(const fuse
             const double v = hbacc::block_sum(racc.value());
             if (threadIdx.x == 0) F.part_b[blockIdx.x] = v;
         }
-        grid.sync();
+        if (grid_barrier(F.bar, nb, F.err)) {
+            status = HB_ERR_TIMEOUT;
+            break;
+        }
         const double rr_new = sum_partials(F.part_b, nb);
         beta = rr_new / rr;
         rr = rr_new;
@@ -143,7 +194,10 @@ __global__ void __launch_bounds__(fused_threads<N>()) cg_fused_kernel(const fuse
             F.x[i] += alpha * pi;
             F.p[i] = F.r[i] + beta * pi;
         }
-        grid.sync();
+        if (grid_barrier(F.bar, nb, F.err)) {
+            status = HB_ERR_TIMEOUT;
+            break;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         hb_cg_state *st = F.st;
@@ -188,7 +242,18 @@ hb_status launch_fused(const fused_args &F, int blocks_cap, cudaStream_t s, bool
     return HB_OK;
 }
 
+// Self-test of the bounded barrier: it waits for one block more than were
+// launched, so every block gives up and sets bit 1 of *err.
+__global__ void barrier_timeout_kernel(unsigned *bar, unsigned *err) { grid_barrier(bar, gridDim.x + 1, err); }
+
 }  // namespace
+
+hb_status hb_selftest_barrier_timeout(unsigned *bar, unsigned *err, cudaStream_t s)
+{
+    void *args[] = {(void *)&bar, (void *)&err};
+    HB_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)barrier_timeout_kernel, dim3(2), dim3(32), args, 0, s));
+    return HB_OK;
+}
 
 // This unit's copy of the derivative tables (every unit that includes the
 // element kernel has its own constant bank).
@@ -242,6 +307,9 @@ hb_status hb_cg_fused_run(const hb_mesh *m, int screen, double lambda, double *x
     F.part_a = m->partials;
     F.part_b = m->partials + HB_RED_BLOCKS;
     F.st = st;
+    F.bar = m->counters + 4;
+    F.err = m->counters + 7;
+    HB_TRY_CUDA(cudaMemsetAsync(F.bar, 0, sizeof(unsigned), s));
     switch (m->N) {
 #define HB_CASE(NN) \
     case NN: return launch_fused<NN>(F, HB_RED_BLOCKS, s, false, nullptr);

@@ -209,6 +209,11 @@ int hb_cg_fused_capacity(int N);
 hb_status hb_cg_fused_upload(const double *D_all);
 hb_status hb_cg_fused_run(const hb_mesh *m, int screen, double lambda, double *x, double *r, double *p, double *Ap,
                           hb_cg_state *st, cudaStream_t s);
+// Self-tests of the bounded device waits (hb_selftest_wait): the staged
+// pipeline's mbarrier wait (sets bit 0 of *err) and the fused CG's grid
+// barrier (bar: a zeroed word; sets bit 1).
+hb_status hb_selftest_mbar_timeout(unsigned *err, cudaStream_t s);
+hb_status hb_selftest_barrier_timeout(unsigned *bar, unsigned *err, cudaStream_t s);
 // Destroys the mesh's captured CG runs (before an array they use is replaced).
 void hb_mesh_drop_graphs(hb_mesh *m);
 

@@ -171,3 +171,27 @@ extern "C" hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int rep
     *rate = work / (best * 1e-3) / 1e9;  // GB/s or GFLOP/s
     return HB_OK;
 }
+
+extern "C" hb_status hb_selftest_wait(int which, hb_status *status, void *stream)
+{
+    hb_clear_error();
+    if (!status) { hb_set_error("null argument"); return HB_ERR_ARG; }
+    if (which != 0 && which != 1) { hb_set_error("which must be 0 or 1"); return HB_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *d = nullptr;  // [0..1] barrier words, [3] error word
+    HB_TRY_CUDA(cudaMalloc((void **)&d, 4 * sizeof(unsigned)));
+    cudaError_t e = cudaMemsetAsync(d, 0, 4 * sizeof(unsigned), s);
+    hb_status r = HB_OK;
+    if (e == cudaSuccess) r = which == 0 ? hb_selftest_mbar_timeout(d + 3, s) : hb_selftest_barrier_timeout(d, d + 3, s);
+    unsigned v = 0;
+    if (e == cudaSuccess && r == HB_OK) e = cudaMemcpyAsync(&v, d + 3, sizeof v, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && r == HB_OK) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (r != HB_OK) return r;
+    if (e != cudaSuccess) {
+        hb_set_error("self-test: %s", cudaGetErrorString(e));
+        return HB_ERR_CUDA;
+    }
+    *status = (v & (which == 0 ? 1u : 2u)) ? HB_ERR_TIMEOUT : HB_OK;
+    return HB_OK;
+}

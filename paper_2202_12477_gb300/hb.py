@@ -132,6 +132,7 @@ _SIGS = [
     ("hb_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
                               C.POINTER(C.c_double), C.c_void_p]),
     ("hb_probe", C.c_int, [C.c_int, C.c_int, C.c_size_t, C.c_int, C.POINTER(C.c_double)]),
+    ("hb_selftest_wait", C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_void_p]),
     ("hb_kernel_launches", C.c_ulonglong, []),
     ("hb_profile_enable", C.c_int, [C.c_int]),
     ("hb_profile_reset", C.c_int, []),
@@ -256,6 +257,14 @@ def hb_probe(kind, prec=HB_F64, nbytes=4 << 30, reps=5) -> float:
     r = C.c_double(0.0)
     _check(lib().hb_probe(kind, prec, nbytes, reps, C.byref(r)))
     return r.value
+
+
+def hb_selftest_wait(which, stream=None) -> int:
+    """Runs a kernel whose bounded wait (0: mbarrier, 1: grid barrier) can
+    never complete; returns the status it reported (HB_ERR_TIMEOUT expected)."""
+    st = C.c_int(-1)
+    _check(lib().hb_selftest_wait(which, C.byref(st), _stream_ptr(stream)))
+    return st.value
 
 
 def hb_kernel_launches() -> int:
