@@ -406,7 +406,9 @@ __device__ __forceinline__ void group_sync()
 template <int N, int EB>
 __host__ __device__ constexpr int ws_consumers() { return (EB * (N + 1) * (N + 1) + 31) / 32 * 32; }
 
-template <int N, bool EO, int EB, int GM = GM_L2G, bool WS = false, bool SP = false>
+// KEEP_IDS: hold the node ids in registers whatever reload_ids() says (for
+// kernels whose residency is fixed by other means, as the serving classes).
+template <int N, bool EO, int EB, int GM = GM_L2G, bool WS = false, bool SP = false, bool KEEP_IDS = false>
 __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, T *sm,
                                              hbacc::dot_acc<S> &acc, const ws_ctx *w = nullptr)
 {
@@ -414,7 +416,7 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
     constexpr int NC = ws_consumers<N, EB>();
     static_assert(!WS || GM == GM_L2G, "the staged pipeline reads x through l2g");
     static_assert(GM != GM_L2G_CG || std::is_same<T, S>::value, "the fused path is FP32 or FP64");
-    constexpr bool kReloadIds = GM != GM_SCAT && reload_ids<N>();
+    constexpr bool kReloadIds = GM != GM_SCAT && !KEEP_IDS && reload_ids<N>();
     using P = pad<N>;
     const S *__restrict__ x = A.x;
     const int32_t *__restrict__ l2g = A.l2g;

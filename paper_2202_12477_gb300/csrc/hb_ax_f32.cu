@@ -101,7 +101,8 @@ __device__ __forceinline__ void serve_groups(const pencil_args &A, T *sm, hbacc:
 {
     constexpr int EB = serve_eb<N, TH>();
     const int64_t ngroups = (A.E + EB - 1) / EB;
-    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) pencil_group<N, true, EB>(A, g, sm, acc);
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x)
+        pencil_group<N, true, EB, GM_L2G, false, false, true>(A, g, sm, acc);
 }
 
 // Degree dispatch over [NN, HI] (only these degrees are instantiated).
