@@ -339,12 +339,13 @@ struct pad {
 // (about 128M local nodes): FP32 N = 3, 7, 9 and 11..13 gain 5-21% with the
 // resident-block counts of f32_blocks(); at N = 5, 8, 10 and 15 the extra
 // loads (and at N = 15 spills) cost more than the residency gains; at N = 14
-// shared memory is the limit either way. Double-float N = 11: 1.44x.
+// shared memory is the limit either way. Double-float (with three element
+// buffers below N = 11, so four blocks fit): N = 5, 7, 10 and 11.
 template <int N>
 __host__ __device__ constexpr bool reload_ids()
 {
     if constexpr (sizeof(S) == 4) return N == 3 || N == 7 || N == 9 || (N >= 11 && N <= 14);
-    else if constexpr (!std::is_same<T, S>::value) return N == 11;
+    else if constexpr (!std::is_same<T, S>::value) return N == 5 || N == 7 || N == 10 || N == 11;
     else return false;
 }
 
@@ -363,10 +364,25 @@ __host__ __device__ constexpr int f32_blocks()
     }
 }
 
+// Element buffers in shared memory per element: 4 (u, then the r, s, t
+// lines), or 3 where the t-line buffer takes the place of u once every r- and
+// s-line has read it (one more block barrier; u is then gone for the
+// epilogue, which reads x again). Three buffers where that lets more blocks
+// reside and residency is the limit: the double-float kernel (issue-bound,
+// shared memory limits it to 3 blocks per SM with 4 buffers at N <= 10).
+// Measured on the full-size double-float operator: N = 7 4.84 -> 4.40 ms,
+// N = 8 5.60 -> 4.95, N = 10 6.99 -> 5.25, N = 1 3.82 -> 3.26; N = 2..5 and 9
+// within 1 %.
+template <int N>
+__host__ __device__ constexpr int nbuf()
+{
+    return (!std::is_same<T, S>::value && (N + 1) * (N + 1) <= 128) ? 3 : 4;
+}
+
 template <int N, int EB>
 __host__ __device__ constexpr int pencil_min_blocks()
 {
-    constexpr int smem = (int)sizeof(T) * 4 * EB * pad<N>::size + 1024;
+    constexpr int smem = (int)sizeof(T) * nbuf<N>() * EB * pad<N>::size + 1024;
     constexpr int by_smem = (228 * 1024) / smem;
     constexpr int by_threads = 2048 / (EB * (N + 1) * (N + 1));
     constexpr int b = by_smem < by_threads ? by_smem : by_threads;
@@ -375,9 +391,10 @@ __host__ __device__ constexpr int pencil_min_blocks()
     // allows, up to f32_blocks().
     if constexpr (std::is_same<T, double>::value) return 1;
     // double-float: bound by the FP32 issue rate, so residency matters too
-    // (up to 3; 2 for n^2 > 128 unless the node ids are reloaded)
+    // (up to 4, 3 at N = 9; for n^2 > 128 2, or 3 where the node ids are
+    // reloaded; measured per degree like FP32)
     constexpr int cap = sizeof(T) == 4 ? f32_blocks<N>()
-                                       : ((N + 1) * (N + 1) > 128 ? (reload_ids<N>() ? 3 : 2) : 3);
+                                       : ((N + 1) * (N + 1) > 128 ? (reload_ids<N>() ? 3 : 2) : (N == 9 ? 3 : 4));
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
@@ -408,7 +425,9 @@ __host__ __device__ constexpr int ws_consumers() { return (EB * (N + 1) * (N + 1
 
 // KEEP_IDS: hold the node ids in registers whatever reload_ids() says (for
 // kernels whose residency is fixed by other means, as the serving classes).
-template <int N, bool EO, int EB, int GM = GM_L2G, bool WS = false, bool SP = false, bool KEEP_IDS = false>
+// NB: element buffers (4, or 3 with the t-line buffer in place of u).
+template <int N, bool EO, int EB, int GM = GM_L2G, bool WS = false, bool SP = false, bool KEEP_IDS = false,
+          int NB = 4>
 __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, T *sm,
                                              hbacc::dot_acc<S> &acc, const ws_ctx *w = nullptr)
 {
@@ -428,10 +447,12 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
     const int p0 = a % n, p1 = a / n;  // line owned in each direction
     const int64_t e = grp * EB + el;
     const bool active = el < EB && e < E;
-    T *U = sm + el * 4 * P::size;  // gathered u (kept: the x values of the epilogue)
-    T *B1 = U + P::size;           // r: u_r, v_r, D^T_r v_r
-    T *B2 = B1 + P::size;          // s
-    T *B3 = B2 + P::size;          // t
+    static_assert(NB == 3 || NB == 4, "three or four element buffers");
+    static_assert(NB == 4 || (!WS && GM == GM_L2G), "three buffers only in the plain kernel");
+    T *U = sm + el * NB * P::size;  // gathered u (with 4 buffers kept: the x values of the epilogue)
+    T *B1 = U + P::size;            // r: u_r, v_r, D^T_r v_r
+    T *B2 = B1 + P::size;           // s
+    T *B3 = NB == 3 ? U : B2 + P::size;  // t
 
     int gl[n];  // node ids of this thread's t-line (i,j) = (p0,p1)
     if (active) {
@@ -480,6 +501,12 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
 #pragma unroll
         for (int m = 0; m < n; m++) in[m] = U[P::at(p0, m, p1)];
         line_st<N, false, EO>(in, [&](int m, T v) { B2[P::at(p0, m, p1)] = v; });
+    }
+    // three buffers: the t-lines overwrite u, so every r- and s-line must have
+    // read it first (each t-line is then read whole before it is written)
+    if constexpr (NB == 3) group_sync<WS, NC>();
+    if (active) {
+        T in[n];
         // t-line (i,j) = (p0,p1)
 #pragma unroll
         for (int m = 0; m < n; m++) in[m] = U[P::at(p0, p1, m)];
@@ -553,7 +580,7 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
                 // element-interior node: its DOF has no other copy (never masked)
                 // (the double-float copy in U holds 47 bits of x: reload the value itself)
                 const int gk = kReloadIds ? __ldg(l2g + e * n3 + a + k * n2) : gl[k];
-                const S xv = std::is_same<T, S>::value ? to_s(U[q]) : __ldg(x + gk);
+                const S xv = (std::is_same<T, S>::value && NB == 4) ? to_s(U[q]) : __ldg(x + gk);
                 const S jw = A.screen ? __ldg(geo + (e * n + k) * 7 * n2 + 6 * n2 + a) : S(1);
                 S y = to_s(yc);
                 y += A.lambda * (jw * xv);
@@ -580,7 +607,8 @@ __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, E
             prefetch_l2(A.geo + e0 * 7 * n3, (size_t)(cnt * 7 * n3) * sizeof(S));
         }
     }
-    pencil_group<N, EO, EB, GM, false, SP>(A, blockIdx.x, reinterpret_cast<T *>(smem_raw), acc);
+    constexpr int NB = GM == GM_L2G ? nbuf<N>() : 4;
+    pencil_group<N, EO, EB, GM, false, SP, false, NB>(A, blockIdx.x, reinterpret_cast<T *>(smem_raw), acc);
     if (A.partials) {
         const double v = hbacc::block_sum(acc.value());
         if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
@@ -792,7 +820,7 @@ hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nbl
     const int which = sp ? (eb_mode == 0 ? 6 : 5)
                          : (eb_mode == 2 && n2 <= 128) ? 1 : (eb_mode == 0 ? 2 : (eb_mode == 3 ? 3 : (eb_mode == 4 ? 4 : 0)));
     auto go = [&](auto kern, int EB) -> hb_status {
-        const size_t smem = sizeof(T) * 4 * (size_t)EB * pad<N>::size;
+        const size_t smem = sizeof(T) * (GM == GM_L2G ? nbuf<N>() : 4) * (size_t)EB * pad<N>::size;
         if (dev >= 0 && dev < 32 && !attr_set[which][dev]) {
             HB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_set[which][dev] = 1;
