@@ -337,14 +337,14 @@ struct pad {
 // epilogue rather than holding n of them in registers through every phase:
 // where that buys more resident blocks. Measured on the full-size operator
 // (about 128M local nodes): FP32 N = 3, 7, 9 and 11..13 gain 5-21% with the
-// resident-block counts of f32_blocks(); at N = 5, 8, 10 and 15 the extra
-// loads (and at N = 15 spills) cost more than the residency gains; at N = 14
-// shared memory is the limit either way. Double-float (with three element
+// resident-block counts of f32_blocks(); N = 8, 14 and 15 gain with three
+// element buffers (nbuf); at N = 5 and 10 the extra loads cost more than the
+// residency gains. Double-float (with three element
 // buffers below N = 11, so four blocks fit): N = 5, 7, 10 and 11.
 template <int N>
 __host__ __device__ constexpr bool reload_ids()
 {
-    if constexpr (sizeof(S) == 4) return N == 3 || N == 7 || N == 9 || (N >= 11 && N <= 14);
+    if constexpr (sizeof(S) == 4) return N == 3 || N == 7 || N == 8 || N == 9 || (N >= 11 && N <= 15);
     else if constexpr (!std::is_same<T, S>::value) return N == 5 || N == 7 || N == 10 || N == 11;
     else return false;
 }
@@ -356,10 +356,10 @@ template <int N>
 __host__ __device__ constexpr int f32_blocks()
 {
     switch (N) {
-    case 3: return 6;
+    case 3: case 8: case 11: return 6;
     case 7: case 9: case 12: return 5;
-    case 11: return 6;
     case 13: case 14: return 4;
+    case 15: return 3;
     default: return (N + 1) * (N + 1) > 128 ? 2 : 4;
     }
 }
@@ -369,13 +369,16 @@ __host__ __device__ constexpr int f32_blocks()
 // s-line has read it (one more block barrier; u is then gone for the
 // epilogue, which reads x again). Three buffers where that lets more blocks
 // reside and residency is the limit: the double-float kernel (issue-bound,
-// shared memory limits it to 3 blocks per SM with 4 buffers at N <= 10).
+// shared memory limits it to 3 blocks per SM with 4 buffers at N <= 10) and
+// the FP32 kernel at N = 8, 14, 15 (operator 4 %, 3 %, 1.5 % faster; at the
+// other degrees registers limit it first or nothing was gained).
 // Measured on the full-size double-float operator: N = 7 4.84 -> 4.40 ms,
 // N = 8 5.60 -> 4.95, N = 10 6.99 -> 5.25, N = 1 3.82 -> 3.26; N = 2..5 and 9
 // within 1 %.
 template <int N>
 __host__ __device__ constexpr int nbuf()
 {
+    if constexpr (sizeof(T) == 4) return (N == 8 || N == 14 || N == 15) ? 3 : 4;
     return (!std::is_same<T, S>::value && (N + 1) * (N + 1) <= 128) ? 3 : 4;
 }
 
