@@ -421,13 +421,20 @@ double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx);
  *                         in the surface CSR order, so Z^T reads contiguous runs
  *                         instead of scattered copies. Needs an int32 per surface
  *                         copy, built when the variant is first set.
+ *   HB_VARIANT_GRID       (with PENCIL | EVEN_ODD, alone or with ONE; not with
+ *                         CSR) the element kernel stores every local value
+ *                         element-major and Z^T is taken on every DOF by the
+ *                         box's lattice arithmetic (no column array): one warp
+ *                         per lattice row sums each DOF's copies in ascending
+ *                         element order, as the CSR does, so y is bitwise the
+ *                         same as with the other pencil variants.
  * Each of HB_F64, HB_F32 and HB_F64X keeps its own variant. HB_F64X takes
- * PENCIL | EVEN_ODD with or without ONE and with or without CSR (the four
- * shapes its double-float kernel is built in); other variants return
+ * PENCIL | EVEN_ODD with or without ONE, and with CSR or GRID or neither (the
+ * six shapes its double-float kernel is built in); other variants return
  * HB_ERR_ARG for it. The default is PENCIL | EVEN_ODD; hb_autotune measures
  * and picks per mesh and precision. */
 enum { HB_VARIANT_PENCIL = 1, HB_VARIANT_EVEN_ODD = 2, HB_VARIANT_EB2 = 4, HB_VARIANT_ONE = 8,
-       HB_VARIANT_TMA = 16, HB_VARIANT_WS = 32, HB_VARIANT_CSR = 64 };
+       HB_VARIANT_TMA = 16, HB_VARIANT_WS = 32, HB_VARIANT_CSR = 64, HB_VARIANT_GRID = 128 };
 hb_status hb_set_kernel_variant(hb_mesh *mesh, hb_precision prec, int variant);
 hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *variant);
 
@@ -436,9 +443,10 @@ hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *var
  * itself). Runs one untimed and `reps` timed applications of A for each
  * variant (0, PENCIL, PENCIL|EVEN_ODD, PENCIL|EB2, PENCIL|EVEN_ODD|EB2,
  * PENCIL|EVEN_ODD|ONE, PENCIL|EVEN_ODD|TMA, PENCIL|EVEN_ODD|WS, PENCIL|EVEN_ODD|CSR,
- * PENCIL|EVEN_ODD|ONE|CSR; for HB_F64X the four it takes) on `stream`, keeps the
- * fastest for `prec` (HB_F64, HB_F32 or HB_F64X) on this mesh and returns it in
- * *best_variant. ms_per_variant (may be NULL) has 128 slots
+ * PENCIL|EVEN_ODD|ONE|CSR, PENCIL|EVEN_ODD|GRID, PENCIL|EVEN_ODD|ONE|GRID; for
+ * HB_F64X the six it takes) on `stream`, keeps the fastest for `prec` (HB_F64,
+ * HB_F32 or HB_F64X) on this mesh and returns it in *best_variant.
+ * ms_per_variant (may be NULL) has 256 slots
  * indexed by variant and receives the mean time of each. Allocates two scratch vectors for the
  * duration of the call; synchronises `stream`. */
 hb_status hb_autotune(hb_mesh *mesh, hb_precision prec, hb_screen screen, double lambda, int reps,

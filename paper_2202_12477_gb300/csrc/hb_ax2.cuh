@@ -429,8 +429,11 @@ __host__ __device__ constexpr int ws_consumers() { return (EB * (N + 1) * (N + 1
 // KEEP_IDS: hold the node ids in registers whatever reload_ids() says (for
 // kernels whose residency is fixed by other means, as the serving classes).
 // NB: element buffers (4, or 3 with the t-line buffer in place of u).
+// FL: every local value to ysurf[e n^3 + node] (element-major, [k][j][i]);
+// no interior finish, lambda term or partial here: the lattice gather does
+// all of Z^T.
 template <int N, bool EO, int EB, int GM = GM_L2G, bool WS = false, bool SP = false, bool KEEP_IDS = false,
-          int NB = 4>
+          int NB = 4, bool FL = false>
 __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, T *sm,
                                              hbacc::dot_acc<S> &acc, const ws_ctx *w = nullptr)
 {
@@ -438,7 +441,8 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
     constexpr int NC = ws_consumers<N, EB>();
     static_assert(!WS || GM == GM_L2G, "the staged pipeline reads x through l2g");
     static_assert(GM != GM_L2G_CG || std::is_same<T, S>::value, "the fused path is FP32 or FP64");
-    constexpr bool kReloadIds = GM != GM_SCAT && !KEEP_IDS && reload_ids<N>();
+    static_assert(!(FL && (SP || WS || GM != GM_L2G)), "the element-major store is a plain-kernel mode");
+    constexpr bool kReloadIds = GM != GM_SCAT && !KEEP_IDS && !FL && reload_ids<N>();
     using P = pad<N>;
     const S *__restrict__ x = A.x;
     const int32_t *__restrict__ l2g = A.l2g;
@@ -559,7 +563,15 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
         line_st<N, true, EO>(in, [&](int m, T v) { B3[P::at(p0, p1, m)] = v; });
     }
     group_sync<WS, NC>();
-    if (active) {
+    if (FL && active) {
+        // element-major: thread (p0,p1) stores its t-line, coalesced across the block
+        S *yl = A.ysurf + e * n3 + a;
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            const int q = P::at(p0, p1, k);
+            yl[k * n2] = to_s(B1[q] + B2[q] + B3[q]);
+        }
+    } else if (active) {
         constexpr int NS = surf_count<N>();
         S *ys = A.ysurf + e * NS;
         const bool ring = p0 == 0 || p0 == N || p1 == 0 || p1 == N;
@@ -595,7 +607,7 @@ __device__ __forceinline__ void pencil_group(const pencil_args &A, int64_t grp, 
     group_sync<WS, NC>();  // the buffers are reused by the next group
 }
 
-template <int N, bool EO, int EB, bool PF = false, int GM = GM_L2G, bool SP = false>
+template <int N, bool EO, int EB, bool PF = false, int GM = GM_L2G, bool SP = false, bool FL = false>
 __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, EB>()))
     ax_pencil_kernel(const pencil_args A)
 {
@@ -611,7 +623,7 @@ __global__ void __launch_bounds__(EB *(N + 1) * (N + 1), (pencil_min_blocks<N, E
         }
     }
     constexpr int NB = GM == GM_L2G ? nbuf<N>() : 4;
-    pencil_group<N, EO, EB, GM, false, SP, false, NB>(A, blockIdx.x, reinterpret_cast<T *>(smem_raw), acc);
+    pencil_group<N, EO, EB, GM, false, SP, false, NB, FL>(A, blockIdx.x, reinterpret_cast<T *>(smem_raw), acc);
     if (A.partials) {
         const double v = hbacc::block_sum(acc.value());
         if (threadIdx.x == 0) A.partials[blockIdx.x] = v;
@@ -808,20 +820,24 @@ namespace {
 // 3 = as 1 with a bulk L2 prefetch of the block's geometric factors at the
 // start (even-odd only), 4 = the persistent warp-specialised kernel (even-odd,
 // odd N, units that define HB_AX2_WS; else as 1). With bit 8 (modes 0 and 1,
-// even-odd) surface values go to their CSR positions (A.spos).
+// even-odd) surface values go to their CSR positions (A.spos); with bit 16
+// (modes 0 and 1, even-odd) every local value goes to A.ysurf element-major.
 template <int N, bool EO, int GM = GM_L2G>
 hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nblocks_out)
 {
     constexpr int n = N + 1, n2 = n * n;
     constexpr int EB1 = n2 >= 256 ? 1 : 256 / n2;
     if (A.E <= 0) return HB_OK;
-    static int attr_set[7][32] = {{0}};
+    static int attr_set[9][32] = {{0}};
     int dev = 0;
     HB_TRY_CUDA(cudaGetDevice(&dev));
-    const bool sp = (eb_mode & 8) != 0;  // CSR-position surface store
+    const bool sp = (eb_mode & 8) != 0;   // CSR-position surface store
+    const bool fl = (eb_mode & 16) != 0;  // element-major store of every local value
     eb_mode &= 7;
-    const int which = sp ? (eb_mode == 0 ? 6 : 5)
-                         : (eb_mode == 2 && n2 <= 128) ? 1 : (eb_mode == 0 ? 2 : (eb_mode == 3 ? 3 : (eb_mode == 4 ? 4 : 0)));
+    const int which = fl ? (eb_mode == 0 ? 8 : 7)
+                      : sp ? (eb_mode == 0 ? 6 : 5)
+                           : (eb_mode == 2 && n2 <= 128) ? 1
+                                                         : (eb_mode == 0 ? 2 : (eb_mode == 3 ? 3 : (eb_mode == 4 ? 4 : 0)));
     auto go = [&](auto kern, int EB) -> hb_status {
         const size_t smem = sizeof(T) * (GM == GM_L2G ? nbuf<N>() : 4) * (size_t)EB * pad<N>::size;
         if (dev >= 0 && dev < 32 && !attr_set[which][dev]) {
@@ -842,6 +858,8 @@ hb_status launch(const pencil_args &A, int eb_mode, cudaStream_t s, int64_t *nbl
         if constexpr (EO) {
             if (which == 6) return go(ax_pencil_kernel<N, EO, 1, false, GM_L2G, true>, 1);
             if (which == 5) return go(ax_pencil_kernel<N, EO, EB1, false, GM_L2G, true>, EB1);
+            if (which == 8) return go(ax_pencil_kernel<N, EO, 1, false, GM_L2G, false, true>, 1);
+            if (which == 7) return go(ax_pencil_kernel<N, EO, EB1, false, GM_L2G, false, true>, EB1);
         }
         // the double-float unit keeps the block shapes the FP64 autotuner picks
         // in practice (base, one element, and their CSR-store forms); the

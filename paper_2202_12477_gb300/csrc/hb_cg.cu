@@ -51,6 +51,15 @@ __global__ void __launch_bounds__(HB_RED_THREADS)
                                                n_axp, partials, counter, st);
 }
 
+template <typename T, int SCREEN, int DOT>
+__global__ void __launch_bounds__(HB_RED_THREADS)
+    assemble_grid_kernel(const T *__restrict__ yL, const lattice_t L, const T *__restrict__ x,
+                         const T *__restrict__ mdiag, double lambda, T *__restrict__ y, double *partials,
+                         unsigned *counter, hb_cg_state *st)
+{
+    assemble_grid_body<T, SCREEN, DOT>(yL, L, x, mdiag, lambda, y, partials, counter, st);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(HB_RED_THREADS)
     dot_kernel(const T *__restrict__ a, const T *__restrict__ b, int64_t n, double *out, double *partials,
@@ -161,6 +170,51 @@ hb_status launch_assemble_surf(const hb_mesh *m, const T *ys, const T *x, T *y, 
     return HB_OK;
 }
 
+// The mesh's box as a lattice (DOF numbering of the node map: unmasked
+// lattice points, first coordinate fastest).
+static lattice_t mesh_lattice(const hb_mesh *m)
+{
+    const hb_mesh_desc &d = m->desc;
+    lattice_t L;
+    L.N = m->N;
+    L.Ex = d.ex;
+    L.Ey = d.ey;
+    L.Ez = d.ez;
+    const unsigned f = d.dirichlet_faces;
+    L.x0 = (f & 1u) ? 1 : 0;
+    L.y0 = (f & 4u) ? 1 : 0;
+    L.z0 = (f & 16u) ? 1 : 0;
+    L.NXu = m->N * d.ex + 1 - L.x0 - ((f & 2u) ? 1 : 0);
+    L.NYu = m->N * d.ey + 1 - L.y0 - ((f & 8u) ? 1 : 0);
+    L.NZu = m->N * d.ez + 1 - L.z0 - ((f & 32u) ? 1 : 0);
+    return L;
+}
+
+// Z^T on every DOF by lattice arithmetic from the element-major local values.
+template <typename T>
+hb_status launch_assemble_grid(const hb_mesh *m, const T *yL, const T *x, T *y, const T *mdiag, int screen,
+                               double lambda, hb_cg_state *st, int dot_mode, cudaStream_t s)
+{
+    const lattice_t L = mesh_lattice(m);
+    const int grid = red_grid(m->n_global);
+    unsigned *ctr = m->counters + 0;
+    hb_prof_scope prof("assemble", s);
+#define HB_ASM(SC, DM) \
+    assemble_grid_kernel<T, SC, DM><<<grid, HB_RED_THREADS, 0, s>>>(yL, L, x, mdiag, lambda, y, m->partials, ctr, st)
+    if (screen == 0) {
+        if (dot_mode == HB_DOT_NONE) HB_ASM(0, HB_DOT_NONE);
+        else if (dot_mode == HB_DOT_TO_TMP) HB_ASM(0, HB_DOT_TO_TMP);
+        else HB_ASM(0, HB_DOT_CG_PAP);
+    } else {
+        if (dot_mode == HB_DOT_NONE) HB_ASM(1, HB_DOT_NONE);
+        else if (dot_mode == HB_DOT_TO_TMP) HB_ASM(1, HB_DOT_TO_TMP);
+        else HB_ASM(1, HB_DOT_CG_PAP);
+    }
+#undef HB_ASM
+    HB_CHECK_LAUNCH();
+    return HB_OK;
+}
+
 }  // namespace hb
 
 using namespace hb;
@@ -196,11 +250,15 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
         const int v64 = m->variant[2];
         const int ebm = hb_variant_eb_mode(v64);
         if ((ebm & 8) && !m->spos) { hb_set_error("surface positions missing for variant %d", v64); return HB_ERR_ARG; }
-        double *partials = dot_mode != HB_DOT_NONE ? m->ax_partials : nullptr;
+        const bool grid = (ebm & 16) != 0;
+        double *partials = (dot_mode != HB_DOT_NONE && !grid) ? m->ax_partials : nullptr;
         int64_t nblk = 0;
         hb_status r = hb_launch_ax2_f64x(m, (const double *)x, (double *)m->yL, (double *)y, lambda, screen,
                                          partials, run, ebm, s, &nblk);
         if (r != HB_OK) return r;
+        if (grid)
+            return launch_assemble_grid<double>(m, (const double *)m->yL, (const double *)x, (double *)y, m->mdiag,
+                                                screen, lambda, st, dot_mode, s);
         return launch_assemble_surf<double>(m, (const double *)m->yL, (const double *)x, (double *)y, m->mdiag,
                                             screen, lambda, partials ? nblk : 0, st, dot_mode, s, (ebm & 8) != 0);
     }
@@ -220,12 +278,16 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
         return hb_launch_assemble_f32(m, (const float *)m->yL, (const float *)x, (float *)y, screen, lambda, st,
                                       dot_mode, s);
     }
-    double *partials = dot_mode != HB_DOT_NONE ? m->ax_partials : nullptr;
+    const bool grid = (ebm & 16) != 0;
+    double *partials = (dot_mode != HB_DOT_NONE && !grid) ? m->ax_partials : nullptr;
     int64_t nblk = 0;
     if (prec == HB_F64) {
         r = hb_launch_ax2_f64(m, (const double *)x, (double *)m->yL, (double *)y, lambda, screen, partials, run, eo,
                               ebm, s, &nblk);
         if (r != HB_OK) return r;
+        if (grid)
+            return launch_assemble_grid<double>(m, (const double *)m->yL, (const double *)x, (double *)y, m->mdiag,
+                                                screen, lambda, st, dot_mode, s);
         return launch_assemble_surf<double>(m, (const double *)m->yL, (const double *)x, (double *)y, m->mdiag,
                                             screen, lambda, partials ? nblk : 0, st, dot_mode, s, (ebm & 8) != 0);
     }
@@ -233,6 +295,9 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
     r = hb_launch_ax2_f32(m, (const float *)x, (float *)m->yL, (float *)y, lambda, screen, partials, run, eo, ebm, s,
                           &nblk);
     if (r != HB_OK) return r;
+    if (grid)
+        return launch_assemble_grid<float>(m, (const float *)m->yL, (const float *)x, (float *)y, m->mdiag32, screen,
+                                           lambda, st, dot_mode, s);
     return launch_assemble_surf<float>(m, (const float *)m->yL, (const float *)x, (float *)y, m->mdiag32, screen,
                                        lambda, partials ? nblk : 0, st, dot_mode, s, (ebm & 8) != 0);
 }
@@ -379,7 +444,9 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
                               HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_EB2, HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE,
                               HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_TMA, HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_WS,
                               HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_CSR,
-                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE | HB_VAR_CSR};
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE | HB_VAR_CSR,
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_GRID,
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE | HB_VAR_GRID};
     {
         hb_status sp = hb_mesh_ensure_spos(m, s);
         if (sp != HB_OK) {

@@ -171,35 +171,41 @@ hb_status hb_ax2_upload_f32(const double *D_all);
 // PENCIL | EO only; FP32 and odd N, else the PENCIL | EO kernel runs).
 // HB_VAR_CSR = surface values written straight to their CSR positions, so the
 // surface gather reads contiguous runs (with PENCIL | EO, alone or with ONE).
+// HB_VAR_GRID = every local value stored element-major and Z^T taken by the
+// box's lattice arithmetic, one warp per lattice row (with PENCIL | EO, alone
+// or with ONE).
 enum { HB_VAR_PENCIL = 1, HB_VAR_EO = 2, HB_VAR_EB2 = 4, HB_VAR_ONE = 8, HB_VAR_TMA = 16, HB_VAR_WS = 32,
-       HB_VAR_CSR = 64, HB_VAR_MAX = 127 };
+       HB_VAR_CSR = 64, HB_VAR_GRID = 128, HB_VAR_MAX = 255 };
 static inline bool hb_valid_variant(int v)
 {
     if (v == 0) return true;
     if (v < 0 || v > HB_VAR_MAX || !(v & HB_VAR_PENCIL)) return false;
     const int extra = v & (HB_VAR_ONE | HB_VAR_TMA | HB_VAR_WS | HB_VAR_EB2);
+    if (v & HB_VAR_GRID) return !(v & HB_VAR_CSR) && (v & HB_VAR_EO) && (extra == 0 || extra == HB_VAR_ONE);
     if (v & HB_VAR_CSR) return (v & HB_VAR_EO) && (extra == 0 || extra == HB_VAR_ONE);
     if (extra & (HB_VAR_ONE | HB_VAR_TMA | HB_VAR_WS))
         return (v & HB_VAR_EO) && (extra == HB_VAR_ONE || extra == HB_VAR_TMA || extra == HB_VAR_WS);
     return true;
 }
 // The double-float unit instantiates the even-odd pencil kernel in its base
-// and one-element shapes and their CSR-store forms only.
+// and one-element shapes and their CSR-store and lattice-gather forms only.
 static inline bool hb_valid_variant_f64x(int v)
 {
     const int base = HB_VAR_PENCIL | HB_VAR_EO;
-    return v == base || v == (base | HB_VAR_ONE) || v == (base | HB_VAR_CSR) || v == (base | HB_VAR_ONE | HB_VAR_CSR);
+    return v == base || v == (base | HB_VAR_ONE) || v == (base | HB_VAR_CSR) || v == (base | HB_VAR_ONE | HB_VAR_CSR) ||
+           v == (base | HB_VAR_GRID) || v == (base | HB_VAR_ONE | HB_VAR_GRID);
 }
 // Slot of hb_mesh::variant for a precision (-1: none).
 static inline int hb_variant_slot(int prec)
 {
     return prec == HB_F64 ? 0 : prec == HB_F32 ? 1 : prec == HB_F64X ? 2 : -1;
 }
-// eb_mode of the pencil launchers for a variant (bit 8: CSR-position surface store)
+// eb_mode of the pencil launchers for a variant (bit 8: CSR-position surface
+// store; bit 16: every local value stored element-major)
 static inline int hb_variant_eb_mode(int v)
 {
     const int b = (v & HB_VAR_ONE) ? 0 : (v & HB_VAR_TMA) ? 3 : (v & HB_VAR_WS) ? 4 : (v & HB_VAR_EB2) ? 2 : 1;
-    return b | ((v & HB_VAR_CSR) ? 8 : 0);
+    return b | ((v & HB_VAR_CSR) ? 8 : 0) | ((v & HB_VAR_GRID) ? 16 : 0);
 }
 // Builds mesh->spos if it is missing (synchronises s).
 hb_status hb_mesh_ensure_spos(hb_mesh *m, cudaStream_t s);

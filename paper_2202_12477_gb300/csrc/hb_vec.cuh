@@ -215,6 +215,100 @@ __device__ __forceinline__ void assemble_surf_body(const T *__restrict__ ys, con
     }
 }
 
+// ---------------------------------------------------------------- lattice assembly
+
+// The box's lattice, for Z^T by index arithmetic: lattice point (I, J, K),
+// 0 <= I <= N Ex, is node (I - N ex, ...) of element (ex, ey, ez); DOFs are
+// the unmasked points, numbered (I - x0) + NXu ((J - y0) + NYu (K - z0))
+// with x0 = 1 if the x = 0 face is Dirichlet (and so on).
+struct lattice_t {
+    int N, Ex, Ey, Ez;
+    int x0, y0, z0;
+    int NXu, NYu, NZu;
+};
+
+// The elements along one axis that hold lattice coordinate I (ascending) and
+// I's local index in each: one inside an element, two on a shared face.
+__device__ __forceinline__ int lattice_axis(int I, int N, int Eax, int (&ec)[2], int (&lc)[2])
+{
+    const int q = I / N, r = I - q * N;
+    if (r != 0) { ec[0] = q; lc[0] = r; return 1; }
+    if (q == 0) { ec[0] = 0; lc[0] = 0; return 1; }
+    if (q == Eax) { ec[0] = Eax - 1; lc[0] = N; return 1; }
+    ec[0] = q - 1; lc[0] = N;
+    ec[1] = q; lc[1] = 0;
+    return 2;
+}
+
+// Z^T on every DOF from the element-major local values yL[e][k][j][i]: y_g =
+// the copies of DOF g summed in ascending element order (the association of
+// the CSR gathers: (c0 + c1) + c2 + ..., a lone copy plus zero) + lambda
+// (x_g | M_gg x_g). Lanes along I, so x, y and the runs of each element row
+// of yL are read and written coalesced. With a dot mode, x.y over all DOFs is
+// reduced on the fixed grid.
+template <typename T, int SCREEN, int DOT>
+__device__ __forceinline__ void assemble_grid_body(const T *__restrict__ yL, const lattice_t L, const T *__restrict__ x,
+                                                   const T *__restrict__ mdiag, double lambda, T *__restrict__ y,
+                                                   double *partials, unsigned *counter, hb_cg_state *st)
+{
+    if (DOT == HB_DOT_CG_PAP && st->run == 0) return;
+    const T lam = (T)lambda;
+    dot_acc<T> acc;
+    const int n = L.N + 1;
+    const int64_t n3 = (int64_t)n * n * n;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nrows = (int64_t)L.NYu * L.NZu;
+    // one warp per lattice row (J, K), lanes along I
+    for (int64_t row = warp; row < nrows; row += nwarps) {
+        const int Ju = (int)(row % L.NYu), Ku = (int)(row / L.NYu);
+        int eyc[2], jc[2], ezc[2], kc[2];
+        const int ny = lattice_axis(L.y0 + Ju, L.N, L.Ey, eyc, jc);
+        const int nz = lattice_axis(L.z0 + Ku, L.N, L.Ez, ezc, kc);
+        const T *__restrict__ xr = x + row * L.NXu;
+        T *__restrict__ yr = y + row * L.NXu;
+        for (int Iu = lane; Iu < L.NXu; Iu += 32) {
+            int exc[2], ic[2];
+            const int nx = lattice_axis(L.x0 + Iu, L.N, L.Ex, exc, ic);
+            T t = T(0);
+            int cnt = 0;
+            for (int cz = 0; cz < nz; cz++)
+                for (int cy = 0; cy < ny; cy++) {
+                    const int64_t base = ((int64_t)eyc[cy] + (int64_t)L.Ey * ezc[cz]) * L.Ex;
+                    const int64_t off = ((int64_t)kc[cz] * n + jc[cy]) * n;
+                    for (int cx = 0; cx < nx; cx++) {
+                        const T v = __ldcs(yL + (base + exc[cx]) * n3 + off + ic[cx]);
+                        t = cnt == 0 ? v : t + v;
+                        cnt++;
+                    }
+                }
+            if (cnt == 1) t = t + T(0);
+            const T xv = xr[Iu];
+            t += SCREEN ? lam * (mdiag[row * L.NXu + Iu] * xv) : lam * xv;
+            yr[Iu] = t;
+            if (DOT) acc.add(xv, t);
+        }
+    }
+    if (DOT) {
+        double vv[1] = {acc.value()}, tot[1];
+        if (grid_sum<1>(vv, partials, counter, tot) && threadIdx.x == 0) {
+            if (DOT == HB_DOT_CG_PAP) {
+                const double pAp = tot[0];
+                st->pAp = pAp;
+                if (!(pAp > 0.0) || !isfinite(pAp)) {
+                    st->status = HB_ERR_BREAKDOWN;
+                    st->run = 0;
+                } else {
+                    st->alpha = st->rr / pAp;
+                }
+            } else {
+                st->dot_tmp = tot[0];
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- dot
 
 template <typename T>

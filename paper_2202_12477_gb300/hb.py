@@ -225,8 +225,9 @@ def hb_u01(seed, stream, idx) -> float:
 HB_VARIANT_PENCIL, HB_VARIANT_EVEN_ODD, HB_VARIANT_EB2, HB_VARIANT_ONE, HB_VARIANT_TMA, HB_VARIANT_WS = \
     1, 2, 4, 8, 16, 32
 HB_VARIANT_CSR = 64
-VARIANTS = [0, 1, 3, 5, 7, 11, 19, 35, 67, 75]  # every valid combination
-VARIANTS_F64X = [3, 11, 67, 75]  # the shapes the double-float kernel is built in
+HB_VARIANT_GRID = 128
+VARIANTS = [0, 1, 3, 5, 7, 11, 19, 35, 67, 75, 131, 139]  # every valid combination
+VARIANTS_F64X = [3, 11, 67, 75, 131, 139]  # the shapes the double-float kernel is built in
 
 
 def hb_set_kernel_variant(h, prec, variant) -> None:
@@ -243,7 +244,7 @@ def hb_autotune(h, prec, screen=HB_SCREEN_IDENTITY, lam=0.1, reps=5, stream=None
     """Times every kernel variant on this mesh, keeps the fastest; returns
     (best variant, {variant: ms})."""
     best = C.c_int(-1)
-    ms = (C.c_double * 128)(*([-1.0] * 128))
+    ms = (C.c_double * 256)(*([-1.0] * 256))
     _check(lib().hb_autotune(h, prec, screen, lam, reps, C.byref(best), ms, _stream_ptr(stream)))
     return best.value, {v: ms[v] for v in VARIANTS if ms[v] >= 0}
 

@@ -65,7 +65,7 @@ def test_full_size_apply_sampled_rows(N):
     x32 = x.astype(np.float32)
     ref32 = orc.apply_A_rows(dims, N, 0.1, 0, x32.astype(np.float64), rows, 0.1)
     x32d = torch.from_numpy(x32).cuda()
-    for variant in (3, 35):  # plain and warp-specialised staged kernels
+    for variant in (3, 35, 131):  # plain, warp-specialised staged, lattice gather
         hb.hb_set_kernel_variant(m.handle, hb.HB_F32, variant)
         y32 = m.apply_A(x32d, lam=0.1).cpu().numpy().astype(np.float64)
         assert np.linalg.norm(y32[rows] - ref32) <= 2e-5 * np.linalg.norm(ref32), variant

@@ -143,6 +143,53 @@ def test_apply_A_double_float(dims, N, variant):
         assert np.abs(y - y_or).max() <= 1e-12 * np.abs(y_or).max()
 
 
+@pytest.mark.parametrize("dims,N,faces", [((3, 2, 2), 3, 0x3F), ((2, 3, 2), 7, 0x15), ((2, 2, 1), 12, 0x2A),
+                                           ((4, 3, 3), 5, 0x00), ((1, 2, 2), 15, 0x3F), ((3, 3, 3), 1, 0x07)])
+def test_lattice_gather_equals_csr_gather(dims, N, faces):
+    """Variant GRID (every local value stored element-major, Z^T by the box's
+    lattice arithmetic) sums each DOF's copies in the CSR gather's order and
+    association, so y is the same as with the surface-CSR variants, value for
+    value, in FP64, FP32 and double-float and both screenings, with partial
+    Dirichlet faces; and it meets the oracle's bar."""
+    m, o = _pair(dims, N, rho=0.15, seed=N + 40, faces=faces)
+    x = inputs.random_vector(m.n_global, seed=700 + N)
+    x32 = x.astype(np.float32)
+    for screen, lam in [(0, 0.1), (1, 0.6)]:
+        for prec, xin in [(hb.HB_F64, _to_dev(x)), (hb.HB_F32, _to_dev(x32, torch.float32)),
+                          (hb.HB_F64X, _to_dev(x))]:
+            ys = {}
+            for v in (3, 67, 131, 139):
+                hb.hb_set_kernel_variant(m.handle, prec, v)
+                ys[v] = m.apply_A(xin, lam=lam, screen=screen, prec=prec).cpu().numpy()
+            for v in (67, 131, 139):
+                assert np.array_equal(ys[v], ys[3]), (prec, screen, v, np.abs(ys[v] - ys[3]).max())
+        y_or = o.apply_A(x, lam, screen)
+        hb.hb_set_kernel_variant(m.handle, hb.HB_F64, 131)
+        y = m.apply_A(_to_dev(x), lam=lam, screen=screen).cpu().numpy()
+        assert _rel(y, y_or) <= 1e-12
+        assert np.abs(y - y_or).max() <= 1e-12 * np.abs(y_or).max()
+
+
+@pytest.mark.parametrize("variant", [131, 139])
+def test_cg_with_lattice_gather(variant):
+    """CG (Algorithm 1) with p.Ap reduced in the lattice gather: 100 fixed
+    iterations follow the oracle's iterates; the mixed solver reaches the FP64
+    residual bar."""
+    m, o = _pair((4, 4, 4), 7, rho=0.1, seed=0)
+    hb.lib().hb_set_cg_fused(m.handle, 1)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, variant)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F32, variant)
+    b = m.rhs(kind=0, seed=0)
+    x_or, *_ = o.cg(b.cpu().numpy(), 0.1, rtol=0.0, max_it=100)
+    x, res = m.cg(b, lam=0.1, rtol=0.0, max_it=100)
+    assert res.status == hb.HB_OK and res.iters == 100
+    assert _rel(x.cpu().numpy(), x_or) <= 1e-12
+    xm, rm = m.cg(b, lam=0.1, rtol=1e-10, max_it=20000, prec=hb.HB_MIXED)
+    assert rm.status == hb.HB_OK
+    bn = b.cpu().numpy()
+    assert np.linalg.norm(bn - o.apply_A(xm.cpu().numpy(), 0.1)) <= 1.05e-10 * np.linalg.norm(bn)
+
+
 def test_double_float_variant_slot():
     """HB_F64X keeps its own variant: it takes only the shapes its kernel is
     built in, and autotuning it leaves the FP64 choice alone."""
