@@ -459,15 +459,18 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
     int best = saved;
     float best_ms = 1e30f;
     hb_status st = HB_OK;
+    // each application also reduces x.y, as every CG iteration does (p.Ap):
+    // variants differ in where that work runs (element kernel or gather)
+    hb_cg_state *tmp = m->state + 1;
     for (int c : candidates) {
         if (prec == HB_F64X && !hb_valid_variant_f64x(c)) continue;
         m->variant[pi] = c;
         // one untimed application (first launch, attribute setup), then `reps` timed ones
-        st = hb_apply_A_impl(m, prec, screen, lambda, x, y, nullptr, HB_DOT_NONE, s);
+        st = hb_apply_A_impl(m, prec, screen, lambda, x, y, tmp, HB_DOT_TO_TMP, s);
         if (st != HB_OK) break;
         if ((e = cudaEventRecord(m->ev0, s)) != cudaSuccess) break;
         for (int r = 0; r < reps && st == HB_OK; r++)
-            st = hb_apply_A_impl(m, prec, screen, lambda, x, y, nullptr, HB_DOT_NONE, s);
+            st = hb_apply_A_impl(m, prec, screen, lambda, x, y, tmp, HB_DOT_TO_TMP, s);
         if (st != HB_OK) break;
         if ((e = cudaEventRecord(m->ev1, s)) != cudaSuccess) break;
         if ((e = cudaEventSynchronize(m->ev1)) != cudaSuccess) break;
