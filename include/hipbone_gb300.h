@@ -440,7 +440,8 @@ hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *var
 
 /* Autotuner (the paper makes its 3-D / 2-D kernel switch a configurable choice
  * made from measurements, Sec. 3.2; here every variant is timed on the mesh
- * itself). Runs one untimed and `reps` timed applications of A for each
+ * itself). Runs one untimed and `reps` timed applications of A, each with the
+ * x.y reduction a CG iteration fuses into it (p.Ap), for each
  * variant (0, PENCIL, PENCIL|EVEN_ODD, PENCIL|EB2, PENCIL|EVEN_ODD|EB2,
  * PENCIL|EVEN_ODD|ONE, PENCIL|EVEN_ODD|TMA, PENCIL|EVEN_ODD|WS, PENCIL|EVEN_ODD|CSR,
  * PENCIL|EVEN_ODD|ONE|CSR, PENCIL|EVEN_ODD|GRID, PENCIL|EVEN_ODD|ONE|GRID; for
