@@ -188,6 +188,11 @@ def test_cg_with_lattice_gather(variant):
     assert rm.status == hb.HB_OK
     bn = b.cpu().numpy()
     assert np.linalg.norm(bn - o.apply_A(xm.cpu().numpy(), 0.1)) <= 1.05e-10 * np.linalg.norm(bn)
+    # the double-float operator in the same variant (what its CG uses at N=7)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F64X, variant)
+    xd, rd = m.cg(b, lam=0.1, rtol=0.0, max_it=100, prec=hb.HB_F64X)
+    assert rd.status == hb.HB_OK and rd.iters == 100
+    assert _rel(xd.cpu().numpy(), x_or) <= 1e-9
 
 
 def test_double_float_variant_slot():
