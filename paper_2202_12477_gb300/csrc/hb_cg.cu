@@ -714,6 +714,8 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
             HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
             HB_TRY_CUDA(cudaStreamSynchronize(s));
             const double rr = m->state_host->rr, bb = m->state_host->bb;
+            // a non-finite b or residual (bb NaN would make rel 0 below) is a breakdown
+            if (!std::isfinite(rr) || !std::isfinite(bb)) { R.status = HB_ERR_BREAKDOWN; rel = rr; break; }
             rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
             if (!std::isfinite(rel)) { R.status = HB_ERR_BREAKDOWN; break; }
             if (bb == 0.0 || rr <= o->rtol * o->rtol * bb) break;

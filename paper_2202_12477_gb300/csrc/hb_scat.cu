@@ -144,9 +144,11 @@ __global__ void __launch_bounds__(HB_RED_THREADS) k_w_init(const double *__restr
         st->tol2 = rtol * rtol * tot[1];
         st->it = 0;
         st->max_it = max_it;
-        st->status = HB_OK;
         st->alpha = st->beta = st->pAp = 0.0;
-        st->run = (max_it > 0 && tot[0] > st->tol2) ? 1 : 0;
+        // a non-finite b (or A x0) is reported as a breakdown, not a NaN residual
+        const bool finite = isfinite(tot[0]) && isfinite(tot[1]);
+        st->status = finite ? HB_OK : HB_ERR_BREAKDOWN;
+        st->run = (finite && max_it > 0 && tot[0] > st->tol2) ? 1 : 0;
         st->next_run = st->run;
     }
 }

@@ -361,9 +361,12 @@ __device__ __forceinline__ void cg_init_body(const double *__restrict__ b, const
         st->tol2 = rtol * rtol * tot[2];
         st->it = 0;
         st->max_it = max_it;
-        st->status = HB_OK;
         st->alpha = st->beta = st->pAp = 0.0;
-        st->run = (max_it > 0 && tot[1] > st->tol2) ? 1 : 0;
+        // a non-finite b (or A x0) would stop the loop at once with a NaN
+        // residual: report it as a breakdown instead
+        const bool finite = isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2]);
+        st->status = finite ? HB_OK : HB_ERR_BREAKDOWN;
+        st->run = (finite && max_it > 0 && tot[1] > st->tol2) ? 1 : 0;
         st->next_run = st->run;
     }
 }

@@ -443,6 +443,28 @@ def test_cg_zero_rhs_and_breakdown():
     assert res.status == hb.HB_ERR_BREAKDOWN
 
 
+def test_cg_non_finite_rhs_is_a_breakdown():
+    """A NaN or infinity in b stops every CG form at once with
+    HB_ERR_BREAKDOWN instead of returning HB_OK with a NaN residual (a fault
+    made on the host: the input)."""
+    m = hb.Mesh(3, 3, 2, 5, perturb=0.1, seed=3)
+    for bad in (float("nan"), float("inf")):
+        b = m.rhs(kind=0, seed=2)
+        b[7] = bad
+        for fused in (1, 2):
+            hb.lib().hb_set_cg_fused(m.handle, fused)
+            x, res = m.cg(b, lam=0.1, rtol=1e-10, max_it=50)
+            assert res.status == hb.HB_ERR_BREAKDOWN and res.iters == 0, (bad, fused, res.status)
+        hb.lib().hb_set_cg_fused(m.handle, 0)
+        for kw in ({"precond": 1}, {"prec": hb.HB_MIXED}, {"prec": hb.HB_F64X}):
+            x, res = m.cg(b, lam=0.1, rtol=1e-10, max_it=50, **kw)
+            assert res.status == hb.HB_ERR_BREAKDOWN, (bad, kw, res.status)
+    # the mesh is still usable afterwards
+    b = m.rhs(kind=0, seed=2)
+    x, res = m.cg(b, lam=0.1, rtol=1e-10, max_it=2000)
+    assert res.status == hb.HB_OK and res.rel_res <= 1e-10
+
+
 def test_autotune_keeps_parity(tmp_path):
     from paper_2202_12477_gb300 import autotune
     m, o = _pair((3, 3, 2), 6, rho=0.2, seed=8)
