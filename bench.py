@@ -7,8 +7,15 @@ seeded uniform right-hand side. One step is one conjugate-gradient iteration
 (one application of A plus the fused vector stage of Algorithm 1); the value is
 the paper's throughput, global DOFs x iterations / s, in GDOF/s.
 
-Prints one JSON line. Other workloads (--workload sweep | c1 | c3 | c4) print
-their own lines; only the default is the headline.
+Prints one JSON line. Other workloads print their own lines; only the
+default is the headline:
+  sweep   operator-only degree sweep N=1..15 on boxes of about 128M local nodes
+  c1      100 FP64 CG iterations on a 4x4x4 box at N=7 (latency-bound)
+  c3      one solve to 1e-10 on an 80x80x80 box at N=7 with a manufactured
+          right-hand side: FP64, mixed precision, Jacobi, double-float
+  c4      mixed-precision stress: N=15, 24x24x24, strong perturbation, three lambdas
+  c5      serving stream of CG requests (sizes 2..32 elements per axis, N in 3..11)
+  split   split operator over virtual ranks; scat: scattered storage; probe: hardware probes
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 """
@@ -357,11 +364,11 @@ def run_gb300(args, rank, world, local):
 
 def run_reference_workloads(args):
     """The reference arm (the oracle, as it stands, on the host cores) on the
-    other configurations: config 1 (A x median of 5, 100 CG iterations), the
-    degree-sweep meshes for N in 3, 7, 11, 15 (A x once, 3 CG iterations, per
-    iteration), and config 3 (per-iteration time, with the time to 1e-10
-    extrapolated from the iteration count the GPU solvers needed, labelled
-    as such)."""
+    other workloads: the 4x4x4 box at N=7 (A x median of 5, 100 CG
+    iterations), the degree-sweep meshes for N in 3, 7, 11, 15 (A x once, 3 CG
+    iterations, per iteration), and the 80x80x80 box at N=7 (per-iteration
+    time, with the time to 1e-10 extrapolated from the iteration count the GPU
+    solvers needed, labelled as such)."""
     from oracle import oracle as orc
     out = {"impl": "reference", "workload": "oracle timings on the host cores", "cores": orc.num_threads(),
            "results": []}
@@ -389,10 +396,10 @@ def run_reference_workloads(args):
         print(json.dumps(rec), flush=True)
         return rec
 
-    one("config 1", (4, 4, 4), 7, 5, 100)
+    one("4x4x4 box, N=7", (4, 4, 4), 7, 5, 100)
     for N in (3, 7, 11, 15):
         one("degree sweep", c2_dims(N), N, 1, 3)
-    r3 = one("config 3 (per iteration)", (80, 80, 80), 7, 1, 1, lam=0.0, kind=1)
+    r3 = one("80x80x80 box, N=7, manufactured rhs (per iteration)", (80, 80, 80), 7, 1, 1, lam=0.0, kind=1)
     # iteration counts of the GPU solvers to 1e-10 on this mesh (FP64 CG 3710)
     r3["time_to_1e-10_s_extrapolated"] = r3["cg_ms_per_iteration"] * 3710 / 1e3
     r3["extrapolation"] = "per-iteration time x 3710 FP64 CG iterations (the GPU FP64 solver's count)"
