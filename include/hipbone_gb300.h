@@ -136,8 +136,12 @@ hb_status hb_mesh_copy_geo(const hb_mesh *mesh, double *host_geo);
 hb_status hb_apply_A(const hb_mesh *mesh, hb_precision prec, hb_screen screen,
                      double lambda, const void *x, void *y, void *stream);
 
-/* a.b over n_global entries, accumulated in FP64 (warp shuffles, then a fixed
- * block order: bitwise reproducible). prec names the element type of a and b.
+/* a.b over n_global entries: the inner products of Algorithm 1 (r.r, p.Ap,
+ * the stopping test's norm), which Sec. 3.5 fuses into the vector kernels of
+ * a CG iteration; this call is the same reduction standing alone. Accumulated
+ * in FP64 (warp shuffles, then a fixed block order: bitwise reproducible).
+ * prec names the element type of a and b (HB_F64: double, HB_F32: float; other
+ * precisions return HB_ERR_ARG).
  * Writes the result to *out_dev (device double, may be NULL) and, if out_host
  * is not NULL, also to *out_host -- which synchronises `stream`. */
 hb_status hb_dot(const hb_mesh *mesh, hb_precision prec, const void *a, const void *b,
@@ -160,8 +164,11 @@ hb_status hb_dot(const hb_mesh *mesh, hb_precision prec, const void *a, const vo
  * the static array; if out_host is not NULL it is also copied there, which
  * synchronises `stream`.
  * The first call on a device takes the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. Every call shares the one array: calls that overlap in time on the
+ * device, with that device current) and keeps it for the life of the process;
+ * make that first call before any stream capture, and do not use the entry
+ * point after a cudaDeviceReset (or any teardown of the device's primary
+ * context) in the same process: the kept address belongs to the old context.
+ * Every call shares the one array: calls that overlap in time on the
  * GPU (different streams, or different host threads) race and give wrong
  * results; serialise them. */
 hb_status hb_dot_noalloc(hb_precision prec, const void *a, const void *b, int64_t n,
@@ -193,7 +200,10 @@ typedef struct {
 typedef struct {
     int iters;             /* CG iterations (all inner iterations in HB_MIXED) */
     int outer_iters;       /* HB_MIXED: defect-correction steps; else 0 */
-    double rel_res;        /* ||r||_2 / ||b||_2 at exit (FP64 residual in HB_MIXED) */
+    double rel_res;        /* ||b - A x||_2 / ||b||_2 at exit, recomputed in FP64 with the
+                              FP64 operator when rtol > 0 (every solver form); with
+                              rtol = 0 (a fixed iteration count, no stopping test)
+                              the recursive residual of Algorithm 1 */
     double time_ms;        /* device time of the solve (CUDA events) */
     hb_status status;
 } hb_cg_result;
@@ -214,7 +224,15 @@ hb_status hb_diag_A(hb_mesh *mesh, hb_screen screen, double lambda, double *host
  * in HB_MIXED to the inner FP32 CG); the stopping test stays on ||r||. The p.Ap
  * and r.r reductions are fused into the kernels that produce their operands
  * (Sec. 3.5). Synchronises `stream`.
- * Returns HB_ERR_BREAKDOWN, HB_ERR_NOT_CONVERGED (rtol > 0 only) or HB_OK;
+ * Stopping test (Algorithm 1's test on the residual, taken relative: ||r|| <=
+ * rtol ||b||): the recursive residual r_{j+1} = r_j - alpha A p_j drifts from
+ * b - A x_{j+1} by rounding, so when it meets the tolerance the solver
+ * recomputes the true residual b - A x in FP64 (FP64 operator); if that one is
+ * still above rtol ||b||, r is replaced by it (p is kept) and the iterations
+ * go on. HB_OK therefore means the true FP64 residual meets rtol; HB_MIXED
+ * tests the true residual at every outer step.
+ * Returns HB_ERR_BREAKDOWN, HB_ERR_NOT_CONVERGED (rtol > 0 only: max_it
+ * iterations ran and the true residual is above rtol) or HB_OK;
  * res (may be NULL) receives the counts, residual and device time. */
 hb_status hb_cg_solve(const hb_mesh *mesh, const hb_cg_opts *opts, const double *b,
                       double *x, hb_cg_result *res, void *stream);
@@ -235,7 +253,10 @@ hb_status hb_set_cg_fused(hb_mesh *mesh, int mode);
  * `stream`, no host wait); hb_cg_iterate enqueues up to `count` more
  * iterations (never past opts->max_it; kernels of a solve that has met rtol
  * return at once) without waiting for the host; hb_cg_finish waits and fills
- * res (time_ms = 0) with the status rules of hb_cg_solve. One stepwise solve
+ * res (time_ms = 0): with rtol > 0 it recomputes the true residual b - A x in
+ * FP64 (one more operator application) and returns HB_ERR_NOT_CONVERGED if it
+ * is above rtol (the stepwise form replaces no residual: its iterations are
+ * over by then). One stepwise solve
  * per mesh at a time; b and x must stay valid until hb_cg_finish, and the
  * mesh's other solver calls must not run in between. */
 hb_status hb_cg_begin(hb_mesh *mesh, const hb_cg_opts *opts, const double *b, double *x, void *stream);
@@ -387,6 +408,14 @@ hb_status hb_server_poll(hb_server *srv, int64_t ticket, hb_cg_result *res, int6
 hb_status hb_server_stats(hb_server *srv, hb_server_stats_t *out);
 /* Stops the worker after its current round and frees every resident solve. */
 hb_status hb_server_destroy(hb_server *srv);
+/* Test hook for the failure path (no device work is faulted): the worker's
+ * next round behaves as if launching it had failed. The server then stops;
+ * every resident solve releases its device memory and every resident or
+ * queued request finishes with HB_ERR_CUDA; polls of any other ticket the
+ * server issued return HB_ERR_CUDA instead of HB_ERR_BUSY, and submits are
+ * refused. The failure happens at the next round, i.e. once a request is
+ * resident. */
+hb_status hb_server_inject_round_error(hb_server *srv);
 
 /* The library's uniform random number, u01(seed, stream, idx) =
  * (splitmix64(seed ^ (stream * 0x9E3779B97F4A7C15) + idx) >> 11) * 2^-53, with

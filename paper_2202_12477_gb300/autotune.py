@@ -31,8 +31,8 @@ def device_key(name: str, sms: int) -> str:
 _PREC_NAME = {hb.HB_F64: "f64", hb.HB_F32: "f32", hb.HB_F64X: "f64x"}
 
 
-def entry_key(N: int, prec: int) -> str:
-    return f"N{N}|{_PREC_NAME[prec]}"
+def entry_key(N: int, prec: int, exclude: int = 0) -> str:
+    return f"N{N}|{_PREC_NAME[prec]}" + (f"|x{exclude}" if exclude else "")
 
 
 def load(path: str | None = None) -> dict:
@@ -54,18 +54,24 @@ def store(cache: dict, path: str | None = None) -> None:
     os.replace(tmp, path)
 
 
-def lookup(cache: dict, dev: str, N: int, prec: int):
-    e = cache.get(dev, {}).get(entry_key(N, prec))
+def lookup(cache: dict, dev: str, N: int, prec: int, exclude: int = 0):
+    e = cache.get(dev, {}).get(entry_key(N, prec, exclude))
     valid = hb.VARIANTS_F64X if prec == hb.HB_F64X else hb.VARIANTS
-    if isinstance(e, dict) and e.get("variant") in valid:
+    if isinstance(e, dict) and e.get("variant") in valid and not (e["variant"] & exclude):
         return e["variant"]
     return None
 
 
-def record(cache: dict, dev: str, N: int, prec: int, variant: int, timings: dict) -> dict:
-    cache.setdefault(dev, {})[entry_key(N, prec)] = {
+def record(cache: dict, dev: str, N: int, prec: int, variant: int, timings: dict, exclude: int = 0) -> dict:
+    cache.setdefault(dev, {})[entry_key(N, prec, exclude)] = {
         "variant": int(variant), "ms": {str(k): float(v) for k, v in timings.items()}}
     return cache
+
+
+def best_allowed(timings: dict, exclude: int) -> int | None:
+    """Fastest timed variant with none of the `exclude` flag bits."""
+    allowed = {v: ms for v, ms in timings.items() if not (int(v) & exclude)}
+    return min(allowed, key=allowed.get) if allowed else None
 
 
 def current_device_key() -> str:
@@ -75,9 +81,12 @@ def current_device_key() -> str:
 
 
 def tune_mesh(mesh, precs=(hb.HB_F64, hb.HB_F32), screen=hb.HB_SCREEN_IDENTITY, lam=0.1, reps=5,
-              path: str | None = None, force: bool = False) -> dict:
+              path: str | None = None, force: bool = False, exclude: int = 0) -> dict:
     """Sets the best variant on `mesh` for each precision, from the cache when
-    present (unless force), else by timing and then recording it."""
+    present (unless force), else by timing and then recording it. `exclude`
+    leaves out every variant with one of those flag bits, e.g.
+    hb.HB_VARIANT_GRID for a choice that holds on any mesh (the lattice
+    gather relies on the box's structure)."""
     dev = current_device_key()
     chosen = {}
     with _lock:
@@ -86,10 +95,13 @@ def tune_mesh(mesh, precs=(hb.HB_F64, hb.HB_F32), screen=hb.HB_SCREEN_IDENTITY, 
         for prec in precs:
             if prec == hb.HB_F32 and not mesh.info.geo32:
                 continue
-            v = None if force else lookup(cache, dev, mesh.N, prec)
+            v = None if force else lookup(cache, dev, mesh.N, prec, exclude)
             if v is None:
                 v, timings = hb.hb_autotune(mesh.handle, prec, screen, lam, reps)
-                record(cache, dev, mesh.N, prec, v, timings)
+                if exclude and v & exclude:
+                    v = best_allowed(timings, exclude)
+                    hb.hb_set_kernel_variant(mesh.handle, prec, v)
+                record(cache, dev, mesh.N, prec, v, timings, exclude)
                 changed = True
             else:
                 hb.hb_set_kernel_variant(mesh.handle, prec, v)

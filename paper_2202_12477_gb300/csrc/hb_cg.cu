@@ -93,6 +93,14 @@ __global__ void __launch_bounds__(HB_RED_THREADS)
 }
 
 __global__ void __launch_bounds__(HB_RED_THREADS)
+    cg_replace_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
+                      double *__restrict__ z, const double *__restrict__ inv_d, int64_t n, double *partials,
+                      unsigned *counter, hb_cg_state *st)
+{
+    cg_replace_body(b, Ax, r, z, inv_d, n, partials, counter, st);
+}
+
+__global__ void __launch_bounds__(HB_RED_THREADS)
     residual_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r, int64_t n,
                     double *partials, unsigned *counter, hb_cg_state *st)
 {
@@ -627,6 +635,28 @@ static hb_status cg_drive(const hb_mesh *m, hb_precision prec, int screen, doubl
     return HB_OK;
 }
 
+// The true residual of the iterate x: r = b - A x with the FP64 operator
+// (whatever precision the iterations ran in), z = M^-1 r, r.z and r.r into
+// the state, which keeps p, alpha and the iteration count; run is set again
+// while the true residual is above the tolerance and iterations remain
+// (residual replacement). Synchronises s; returns the state in *out.
+static hb_status cg_true_residual(const hb_mesh *m, const hb_cg_opts *o, const double *b, const double *x, double *r,
+                                  double *Ap, double *z, const double *inv_d, hb_cg_state *st, cudaStream_t s,
+                                  hb_cg_state *out)
+{
+    const int64_t n = m->n_global;
+    hb_status rs = hb_apply_A_impl(m, HB_F64, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
+    if (rs != HB_OK) return rs;
+    hb_count_launch();
+    cg_replace_kernel<<<red_grid(n), HB_RED_THREADS, 0, s>>>(b, Ap, r, z, inv_d, n, m->partials, m->counters + 2,
+                                                              st);
+    HB_CHECK_LAUNCH();
+    HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
+    HB_TRY_CUDA(cudaStreamSynchronize(s));
+    *out = *m->state_host;
+    return HB_OK;
+}
+
 // Fused CG: FP64 without a preconditioner, when every element of the mesh
 // fits in one cooperative launch (one per block; mode 0: and the mesh is
 // small enough that latency sets the time, at most 300 elements, where it
@@ -695,6 +725,20 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
         } else {
             rs = cg_drive<double>(m, o->prec, o->screen, o->lambda, x, r, p, Ap, z, inv_d, st, o->max_it, s, &fin);
             if (rs != HB_OK) return rs;
+        }
+        // With a tolerance, the stop is decided on the true residual b - A x
+        // (FP64 operator): where the recursive residual met it and the true
+        // one does not, r is replaced by the true residual and the iterations
+        // go on (each pass adds at least one iteration, up to max_it).
+        if (o->rtol > 0.0) {
+            while (fin.status == HB_OK) {
+                rs = cg_true_residual(m, o, b, x, r, Ap, z, inv_d, st, s, &fin);
+                if (rs != HB_OK) return rs;
+                if (!fin.run) break;
+                rs = cg_drive<double>(m, o->prec, o->screen, o->lambda, x, r, p, Ap, z, inv_d, st,
+                                      o->max_it - fin.it, s, &fin);
+                if (rs != HB_OK) return rs;
+            }
         }
         R.iters = fin.it;
         R.rel_res = fin.bb > 0.0 ? sqrt(fin.res2 / fin.bb) : 0.0;
@@ -838,11 +882,20 @@ extern "C" hb_status hb_cg_finish(hb_mesh *m, hb_cg_result *res, void *stream)
     if (m->n_global > 0) {
         HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, m->state, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
         HB_TRY_CUDA(cudaStreamSynchronize(s));
-        const hb_cg_state fin = *m->state_host;
+        hb_cg_state fin = *m->state_host;
+        const hb_cg_opts &o = m->step.o;
+        if (o.rtol > 0.0 && fin.status == HB_OK) {
+            // report the true residual b - A x (no replacement: the iterations are over)
+            const int64_t ns = cg_stride(m->n_global);
+            double *r = (double *)m->cg_vec, *p = r + ns, *Ap = p + ns, *z = Ap + ns;
+            hb_status rs = cg_true_residual(m, &o, m->step.b, m->step.x, r, Ap, z, o.precond ? m->inv_diag : nullptr,
+                                            m->state, s, &fin);
+            if (rs != HB_OK) return rs;
+        }
         R.iters = fin.it;
         R.rel_res = fin.bb > 0.0 ? sqrt(fin.res2 / fin.bb) : 0.0;
         if (fin.status == HB_ERR_BREAKDOWN) R.status = HB_ERR_BREAKDOWN;
-        else if (m->step.o.rtol > 0.0 && fin.res2 > fin.tol2) R.status = HB_ERR_NOT_CONVERGED;
+        else if (o.rtol > 0.0 && fin.res2 > fin.tol2) R.status = HB_ERR_NOT_CONVERGED;
         const hb_status de = check_dev_err(m, s);
         if (de != HB_OK) R.status = de;
     }

@@ -183,6 +183,13 @@ __global__ void __launch_bounds__(HB_RED_THREADS) k_cg_init(const double *b, con
     hb::cg_init_body(b, Ax, r, p, nullptr, n, rtol, max_it, partials, counter, st);
 }
 
+__global__ void __launch_bounds__(HB_RED_THREADS) k_cg_replace(const double *b, const double *Ax, double *r,
+                                                                int64_t n, double *partials, unsigned *counter,
+                                                                hb_cg_state *st)
+{
+    hb::cg_replace_body(b, Ax, r, nullptr, nullptr, n, partials, counter, st);
+}
+
 __global__ void __launch_bounds__(HB_RED_THREADS) k_cg_update_r(double *r, const double *Ap, int64_t n,
                                                                  double *partials, unsigned *counter,
                                                                  hb_cg_state *st)
@@ -906,15 +913,29 @@ extern "C" hb_status hb_part_cg_solve(const hb_part *part, const hb_cg_opts *o, 
     hb_count_launch();
     k_cg_init<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, p, n, o->rtol, o->max_it, P->partials, P->counters + 2, st);
     HB_CHECK_LAUNCH();
-    // iterations in chunks; kernels of a finished solve return at once
-    int done = 0, chunk = 16;
+    // iterations in chunks; kernels of a finished solve return at once. With a
+    // tolerance, a stop of the recursive residual is checked on the true one
+    // (b - A x, replacing r; the iterations go on while it is above rtol).
+    int chunk = 16;
+    bool checked = false;
     hb_cg_state fin{};
     for (;;) {
         HB_TRY_CUDA(cudaMemcpyAsync(P->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
         HB_TRY_CUDA(cudaStreamSynchronize(s));
         fin = *P->state_host;
-        if (!fin.run || done >= o->max_it) break;
-        const int cnt = std::min(chunk, o->max_it - done);
+        if (!fin.run || fin.it >= o->max_it) {
+            if (o->rtol > 0.0 && fin.status == HB_OK && !checked) {
+                if ((rs = part_apply(P, o->screen, o->lambda, x, Ap, nullptr, s)) != HB_OK) return rs;
+                hb_count_launch();
+                k_cg_replace<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, n, P->partials, P->counters + 2, st);
+                HB_CHECK_LAUNCH();
+                checked = true;
+                continue;
+            }
+            break;
+        }
+        checked = false;
+        const int cnt = std::min(chunk, o->max_it - fin.it);
         for (int it = 0; it < cnt; it++) {
             if ((rs = part_apply(P, o->screen, o->lambda, p, Ap, &st->run, s)) != HB_OK) return rs;
             {
@@ -933,7 +954,6 @@ extern "C" hb_status hb_part_cg_solve(const hb_part *part, const hb_cg_opts *o, 
                 HB_CHECK_LAUNCH();
             }
         }
-        done += cnt;
         chunk = std::min(chunk * 2, 256);
     }
     HB_TRY_CUDA(cudaEventRecord(P->ev1, s));

@@ -203,6 +203,7 @@ struct hb_server {
     std::mutex mu;
     std::condition_variable cv;
     bool stop = false;
+    bool inject_round_error = false;  // test hook: the next round reports a failed CUDA call
     int64_t next_ticket = 1;
     hb_server_stats_t stats{};
     char err[256] = {0};
@@ -384,6 +385,18 @@ static void retire(hb_server *S, int si, finished &f)
     sl = slot{};
 }
 
+// Frees a resident slot's vectors and mesh without reading its results (the
+// failure path: the round that should have advanced it did not complete).
+static void release_slot(hb_server *S, int si)
+{
+    slot &sl = S->slots[si];
+    cudaFree(sl.mem);
+    hb_mesh_destroy(sl.mesh);
+    S->used -= std::min(S->used, sl.bytes);
+    S->h_desc[si].active = 0;
+    sl = slot{};
+}
+
 static void worker_loop(hb_server *S)
 {
     cudaSetDevice(S->device);
@@ -435,9 +448,11 @@ static void worker_loop(hb_server *S)
             S->cv.wait_for(lk, std::chrono::milliseconds(2));
             continue;
         }
+        const bool fail_round = S->inject_round_error;
+        S->inject_round_error = false;
         lk.unlock();
         // one round for every resident solve
-        cudaError_t e = cudaGraphLaunch(S->exec, S->s_main);
+        cudaError_t e = fail_round ? cudaErrorLaunchFailure : cudaGraphLaunch(S->exec, S->s_main);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(S->h_state, S->d_state, sizeof(hb_slot_state) * S->cap, cudaMemcpyDeviceToHost,
                                 S->s_main);
@@ -445,15 +460,27 @@ static void worker_loop(hb_server *S)
         lk.lock();
         S->stats.rounds++;
         if (e != cudaSuccess) {
-            snprintf(S->err, sizeof S->err, "round: %s", cudaGetErrorString(e));
-            // fail every resident request; the server stops
+            snprintf(S->err, sizeof S->err, "round%s: %s", fail_round ? " (injected)" : "", cudaGetErrorString(e));
+            // the server stops: every resident request fails and releases its
+            // memory, every queued one fails too, so each ticket resolves
             for (int i = 0; i < S->cap; i++)
                 if (S->slots[i].busy) {
                     finished f{};
                     f.res.status = HB_ERR_CUDA;
+                    f.latency_ms = f.res.time_ms = (now_s() - S->slots[i].req.t_submit) * 1e3;
                     S->done[S->slots[i].req.ticket] = std::move(f);
-                    S->slots[i].busy = false;
+                    release_slot(S, i);
                 }
+            for (const request &rq : S->pending) {
+                finished f{};
+                f.res.status = HB_ERR_CUDA;
+                f.latency_ms = f.res.time_ms = (now_s() - rq.t_submit) * 1e3;
+                S->done[rq.ticket] = std::move(f);
+            }
+            S->pending.clear();
+            S->stats.active = 0;
+            S->stats.pending = 0;
+            S->stats.mem_used = S->used;
             S->stop = true;
             S->cv.notify_all();
             break;
@@ -556,7 +583,11 @@ extern "C" hb_status hb_server_poll(hb_server *S, int64_t ticket, hb_cg_result *
     std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->done.find(ticket);
     if (it == S->done.end()) {
-        if (ticket >= 1 && ticket < S->next_ticket) return HB_ERR_BUSY;  // queued or running
+        if (ticket >= 1 && ticket < S->next_ticket) {
+            // a stopped server runs nothing more: report its error, not "busy"
+            if (S->stop) { hb_set_error("server stopped: %s", S->err); return HB_ERR_CUDA; }
+            return HB_ERR_BUSY;  // queued or running
+        }
         hb_set_error("unknown ticket %lld", (long long)ticket);
         return HB_ERR_NOT_FOUND;
     }
@@ -565,6 +596,16 @@ extern "C" hb_status hb_server_poll(hb_server *S, int64_t ticket, hb_cg_result *
     if (x_host && !it->second.x.empty())
         memcpy(x_host, it->second.x.data(), sizeof(double) * it->second.x.size());
     S->done.erase(it);
+    return HB_OK;
+}
+
+extern "C" hb_status hb_server_inject_round_error(hb_server *S)
+{
+    hb_clear_error();
+    if (!S) { hb_set_error("null server"); return HB_ERR_ARG; }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->inject_round_error = true;
+    S->cv.notify_all();
     return HB_OK;
 }
 

@@ -371,6 +371,42 @@ __device__ __forceinline__ void cg_init_body(const double *__restrict__ b, const
     }
 }
 
+// Residual replacement for the stopping test of Algorithm 1. The recursive
+// residual r_{j+1} = r_j - alpha A p drifts from b - A x_j by rounding; a
+// solve whose recursive residual meets the tolerance therefore checks the true
+// one: r = b - Ax recomputed in FP64 (Ax from the caller's x), z = M^-1 r,
+// new r.z (alpha's numerator) and r.r; p, alpha and the iteration count stay.
+// The solve runs on while the true residual is above the tolerance and
+// iterations remain; a non-finite residual is a breakdown.
+__device__ __forceinline__ void cg_replace_body(const double *__restrict__ b, const double *__restrict__ Ax,
+                                                double *__restrict__ r, double *__restrict__ z,
+                                                const double *__restrict__ inv_d, int64_t n, double *partials,
+                                                unsigned *counter, hb_cg_state *st)
+{
+    dot_acc<double> rz, rr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = b[i] - Ax[i];
+        r[i] = ri;
+        if (inv_d) {
+            const double zi = ri * inv_d[i];
+            z[i] = zi;
+            rz.add(ri, zi);
+        } else {
+            rz.add(ri, ri);
+        }
+        rr.add(ri, ri);
+    }
+    double v[2] = {rz.value(), rr.value()}, tot[2];
+    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        st->rr = tot[0];
+        st->res2 = tot[1];
+        const bool finite = isfinite(tot[0]) && isfinite(tot[1]);
+        if (!finite) st->status = HB_ERR_BREAKDOWN;
+        st->run = (finite && st->status == HB_OK && st->it < st->max_it && tot[1] > st->tol2) ? 1 : 0;
+        st->next_run = st->run;
+    }
+}
+
 // Algorithm 1: r -= alpha Ap and the new r.r. With the
 // preconditioner (PREC) also z = M^-1 r, the new r.z (for beta) and r.r (for
 // the stopping test); without it r.r serves both.

@@ -127,6 +127,7 @@ _SIGS = [
                                  C.c_void_p]),
     ("hb_server_stats", C.c_int, [C.c_void_p, C.POINTER(hb_server_stats_t)]),
     ("hb_server_destroy", C.c_int, [C.c_void_p]),
+    ("hb_server_inject_round_error", C.c_int, [C.c_void_p]),
     ("hb_set_kernel_variant", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     ("hb_get_kernel_variant", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     ("hb_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -580,6 +581,10 @@ class Server:
             if time.time() - t0 > timeout:
                 raise TimeoutError(f"ticket {ticket} not done after {timeout} s")
             time.sleep(interval)
+
+    def inject_round_error(self) -> None:
+        """Test hook: the next round fails as if its launch had failed."""
+        _check(lib().hb_server_inject_round_error(self.handle))
 
     def stats(self) -> hb_server_stats_t:
         st = hb_server_stats_t()

@@ -36,3 +36,19 @@ def test_cache_rejects_garbage(tmp_path):
 def test_env_override(monkeypatch, tmp_path):
     monkeypatch.setenv("HB_AUTOTUNE_CACHE", str(tmp_path / "x.json"))
     assert at.cache_path() == str(tmp_path / "x.json")
+
+
+def test_general_mesh_choice_leaves_out_the_lattice_gather(tmp_path):
+    # the lattice-gather variants (GRID bit) rely on the box's structure; a
+    # choice that must hold on any mesh takes the fastest of the others
+    timings = {3: 12.5, 75: 12.3, 131: 12.1, 139: 12.2}
+    assert at.best_allowed(timings, hb.HB_VARIANT_GRID) == 75
+    assert at.best_allowed(timings, 0) == 131
+    dev = at.device_key("NVIDIA GB300", 152)
+    c = at.record({}, dev, 7, hb.HB_F64, 131, timings)
+    at.record(c, dev, 7, hb.HB_F64, 75, timings, exclude=hb.HB_VARIANT_GRID)
+    assert at.lookup(c, dev, 7, hb.HB_F64) == 131
+    assert at.lookup(c, dev, 7, hb.HB_F64, exclude=hb.HB_VARIANT_GRID) == 75
+    # a stored entry that breaks its own exclusion is not trusted
+    c[dev][at.entry_key(7, hb.HB_F64, hb.HB_VARIANT_GRID)]["variant"] = 139
+    assert at.lookup(c, dev, 7, hb.HB_F64, exclude=hb.HB_VARIANT_GRID) is None

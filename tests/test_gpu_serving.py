@@ -101,3 +101,20 @@ def test_server_argument_errors():
     with pytest.raises(hb.HBError):
         srv.poll(999)  # never issued
     srv.close()
+
+
+def test_failed_round_resolves_every_ticket_and_frees_memory():
+    # The failure is made on the host (the test hook makes the worker treat a
+    # round as a failed launch); no device work faults.
+    srv = hb.Server(8 << 30, max_slots=2, iters_per_launch=2)
+    reqs = [dict(ex=6, ey=6, ez=6, N=7, rtol=1e-12, seed=s, rhs_seed=s) for s in range(5)]
+    tickets = [srv.submit(**r) for r in reqs]
+    srv.inject_round_error()
+    statuses = [srv.wait(t, timeout=120.0)[0].status for t in tickets]
+    assert all(s in (hb.HB_OK, hb.HB_ERR_CUDA) for s in statuses), statuses
+    assert hb.HB_ERR_CUDA in statuses
+    st = srv.stats()
+    assert st.active == 0 and st.pending == 0 and st.mem_used == 0
+    with pytest.raises(hb.HBError):
+        srv.submit(**REQ)  # a stopped server takes no new work
+    srv.close()

@@ -57,6 +57,25 @@ def test_noalloc_dot_matches_hb_dot_twice(dims, N, dtype, prec, bar):
     m.close()
 
 
+def test_noalloc_dot_allocates_no_device_memory():
+    """The property the entry point exists for: after a first call (which
+    takes the scratch array's address), further calls leave the device's
+    free memory unchanged."""
+    n = 1 << 20
+    a = torch.from_numpy(inputs.random_vector(n, 21, "normal")).cuda()
+    b = torch.from_numpy(inputs.random_vector(n, 22, "normal")).cuda()
+    st, first = _noalloc(hb.HB_F64, a, b, n)
+    assert st == hb.HB_OK, hb.lib().hb_last_error()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(8):
+        st, v = _noalloc(hb.HB_F64, a, b, n)
+        assert st == hb.HB_OK and v == first
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+
+
 def test_noalloc_dot_rejects_lengths_beyond_its_scratch():
     a = torch.zeros(16, dtype=torch.float64, device="cuda")
     st, _ = _noalloc(hb.HB_F64, a, a, MAX_N + 1)
