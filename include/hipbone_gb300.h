@@ -457,13 +457,27 @@ double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx);
  *                         per lattice row sums each DOF's copies in ascending
  *                         element order, as the CSR does, so y is bitwise the
  *                         same as with the other pencil variants.
+ *   HB_VARIANT_TC         (alone; HB_F64 at N = 7) the tensor-core element kernel:
+ *                         every derivative contraction (D and D^T along r, s, t) runs
+ *                         on the tensor cores (tcgen05.mma, FP16 inputs, FP32
+ *                         accumulators in tensor memory) exactly, on an
+ *                         Ozaki-style split of the element's values and of D into
+ *                         seven 8-bit digits on a per-element fixed-point grid
+ *                         (every product and partial sum an integer below 2^24);
+ *                         the exact digit sums are combined in int64 and the
+ *                         metric step runs in FP64. Error per contraction about
+ *                         2^-53 of the element's largest |value| times sum |D|,
+ *                         the FP64 rounding level; an element holding a
+ *                         non-finite value gives NaN. Same surface store and
+ *                         gather as the pencil kernels.
  * Each of HB_F64, HB_F32 and HB_F64X keeps its own variant. HB_F64X takes
  * PENCIL | EVEN_ODD with or without ONE, and with CSR or GRID or neither (the
  * six shapes its double-float kernel is built in); other variants return
  * HB_ERR_ARG for it. The default is PENCIL | EVEN_ODD; hb_autotune measures
  * and picks per mesh and precision. */
 enum { HB_VARIANT_PENCIL = 1, HB_VARIANT_EVEN_ODD = 2, HB_VARIANT_EB2 = 4, HB_VARIANT_ONE = 8,
-       HB_VARIANT_TMA = 16, HB_VARIANT_WS = 32, HB_VARIANT_CSR = 64, HB_VARIANT_GRID = 128 };
+       HB_VARIANT_TMA = 16, HB_VARIANT_WS = 32, HB_VARIANT_CSR = 64, HB_VARIANT_GRID = 128,
+       HB_VARIANT_TC = 256 };
 hb_status hb_set_kernel_variant(hb_mesh *mesh, hb_precision prec, int variant);
 hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *variant);
 
@@ -473,10 +487,10 @@ hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *var
  * x.y reduction a CG iteration fuses into it (p.Ap), for each
  * variant (0, PENCIL, PENCIL|EVEN_ODD, PENCIL|EB2, PENCIL|EVEN_ODD|EB2,
  * PENCIL|EVEN_ODD|ONE, PENCIL|EVEN_ODD|TMA, PENCIL|EVEN_ODD|WS, PENCIL|EVEN_ODD|CSR,
- * PENCIL|EVEN_ODD|ONE|CSR, PENCIL|EVEN_ODD|GRID, PENCIL|EVEN_ODD|ONE|GRID; for
- * HB_F64X the six it takes) on `stream`, keeps the fastest for `prec` (HB_F64,
- * HB_F32 or HB_F64X) on this mesh and returns it in *best_variant.
- * ms_per_variant (may be NULL) has 256 slots
+ * PENCIL|EVEN_ODD|ONE|CSR, PENCIL|EVEN_ODD|GRID, PENCIL|EVEN_ODD|ONE|GRID, and TC
+ * for HB_F64 at N = 7; for HB_F64X the six it takes) on `stream`, keeps the
+ * fastest for `prec` (HB_F64, HB_F32 or HB_F64X) on this mesh and returns it in
+ * *best_variant. ms_per_variant (may be NULL) has 512 slots
  * indexed by variant and receives the mean time of each. Allocates two scratch vectors for the
  * duration of the call; synchronises `stream`. */
 hb_status hb_autotune(hb_mesh *mesh, hb_precision prec, hb_screen screen, double lambda, int reps,
@@ -524,6 +538,19 @@ hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int reps, double *
  * kernel gave up and reported it (the expected outcome), HB_OK if it reported
  * nothing. Takes about a second; synchronises `stream`. */
 hb_status hb_selftest_wait(int which, hb_status *status, void *stream);
+
+/* Self-check of the tensor-core operand layouts the tensor-core element
+ * kernel uses (no paper counterpart: a check of the hardware interface).
+ * Computes D = A B^T through tcgen05.mma kind::f16 (M = 128, N = 48, K = 48 in
+ * three steps of 16; FP16 operands from shared memory, FP32 accumulator in
+ * tensor memory) on one thread block. A_host: 128 x 48, B_host: 48 x 48,
+ * D_host: 128 x 48 floats, row-major; inputs are rounded to FP16. mode bit 0:
+ * A staged MN-major instead of K-major; bit 1: the descriptors' leading and
+ * stride byte-offset fields exchanged (a wrong layout on purpose, to tell the
+ * two conventions apart; it stays inside the zeroed staging area). *status
+ * receives HB_OK, or HB_ERR_TIMEOUT if the bounded wait for the MMA ran out.
+ * Allocates and synchronises the current device. */
+hb_status hb_tc_selftest(int mode, const float *A_host, const float *B_host, float *D_host, hb_status *status);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char *hb_last_error(void);

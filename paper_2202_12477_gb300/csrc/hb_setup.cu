@@ -170,6 +170,7 @@ hb_status hb_ensure_device_tables()
     { hb_status st2 = hb_ax2_upload_f32(D64.data()); if (st2 != HB_OK) return st2; }
     { hb_status st2 = hb_ax2_upload_f64x(D64.data()); if (st2 != HB_OK) return st2; }
     { hb_status st2 = hb_cg_fused_upload(D64.data()); if (st2 != HB_OK) return st2; }
+    { hb_status st2 = hb_tc_upload(); if (st2 != HB_OK) return st2; }
     HB_TRY_CUDA(cudaMemcpyToSymbol(g_D64, D64.data(), sizeof(double) * kTableSize));
     HB_TRY_CUDA(cudaMemcpyToSymbol(g_D32, D32.data(), sizeof(float) * kTableSize));
     HB_TRY_CUDA(cudaMemcpyToSymbol(g_xi64, xi.data(), sizeof(double) * 256));

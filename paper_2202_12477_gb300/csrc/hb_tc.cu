@@ -2,8 +2,12 @@
 // layouts the tensor-core element kernel relies on.
 #include <cuda_fp16.h>
 
+#include <cmath>
+#include <cstring>
+
 #include "hb_internal.h"
 #include "hb_tc.cuh"
+#include "hb_acc.cuh"
 
 namespace {
 
@@ -150,5 +154,549 @@ extern "C" hb_status hb_tc_selftest(int mode, const float *A_host, const float *
         return HB_ERR_CUDA;
     }
     *status = herr ? HB_ERR_TIMEOUT : HB_OK;
+    return HB_OK;
+}
+
+// ---------------------------------------------------------------- tensor-core FP64 element kernel
+//
+// y_L = S_L Z x (Sec. 2, Eq. stiffness) for N = 7 with every derivative
+// contraction (D along r, s, t and D^T along r, s, t; 12 n^4 of the
+// 12 n^4 + 15 n^3 flops of an element) on the tensor cores, exactly, and the
+// metric step (the 6 geometric factors, 15 n^3 flops) in FP64 on the CUDA
+// cores.
+//
+// Exact contractions from FP16 products (an Ozaki-style split into slices):
+//   - the element's values u are put on one fixed-point grid,
+//     X = round(u / 2^E) with 2^E the unit of the element's largest exponent
+//     (|X| < 2^53: the rounding is below the last bit of the largest value),
+//     and written as seven base-256 digits, X = sum_j u_j 256^(6-j), u_0
+//     signed (|u_0| <= 32), u_1..u_6 unsigned bytes;
+//   - D is scaled to integers D_int = round(D 2^s) (|D_int| < 2^55) and written
+//     as seven balanced digits b_d in [-128, 128];
+//   - digit products are integers below 2^16 and every sum the tensor core
+//     forms stays below 2^24, so FP16 inputs with FP32 accumulation add them
+//     without rounding. For each diagonal t = j + d <= 7 the MMA forms
+//     S_t = sum_{j+d=t} sum_m b_d[i][m] u_j[m] in its own accumulator
+//     column; D u = 2^(E-s) sum_t 256^(12-t) S_t up to the dropped diagonals
+//     t >= 8, which weigh below 2^-58 of the largest term;
+//   - a digit enters the MMA as the FP16 number 256 + u_j (384 + u_0), whose
+//     bit pattern is 0x5C00 | (u_j << 2): no conversion instruction. The
+//     offsets contribute a constant per accumulator column, removed inside the
+//     same MMA by an eighth K block: 128 in the A operand times the constant's
+//     negative / 128 (split into FP16-exact parts) in the B operand;
+//   - the exact integers S_t are read back (FP32 -> int32 by adding 1.5 2^23),
+//     combined in two int64 halves and turned into doubles with the exponent
+//     of the element's grid (exact), summed with one FP64 add.
+// Per two-element tile (128 lines per direction, M = 128) and direction: one
+// MMA chain of four K = 16 steps, A = the lines' digits (128 x 64, K-major),
+// B = the digit stack of D (64 x 64: output index i x diagonal t by digit j x
+// line position m), accumulator 128 x 64 FP32 in TMEM columns dir*64.
+namespace {
+namespace tcax {
+
+constexpr int N = 7, n = 8, n2 = 64, n3 = 512;
+constexpr int NS = 2 * n2 + 4 * N * (N - 1);  // surface nodes of an element
+constexpr int THREADS = 128;                  // one thread per line of a two-element tile
+constexpr int ABUF = 8 * 2048;                // one direction's A operand: 8 K blocks x 128 rows x 8 FP16
+constexpr int BIMG = 64 * 64 * 2;             // one B operand image (64 x 64 FP16)
+constexpr int EXS = 576;                      // padded node stride of an element in the exchange buffers
+constexpr int OFF_A = 0;
+constexpr int OFF_B = OFF_A + 3 * ABUF;
+constexpr int OFF_X = OFF_B + 2 * BIMG;
+constexpr int OFF_MISC = OFF_X + 2 * 2 * EXS * 8;
+constexpr int SMEM = OFF_MISC + 64;
+constexpr unsigned TMEM_COLS = 256;
+
+// B operand images of D (0) and D^T (1) in the shared-memory layout (K-major,
+// N chunk stride 128 bytes, K chunk stride 1024), and s (D_int = D 2^s).
+__device__ __align__(16) uint16_t g_tc_bimg[2][64 * 64];
+__constant__ int c_tc_dshift;
+
+struct tc_args {
+    const double *x;
+    const int32_t *l2g;
+    const double *geo;
+    double *ysurf;
+    double *y;
+    int64_t E;
+    const int *run;
+    double lambda;
+    int screen;
+    double *partials;
+    unsigned *err;
+};
+
+// node (i, j, k) of element el in the padded exchange buffers
+__device__ __forceinline__ int xq(int el, int i, int j, int k) { return el * EXS + k * 72 + j * 9 + i; }
+
+__device__ __forceinline__ unsigned exp_bits(double v)
+{
+    return (unsigned)(__double_as_longlong(v) >> 52) & 0x7FFu;
+}
+
+// v on the grid of unit 2^(emax - 1075): round(|v| / unit) with the sign of v
+// (|result| < 2^53; zero and subnormal v give 0).
+__device__ __forceinline__ long long to_fixed(double v, unsigned emax)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+    if (e == 0) return 0;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned sh = emax - e;
+    long long X;
+    if (sh == 0) X = (long long)m;
+    else if (sh > 53) X = 0;
+    else X = (long long)((m + (1ull << (sh - 1))) >> sh);
+    return (b >> 63) ? -X : X;
+}
+
+// v * 2^off as a double for |v| < 2^53 (exact; results below the normal
+// range flush to zero, above it give infinity).
+__device__ __forceinline__ double i2d_scaled(long long v, int off)
+{
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
+    unsigned long long mag = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int lz = __clzll((long long)mag);
+    mag <<= (lz - 11);
+    const int ex = 1023 + 63 - lz + off;
+    if (ex <= 0) return 0.0;
+    if (ex >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | (mag & 0xFFFFFFFFFFFFFull)));
+}
+
+// FP16 bit patterns of the seven digits of X as the MMA takes them.
+__device__ __forceinline__ void digits_of(long long X, uint16_t (&h)[7])
+{
+    const int hi = (int)(X >> 32);
+    const unsigned lo = (unsigned)X;
+    h[0] = (uint16_t)(0x5C00u | ((unsigned)(128 + (hi >> 16)) << 2));
+    h[1] = (uint16_t)(0x5C00u | ((((unsigned)hi >> 8) & 0xFFu) << 2));
+    h[2] = (uint16_t)(0x5C00u | (((unsigned)hi & 0xFFu) << 2));
+    h[3] = (uint16_t)(0x5C00u | ((lo >> 24) << 2));
+    h[4] = (uint16_t)(0x5C00u | (((lo >> 16) & 0xFFu) << 2));
+    h[5] = (uint16_t)(0x5C00u | (((lo >> 8) & 0xFFu) << 2));
+    h[6] = (uint16_t)(0x5C00u | ((lo & 0xFFu) << 2));
+}
+
+// A operand rows (K-major, row chunk stride 128 bytes, K block stride 2048):
+//   r: row (el, k, j), position m = i;  s: row (el, k, i), m = j;  t: row (el, j, i), m = k.
+__device__ __forceinline__ unsigned char *arow(unsigned char *Ab, int dir, int blk, int el, int chunk, int row,
+                                               int m)
+{
+    return Ab + dir * ABUF + blk * 2048 + (el * 8 + chunk) * 128 + row * 16 + m * 2;
+}
+
+// Writes the digits of the thread's t-line values X[k] (node (ti, tj, k)) to
+// the A operands of the directions in `dirs` (bit 0 r, bit 1 s, bit 2 t).
+__device__ __forceinline__ void stage(unsigned char *Ab, int el, int ti, int tj, const long long (&X)[n], int dirs)
+{
+    uint16_t h[n][7];
+#pragma unroll
+    for (int k = 0; k < n; k++) digits_of(X[k], h[k]);
+#pragma unroll
+    for (int d = 0; d < 7; d++) {
+        if (dirs & 4) {
+            uint4 v;
+            v.x = (unsigned)h[0][d] | ((unsigned)h[1][d] << 16);
+            v.y = (unsigned)h[2][d] | ((unsigned)h[3][d] << 16);
+            v.z = (unsigned)h[4][d] | ((unsigned)h[5][d] << 16);
+            v.w = (unsigned)h[6][d] | ((unsigned)h[7][d] << 16);
+            *reinterpret_cast<uint4 *>(arow(Ab, 2, d, el, tj, ti, 0)) = v;
+        }
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            if (dirs & 1) *reinterpret_cast<uint16_t *>(arow(Ab, 0, d, el, k, tj, ti)) = h[k][d];
+            if (dirs & 2) *reinterpret_cast<uint16_t *>(arow(Ab, 1, d, el, k, ti, tj)) = h[k][d];
+        }
+    }
+}
+
+// One MMA chain per direction: accumulator columns dir*64 .. dir*64 + 63.
+__device__ __forceinline__ void issue(unsigned tmem, const unsigned char *Ab, const unsigned char *Bi)
+{
+    constexpr uint32_t idesc = hbtc::idesc_f16(128, 64, false, false);
+    const unsigned b0 = hbtc::smem_addr(Bi);
+#pragma unroll
+    for (int dir = 0; dir < 3; dir++) {
+        const unsigned a0 = hbtc::smem_addr(Ab + dir * ABUF);
+#pragma unroll
+        for (int ks = 0; ks < 4; ks++)
+            hbtc::mma_f16(tmem + dir * 64, hbtc::smem_desc(a0 + ks * 4096, 2048, 128),
+                          hbtc::smem_desc(b0 + ks * 2048, 1024, 128), idesc, ks > 0);
+    }
+}
+
+// The exact diagonal sums of two outputs (16 accumulator columns: output
+// 2c and 2c+1, diagonals 0..7 each) as int64 halves: value = 2^72 hi + 2^40 lo
+// in units of the element's grid times 2^-s.
+__device__ __forceinline__ void combine(const uint32_t (&v)[16], int o, long long &hi, long long &lo)
+{
+    int S[8];
+#pragma unroll
+    for (int t = 0; t < 8; t++) S[t] = __float_as_int(__fadd_rn(__uint_as_float(v[o * 8 + t]), 12582912.0f)) - 0x4B400000;
+    hi = ((long long)S[0] << 24) + ((long long)S[1] << 16) + ((long long)S[2] << 8) + (long long)S[3];
+    lo = ((long long)S[4] << 24) + ((long long)S[5] << 16) + ((long long)S[6] << 8) + (long long)S[7];
+}
+
+__device__ __forceinline__ unsigned warp_max_to_smem(unsigned v, unsigned *wexp)
+{
+    v = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) wexp[threadIdx.x >> 5] = v;
+    return v;
+}
+
+__device__ __forceinline__ int ring_index7(int i, int j)
+{
+    return j == 0 ? i : (j == N ? N + 1 + i : 2 * (N + 1) + 2 * (j - 1) + (i == N ? 1 : 0));
+}
+
+__global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
+{
+    if (A.run && *A.run == 0) return;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int el = tid >> 6, a = tid & 63, ti = a & 7, tj = a >> 3;
+    unsigned char *Ab = sm + OFF_A;
+    unsigned char *Bi = sm + OFF_B;
+    double *ExR = reinterpret_cast<double *>(sm + OFF_X);
+    double *ExS = ExR + 2 * EXS;
+    long long *Yhi = reinterpret_cast<long long *>(ExR);
+    long long *Ylo = reinterpret_cast<long long *>(ExS);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + OFF_MISC);
+    unsigned *tptr = reinterpret_cast<unsigned *>(sm + OFF_MISC + 8);
+    unsigned *wexp = reinterpret_cast<unsigned *>(sm + OFF_MISC + 16);
+
+    // once per block: the B images, the offset-correction K block (128.0 in
+    // every row of the three A operands), the barrier and the TMEM columns
+    for (int q = tid; q < 2 * BIMG / 16; q += THREADS)
+        reinterpret_cast<uint4 *>(Bi)[q] = reinterpret_cast<const uint4 *>(&g_tc_bimg[0][0])[q];
+    for (int q = tid; q < 3 * 128; q += THREADS)
+        reinterpret_cast<uint4 *>(Ab + (q >> 7) * ABUF + 7 * 2048)[q & 127] =
+            make_uint4(0x58005800u, 0x58005800u, 0x58005800u, 0x58005800u);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(hbtc::smem_addr(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) hbtc::tmem_alloc(tptr, TMEM_COLS);
+    hbtc::fence_async_smem();
+    hbtc::fence_before_sync();
+    __syncthreads();
+    hbtc::fence_after_sync();
+    const unsigned tmem = *tptr;
+    const int dshift = c_tc_dshift;
+    // this thread's TMEM lane (row of every accumulator)
+    const unsigned tl = tmem + ((unsigned)(warp * 32) << 16);
+
+    hbacc::dot_acc<double> acc;
+    unsigned phase = 0;
+    int gave_up = 0;
+    const int64_t ntiles = (A.E + 1) / 2;
+    for (int64_t g = blockIdx.x; g < ntiles; g += gridDim.x) {
+        const int64_t e = 2 * g + el;
+        const bool active = e < A.E;
+        // ---- gather u along the t-line (ti, tj); the factors load meanwhile
+        int gid[n];
+        double u[n];
+        const int32_t *lg = A.l2g + e * n3 + a;
+#pragma unroll
+        for (int k = 0; k < n; k++) gid[k] = active ? __ldcs(lg + k * n2) : -1;
+#pragma unroll
+        for (int k = 0; k < n; k++) u[k] = gid[k] >= 0 ? __ldg(A.x + gid[k]) : 0.0;
+        double G[n][6];
+        const double *ge = A.geo + e * 7 * n3 + a;
+#pragma unroll
+        for (int k = 0; k < n; k++)
+#pragma unroll
+            for (int c = 0; c < 6; c++) G[k][c] = active ? __ldcs(ge + k * 7 * n2 + c * n2) : 0.0;
+        unsigned em = 0;
+#pragma unroll
+        for (int k = 0; k < n; k++) em = max(em, exp_bits(u[k]));
+        warp_max_to_smem(em, wexp);
+        __syncthreads();
+        const unsigned eu = max(wexp[2 * el], wexp[2 * el + 1]);
+        {
+            long long X[n];
+#pragma unroll
+            for (int k = 0; k < n; k++) X[k] = eu == 0x7FFu ? 0 : to_fixed(u[k], eu);
+            stage(Ab, el, ti, tj, X, 7);
+        }
+        hbtc::fence_async_smem();
+        hbtc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            hbtc::fence_after_sync();
+            issue(tmem, Ab, Bi);
+            hbtc::mma_commit(bar);
+        }
+        // ---- gradients: r and s through the exchange buffers, t kept here
+        if (!tc_wait(bar, phase, A.err)) gave_up = 1;
+        phase ^= 1u;
+        hbtc::fence_after_sync();
+        const int goff = (int)eu - 1075 - dshift;
+        const bool ubad = eu == 0x7FFu;
+        double gt[n];
+#pragma unroll
+        for (int dir = 0; dir < 3; dir++) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                uint32_t v[16];
+                hbtc::tmem_ld16(tl + dir * 64 + c * 16, v);
+                hbtc::tmem_wait_ld(v);
+#pragma unroll
+                for (int o = 0; o < 2; o++) {
+                    long long hi, lo;
+                    combine(v, o, hi, lo);
+                    const double gv = ubad ? __longlong_as_double(0x7FF8000000000000ll)
+                                           : i2d_scaled(hi, goff + 72) + i2d_scaled(lo, goff + 40);
+                    const int out = 2 * c + o;
+                    // lane tid: r row (el, k, j) = tid, s row (el, k, i) = tid, t row (el, j, i) = tid
+                    if (dir == 0) ExR[xq(el, out, tid & 7, (tid >> 3) & 7)] = gv;
+                    else if (dir == 1) ExS[xq(el, tid & 7, out, (tid >> 3) & 7)] = gv;
+                    else gt[out] = gv;
+                }
+            }
+        }
+        hbtc::fence_before_sync();
+        __syncthreads();
+        // ---- metric (FP64): v = G grad at the t-line's nodes
+        double vr[n], vs[n], vt[n];
+        unsigned evm = 0;
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            const int q = xq(el, ti, tj, k);
+            const double ur = ExR[q], us = ExS[q], ut = gt[k];
+            vr[k] = fma(G[k][2], ut, fma(G[k][1], us, G[k][0] * ur));
+            vs[k] = fma(G[k][4], ut, fma(G[k][3], us, G[k][1] * ur));
+            vt[k] = fma(G[k][5], ut, fma(G[k][4], us, G[k][2] * ur));
+            evm = max(evm, max(exp_bits(vr[k]), max(exp_bits(vs[k]), exp_bits(vt[k]))));
+        }
+        warp_max_to_smem(evm, wexp);
+        __syncthreads();
+        const unsigned ev = max(wexp[2 * el], wexp[2 * el + 1]);
+        {
+            long long X[n];
+#pragma unroll
+            for (int k = 0; k < n; k++) X[k] = ev == 0x7FFu ? 0 : to_fixed(vr[k], ev);
+            stage(Ab, el, ti, tj, X, 1);
+#pragma unroll
+            for (int k = 0; k < n; k++) X[k] = ev == 0x7FFu ? 0 : to_fixed(vs[k], ev);
+            stage(Ab, el, ti, tj, X, 2);
+#pragma unroll
+            for (int k = 0; k < n; k++) X[k] = ev == 0x7FFu ? 0 : to_fixed(vt[k], ev);
+            stage(Ab, el, ti, tj, X, 4);
+        }
+        hbtc::fence_async_smem();
+        hbtc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            hbtc::fence_after_sync();
+            issue(tmem, Ab, Bi + BIMG);
+            hbtc::mma_commit(bar);
+        }
+        // ---- D^T along r and s summed exactly into the exchange buffers, t here
+        if (!tc_wait(bar, phase, A.err)) gave_up = 1;
+        phase ^= 1u;
+        hbtc::fence_after_sync();
+#pragma unroll
+        for (int dir = 0; dir < 2; dir++) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                uint32_t v[16];
+                hbtc::tmem_ld16(tl + dir * 64 + c * 16, v);
+                hbtc::tmem_wait_ld(v);
+#pragma unroll
+                for (int o = 0; o < 2; o++) {
+                    long long hi, lo;
+                    combine(v, o, hi, lo);
+                    const int out = 2 * c + o;
+                    if (dir == 0) {
+                        const int q = xq(el, out, tid & 7, (tid >> 3) & 7);
+                        Yhi[q] = hi;
+                        Ylo[q] = lo;
+                    } else {
+                        const int q = xq(el, tid & 7, out, (tid >> 3) & 7);
+                        Yhi[q] += hi;
+                        Ylo[q] += lo;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        {
+            const int yoff = (int)ev - 1075 - dshift;
+            const bool vbad = ev == 0x7FFu;
+            double *ys = A.ysurf + e * NS;
+            const bool ring = ti == 0 || ti == N || tj == 0 || tj == N;
+            const int r = ring ? ring_index7(ti, tj) : 0;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                uint32_t v[16];
+                hbtc::tmem_ld16(tl + 2 * 64 + c * 16, v);
+                hbtc::tmem_wait_ld(v);
+#pragma unroll
+                for (int o = 0; o < 2; o++) {
+                    long long hi, lo;
+                    combine(v, o, hi, lo);
+                    const int k = 2 * c + o;
+                    const int q = xq(el, ti, tj, k);
+                    hi += Yhi[q];
+                    lo += Ylo[q];
+                    const double yc = vbad ? __longlong_as_double(0x7FF8000000000000ll)
+                                           : i2d_scaled(hi, yoff + 72) + i2d_scaled(lo, yoff + 40);
+                    if (!active) continue;
+                    if (k == 0) {
+                        ys[a] = yc;
+                    } else if (k == N) {
+                        ys[n2 + a] = yc;
+                    } else if (ring) {
+                        ys[2 * n2 + (k - 1) * 4 * N + r] = yc;
+                    } else {
+                        // element-interior node: its DOF has no other copy
+                        const double xv = u[k];
+                        const double jw = A.screen ? __ldg(A.geo + (e * n + k) * 7 * n2 + 6 * n2 + a) : 1.0;
+                        double yy = yc;
+                        yy += A.lambda * (jw * xv);
+                        A.y[gid[k]] = yy;
+                        acc.add(xv, yy);
+                    }
+                }
+            }
+        }
+        hbtc::fence_before_sync();
+        __syncthreads();
+        if (__syncthreads_or(gave_up)) break;
+    }
+    if (A.partials) {
+        const double v = hbacc::block_sum(acc.value());
+        if (tid == 0) A.partials[blockIdx.x] = v;
+    }
+    // a wait that gave up left MMAs in flight: wait for them (bounded) before
+    // the TMEM columns are released
+    if (__syncthreads_or(gave_up)) {
+        if (tid == 0) tc_wait(bar, phase ^ 1u, A.err);
+        __syncthreads();
+    }
+    hbtc::fence_before_sync();
+    __syncthreads();
+    hbtc::fence_after_sync();
+    if (warp == 0) hbtc::tmem_free(tmem, TMEM_COLS);
+}
+
+// ---- host: B images and launch
+
+// FP16 bit pattern of an integer that FP16 holds exactly.
+static uint16_t fp16_exact(long long v)
+{
+    if (v == 0) return 0;
+    const uint16_t sgn = v < 0 ? 0x8000 : 0;
+    unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+    int e = 63 - __builtin_clzll(a);
+    const unsigned long long f = e >= 10 ? (a >> (e - 10)) : (a << (10 - e));
+    return (uint16_t)(sgn | (uint16_t)((e + 15) << 10) | (uint16_t)(f & 0x3FF));
+}
+
+// Largest part of c (toward zero) that FP16 holds exactly: its top 11 bits.
+static long long fp16_part(long long c)
+{
+    const unsigned long long a = (unsigned long long)(c < 0 ? -c : c);
+    const int e = 63 - __builtin_clzll(a);
+    const unsigned long long p = e > 10 ? (a >> (e - 10)) << (e - 10) : a;
+    return c < 0 ? -(long long)p : (long long)p;
+}
+
+}  // namespace tcax
+}  // namespace
+
+// Builds the B images from the degree-7 derivative matrix and uploads them to
+// the current device (once per device, from hb_ensure_device_tables).
+hb_status hb_tc_upload()
+{
+    using namespace tcax;
+    double xi[n], w[n], D[n * n];
+    hb_reference_element(N, xi, w, D);
+    double mx = 0.0;
+    for (int q = 0; q < n * n; q++) mx = std::fmax(mx, std::fabs(D[q]));
+    const int s = 55 - (std::ilogb(mx) + 1);
+    static uint16_t img[2][64 * 64];
+    for (int tr = 0; tr < 2; tr++) {
+        int b[7][n][n];  // digit d of D_int[i][m] (D^T for tr = 1), weight 256^(6-d)
+        for (int i = 0; i < n; i++)
+            for (int m = 0; m < n; m++) {
+                const double v = tr ? D[m * n + i] : D[i * n + m];
+                long long q = std::llround(std::ldexp(v, s));
+                for (int d = 6; d >= 1; d--) {
+                    const long long r = ((q + 128) & 255) - 128;
+                    b[d][i][m] = (int)r;
+                    q = (q - r) >> 8;
+                }
+                if (q < -128 || q > 128) {
+                    hb_set_error("tensor-core split: leading digit %lld out of range", q);
+                    return HB_ERR_ARG;
+                }
+                b[0][i][m] = (int)q;
+            }
+        uint16_t *im = img[tr];
+        std::memset(im, 0, sizeof img[0]);
+        auto put = [&](int i, int t, int blk, int m, long long val) {
+            im[(i * 128 + t * 16 + blk * 1024 + m * 2) / 2] = fp16_exact(val);
+        };
+        for (int i = 0; i < n; i++)
+            for (int t = 0; t < 8; t++) {
+                long long beta = 0;  // what the digit offsets add to column (i, t)
+                for (int j = 0; j < 7; j++) {
+                    const int d = t - j;
+                    if (d < 0 || d > 6) continue;
+                    long long rs = 0;
+                    for (int m = 0; m < n; m++) {
+                        put(i, t, j, m, b[d][i][m]);
+                        rs += b[d][i][m];
+                    }
+                    beta += (j == 0 ? 384 : 256) * rs;
+                }
+                // K block 7: 128 (A side) times parts summing to -beta / 128
+                long long c = -beta / 128;
+                for (int m = 0; m < n && c != 0; m++) {
+                    const long long p = fp16_part(c);
+                    put(i, t, 7, m, p);
+                    c -= p;
+                }
+                if (c != 0) {
+                    hb_set_error("tensor-core split: offset correction does not fit");
+                    return HB_ERR_ARG;
+                }
+            }
+    }
+    HB_TRY_CUDA(cudaMemcpyToSymbol(g_tc_bimg, img, sizeof img));
+    HB_TRY_CUDA(cudaMemcpyToSymbol(c_tc_dshift, &s, sizeof s));
+    return HB_OK;
+}
+
+// Tensor-core FP64 element kernel (N = 7): interior DOFs finished here (y,
+// lambda term, partial of x.y per block), surface values to ysurf for the
+// surface gather. Persistent grid: two blocks per SM at most.
+hb_status hb_launch_ax_tc_f64(const hb_mesh *m, const double *x, double *ysurf, double *y, double lambda,
+                              int screen, double *partials, const int *run, cudaStream_t s, int64_t *nblocks)
+{
+    using namespace tcax;
+    if (m->N != N) { hb_set_error("the tensor-core element kernel is built for N = 7 only"); return HB_ERR_ARG; }
+    if (!m->geo) { hb_set_error("mesh has no double geometric factors"); return HB_ERR_ARG; }
+    if (m->E <= 0) return HB_OK;
+    int dev = 0;
+    HB_TRY_CUDA(cudaGetDevice(&dev));
+    static int attr_set[64] = {0}, sms[64] = {0};
+    if (dev < 0 || dev >= 64) { hb_set_error("device index %d unsupported", dev); return HB_ERR_ARG; }
+    if (!attr_set[dev]) {
+        HB_TRY_CUDA(cudaFuncSetAttribute(ax_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+        HB_TRY_CUDA(cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev));
+        attr_set[dev] = 1;
+    }
+    const int64_t ntiles = (m->E + 1) / 2;
+    const int64_t grid = ntiles < 2 * (int64_t)sms[dev] ? ntiles : 2 * (int64_t)sms[dev];
+    if (nblocks) *nblocks = grid;
+    tc_args A{x, m->l2g, m->geo, ysurf, y, m->E, run, lambda, screen, partials, m->counters + 7};
+    hb_prof_scope prof("ax_local", s);
+    ax_tc_kernel<<<(unsigned)grid, THREADS, SMEM, s>>>(A);
+    HB_CHECK_LAUNCH();
     return HB_OK;
 }

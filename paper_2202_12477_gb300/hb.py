@@ -128,6 +128,7 @@ _SIGS = [
     ("hb_server_stats", C.c_int, [C.c_void_p, C.POINTER(hb_server_stats_t)]),
     ("hb_server_destroy", C.c_int, [C.c_void_p]),
     ("hb_server_inject_round_error", C.c_int, [C.c_void_p]),
+    ("hb_tc_selftest", C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     ("hb_set_kernel_variant", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     ("hb_get_kernel_variant", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     ("hb_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -227,7 +228,8 @@ HB_VARIANT_PENCIL, HB_VARIANT_EVEN_ODD, HB_VARIANT_EB2, HB_VARIANT_ONE, HB_VARIA
     1, 2, 4, 8, 16, 32
 HB_VARIANT_CSR = 64
 HB_VARIANT_GRID = 128
-VARIANTS = [0, 1, 3, 5, 7, 11, 19, 35, 67, 75, 131, 139]  # every valid combination
+HB_VARIANT_TC = 256  # tensor-core element kernel (HB_F64, N = 7)
+VARIANTS = [0, 1, 3, 5, 7, 11, 19, 35, 67, 75, 131, 139]  # every valid combination of the pencil flags
 VARIANTS_F64X = [3, 11, 67, 75, 131, 139]  # the shapes the double-float kernel is built in
 
 
@@ -245,9 +247,9 @@ def hb_autotune(h, prec, screen=HB_SCREEN_IDENTITY, lam=0.1, reps=5, stream=None
     """Times every kernel variant on this mesh, keeps the fastest; returns
     (best variant, {variant: ms})."""
     best = C.c_int(-1)
-    ms = (C.c_double * 256)(*([-1.0] * 256))
+    ms = (C.c_double * 512)(*([-1.0] * 512))
     _check(lib().hb_autotune(h, prec, screen, lam, reps, C.byref(best), ms, _stream_ptr(stream)))
-    return best.value, {v: ms[v] for v in VARIANTS if ms[v] >= 0}
+    return best.value, {v: ms[v] for v in VARIANTS + [HB_VARIANT_TC] if ms[v] >= 0}
 
 
 HB_PROBE_STREAM81_FP, HB_PROBE_STREAM81_BITS, HB_PROBE_COPY, HB_PROBE_FMA = 0, 1, 2, 3
@@ -601,3 +603,16 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def hb_tc_selftest(mode, A, B):
+    """D = A B^T on the tensor cores (see the C header); A 128x48, B 48x48
+    float32 numpy arrays. Returns (D, status)."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    D = np.zeros((128, 48), dtype=np.float32)
+    st = C.c_int(-1)
+    _check(lib().hb_tc_selftest(mode, A.ctypes.data_as(C.c_void_p), B.ctypes.data_as(C.c_void_p),
+                                D.ctypes.data_as(C.c_void_p), C.byref(st)))
+    return D, st.value
