@@ -3,7 +3,8 @@ shared memory and an FP32 accumulator in tensor memory), checked through the
 C ABI against numpy: D = A B^T on integer-valued inputs small enough that
 every product and every sum is exact in FP32, so the comparison is bit-exact.
 These are the layouts the tensor-core element kernel stages its operands in:
-K-major and MN-major A, K-major B."""
+K-major A and B (the entry point can also stage A MN-major, a layout the
+kernel does not use)."""
 import numpy as np
 import pytest
 
@@ -21,9 +22,9 @@ def _cuda():
     hb.lib()
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_tc_layouts_exact(mode):
-    rng = np.random.Generator(np.random.PCG64(5 + mode))
+def test_tc_layouts_exact():
+    mode = 0  # K-major A and B, the layouts the element kernel stages
+    rng = np.random.Generator(np.random.PCG64(5))
     A = rng.integers(-256, 257, size=(128, 48)).astype(np.float32)
     B = rng.integers(-256, 257, size=(48, 48)).astype(np.float32)
     D, st = hb.hb_tc_selftest(mode, A, B)
