@@ -196,7 +196,8 @@ namespace tcax {
 
 constexpr int N = 7, n = 8, n2 = 64, n3 = 512;
 constexpr int NS = 2 * n2 + 4 * N * (N - 1);  // surface nodes of an element
-constexpr int THREADS = 128;                  // one thread per line of a two-element tile
+constexpr int THREADS = 256;                  // two threads per line of a two-element tile
+constexpr int KH = 4;                         // nodes of its line a thread owns (half of n)
 constexpr int ABUF = 8 * 2048;                // one direction's A operand: 8 K blocks x 128 rows x 8 FP16
 constexpr int BIMG = 64 * 64 * 2;             // one B operand image (64 x 64 FP16)
 constexpr int EXS = 576;                      // padded node stride of an element in the exchange buffers
@@ -250,19 +251,40 @@ __device__ __forceinline__ long long to_fixed(double v, unsigned emax)
     return (b >> 63) ? -X : X;
 }
 
-// v * 2^off as a double for |v| < 2^53 (exact; results below the normal
-// range flush to zero, above it give infinity).
-__device__ __forceinline__ double i2d_scaled(long long v, int off)
+// (H 2^32 + L) 2^off as a double, rounded to nearest (ties to even), for
+// |H| < 2^42: the magnitude is split into a 64-bit top word and 32 low bits,
+// the top 53 bits kept and the rest decide the rounding. Results below the
+// normal range flush to zero, above it give infinity.
+__device__ __forceinline__ double fix96_to_double(long long H, unsigned L, int off)
 {
-    if (v == 0) return 0.0;
-    const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
-    unsigned long long mag = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    const int lz = __clzll((long long)mag);
-    mag <<= (lz - 11);
-    const int ex = 1023 + 63 - lz + off;
-    if (ex <= 0) return 0.0;
+    const bool neg = H < 0;
+    const unsigned long long mh = neg ? (unsigned long long)(-H) - (L != 0u ? 1ull : 0ull) : (unsigned long long)H;
+    const unsigned ml = neg ? 0u - L : L;
+    unsigned long long W;
+    int ex;
+    if (mh < (1ull << 21)) {
+        // below 2^53: exact
+        W = (mh << 32) | ml;
+        if (W == 0) return 0.0;
+        const int lz = __clzll((long long)W);
+        W <<= (lz - 11);
+        ex = 1086 - lz + off;
+    } else {
+        const int lz = __clzll((long long)mh);  // 22 .. 42
+        int sh = 43 - lz;                        // 1 .. 21 bits below the kept 53
+        W = (mh << (32 - sh)) | (ml >> sh);
+        const unsigned rem = ml & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        if (rem > half || (rem == half && (W & 1ull))) W += 1ull;
+        if (W >> 53) {
+            W >>= 1;
+            sh += 1;
+        }
+        ex = 1075 + sh + off;
+    }
+    const unsigned long long sgn = neg ? 0x8000000000000000ull : 0ull;
+    if (ex <= 0) return __longlong_as_double((long long)sgn);
     if (ex >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | (mag & 0xFFFFFFFFFFFFFull)));
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | (W & 0xFFFFFFFFFFFFFull)));
 }
 
 // FP16 bit patterns of the seven digits of X as the MMA takes them.
@@ -287,27 +309,26 @@ __device__ __forceinline__ unsigned char *arow(unsigned char *Ab, int dir, int b
     return Ab + dir * ABUF + blk * 2048 + (el * 8 + chunk) * 128 + row * 16 + m * 2;
 }
 
-// Writes the digits of the thread's t-line values X[k] (node (ti, tj, k)) to
+// Writes the digits of the thread's values X[q] (node (ti, tj, k0 + q)) to
 // the A operands of the directions in `dirs` (bit 0 r, bit 1 s, bit 2 t).
-__device__ __forceinline__ void stage(unsigned char *Ab, int el, int ti, int tj, const long long (&X)[n], int dirs)
+__device__ __forceinline__ void stage(unsigned char *Ab, int el, int ti, int tj, int k0, const long long (&X)[KH],
+                                      int dirs)
 {
-    uint16_t h[n][7];
+    uint16_t h[KH][7];
 #pragma unroll
-    for (int k = 0; k < n; k++) digits_of(X[k], h[k]);
+    for (int q = 0; q < KH; q++) digits_of(X[q], h[q]);
 #pragma unroll
     for (int d = 0; d < 7; d++) {
         if (dirs & 4) {
-            uint4 v;
+            uint2 v;
             v.x = (unsigned)h[0][d] | ((unsigned)h[1][d] << 16);
             v.y = (unsigned)h[2][d] | ((unsigned)h[3][d] << 16);
-            v.z = (unsigned)h[4][d] | ((unsigned)h[5][d] << 16);
-            v.w = (unsigned)h[6][d] | ((unsigned)h[7][d] << 16);
-            *reinterpret_cast<uint4 *>(arow(Ab, 2, d, el, tj, ti, 0)) = v;
+            *reinterpret_cast<uint2 *>(arow(Ab, 2, d, el, tj, ti, k0)) = v;
         }
 #pragma unroll
-        for (int k = 0; k < n; k++) {
-            if (dirs & 1) *reinterpret_cast<uint16_t *>(arow(Ab, 0, d, el, k, tj, ti)) = h[k][d];
-            if (dirs & 2) *reinterpret_cast<uint16_t *>(arow(Ab, 1, d, el, k, ti, tj)) = h[k][d];
+        for (int q = 0; q < KH; q++) {
+            if (dirs & 1) *reinterpret_cast<uint16_t *>(arow(Ab, 0, d, el, k0 + q, tj, ti)) = h[q][d];
+            if (dirs & 2) *reinterpret_cast<uint16_t *>(arow(Ab, 1, d, el, k0 + q, ti, tj)) = h[q][d];
         }
     }
 }
@@ -327,23 +348,24 @@ __device__ __forceinline__ void issue(unsigned tmem, const unsigned char *Ab, co
     }
 }
 
-// The exact diagonal sums of two outputs (16 accumulator columns: output
-// 2c and 2c+1, diagonals 0..7 each) as int64 halves: value = 2^72 hi + 2^40 lo
-// in units of the element's grid times 2^-s.
+// The exact diagonal sums of output o of a 16-column chunk (diagonals 0..7)
+// as the halves hi = sum_{t<4} S_t 256^(3-t), lo = sum_{t>=4} S_t 256^(7-t):
+// the output is 2^72 hi + 2^40 lo in units of the element's grid times 2^-s.
+// Each S_t is an integer below 2^22 in magnitude, read exactly from its float
+// by adding 1.5 2^23.
 __device__ __forceinline__ void combine(const uint32_t (&v)[16], int o, long long &hi, long long &lo)
 {
     int S[8];
 #pragma unroll
     for (int t = 0; t < 8; t++) S[t] = __float_as_int(__fadd_rn(__uint_as_float(v[o * 8 + t]), 12582912.0f)) - 0x4B400000;
-    hi = ((long long)S[0] << 24) + ((long long)S[1] << 16) + ((long long)S[2] << 8) + (long long)S[3];
-    lo = ((long long)S[4] << 24) + ((long long)S[5] << 16) + ((long long)S[6] << 8) + (long long)S[7];
+    hi = (long long)(S[0] * 256 + S[1]) * 65536 + (long long)(S[2] * 256 + S[3]);
+    lo = (long long)(S[4] * 256 + S[5]) * 65536 + (long long)(S[6] * 256 + S[7]);
 }
 
-__device__ __forceinline__ unsigned warp_max_to_smem(unsigned v, unsigned *wexp)
+// 2^off (2^32 hi + lo) as a double (rounded once).
+__device__ __forceinline__ double halves_to_double(long long hi, long long lo, int off)
 {
-    v = __reduce_max_sync(0xffffffffu, v);
-    if ((threadIdx.x & 31) == 0) wexp[threadIdx.x >> 5] = v;
-    return v;
+    return fix96_to_double(hi + (lo >> 32), (unsigned)(lo & 0xFFFFFFFFll), off);
 }
 
 __device__ __forceinline__ int ring_index7(int i, int j)
@@ -351,12 +373,27 @@ __device__ __forceinline__ int ring_index7(int i, int j)
     return j == 0 ? i : (j == N ? N + 1 + i : 2 * (N + 1) + 2 * (j - 1) + (i == N ? 1 : 0));
 }
 
+// Largest biased exponent over element el (warps 0, 1, 4, 5 hold element 0,
+// warps 2, 3, 6, 7 element 1). Every thread calls it; it synchronises.
+__device__ __forceinline__ unsigned element_max(unsigned v, unsigned *wexp, int el)
+{
+    v = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) wexp[threadIdx.x >> 5] = v;
+    __syncthreads();
+    return max(max(wexp[2 * el], wexp[2 * el + 1]), max(wexp[4 + 2 * el], wexp[5 + 2 * el]));
+}
+
+// Thread tid: line tau = tid % 128 of the tile (TMEM lane tau; element
+// el = tau / 64; t-line (ti, tj) = (tau % 8, tau / 8 % 8)) and half h = tid / 128:
+// nodes k = 4h .. 4h + 3 of its t-line, outputs 4h .. 4h + 3 of its r-, s-
+// and t-line rows.
 __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
 {
     if (A.run && *A.run == 0) return;
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int el = tid >> 6, a = tid & 63, ti = a & 7, tj = a >> 3;
+    const int tau = tid & 127, h = tid >> 7, k0 = KH * h;
+    const int el = tau >> 6, a = tau & 63, ti = a & 7, tj = a >> 3;
     unsigned char *Ab = sm + OFF_A;
     unsigned char *Bi = sm + OFF_B;
     double *ExR = reinterpret_cast<double *>(sm + OFF_X);
@@ -385,8 +422,8 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
     hbtc::fence_after_sync();
     const unsigned tmem = *tptr;
     const int dshift = c_tc_dshift;
-    // this thread's TMEM lane (row of every accumulator)
-    const unsigned tl = tmem + ((unsigned)(warp * 32) << 16);
+    // this thread's TMEM lane and its two 16-column chunks (outputs 4h .. 4h + 3)
+    const unsigned tl = tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(32 * h);
 
     hbacc::dot_acc<double> acc;
     unsigned phase = 0;
@@ -395,31 +432,29 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
     for (int64_t g = blockIdx.x; g < ntiles; g += gridDim.x) {
         const int64_t e = 2 * g + el;
         const bool active = e < A.E;
-        // ---- gather u along the t-line (ti, tj); the factors load meanwhile
-        int gid[n];
-        double u[n];
+        // ---- gather u at the thread's nodes; the factors load meanwhile
+        int gid[KH];
+        double u[KH];
         const int32_t *lg = A.l2g + e * n3 + a;
 #pragma unroll
-        for (int k = 0; k < n; k++) gid[k] = active ? __ldcs(lg + k * n2) : -1;
+        for (int q = 0; q < KH; q++) gid[q] = active ? __ldcs(lg + (k0 + q) * n2) : -1;
 #pragma unroll
-        for (int k = 0; k < n; k++) u[k] = gid[k] >= 0 ? __ldg(A.x + gid[k]) : 0.0;
-        double G[n][6];
+        for (int q = 0; q < KH; q++) u[q] = gid[q] >= 0 ? __ldg(A.x + gid[q]) : 0.0;
+        double G[KH][6];
         const double *ge = A.geo + e * 7 * n3 + a;
 #pragma unroll
-        for (int k = 0; k < n; k++)
+        for (int q = 0; q < KH; q++)
 #pragma unroll
-            for (int c = 0; c < 6; c++) G[k][c] = active ? __ldcs(ge + k * 7 * n2 + c * n2) : 0.0;
+            for (int c = 0; c < 6; c++) G[q][c] = active ? __ldcs(ge + (k0 + q) * 7 * n2 + c * n2) : 0.0;
         unsigned em = 0;
 #pragma unroll
-        for (int k = 0; k < n; k++) em = max(em, exp_bits(u[k]));
-        warp_max_to_smem(em, wexp);
-        __syncthreads();
-        const unsigned eu = max(wexp[2 * el], wexp[2 * el + 1]);
+        for (int q = 0; q < KH; q++) em = max(em, exp_bits(u[q]));
+        const unsigned eu = element_max(em, wexp, el);
         {
-            long long X[n];
+            long long X[KH];
 #pragma unroll
-            for (int k = 0; k < n; k++) X[k] = eu == 0x7FFu ? 0 : to_fixed(u[k], eu);
-            stage(Ab, el, ti, tj, X, 7);
+            for (int q = 0; q < KH; q++) X[q] = eu == 0x7FFu ? 0 : to_fixed(u[q], eu);
+            stage(Ab, el, ti, tj, k0, X, 7);
         }
         hbtc::fence_async_smem();
         hbtc::fence_before_sync();
@@ -433,13 +468,13 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
         if (!tc_wait(bar, phase, A.err)) gave_up = 1;
         phase ^= 1u;
         hbtc::fence_after_sync();
-        const int goff = (int)eu - 1075 - dshift;
+        const int goff = (int)eu - 1075 - dshift + 40;
         const bool ubad = eu == 0x7FFu;
-        double gt[n];
+        double gt[KH];
 #pragma unroll
         for (int dir = 0; dir < 3; dir++) {
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
+            for (int c = 0; c < 2; c++) {
                 uint32_t v[16];
                 hbtc::tmem_ld16(tl + dir * 64 + c * 16, v);
                 hbtc::tmem_wait_ld(v);
@@ -447,44 +482,41 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
                 for (int o = 0; o < 2; o++) {
                     long long hi, lo;
                     combine(v, o, hi, lo);
-                    const double gv = ubad ? __longlong_as_double(0x7FF8000000000000ll)
-                                           : i2d_scaled(hi, goff + 72) + i2d_scaled(lo, goff + 40);
-                    const int out = 2 * c + o;
-                    // lane tid: r row (el, k, j) = tid, s row (el, k, i) = tid, t row (el, j, i) = tid
-                    if (dir == 0) ExR[xq(el, out, tid & 7, (tid >> 3) & 7)] = gv;
-                    else if (dir == 1) ExS[xq(el, tid & 7, out, (tid >> 3) & 7)] = gv;
-                    else gt[out] = gv;
+                    const double gv = ubad ? __longlong_as_double(0x7FF8000000000000ll) : halves_to_double(hi, lo, goff);
+                    const int out = k0 + 2 * c + o;
+                    // lane tau: r row (el, k, j), s row (el, k, i), t row (el, j, i)
+                    if (dir == 0) ExR[xq(el, out, tau & 7, (tau >> 3) & 7)] = gv;
+                    else if (dir == 1) ExS[xq(el, tau & 7, out, (tau >> 3) & 7)] = gv;
+                    else gt[2 * c + o] = gv;
                 }
             }
         }
         hbtc::fence_before_sync();
         __syncthreads();
-        // ---- metric (FP64): v = G grad at the t-line's nodes
-        double vr[n], vs[n], vt[n];
+        // ---- metric (FP64): v = G grad at the thread's nodes
+        double vr[KH], vs[KH], vt[KH];
         unsigned evm = 0;
 #pragma unroll
-        for (int k = 0; k < n; k++) {
-            const int q = xq(el, ti, tj, k);
-            const double ur = ExR[q], us = ExS[q], ut = gt[k];
-            vr[k] = fma(G[k][2], ut, fma(G[k][1], us, G[k][0] * ur));
-            vs[k] = fma(G[k][4], ut, fma(G[k][3], us, G[k][1] * ur));
-            vt[k] = fma(G[k][5], ut, fma(G[k][4], us, G[k][2] * ur));
-            evm = max(evm, max(exp_bits(vr[k]), max(exp_bits(vs[k]), exp_bits(vt[k]))));
+        for (int q = 0; q < KH; q++) {
+            const int xi = xq(el, ti, tj, k0 + q);
+            const double ur = ExR[xi], us = ExS[xi], ut = gt[q];
+            vr[q] = fma(G[q][2], ut, fma(G[q][1], us, G[q][0] * ur));
+            vs[q] = fma(G[q][4], ut, fma(G[q][3], us, G[q][1] * ur));
+            vt[q] = fma(G[q][5], ut, fma(G[q][4], us, G[q][2] * ur));
+            evm = max(evm, max(exp_bits(vr[q]), max(exp_bits(vs[q]), exp_bits(vt[q]))));
         }
-        warp_max_to_smem(evm, wexp);
-        __syncthreads();
-        const unsigned ev = max(wexp[2 * el], wexp[2 * el + 1]);
+        const unsigned ev = element_max(evm, wexp, el);
         {
-            long long X[n];
+            long long X[KH];
 #pragma unroll
-            for (int k = 0; k < n; k++) X[k] = ev == 0x7FFu ? 0 : to_fixed(vr[k], ev);
-            stage(Ab, el, ti, tj, X, 1);
+            for (int q = 0; q < KH; q++) X[q] = ev == 0x7FFu ? 0 : to_fixed(vr[q], ev);
+            stage(Ab, el, ti, tj, k0, X, 1);
 #pragma unroll
-            for (int k = 0; k < n; k++) X[k] = ev == 0x7FFu ? 0 : to_fixed(vs[k], ev);
-            stage(Ab, el, ti, tj, X, 2);
+            for (int q = 0; q < KH; q++) X[q] = ev == 0x7FFu ? 0 : to_fixed(vs[q], ev);
+            stage(Ab, el, ti, tj, k0, X, 2);
 #pragma unroll
-            for (int k = 0; k < n; k++) X[k] = ev == 0x7FFu ? 0 : to_fixed(vt[k], ev);
-            stage(Ab, el, ti, tj, X, 4);
+            for (int q = 0; q < KH; q++) X[q] = ev == 0x7FFu ? 0 : to_fixed(vt[q], ev);
+            stage(Ab, el, ti, tj, k0, X, 4);
         }
         hbtc::fence_async_smem();
         hbtc::fence_before_sync();
@@ -501,7 +533,7 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
 #pragma unroll
         for (int dir = 0; dir < 2; dir++) {
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
+            for (int c = 0; c < 2; c++) {
                 uint32_t v[16];
                 hbtc::tmem_ld16(tl + dir * 64 + c * 16, v);
                 hbtc::tmem_wait_ld(v);
@@ -509,13 +541,13 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
                 for (int o = 0; o < 2; o++) {
                     long long hi, lo;
                     combine(v, o, hi, lo);
-                    const int out = 2 * c + o;
+                    const int out = k0 + 2 * c + o;
                     if (dir == 0) {
-                        const int q = xq(el, out, tid & 7, (tid >> 3) & 7);
+                        const int q = xq(el, out, tau & 7, (tau >> 3) & 7);
                         Yhi[q] = hi;
                         Ylo[q] = lo;
                     } else {
-                        const int q = xq(el, tid & 7, out, (tid >> 3) & 7);
+                        const int q = xq(el, tau & 7, out, (tau >> 3) & 7);
                         Yhi[q] += hi;
                         Ylo[q] += lo;
                     }
@@ -524,13 +556,13 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
             __syncthreads();
         }
         {
-            const int yoff = (int)ev - 1075 - dshift;
+            const int yoff = (int)ev - 1075 - dshift + 40;
             const bool vbad = ev == 0x7FFu;
             double *ys = A.ysurf + e * NS;
             const bool ring = ti == 0 || ti == N || tj == 0 || tj == N;
             const int r = ring ? ring_index7(ti, tj) : 0;
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
+            for (int c = 0; c < 2; c++) {
                 uint32_t v[16];
                 hbtc::tmem_ld16(tl + 2 * 64 + c * 16, v);
                 hbtc::tmem_wait_ld(v);
@@ -538,12 +570,11 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
                 for (int o = 0; o < 2; o++) {
                     long long hi, lo;
                     combine(v, o, hi, lo);
-                    const int k = 2 * c + o;
-                    const int q = xq(el, ti, tj, k);
-                    hi += Yhi[q];
-                    lo += Ylo[q];
-                    const double yc = vbad ? __longlong_as_double(0x7FF8000000000000ll)
-                                           : i2d_scaled(hi, yoff + 72) + i2d_scaled(lo, yoff + 40);
+                    const int qq = 2 * c + o, k = k0 + qq;
+                    const int xi = xq(el, ti, tj, k);
+                    hi += Yhi[xi];
+                    lo += Ylo[xi];
+                    const double yc = vbad ? __longlong_as_double(0x7FF8000000000000ll) : halves_to_double(hi, lo, yoff);
                     if (!active) continue;
                     if (k == 0) {
                         ys[a] = yc;
@@ -553,18 +584,17 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
                         ys[2 * n2 + (k - 1) * 4 * N + r] = yc;
                     } else {
                         // element-interior node: its DOF has no other copy
-                        const double xv = u[k];
+                        const double xv = u[qq];
                         const double jw = A.screen ? __ldg(A.geo + (e * n + k) * 7 * n2 + 6 * n2 + a) : 1.0;
                         double yy = yc;
                         yy += A.lambda * (jw * xv);
-                        A.y[gid[k]] = yy;
+                        A.y[gid[qq]] = yy;
                         acc.add(xv, yy);
                     }
                 }
             }
         }
         hbtc::fence_before_sync();
-        __syncthreads();
         if (__syncthreads_or(gave_up)) break;
     }
     if (A.partials) {
