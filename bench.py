@@ -314,11 +314,42 @@ def run_gb300(args, rank, world, local):
     # scaled to this launch by local nodes; only for the captured (degree,
     # variant) pairs.
     per_node = {(7, 3): 64.77, (7, 11): 64.66, (7, 67): 67.53, (7, 75): 67.42, (7, 131): 62.33,
-                (7, 139): 62.38}.get((N, variant))
+                (7, 139): 62.38, (7, 256): 64.70}.get((N, variant))
     traffic = per_node * NL if per_node else None
     ax_flops = acc.op_local_flops(E, N)
     ax_bytes = acc.ax_local_bytes(NG, NL, 8)
     achieved_tf = ax_flops / (ax["ms_avg"] * 1e-3) / 1e12
+    achieved_gbs = ax_bytes / (ax["ms_avg"] * 1e-3) / 1e9
+    hbm_view = {"algorithmic_bytes_per_launch": ax_bytes, "achieved_gbs": achieved_gbs,
+                "peak_gbs": pk["hbm_gbs"], "peak_src": pk["hbm_src"], "frac": achieved_gbs / pk["hbm_gbs"]}
+    if variant == hb.HB_VARIANT_TC:
+        # tensor-core element kernel: the contractions run on the tensor cores,
+        # so its roof is HBM; the FP64 work left on the CUDA cores (the metric
+        # step, 15 n^3 flops per element) is shown against the FP64 pipe
+        metric_flops = 15 * (N + 1) ** 3 * E
+        metric_tf = metric_flops / (ax["ms_avg"] * 1e-3) / 1e12
+        roofline = {"bound": "hbm", "kernel": "ax_local (FP64, tensor-core contractions)",
+                    "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved_gbs / pk["hbm_gbs"], "peak_src": pk["hbm_src"],
+                    "bytes_per_launch": ax_bytes, "ms_per_launch": ax["ms_avg"],
+                    "bytes_note": "algorithmic bytes esz N_G + (4 + 7 esz) N_L: x once, node map, six "
+                                  "metric factors, the element-local result once",
+                    "traffic": traffic,
+                    "traffic_note": "ncu dram bytes (read+write) per launch, scaled from a 32x32x30 capture",
+                    "fp64_view": {"metric_flops_per_launch": metric_flops, "achieved_tflops": metric_tf,
+                                  "peak_tflops": pk["fp64_tflops"],
+                                  "frac": metric_tf / pk["fp64_tflops"]},
+                    "flops_view": {"algorithmic_flops_per_launch": ax_flops, "achieved_tflops": achieved_tf}}
+    else:
+        roofline = {"bound": "alu", "kernel": "ax_local (FP64)", "achieved": achieved_tf,
+                    "peak": pk["fp64_tflops"], "unit": "TFLOP/s", "frac": achieved_tf / pk["fp64_tflops"],
+                    "peak_src": "derived: 2 FP64 FMA/clk/SM (measured probe) x 152 SMs x 2070 MHz",
+                    "flops_per_launch": ax_flops, "ms_per_launch": ax["ms_avg"],
+                    "flops_note": "algorithmic flops E(12n^4+15n^3) of the dense contractions; the kernel's "
+                                  "even-odd split of D executes fewer FP64 operations, so frac can pass 1",
+                    "traffic": traffic,
+                    "traffic_note": "ncu dram bytes (read+write) per launch, scaled from a 32x32x30 capture",
+                    "hbm_view": hbm_view}
     out = {
         "metric": "Ax GDOF/s (FP64; one CG iteration = one A x and its fused vector stage)",
         "value": aggregate_rate(world, NG * args.steps, t_max) / 1e9,
@@ -339,18 +370,7 @@ def run_gb300(args, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": f"inputs larger than L2: {7 * 8 * NL / 1e9:.1f} GB of geometric factors streamed "
                          f"per step (L2 129 MB)"},
-        "roofline": {"bound": "alu", "kernel": "ax_local (FP64)", "achieved": achieved_tf,
-                     "peak": pk["fp64_tflops"], "unit": "TFLOP/s", "frac": achieved_tf / pk["fp64_tflops"],
-                     "peak_src": "derived: 2 FP64 FMA/clk/SM (measured probe) x 152 SMs x 2070 MHz",
-                     "flops_per_launch": ax_flops, "ms_per_launch": ax["ms_avg"],
-                     "flops_note": "algorithmic flops E(12n^4+15n^3) of the dense contractions; the kernel's "
-                                   "even-odd split of D executes fewer FP64 operations, so frac can pass 1",
-                     "traffic": traffic,
-                     "traffic_note": "ncu dram bytes (read+write) per launch, scaled from a 32x32x30 capture",
-                     "hbm_view": {"algorithmic_bytes_per_launch": ax_bytes,
-                                  "achieved_gbs": ax_bytes / (ax["ms_avg"] * 1e-3) / 1e9,
-                                  "peak_gbs": pk["hbm_gbs"], "peak_src": pk["hbm_src"],
-                                  "frac": ax_bytes / (ax["ms_avg"] * 1e-3) / 1e9 / pk["hbm_gbs"]}},
+        "roofline": roofline,
         "kernels": kern,
         "ax_only_gdofs": NG / ((kern["ax_local"]["ms_avg"] + kern["assemble"]["ms_avg"]) * 1e-3) / 1e9,
         "fom_gflops_nekbone": acc.nekbone_flops(E, N) * args.steps / (t_max * 1e-3) / 1e9,
