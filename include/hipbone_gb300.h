@@ -457,7 +457,7 @@ double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx);
  *                         per lattice row sums each DOF's copies in ascending
  *                         element order, as the CSR does, so y is bitwise the
  *                         same as with the other pencil variants.
- *   HB_VARIANT_TC         (alone; HB_F64 at N = 7) the tensor-core element kernel:
+ *   HB_VARIANT_TC         (alone or with CSR; HB_F64 at N = 7) the tensor-core element kernel:
  *                         every derivative contraction (D and D^T along r, s, t) runs
  *                         on the tensor cores (tcgen05.mma, FP16 inputs, FP32
  *                         accumulators in tensor memory) exactly, on an
@@ -469,7 +469,8 @@ double hb_u01(uint64_t seed, uint64_t stream, uint64_t idx);
  *                         2^-53 of the element's largest |value| times sum |D|,
  *                         the FP64 rounding level; an element holding a
  *                         non-finite value gives NaN. Same surface store and
- *                         gather as the pencil kernels.
+ *                         gather as the pencil kernels (with CSR: the CSR-position
+ *                         store and contiguous gather).
  * Each of HB_F64, HB_F32 and HB_F64X keeps its own variant. HB_F64X takes
  * PENCIL | EVEN_ODD with or without ONE, and with CSR or GRID or neither (the
  * six shapes its double-float kernel is built in); other variants return
@@ -487,8 +488,8 @@ hb_status hb_get_kernel_variant(const hb_mesh *mesh, hb_precision prec, int *var
  * x.y reduction a CG iteration fuses into it (p.Ap), for each
  * variant (0, PENCIL, PENCIL|EVEN_ODD, PENCIL|EB2, PENCIL|EVEN_ODD|EB2,
  * PENCIL|EVEN_ODD|ONE, PENCIL|EVEN_ODD|TMA, PENCIL|EVEN_ODD|WS, PENCIL|EVEN_ODD|CSR,
- * PENCIL|EVEN_ODD|ONE|CSR, PENCIL|EVEN_ODD|GRID, PENCIL|EVEN_ODD|ONE|GRID, and TC
- * for HB_F64 at N = 7; for HB_F64X the six it takes) on `stream`, keeps the
+ * PENCIL|EVEN_ODD|ONE|CSR, PENCIL|EVEN_ODD|GRID, PENCIL|EVEN_ODD|ONE|GRID, and TC,
+ * TC|CSR for HB_F64 at N = 7; for HB_F64X the six it takes) on `stream`, keeps the
  * fastest for `prec` (HB_F64, HB_F32 or HB_F64X) on this mesh and returns it in
  * *best_variant. ms_per_variant (may be NULL) has 512 slots
  * indexed by variant and receives the mean time of each. Allocates two scratch vectors for the
@@ -523,9 +524,11 @@ hb_status hb_profile_read(const char *name, double *total_ms, long long *launche
  *   HB_PROBE_COPY          16-byte vector copy
  *   HB_PROBE_FMA           independent FMA chains in `prec`
  *   HB_PROBE_DMMA          FP64 warp matrix multiply-accumulate (mma.sync m8n8k4)
- *   HB_PROBE_DMMA_FMA      the two above interleaved in one loop (prec ignored) */
+ *   HB_PROBE_DMMA_FMA      the two above interleaved in one loop (prec ignored)
+ *   HB_PROBE_CVT64         int64 -> FP64 -> int64 conversion chains; *rate in
+ *                          G conversions/s (prec ignored) */
 enum { HB_PROBE_STREAM81_FP = 0, HB_PROBE_STREAM81_BITS = 1, HB_PROBE_COPY = 2, HB_PROBE_FMA = 3,
-       HB_PROBE_DMMA = 4, HB_PROBE_DMMA_FMA = 5 };
+       HB_PROBE_DMMA = 4, HB_PROBE_DMMA_FMA = 5, HB_PROBE_CVT64 = 6 };
 hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int reps, double *rate);
 
 /* Self-test of the bounded device waits (every wait in this library's

@@ -57,7 +57,7 @@ def store(cache: dict, path: str | None = None) -> None:
 def lookup(cache: dict, dev: str, N: int, prec: int, exclude: int = 0):
     e = cache.get(dev, {}).get(entry_key(N, prec, exclude))
     valid = hb.VARIANTS_F64X if prec == hb.HB_F64X else (
-        hb.VARIANTS + [hb.HB_VARIANT_TC] if prec == hb.HB_F64 and N == 7 else hb.VARIANTS)
+        hb.VARIANTS + hb.VARIANTS_TC if prec == hb.HB_F64 and N == 7 else hb.VARIANTS)
     if isinstance(e, dict) and e.get("variant") in valid and not (e["variant"] & exclude):
         return e["variant"]
     return None

@@ -271,15 +271,17 @@ hb_status hb_apply_A_impl(const hb_mesh *m, hb_precision prec, int screen, doubl
                                             screen, lambda, partials ? nblk : 0, st, dot_mode, s, (ebm & 8) != 0);
     }
     const int v = m->variant[hb_variant_slot(prec)];
-    if (v == HB_VAR_TC) {
+    if (v & HB_VAR_TC) {
         if (prec != HB_F64) { hb_set_error("the tensor-core element kernel is FP64 only"); return HB_ERR_ARG; }
+        const bool csr = (v & HB_VAR_CSR) != 0;
+        if (csr && !m->spos) { hb_set_error("surface positions missing for variant %d", v); return HB_ERR_ARG; }
         double *partials = dot_mode != HB_DOT_NONE ? m->ax_partials : nullptr;
         int64_t nblk = 0;
         hb_status r = hb_launch_ax_tc_f64(m, (const double *)x, (double *)m->yL, (double *)y, lambda, screen,
-                                          partials, run, s, &nblk);
+                                          partials, run, csr, s, &nblk);
         if (r != HB_OK) return r;
         return launch_assemble_surf<double>(m, (const double *)m->yL, (const double *)x, (double *)y, m->mdiag,
-                                            screen, lambda, partials ? nblk : 0, st, dot_mode, s, false);
+                                            screen, lambda, partials ? nblk : 0, st, dot_mode, s, csr);
     }
     const int eo = (v & HB_VAR_EO) ? 1 : 0, ebm = hb_variant_eb_mode(v);
     if ((ebm & 8) && !m->spos) { hb_set_error("surface positions missing for variant %d", v); return HB_ERR_ARG; }
@@ -352,7 +354,7 @@ extern "C" hb_status hb_set_kernel_variant(hb_mesh *m, hb_precision prec, int va
         hb_set_error("invalid kernel variant %d for precision %d", variant, (int)prec);
         return HB_ERR_ARG;
     }
-    if (variant == HB_VAR_TC && (prec != HB_F64 || m->N != 7)) {
+    if ((variant & HB_VAR_TC) && (prec != HB_F64 || m->N != 7)) {
         hb_set_error("the tensor-core element kernel (variant %d) is built for HB_F64 at N = 7", HB_VAR_TC);
         return HB_ERR_ARG;
     }
@@ -468,7 +470,8 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
                               HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_CSR,
                               HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE | HB_VAR_CSR,
                               HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_GRID,
-                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE | HB_VAR_GRID, HB_VAR_TC};
+                              HB_VAR_PENCIL | HB_VAR_EO | HB_VAR_ONE | HB_VAR_GRID, HB_VAR_TC,
+                              HB_VAR_TC | HB_VAR_CSR};
     {
         hb_status sp = hb_mesh_ensure_spos(m, s);
         if (sp != HB_OK) {
@@ -485,7 +488,7 @@ extern "C" hb_status hb_autotune(hb_mesh *m, hb_precision prec, hb_screen screen
     // variants differ in where that work runs (element kernel or gather)
     hb_cg_state *tmp = m->state + 1;
     for (int c : candidates) {
-        if (c == HB_VAR_TC && (prec != HB_F64 || m->N != 7)) continue;
+        if ((c & HB_VAR_TC) && (prec != HB_F64 || m->N != 7)) continue;
         if (prec == HB_F64X && !hb_valid_variant_f64x(c)) continue;
         m->variant[pi] = c;
         // one untimed application (first launch, attribute setup), then `reps` timed ones

@@ -162,7 +162,8 @@ hb_status hb_ax2_upload_f64x(const double *D_all);
 // Tensor-core FP64 element kernel (N = 7; see HB_VAR_TC) and its tables.
 hb_status hb_tc_upload();
 hb_status hb_launch_ax_tc_f64(const hb_mesh *m, const double *x, double *ysurf, double *y, double lambda,
-                              int screen, double *partials, const int *run, cudaStream_t s, int64_t *nblocks);
+                              int screen, double *partials, const int *run, bool csr_store, cudaStream_t s,
+                              int64_t *nblocks);
 hb_status hb_ax2_upload_f64(const double *D_all);
 hb_status hb_ax2_upload_f32(const double *D_all);
 
@@ -178,14 +179,14 @@ hb_status hb_ax2_upload_f32(const double *D_all);
 // HB_VAR_GRID = every local value stored element-major and Z^T taken by the
 // box's lattice arithmetic, one warp per lattice row (with PENCIL | EO, alone
 // or with ONE).
-// HB_VAR_TC = the tensor-core element kernel (alone; FP64, N = 7): every
-// derivative contraction exact on tcgen05 from FP16 digit slices, the metric
-// step in FP64.
+// HB_VAR_TC = the tensor-core element kernel (alone or with HB_VAR_CSR; FP64,
+// N = 7): every derivative contraction exact on tcgen05 from FP16 digit
+// slices, the metric step in FP64.
 enum { HB_VAR_PENCIL = 1, HB_VAR_EO = 2, HB_VAR_EB2 = 4, HB_VAR_ONE = 8, HB_VAR_TMA = 16, HB_VAR_WS = 32,
        HB_VAR_CSR = 64, HB_VAR_GRID = 128, HB_VAR_MAX = 255, HB_VAR_TC = 256 };
 static inline bool hb_valid_variant(int v)
 {
-    if (v == 0 || v == HB_VAR_TC) return true;
+    if (v == 0 || v == HB_VAR_TC || v == (HB_VAR_TC | HB_VAR_CSR)) return true;
     if (v < 0 || v > HB_VAR_MAX || !(v & HB_VAR_PENCIL)) return false;
     const int extra = v & (HB_VAR_ONE | HB_VAR_TMA | HB_VAR_WS | HB_VAR_EB2);
     if (v & HB_VAR_GRID) return !(v & HB_VAR_CSR) && (v & HB_VAR_EO) && (extra == 0 || extra == HB_VAR_ONE);

@@ -85,6 +85,24 @@ __global__ void probe_dmma(double *out, int iters)
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// 64-bit conversions: eight independent chains of int64 -> FP64 -> int64
+// (cvt.rn.f64.s64, cvt.rni.s64.f64), two conversions and one integer add per
+// step: which unit runs them decides whether they compete with FP64 FMAs.
+__global__ void probe_cvt64(double *out, int iters)
+{
+    long long a[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) a[q] = (long long)threadIdx.x * 977 + q;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) a[q] = __double2ll_rn(__ll2double_rn(a[q])) + 3;
+    }
+    long long s = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) s += a[q];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = (double)s;
+}
+
 }  // namespace
 
 extern "C" hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int reps, double *rate)
@@ -98,7 +116,8 @@ extern "C" hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int rep
     const size_t esz = prec == HB_F64 ? 8 : 4;
     void *buf = nullptr;
     size_t alloc = bytes;
-    if (kind == HB_PROBE_FMA || kind == HB_PROBE_DMMA || kind == HB_PROBE_DMMA_FMA) alloc = (size_t)grid * threads * 8;
+    if (kind == HB_PROBE_FMA || kind == HB_PROBE_DMMA || kind == HB_PROBE_DMMA_FMA || kind == HB_PROBE_CVT64)
+        alloc = (size_t)grid * threads * 8;
     if (alloc < 4096) alloc = 4096;
     HB_TRY_CUDA(cudaMalloc(&buf, alloc));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -137,6 +156,10 @@ extern "C" hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int rep
                 probe_dmma<false><<<grid, threads>>>((double *)buf, iters);
             else
                 probe_dmma<true><<<grid, threads>>>((double *)buf, iters);
+        } else if (kind == HB_PROBE_CVT64) {
+            const int iters = 1024;
+            work = 2.0 * 8 * iters * (double)grid * threads;  // conversions
+            probe_cvt64<<<grid, threads>>>((double *)buf, iters);
         } else {
             const int iters = 4096;
             work = 2.0 * 8 * iters * (double)grid * threads;
@@ -148,7 +171,7 @@ extern "C" hb_status hb_probe(int kind, hb_precision prec, size_t bytes, int rep
         hb_count_launch();
     };
     float best = 1e30f;
-    if (kind < HB_PROBE_STREAM81_FP || kind > HB_PROBE_DMMA_FMA) {
+    if (kind < HB_PROBE_STREAM81_FP || kind > HB_PROBE_CVT64) {
         hb_set_error("unknown probe kind %d", kind);
         e = cudaErrorInvalidValue;
     }

@@ -225,6 +225,7 @@ struct tc_args {
     int screen;
     double *partials;
     unsigned *err;
+    const int32_t *spos;  // SP kernels: CSR position of every surface copy (-1 masked)
 };
 
 // node (i, j, k) of element el in the padded exchange buffers
@@ -236,69 +237,62 @@ __device__ __forceinline__ unsigned exp_bits(double v)
 }
 
 // v on the grid of unit 2^(emax - 1075): round(|v| / unit) with the sign of v
-// (|result| < 2^53; zero and subnormal v give 0).
+// (|result| < 2^53; zero and subnormal v give 0). Integer instructions only:
+// 64-bit conversions run at the FP64 rate on this GPU.
 __device__ __forceinline__ long long to_fixed(double v, unsigned emax)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
-    if (e == 0) return 0;
-    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const unsigned sh = emax - e;
-    long long X;
-    if (sh == 0) X = (long long)m;
-    else if (sh > 53) X = 0;
-    else X = (long long)((m + (1ull << (sh - 1))) >> sh);
+    const unsigned long long m = e ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+    const unsigned sh = min(emax - e, 62u);
+    // round(m / 2^sh) = floor((2m + 2^sh) / 2^(sh+1)), also for sh = 0
+    const long long X = (long long)(((m << 1) + (1ull << sh)) >> (sh + 1));
     return (b >> 63) ? -X : X;
 }
 
-// (H 2^32 + L) 2^off as a double, rounded to nearest (ties to even), for
-// |H| < 2^42: the magnitude is split into a 64-bit top word and 32 low bits,
-// the top 53 bits kept and the rest decide the rounding. Results below the
-// normal range flush to zero, above it give infinity.
-__device__ __forceinline__ double fix96_to_double(long long H, unsigned L, int off)
+// T 2^off as a double, rounded to nearest (ties away from zero) from the
+// integer T (any int64): normalise |T| so its top bit is bit 63, keep 53 bits,
+// round on the 11 below, and let a carry out of the mantissa step into the
+// exponent. Results below the normal range flush to zero, above it give
+// infinity.
+__device__ __forceinline__ double i64_to_double(long long T, int off)
 {
-    const bool neg = H < 0;
-    const unsigned long long mh = neg ? (unsigned long long)(-H) - (L != 0u ? 1ull : 0ull) : (unsigned long long)H;
-    const unsigned ml = neg ? 0u - L : L;
-    unsigned long long W;
-    int ex;
-    if (mh < (1ull << 21)) {
-        // below 2^53: exact
-        W = (mh << 32) | ml;
-        if (W == 0) return 0.0;
-        const int lz = __clzll((long long)W);
-        W <<= (lz - 11);
-        ex = 1086 - lz + off;
-    } else {
-        const int lz = __clzll((long long)mh);  // 22 .. 42
-        int sh = 43 - lz;                        // 1 .. 21 bits below the kept 53
-        W = (mh << (32 - sh)) | (ml >> sh);
-        const unsigned rem = ml & ((1u << sh) - 1u), half = 1u << (sh - 1);
-        if (rem > half || (rem == half && (W & 1ull))) W += 1ull;
-        if (W >> 53) {
-            W >>= 1;
-            sh += 1;
-        }
-        ex = 1075 + sh + off;
-    }
-    const unsigned long long sgn = neg ? 0x8000000000000000ull : 0ull;
+    if (T == 0) return 0.0;
+    const unsigned long long sgn = (unsigned long long)T & 0x8000000000000000ull;
+    unsigned long long M = T < 0 ? 0ull - (unsigned long long)T : (unsigned long long)T;
+    const int lz = __clzll((long long)M);
+    M <<= lz;
+    const unsigned long long mant = (M >> 11) + ((M >> 10) & 1ull);  // 2^52 .. 2^53
+    const int ex = 1023 + 63 - lz + off;
     if (ex <= 0) return __longlong_as_double((long long)sgn);
     if (ex >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | (W & 0xFFFFFFFFFFFFFull)));
+    return __longlong_as_double((long long)(sgn | (((unsigned long long)(ex - 1) << 52) + mant)));
 }
 
-// FP16 bit patterns of the seven digits of X as the MMA takes them.
-__device__ __forceinline__ void digits_of(long long X, uint16_t (&h)[7])
+// 2^off (2^32 hi + lo) as a double: exactly as one int64 while that fits
+// (|hi| < 2^30), else from its value / 2^10 rounded down (the dropped bits
+// are below 2^-53 of a value of at least 2^63).
+__device__ __forceinline__ double halves_to_double(long long hi, long long lo, int off)
 {
-    const int hi = (int)(X >> 32);
-    const unsigned lo = (unsigned)X;
-    h[0] = (uint16_t)(0x5C00u | ((unsigned)(128 + (hi >> 16)) << 2));
-    h[1] = (uint16_t)(0x5C00u | ((((unsigned)hi >> 8) & 0xFFu) << 2));
-    h[2] = (uint16_t)(0x5C00u | (((unsigned)hi & 0xFFu) << 2));
-    h[3] = (uint16_t)(0x5C00u | ((lo >> 24) << 2));
-    h[4] = (uint16_t)(0x5C00u | (((lo >> 16) & 0xFFu) << 2));
-    h[5] = (uint16_t)(0x5C00u | (((lo >> 8) & 0xFFu) << 2));
-    h[6] = (uint16_t)(0x5C00u | ((lo & 0xFFu) << 2));
+    const bool small = (unsigned long long)(hi + (1ll << 30)) < (1ull << 31);
+    return small ? i64_to_double((long long)((unsigned long long)hi << 32) + lo, off)
+                 : i64_to_double((long long)((unsigned long long)hi << 22) + (lo >> 10), off + 10);
+}
+
+// FP16 bit patterns of digit d of two values (a in the low half, b in the
+// high half of the result): digit d is byte (6 - d) of X on the little-endian
+// 64-bit word (bytes 0..5 for d = 6..1, byte 6 signed for d = 0); the MMA
+// takes digit u as the FP16 number 256 + u (384 + u_0 for d = 0), bit pattern
+// 0x5C00 | (u << 2).
+__device__ __forceinline__ unsigned digit_pair(long long Xa, long long Xb, int d)
+{
+    const int byte = 6 - d;
+    const unsigned wa = byte >= 4 ? (unsigned)((unsigned long long)Xa >> 32) : (unsigned)Xa;
+    const unsigned wb = byte >= 4 ? (unsigned)((unsigned long long)Xb >> 32) : (unsigned)Xb;
+    const unsigned p = (unsigned)(byte & 3);
+    unsigned w = __byte_perm(wa, wb, p | ((4u + p) << 8)) & 0x00FF00FFu;
+    if (d == 0) w ^= 0x00800080u;  // u_0 + 128 for the signed leading digit
+    return (w << 2) | 0x5C005C00u;
 }
 
 // A operand rows (K-major, row chunk stride 128 bytes, K block stride 2048):
@@ -314,21 +308,15 @@ __device__ __forceinline__ unsigned char *arow(unsigned char *Ab, int dir, int b
 __device__ __forceinline__ void stage(unsigned char *Ab, int el, int ti, int tj, int k0, const long long (&X)[KH],
                                       int dirs)
 {
-    uint16_t h[KH][7];
-#pragma unroll
-    for (int q = 0; q < KH; q++) digits_of(X[q], h[q]);
 #pragma unroll
     for (int d = 0; d < 7; d++) {
-        if (dirs & 4) {
-            uint2 v;
-            v.x = (unsigned)h[0][d] | ((unsigned)h[1][d] << 16);
-            v.y = (unsigned)h[2][d] | ((unsigned)h[3][d] << 16);
-            *reinterpret_cast<uint2 *>(arow(Ab, 2, d, el, tj, ti, k0)) = v;
-        }
+        const unsigned w01 = digit_pair(X[0], X[1], d), w23 = digit_pair(X[2], X[3], d);
+        if (dirs & 4) *reinterpret_cast<uint2 *>(arow(Ab, 2, d, el, tj, ti, k0)) = make_uint2(w01, w23);
+        const uint16_t h[KH] = {(uint16_t)w01, (uint16_t)(w01 >> 16), (uint16_t)w23, (uint16_t)(w23 >> 16)};
 #pragma unroll
         for (int q = 0; q < KH; q++) {
-            if (dirs & 1) *reinterpret_cast<uint16_t *>(arow(Ab, 0, d, el, k0 + q, tj, ti)) = h[q][d];
-            if (dirs & 2) *reinterpret_cast<uint16_t *>(arow(Ab, 1, d, el, k0 + q, ti, tj)) = h[q][d];
+            if (dirs & 1) *reinterpret_cast<uint16_t *>(arow(Ab, 0, d, el, k0 + q, tj, ti)) = h[q];
+            if (dirs & 2) *reinterpret_cast<uint16_t *>(arow(Ab, 1, d, el, k0 + q, ti, tj)) = h[q];
         }
     }
 }
@@ -352,20 +340,20 @@ __device__ __forceinline__ void issue(unsigned tmem, const unsigned char *Ab, co
 // as the halves hi = sum_{t<4} S_t 256^(3-t), lo = sum_{t>=4} S_t 256^(7-t):
 // the output is 2^72 hi + 2^40 lo in units of the element's grid times 2^-s.
 // Each S_t is an integer below 2^22 in magnitude, read exactly from its float
-// by adding 1.5 2^23.
+// f as bits(f + 1.5 2^23) - 0x4B400000.
 __device__ __forceinline__ void combine(const uint32_t (&v)[16], int o, long long &hi, long long &lo)
 {
-    int S[8];
+    int B[8];
 #pragma unroll
-    for (int t = 0; t < 8; t++) S[t] = __float_as_int(__fadd_rn(__uint_as_float(v[o * 8 + t]), 12582912.0f)) - 0x4B400000;
-    hi = (long long)(S[0] * 256 + S[1]) * 65536 + (long long)(S[2] * 256 + S[3]);
-    lo = (long long)(S[4] * 256 + S[5]) * 65536 + (long long)(S[6] * 256 + S[7]);
-}
-
-// 2^off (2^32 hi + lo) as a double (rounded once).
-__device__ __forceinline__ double halves_to_double(long long hi, long long lo, int off)
-{
-    return fix96_to_double(hi + (lo >> 32), (unsigned)(lo & 0xFFFFFFFFll), off);
+    for (int t = 0; t < 8; t++) B[t] = __float_as_int(__fadd_rn(__uint_as_float(v[o * 8 + t]), 12582912.0f));
+    // S_a 256 + S_b fits an int32: form it modulo 2^32 from the raw bits
+    constexpr unsigned kBias = 0x4B400000u * 257u;
+    const int m0 = (int)((unsigned)B[0] * 256u + (unsigned)B[1] - kBias);
+    const int m1 = (int)((unsigned)B[2] * 256u + (unsigned)B[3] - kBias);
+    const int m2 = (int)((unsigned)B[4] * 256u + (unsigned)B[5] - kBias);
+    const int m3 = (int)((unsigned)B[6] * 256u + (unsigned)B[7] - kBias);
+    hi = (long long)m0 * 65536 + m1;
+    lo = (long long)m2 * 65536 + m3;
 }
 
 __device__ __forceinline__ int ring_index7(int i, int j)
@@ -387,6 +375,7 @@ __device__ __forceinline__ unsigned element_max(unsigned v, unsigned *wexp, int 
 // el = tau / 64; t-line (ti, tj) = (tau % 8, tau / 8 % 8)) and half h = tid / 128:
 // nodes k = 4h .. 4h + 3 of its t-line, outputs 4h .. 4h + 3 of its r-, s-
 // and t-line rows.
+template <bool SP>
 __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
 {
     if (A.run && *A.run == 0) return;
@@ -429,17 +418,30 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
     unsigned phase = 0;
     int gave_up = 0;
     const int64_t ntiles = (A.E + 1) / 2;
+    // node ids and x at the thread's nodes, loaded one tile ahead
+    int gid_n[KH];
+    double u_n[KH];
+    auto gather = [&](int64_t gg) {
+        const int64_t ee = 2 * gg + el;
+        const bool act = gg < ntiles && ee < A.E;
+        const int32_t *lg = A.l2g + ee * n3 + a;
+#pragma unroll
+        for (int q = 0; q < KH; q++) gid_n[q] = act ? __ldcs(lg + (k0 + q) * n2) : -1;
+#pragma unroll
+        for (int q = 0; q < KH; q++) u_n[q] = gid_n[q] >= 0 ? __ldg(A.x + gid_n[q]) : 0.0;
+    };
+    gather(blockIdx.x);
     for (int64_t g = blockIdx.x; g < ntiles; g += gridDim.x) {
         const int64_t e = 2 * g + el;
         const bool active = e < A.E;
-        // ---- gather u at the thread's nodes; the factors load meanwhile
+        // ---- u at the thread's nodes (gathered ahead); the factors load meanwhile
         int gid[KH];
         double u[KH];
-        const int32_t *lg = A.l2g + e * n3 + a;
 #pragma unroll
-        for (int q = 0; q < KH; q++) gid[q] = active ? __ldcs(lg + (k0 + q) * n2) : -1;
-#pragma unroll
-        for (int q = 0; q < KH; q++) u[q] = gid[q] >= 0 ? __ldg(A.x + gid[q]) : 0.0;
+        for (int q = 0; q < KH; q++) {
+            gid[q] = gid_n[q];
+            u[q] = u_n[q];
+        }
         double G[KH][6];
         const double *ge = A.geo + e * 7 * n3 + a;
 #pragma unroll
@@ -473,15 +475,17 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
         double gt[KH];
 #pragma unroll
         for (int dir = 0; dir < 3; dir++) {
+            uint32_t vv[2][16];
+            hbtc::tmem_ld16(tl + dir * 64, vv[0]);
+            hbtc::tmem_ld16(tl + dir * 64 + 16, vv[1]);
+            hbtc::tmem_wait_ld(vv[0]);
+            hbtc::tmem_wait_ld(vv[1]);
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                uint32_t v[16];
-                hbtc::tmem_ld16(tl + dir * 64 + c * 16, v);
-                hbtc::tmem_wait_ld(v);
 #pragma unroll
                 for (int o = 0; o < 2; o++) {
                     long long hi, lo;
-                    combine(v, o, hi, lo);
+                    combine(vv[c], o, hi, lo);
                     const double gv = ubad ? __longlong_as_double(0x7FF8000000000000ll) : halves_to_double(hi, lo, goff);
                     const int out = k0 + 2 * c + o;
                     // lane tau: r row (el, k, j), s row (el, k, i), t row (el, j, i)
@@ -526,21 +530,24 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
             issue(tmem, Ab, Bi + BIMG);
             hbtc::mma_commit(bar);
         }
+        gather(g + gridDim.x);
         // ---- D^T along r and s summed exactly into the exchange buffers, t here
         if (!tc_wait(bar, phase, A.err)) gave_up = 1;
         phase ^= 1u;
         hbtc::fence_after_sync();
 #pragma unroll
         for (int dir = 0; dir < 2; dir++) {
+            uint32_t vv[2][16];
+            hbtc::tmem_ld16(tl + dir * 64, vv[0]);
+            hbtc::tmem_ld16(tl + dir * 64 + 16, vv[1]);
+            hbtc::tmem_wait_ld(vv[0]);
+            hbtc::tmem_wait_ld(vv[1]);
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                uint32_t v[16];
-                hbtc::tmem_ld16(tl + dir * 64 + c * 16, v);
-                hbtc::tmem_wait_ld(v);
 #pragma unroll
                 for (int o = 0; o < 2; o++) {
                     long long hi, lo;
-                    combine(v, o, hi, lo);
+                    combine(vv[c], o, hi, lo);
                     const int out = k0 + 2 * c + o;
                     if (dir == 0) {
                         const int q = xq(el, out, tau & 7, (tau >> 3) & 7);
@@ -561,22 +568,29 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
             double *ys = A.ysurf + e * NS;
             const bool ring = ti == 0 || ti == N || tj == 0 || tj == N;
             const int r = ring ? ring_index7(ti, tj) : 0;
+            uint32_t vv[2][16];
+            hbtc::tmem_ld16(tl + 2 * 64, vv[0]);
+            hbtc::tmem_ld16(tl + 2 * 64 + 16, vv[1]);
+            hbtc::tmem_wait_ld(vv[0]);
+            hbtc::tmem_wait_ld(vv[1]);
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                uint32_t v[16];
-                hbtc::tmem_ld16(tl + 2 * 64 + c * 16, v);
-                hbtc::tmem_wait_ld(v);
 #pragma unroll
                 for (int o = 0; o < 2; o++) {
                     long long hi, lo;
-                    combine(v, o, hi, lo);
+                    combine(vv[c], o, hi, lo);
                     const int qq = 2 * c + o, k = k0 + qq;
                     const int xi = xq(el, ti, tj, k);
                     hi += Yhi[xi];
                     lo += Ylo[xi];
                     const double yc = vbad ? __longlong_as_double(0x7FF8000000000000ll) : halves_to_double(hi, lo, yoff);
                     if (!active) continue;
-                    if (k == 0) {
+                    if (SP && (k == 0 || k == N || ring)) {
+                        // straight to the copy's CSR position (the gather reads contiguous runs)
+                        const int sidx = k == 0 ? a : (k == N ? n2 + a : 2 * n2 + (k - 1) * 4 * N + r);
+                        const int pos = __ldg(A.spos + e * NS + sidx);
+                        if (pos >= 0) A.ysurf[pos] = yc;
+                    } else if (k == 0) {
                         ys[a] = yc;
                     } else if (k == N) {
                         ys[n2 + a] = yc;
@@ -706,7 +720,8 @@ hb_status hb_tc_upload()
 // lambda term, partial of x.y per block), surface values to ysurf for the
 // surface gather. Persistent grid: two blocks per SM at most.
 hb_status hb_launch_ax_tc_f64(const hb_mesh *m, const double *x, double *ysurf, double *y, double lambda,
-                              int screen, double *partials, const int *run, cudaStream_t s, int64_t *nblocks)
+                              int screen, double *partials, const int *run, bool csr_store, cudaStream_t s,
+                              int64_t *nblocks)
 {
     using namespace tcax;
     if (m->N != N) { hb_set_error("the tensor-core element kernel is built for N = 7 only"); return HB_ERR_ARG; }
@@ -716,17 +731,21 @@ hb_status hb_launch_ax_tc_f64(const hb_mesh *m, const double *x, double *ysurf, 
     HB_TRY_CUDA(cudaGetDevice(&dev));
     static int attr_set[64] = {0}, sms[64] = {0};
     if (dev < 0 || dev >= 64) { hb_set_error("device index %d unsupported", dev); return HB_ERR_ARG; }
+    if (csr_store && !m->spos) { hb_set_error("surface positions missing"); return HB_ERR_ARG; }
     if (!attr_set[dev]) {
-        HB_TRY_CUDA(cudaFuncSetAttribute(ax_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+        HB_TRY_CUDA(cudaFuncSetAttribute(ax_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+        HB_TRY_CUDA(cudaFuncSetAttribute(ax_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
         HB_TRY_CUDA(cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev));
         attr_set[dev] = 1;
     }
     const int64_t ntiles = (m->E + 1) / 2;
     const int64_t grid = ntiles < 2 * (int64_t)sms[dev] ? ntiles : 2 * (int64_t)sms[dev];
     if (nblocks) *nblocks = grid;
-    tc_args A{x, m->l2g, m->geo, ysurf, y, m->E, run, lambda, screen, partials, m->counters + 7};
+    tc_args A{x, m->l2g, m->geo, ysurf, y, m->E, run, lambda, screen, partials, m->counters + 7,
+              csr_store ? m->spos : nullptr};
     hb_prof_scope prof("ax_local", s);
-    ax_tc_kernel<<<(unsigned)grid, THREADS, SMEM, s>>>(A);
+    if (csr_store) ax_tc_kernel<true><<<(unsigned)grid, THREADS, SMEM, s>>>(A);
+    else ax_tc_kernel<false><<<(unsigned)grid, THREADS, SMEM, s>>>(A);
     HB_CHECK_LAUNCH();
     return HB_OK;
 }

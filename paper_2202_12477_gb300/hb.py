@@ -229,6 +229,7 @@ HB_VARIANT_PENCIL, HB_VARIANT_EVEN_ODD, HB_VARIANT_EB2, HB_VARIANT_ONE, HB_VARIA
 HB_VARIANT_CSR = 64
 HB_VARIANT_GRID = 128
 HB_VARIANT_TC = 256  # tensor-core element kernel (HB_F64, N = 7)
+VARIANTS_TC = [HB_VARIANT_TC, HB_VARIANT_TC | HB_VARIANT_CSR]  # alone, and with the CSR-position store
 VARIANTS = [0, 1, 3, 5, 7, 11, 19, 35, 67, 75, 131, 139]  # every valid combination of the pencil flags
 VARIANTS_F64X = [3, 11, 67, 75, 131, 139]  # the shapes the double-float kernel is built in
 
@@ -249,11 +250,11 @@ def hb_autotune(h, prec, screen=HB_SCREEN_IDENTITY, lam=0.1, reps=5, stream=None
     best = C.c_int(-1)
     ms = (C.c_double * 512)(*([-1.0] * 512))
     _check(lib().hb_autotune(h, prec, screen, lam, reps, C.byref(best), ms, _stream_ptr(stream)))
-    return best.value, {v: ms[v] for v in VARIANTS + [HB_VARIANT_TC] if ms[v] >= 0}
+    return best.value, {v: ms[v] for v in VARIANTS + VARIANTS_TC if ms[v] >= 0}
 
 
 HB_PROBE_STREAM81_FP, HB_PROBE_STREAM81_BITS, HB_PROBE_COPY, HB_PROBE_FMA = 0, 1, 2, 3
-HB_PROBE_DMMA, HB_PROBE_DMMA_FMA = 4, 5
+HB_PROBE_DMMA, HB_PROBE_DMMA_FMA, HB_PROBE_CVT64 = 4, 5, 6
 
 
 def hb_probe(kind, prec=HB_F64, nbytes=4 << 30, reps=5) -> float:

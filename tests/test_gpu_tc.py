@@ -40,12 +40,13 @@ from oracle import oracle as orc  # noqa: E402
 from paper_2202_12477_gb300 import inputs  # noqa: E402
 
 TC = hb.HB_VARIANT_TC
+TC_VARIANTS = hb.VARIANTS_TC
 
 
-def _pair(dims, rho=0.15, seed=0, faces=0x3F):
+def _pair(dims, rho=0.15, seed=0, faces=0x3F, variant=TC):
     m = hb.Mesh(*dims, 7, perturb=rho, seed=seed, faces=faces, fp32=False)
     o = orc.Mesh(*dims, 7, rho=rho, seed=seed, faces=faces)
-    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, TC)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, variant)
     return m, o
 
 
@@ -63,8 +64,9 @@ def _check(y, y_or, bar=1e-12):
 @pytest.mark.parametrize("dims", [(1, 1, 1), (2, 1, 1), (3, 1, 1), (3, 3, 3), (5, 4, 3)])
 @pytest.mark.parametrize("screen,lam", [(0, 0.1), (1, 0.7), (0, 0.0)])
 @pytest.mark.parametrize("faces", [0x3F, 0x15, 0x00])
-def test_tc_apply_matches_oracle(dims, screen, lam, faces):
-    m, o = _pair(dims, seed=sum(dims) + faces, faces=faces)
+@pytest.mark.parametrize("variant", TC_VARIANTS)
+def test_tc_apply_matches_oracle(dims, screen, lam, faces, variant):
+    m, o = _pair(dims, seed=sum(dims) + faces, faces=faces, variant=variant)
     x = inputs.random_vector(m.n_global, seed=400 + sum(dims))
     y = m.apply_A(_dev(x), lam=lam, screen=screen).cpu().numpy()
     _check(y, o.apply_A(x, lam, screen))
@@ -72,11 +74,12 @@ def test_tc_apply_matches_oracle(dims, screen, lam, faces):
 
 
 @pytest.mark.parametrize("scale", [1e-200, 1e-30, 1.0, 1e30, 1e200])
-def test_tc_apply_any_magnitude(scale):
+@pytest.mark.parametrize("variant", TC_VARIANTS)
+def test_tc_apply_any_magnitude(scale, variant):
     """The fixed-point grid follows each element's largest exponent: results
     keep the FP64 bar at any scale, and across elements of very different
     magnitudes (each element's rounding is relative to its own values)."""
-    m, o = _pair((3, 3, 2), seed=3)
+    m, o = _pair((3, 3, 2), seed=3, variant=variant)
     x = inputs.random_vector(m.n_global, seed=41) * scale
     y = m.apply_A(_dev(x), lam=0.1).cpu().numpy()
     _check(y, o.apply_A(x, 0.1, 0))
@@ -123,15 +126,16 @@ def test_tc_variant_rules():
         with pytest.raises(hb.HBError):
             hb.hb_set_kernel_variant(m.handle, prec, TC)
     v, ms = hb.hb_autotune(m.handle, hb.HB_F64, reps=2)
-    assert TC in ms and v in ms
+    assert all(t in ms for t in TC_VARIANTS) and v in ms
     m.close()
 
 
-def test_tc_cg_follows_oracle():
+@pytest.mark.parametrize("variant", TC_VARIANTS)
+def test_tc_cg_follows_oracle(variant):
     """Config 1 (4x4x4, N = 7): 100 fixed FP64 CG iterations with the
     tensor-core kernel in the launched solver, against the oracle's iterate;
     then a converged solve whose true residual meets the tolerance."""
-    m, o = _pair((4, 4, 4), rho=0.1, seed=0)
+    m, o = _pair((4, 4, 4), rho=0.1, seed=0, variant=variant)
     hb.lib().hb_set_cg_fused(m.handle, 1)
     b = m.rhs(kind=0, seed=0)
     x_or, *_ = o.cg(b.cpu().numpy(), 0.1, rtol=0.0, max_it=100)
@@ -145,13 +149,14 @@ def test_tc_cg_follows_oracle():
     m.close()
 
 
-def test_tc_full_size_sampled_rows():
+@pytest.mark.parametrize("variant", TC_VARIANTS)
+def test_tc_full_size_sampled_rows(variant):
     """The degree-sweep box at N = 7 (64 x 64 x 61, 1.28e8 local nodes), in
     the launch configuration the benchmark times: sampled rows against the
     oracle's row-by-row evaluation, and symmetry on the whole vector."""
     dims = (64, 64, 61)
     m = hb.Mesh(*dims, 7, perturb=0.1, seed=0, fp32=False)
-    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, TC)
+    hb.hb_set_kernel_variant(m.handle, hb.HB_F64, variant)
     x = inputs.random_vector(m.n_global, seed=11)
     rows = inputs.sample_indices(m.n_global, 600, 12)
     ref = orc.apply_A_rows(dims, 7, 0.1, 0, x, rows, 0.1)
