@@ -243,10 +243,11 @@ __device__ __forceinline__ long long to_fixed(double v, unsigned emax)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
-    const unsigned long long m = e ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+    // 2m with the implicit bit (m the 53-bit significand), 0 for zero and subnormals
+    const unsigned long long m2 = e ? ((b << 1) & 0x1FFFFFFFFFFFFEull) | (1ull << 53) : 0ull;
     const unsigned sh = min(emax - e, 62u);
-    // round(m / 2^sh) = floor((2m + 2^sh) / 2^(sh+1)), also for sh = 0
-    const long long X = (long long)(((m << 1) + (1ull << sh)) >> (sh + 1));
+    // round(m / 2^sh), halves up: (floor(2m / 2^sh) + 1) / 2
+    const long long X = (long long)(((m2 >> sh) + 1ull) >> 1);
     return (b >> 63) ? -X : X;
 }
 
@@ -275,8 +276,9 @@ __device__ __forceinline__ double i64_to_double(long long T, int off)
 __device__ __forceinline__ double halves_to_double(long long hi, long long lo, int off)
 {
     const bool small = (unsigned long long)(hi + (1ll << 30)) < (1ull << 31);
-    return small ? i64_to_double((long long)((unsigned long long)hi << 32) + lo, off)
-                 : i64_to_double((long long)((unsigned long long)hi << 22) + (lo >> 10), off + 10);
+    const int sh = small ? 0 : 10;
+    const long long T = (long long)((unsigned long long)hi << (32 - sh)) + (lo >> sh);
+    return i64_to_double(T, off + sh);
 }
 
 // FP16 bit patterns of digit d of two values (a in the low half, b in the
@@ -467,8 +469,11 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
             hbtc::mma_commit(bar);
         }
         // ---- gradients: r and s through the exchange buffers, t kept here
-        if (!tc_wait(bar, phase, A.err)) gave_up = 1;
+        // (one warp polls the barrier; the others wait at the block barrier,
+        // which takes no issue slots)
+        if (warp == 0 && !tc_wait(bar, phase, A.err)) gave_up = 1;
         phase ^= 1u;
+        __syncthreads();
         hbtc::fence_after_sync();
         const int goff = (int)eu - 1075 - dshift + 40;
         const bool ubad = eu == 0x7FFu;
@@ -532,8 +537,9 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
         }
         gather(g + gridDim.x);
         // ---- D^T along r and s summed exactly into the exchange buffers, t here
-        if (!tc_wait(bar, phase, A.err)) gave_up = 1;
+        if (warp == 0 && !tc_wait(bar, phase, A.err)) gave_up = 1;
         phase ^= 1u;
+        __syncthreads();
         hbtc::fence_after_sync();
 #pragma unroll
         for (int dir = 0; dir < 2; dir++) {
