@@ -188,9 +188,11 @@ extern "C" hb_status hb_tc_selftest(int mode, const float *A_host, const float *
 //     combined in two int64 halves and turned into doubles with the exponent
 //     of the element's grid (exact), summed with one FP64 add.
 // Per two-element tile (128 lines per direction, M = 128) and direction: one
-// MMA chain of four K = 16 steps, A = the lines' digits (128 x 64, K-major),
-// B = the digit stack of D (64 x 64: output index i x diagonal t by digit j x
-// line position m), accumulator 128 x 64 FP32 in TMEM columns dir*64.
+// MMA chain of four K = 16 steps, A = the lines' digits (128 x 64, K-major,
+// K ordered (line position m, digit j) so that one node's seven digits and the
+// offset-correction slot j = 7 are one 16-byte row piece), B = the digit
+// stack of D (64 x 64: output index i x diagonal t by the same K), accumulator
+// 128 x 64 FP32 in TMEM columns dir*64.
 namespace {
 namespace tcax {
 
@@ -198,7 +200,12 @@ constexpr int N = 7, n = 8, n2 = 64, n3 = 512;
 constexpr int NS = 2 * n2 + 4 * N * (N - 1);  // surface nodes of an element
 constexpr int THREADS = 256;                  // two threads per line of a two-element tile
 constexpr int KH = 4;                         // nodes of its line a thread owns (half of n)
-constexpr int ABUF = 8 * 2048;                // one direction's A operand: 8 K blocks x 128 rows x 8 FP16
+// One direction's A operand: 8 K chunks (m) of 128 rows x 8 FP16 (16 bytes);
+// rows 16 bytes apart, row chunks of 8 at 128 bytes, K chunks LBO apart. The
+// r operand's K chunks sit 2064 bytes apart (16 bytes more than a chunk), so
+// the eight threads of a store phase, which differ in m, hit different banks.
+constexpr int LBO_R = 2064, LBO_ST = 2048;
+constexpr int ABUF = 7 * LBO_R + 2048 + 112;  // 16,608 bytes, a multiple of 16
 constexpr int BIMG = 64 * 64 * 2;             // one B operand image (64 x 64 FP16)
 constexpr int EXS = 576;                      // padded node stride of an element in the exchange buffers
 constexpr int OFF_A = 0;
@@ -281,49 +288,42 @@ __device__ __forceinline__ double halves_to_double(long long hi, long long lo, i
     return i64_to_double(T, off + sh);
 }
 
-// FP16 bit patterns of digit d of two values (a in the low half, b in the
-// high half of the result): digit d is byte (6 - d) of X on the little-endian
-// 64-bit word (bytes 0..5 for d = 6..1, byte 6 signed for d = 0); the MMA
-// takes digit u as the FP16 number 256 + u (384 + u_0 for d = 0), bit pattern
-// 0x5C00 | (u << 2).
-__device__ __forceinline__ unsigned digit_pair(long long Xa, long long Xb, int d)
+// The A-operand row piece of one node: the FP16 bit patterns of the seven
+// digits of X (digit j is byte 6 - j of the little-endian 64-bit word; byte 6
+// is the signed leading digit u_0) as the MMA takes them -- digit u as the FP16
+// number 256 + u (384 + u_0 for j = 0), pattern 0x5C00 | (u << 2) -- and the
+// offset-correction slot, FP16 128.0 (0x5800).
+__device__ __forceinline__ uint4 row_piece(long long X)
 {
-    const int byte = 6 - d;
-    const unsigned wa = byte >= 4 ? (unsigned)((unsigned long long)Xa >> 32) : (unsigned)Xa;
-    const unsigned wb = byte >= 4 ? (unsigned)((unsigned long long)Xb >> 32) : (unsigned)Xb;
-    const unsigned p = (unsigned)(byte & 3);
-    unsigned w = __byte_perm(wa, wb, p | ((4u + p) << 8)) & 0x00FF00FFu;
-    if (d == 0) w ^= 0x00800080u;  // u_0 + 128 for the signed leading digit
-    return (w << 2) | 0x5C005C00u;
+    const unsigned lo = (unsigned)X, hi = (unsigned)((unsigned long long)X >> 32);
+    uint4 r;
+    // __byte_perm(a, b, s): result byte n is byte (nibble n of s) of b:a; the
+    // zero word supplies the empty bytes
+    r.x = ((__byte_perm(hi, 0u, 0x4142u) ^ 0x00000080u) << 2) | 0x5C005C00u;           // u_0 + 128, u_1
+    r.y = ((__byte_perm(lo, hi, 0x0304u) & 0x00FF00FFu) << 2) | 0x5C005C00u;           // u_2, u_3
+    r.z = (__byte_perm(lo, 0u, 0x4142u) << 2) | 0x5C005C00u;                          // u_4, u_5
+    r.w = ((lo & 0xFFu) << 2) | 0x58005C00u;                                          // u_6, 128.0
+    return r;
 }
 
-// A operand rows (K-major, row chunk stride 128 bytes, K block stride 2048):
-//   r: row (el, k, j), position m = i;  s: row (el, k, i), m = j;  t: row (el, j, i), m = k.
-__device__ __forceinline__ unsigned char *arow(unsigned char *Ab, int dir, int blk, int el, int chunk, int row,
-                                               int m)
-{
-    return Ab + dir * ABUF + blk * 2048 + (el * 8 + chunk) * 128 + row * 16 + m * 2;
-}
-
-// Writes the digits of the thread's values X[q] (node (ti, tj, k0 + q)) to
-// the A operands of the directions in `dirs` (bit 0 r, bit 1 s, bit 2 t).
+// Stores the row pieces of the thread's nodes (ti, tj, k0 + q) in the A
+// operands of the directions in `dirs` (bit 0 r, bit 1 s, bit 2 t):
+//   r: row (el, k, j), K chunk m = i;  s: row (el, k, i), m = j;  t: row (el, j, i), m = k.
 __device__ __forceinline__ void stage(unsigned char *Ab, int el, int ti, int tj, int k0, const long long (&X)[KH],
                                       int dirs)
 {
 #pragma unroll
-    for (int d = 0; d < 7; d++) {
-        const unsigned w01 = digit_pair(X[0], X[1], d), w23 = digit_pair(X[2], X[3], d);
-        if (dirs & 4) *reinterpret_cast<uint2 *>(arow(Ab, 2, d, el, tj, ti, k0)) = make_uint2(w01, w23);
-        const uint16_t h[KH] = {(uint16_t)w01, (uint16_t)(w01 >> 16), (uint16_t)w23, (uint16_t)(w23 >> 16)};
-#pragma unroll
-        for (int q = 0; q < KH; q++) {
-            if (dirs & 1) *reinterpret_cast<uint16_t *>(arow(Ab, 0, d, el, k0 + q, tj, ti)) = h[q];
-            if (dirs & 2) *reinterpret_cast<uint16_t *>(arow(Ab, 1, d, el, k0 + q, ti, tj)) = h[q];
-        }
+    for (int q = 0; q < KH; q++) {
+        const int k = k0 + q;
+        const uint4 p = row_piece(X[q]);
+        if (dirs & 1) *reinterpret_cast<uint4 *>(Ab + 0 * ABUF + ti * LBO_R + (el * 8 + k) * 128 + tj * 16) = p;
+        if (dirs & 2) *reinterpret_cast<uint4 *>(Ab + 1 * ABUF + tj * LBO_ST + (el * 8 + k) * 128 + ti * 16) = p;
+        if (dirs & 4) *reinterpret_cast<uint4 *>(Ab + 2 * ABUF + k * LBO_ST + (el * 8 + tj) * 128 + ti * 16) = p;
     }
 }
 
 // One MMA chain per direction: accumulator columns dir*64 .. dir*64 + 63.
+// K step ks covers the K chunks m = 2 ks, 2 ks + 1 of A and B.
 __device__ __forceinline__ void issue(unsigned tmem, const unsigned char *Ab, const unsigned char *Bi)
 {
     constexpr uint32_t idesc = hbtc::idesc_f16(128, 64, false, false);
@@ -331,9 +331,10 @@ __device__ __forceinline__ void issue(unsigned tmem, const unsigned char *Ab, co
 #pragma unroll
     for (int dir = 0; dir < 3; dir++) {
         const unsigned a0 = hbtc::smem_addr(Ab + dir * ABUF);
+        const unsigned lbo = dir == 0 ? LBO_R : LBO_ST;
 #pragma unroll
         for (int ks = 0; ks < 4; ks++)
-            hbtc::mma_f16(tmem + dir * 64, hbtc::smem_desc(a0 + ks * 4096, 2048, 128),
+            hbtc::mma_f16(tmem + dir * 64, hbtc::smem_desc(a0 + ks * 2 * lbo, lbo, 128),
                           hbtc::smem_desc(b0 + ks * 2048, 1024, 128), idesc, ks > 0);
     }
 }
@@ -395,13 +396,9 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
     unsigned *tptr = reinterpret_cast<unsigned *>(sm + OFF_MISC + 8);
     unsigned *wexp = reinterpret_cast<unsigned *>(sm + OFF_MISC + 16);
 
-    // once per block: the B images, the offset-correction K block (128.0 in
-    // every row of the three A operands), the barrier and the TMEM columns
+    // once per block: the B images, the barrier and the TMEM columns
     for (int q = tid; q < 2 * BIMG / 16; q += THREADS)
         reinterpret_cast<uint4 *>(Bi)[q] = reinterpret_cast<const uint4 *>(&g_tc_bimg[0][0])[q];
-    for (int q = tid; q < 3 * 128; q += THREADS)
-        reinterpret_cast<uint4 *>(Ab + (q >> 7) * ABUF + 7 * 2048)[q & 127] =
-            make_uint4(0x58005800u, 0x58005800u, 0x58005800u, 0x58005800u);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(hbtc::smem_addr(bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -688,8 +685,9 @@ hb_status hb_tc_upload()
             }
         uint16_t *im = img[tr];
         std::memset(im, 0, sizeof img[0]);
-        auto put = [&](int i, int t, int blk, int m, long long val) {
-            im[(i * 128 + t * 16 + blk * 1024 + m * 2) / 2] = fp16_exact(val);
+        // element (row (i, t), K (m, digit j)) at i * 128 + t * 16 + m * 1024 + j * 2
+        auto put = [&](int i, int t, int j, int m, long long val) {
+            im[(i * 128 + t * 16 + m * 1024 + j * 2) / 2] = fp16_exact(val);
         };
         for (int i = 0; i < n; i++)
             for (int t = 0; t < 8; t++) {
@@ -704,7 +702,7 @@ hb_status hb_tc_upload()
                     }
                     beta += (j == 0 ? 384 : 256) * rs;
                 }
-                // K block 7: 128 (A side) times parts summing to -beta / 128
+                // slot j = 7 of each K chunk: 128 (A side) times parts summing to -beta / 128
                 long long c = -beta / 128;
                 for (int m = 0; m < n && c != 0; m++) {
                     const long long p = fp16_part(c);
