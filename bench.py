@@ -7,6 +7,12 @@ seeded uniform right-hand side. One step is one conjugate-gradient iteration
 (one application of A plus the fused vector stage of Algorithm 1); the value is
 the paper's throughput, global DOFs x iterations / s, in GDOF/s.
 
+The same line carries, measured in the same run on one GPU, the metric's
+other two parts: "c3", the single large solve (N=7, 80^3 elements) to a true
+relative residual of 1e-10 with FP64 CG and the mixed-precision solvers, and
+"c5", the serving stream (a stated number of the serving config's requests)
+with solves/s and p50 / p99 latency beside one-at-a-time FP64 and mixed solves.
+
 Prints one JSON line. Other workloads print their own lines; only the
 default is the headline:
   sweep   operator-only degree sweep N=1..15 on boxes of about 128M local nodes
@@ -390,6 +396,16 @@ def run_gb300(args, rank, world, local):
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(N)
+    if world == 1:
+        # the metric's other two parts, measured in the same run: time to a
+        # true 1e-10 (FP64 vs mixed) and served solves/s with p50 / p99
+        del m, x, b, b_host, x_host, b_dev, x_dev
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        if not args.no_c3:
+            out["c3"] = c3_compact()
+        if not args.no_c5:
+            out["c5"] = c5_compact(args.c5_default_requests)
     dist.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -561,6 +577,35 @@ def _solve_report(m, b, lam, prec, rtol, screen=0, max_it=200000, inner_rtol=1e-
                "rel_res_fp64": rel}
 
 
+def c3_compact(E1=80, N=7):
+    """The single large solve (N=7, 80^3 elements, manufactured rhs, lambda 0)
+    to a true relative residual of 1e-10: plain FP64 CG, the FP32-inner / FP64
+    defect-correction solver, and the same with the Jacobi preconditioner on
+    its inner CG. Each time is one hb_cg_solve; rel_res_fp64 is recomputed
+    here with the FP64 operator."""
+    import torch
+
+    from paper_2202_12477_gb300 import autotune, hb
+    m = hb.Mesh(E1, E1, E1, N, perturb=0.1, seed=0, fp32=True)
+    chosen = autotune.tune_mesh(m, lam=0.0, exclude=hb.HB_VARIANT_GRID)
+    b = m.rhs(kind=1, lam=0.0)
+    out = {"workload": f"single large solve N={N}, {E1}^3 elements, perturb 0.1h, manufactured rhs, lambda 0, "
+                       f"true relative residual 1e-10",
+           "n_global": m.n_global, "kernel_variants": {"f64": chosen[hb.HB_F64], "f32": chosen[hb.HB_F32]}}
+    x64, r = _solve_report(m, b, 0.0, hb.HB_F64, 1e-10)
+    out["fp64"] = r
+    xm, r = _solve_report(m, b, 0.0, hb.HB_MIXED, 1e-10)
+    out["mixed"] = r
+    _, r = _solve_report(m, b, 0.0, hb.HB_MIXED, 1e-10, precond=1)
+    out["mixed_jacobi"] = r
+    out["mixed_vs_fp64_rel_err"] = float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))
+    out["speedup_mixed_over_fp64"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
+    out["speedup_mixed_jacobi_over_fp64"] = out["fp64"]["time_s"] / out["mixed_jacobi"]["time_s"]
+    del x64, xm, b
+    m.close()
+    return out
+
+
 def run_c3(args, rank, world, local):
     """Single large solve: N=7, 80^3 elements, manufactured rhs, FP64 CG vs
     FP32-inner / FP64 defect correction, both to relative residual 1e-10."""
@@ -691,6 +736,54 @@ def _serve_run(reqs, arrivals, budget, slots, k):
     rounds = st.rounds
     srv.close()
     return [lat[t] for t in tickets], [status[t] for t in tickets], makespan, rounds
+
+
+def c5_compact(n_requests, emax=32, budget_gb=160.0, slots=32, k=16):
+    """The serving stream on n_requests requests (Ek uniform 2..emax, N in
+    3..11 odd, rtol 1e-8 / 1e-10, mixed precision): capacity with every
+    request submitted at once, then Poisson arrivals at 0.5, 0.8 and 1.0 x that
+    capacity (solves/s, p50, p99 latency from submit to completion), beside
+    the same requests solved one at a time with hb_cg_solve in FP64 and in
+    mixed precision."""
+    import numpy as np
+    import torch
+
+    from paper_2202_12477_gb300 import hb
+    reqs = _c5_requests(n_requests, 2, emax)
+    budget = int(budget_gb * (1 << 30))
+    out = {"workload": f"serving stream: {len(reqs)} of the 2,000 requests of the serving config (Ek uniform "
+                       f"2..{emax}, N in 3..11 odd, rtol 1e-8 / 1e-10), mixed precision, {slots} slots, {k} inner "
+                       f"iterations per launch, budget {budget_gb} GB"}
+    lat, sts, mk, rounds = _serve_run(reqs, [0.0] * len(reqs), budget, slots, k)
+    cap = len(reqs) / mk
+    out["capacity_solves_per_s"] = cap
+    out["all_at_once"] = {"solves_per_s": cap, "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99)), "ok": int(sum(s == hb.HB_OK for s in sts))}
+    rng = np.random.Generator(np.random.PCG64(1))
+    for f in (0.5, 0.8, 1.0):
+        arr = np.cumsum(rng.exponential(1.0 / (f * cap), size=len(reqs)))
+        arr -= arr[0]
+        lat, sts, mk, rounds = _serve_run(reqs, list(arr), budget, slots, k)
+        out[f"load_{f:.1f}"] = {"solves_per_s": len(reqs) / mk, "p50_ms": float(np.percentile(lat, 50)),
+                                "p99_ms": float(np.percentile(lat, 99)),
+                                "ok": int(sum(s == hb.HB_OK for s in sts))}
+    for prec, name in ((hb.HB_F64, "sequential_fp64"), (hb.HB_MIXED, "sequential_mixed")):
+        t0 = time.perf_counter()
+        lat = []
+        for r in reqs:
+            ts = time.perf_counter()
+            m = hb.Mesh(r["ex"], r["ey"], r["ez"], r["N"], perturb=0.1, seed=r["seed"], fp32=True)
+            b = m.rhs(kind=0, seed=r["rhs_seed"])
+            m.cg(b, lam=0.1, rtol=r["rtol"], max_it=200000, prec=prec)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - ts) * 1e3)
+            m.close()
+        mk = time.perf_counter() - t0
+        out[name] = {"solves_per_s": len(reqs) / mk, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99))}
+    out["served_over_sequential_fp64"] = cap / out["sequential_fp64"]["solves_per_s"]
+    out["served_over_sequential_mixed"] = cap / out["sequential_mixed"]["solves_per_s"]
+    return out
 
 
 def run_c5(args, rank, world, local):
@@ -943,6 +1036,10 @@ def main():
     ap.add_argument("--reps", type=int, default=50)
     ap.add_argument("--local-nodes", type=float, default=1.28e8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c3", action="store_true", help="leave the time-to-1e-10 solves out of the default line")
+    ap.add_argument("--no-c5", action="store_true", help="leave the serving stream out of the default line")
+    ap.add_argument("--c5-default-requests", type=int, default=300,
+                    help="requests of the serving stream measured in the default line")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300" and args.workload == "c2":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
