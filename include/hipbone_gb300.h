@@ -228,9 +228,11 @@ hb_status hb_diag_A(hb_mesh *mesh, hb_screen screen, double lambda, double *host
  * rtol ||b||): the recursive residual r_{j+1} = r_j - alpha A p_j drifts from
  * b - A x_{j+1} by rounding, so when it meets the tolerance the solver
  * recomputes the true residual b - A x in FP64 (FP64 operator); if that one is
- * still above rtol ||b||, r is replaced by it (p is kept) and the iterations
- * go on. HB_OK therefore means the true FP64 residual meets rtol; HB_MIXED
- * tests the true residual at every outer step.
+ * still above rtol ||b||, Algorithm 1 restarts from x with it (p = M^-1 r) and
+ * the iterations go on, while each restart lowers the true residual by at
+ * least a tenth (else the rounding floor of the operator is above rtol and the
+ * solve ends, HB_ERR_NOT_CONVERGED). HB_OK therefore means the true FP64
+ * residual meets rtol; HB_MIXED tests the true residual at every outer step.
  * Returns HB_ERR_BREAKDOWN, HB_ERR_NOT_CONVERGED (rtol > 0 only: max_it
  * iterations ran and the true residual is above rtol) or HB_OK;
  * res (may be NULL) receives the counts, residual and device time. */
@@ -255,8 +257,8 @@ hb_status hb_set_cg_fused(hb_mesh *mesh, int mode);
  * return at once) without waiting for the host; hb_cg_finish waits and fills
  * res (time_ms = 0): with rtol > 0 it recomputes the true residual b - A x in
  * FP64 (one more operator application) and returns HB_ERR_NOT_CONVERGED if it
- * is above rtol (the stepwise form replaces no residual: its iterations are
- * over by then). One stepwise solve
+ * is above rtol (the stepwise form does not restart: its iterations are over
+ * by then). One stepwise solve
  * per mesh at a time; b and x must stay valid until hb_cg_finish, and the
  * mesh's other solver calls must not run in between. */
 hb_status hb_cg_begin(hb_mesh *mesh, const hb_cg_opts *opts, const double *b, double *x, void *stream);

@@ -93,11 +93,11 @@ __global__ void __launch_bounds__(HB_RED_THREADS)
 }
 
 __global__ void __launch_bounds__(HB_RED_THREADS)
-    cg_replace_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
-                      double *__restrict__ z, const double *__restrict__ inv_d, int64_t n, double *partials,
-                      unsigned *counter, hb_cg_state *st)
+    cg_restart_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
+                      double *__restrict__ p, double *__restrict__ z, const double *__restrict__ inv_d, int64_t n,
+                      double *partials, unsigned *counter, hb_cg_state *st)
 {
-    cg_replace_body(b, Ax, r, z, inv_d, n, partials, counter, st);
+    cg_restart_body(b, Ax, r, p, z, inv_d, n, partials, counter, st);
 }
 
 __global__ void __launch_bounds__(HB_RED_THREADS)
@@ -654,20 +654,20 @@ static hb_status cg_drive(const hb_mesh *m, hb_precision prec, int screen, doubl
 }
 
 // The true residual of the iterate x: r = b - A x with the FP64 operator
-// (whatever precision the iterations ran in), z = M^-1 r, r.z and r.r into
-// the state, which keeps p, alpha and the iteration count; run is set again
-// while the true residual is above the tolerance and iterations remain
-// (residual replacement). Synchronises s; returns the state in *out.
+// (whatever precision the iterations ran in), z = M^-1 r, p = z, r.z and r.r
+// into the state, which keeps the iteration count; run is set again while the
+// true residual is above the tolerance and iterations remain (a restart of
+// Algorithm 1 from x). Synchronises s; returns the state in *out.
 static hb_status cg_true_residual(const hb_mesh *m, const hb_cg_opts *o, const double *b, const double *x, double *r,
-                                  double *Ap, double *z, const double *inv_d, hb_cg_state *st, cudaStream_t s,
-                                  hb_cg_state *out)
+                                  double *p, double *Ap, double *z, const double *inv_d, hb_cg_state *st,
+                                  cudaStream_t s, hb_cg_state *out)
 {
     const int64_t n = m->n_global;
     hb_status rs = hb_apply_A_impl(m, HB_F64, o->screen, o->lambda, x, Ap, nullptr, HB_DOT_NONE, s);
     if (rs != HB_OK) return rs;
     hb_count_launch();
-    cg_replace_kernel<<<red_grid(n), HB_RED_THREADS, 0, s>>>(b, Ap, r, z, inv_d, n, m->partials, m->counters + 2,
-                                                              st);
+    cg_restart_kernel<<<red_grid(n), HB_RED_THREADS, 0, s>>>(b, Ap, r, p, z, inv_d, n, m->partials,
+                                                              m->counters + 2, st);
     HB_CHECK_LAUNCH();
     HB_TRY_CUDA(cudaMemcpyAsync(m->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
     HB_TRY_CUDA(cudaStreamSynchronize(s));
@@ -746,13 +746,19 @@ extern "C" hb_status hb_cg_solve(const hb_mesh *mc, const hb_cg_opts *o, const d
         }
         // With a tolerance, the stop is decided on the true residual b - A x
         // (FP64 operator): where the recursive residual met it and the true
-        // one does not, r is replaced by the true residual and the iterations
-        // go on (each pass adds at least one iteration, up to max_it).
+        // one does not, Algorithm 1 restarts from x with the true residual
+        // (each pass adds at least one iteration, up to max_it). A restart
+        // that does not lower the true residual by a tenth of its norm ends
+        // the solve (HB_ERR_NOT_CONVERGED): the operator's rounding floor is
+        // then above the tolerance.
         if (o->rtol > 0.0) {
+            double prev = -1.0;
             while (fin.status == HB_OK) {
-                rs = cg_true_residual(m, o, b, x, r, Ap, z, inv_d, st, s, &fin);
+                rs = cg_true_residual(m, o, b, x, r, p, Ap, z, inv_d, st, s, &fin);
                 if (rs != HB_OK) return rs;
                 if (!fin.run) break;
+                if (prev >= 0.0 && fin.res2 > 0.81 * prev) break;
+                prev = fin.res2;
                 rs = cg_drive<double>(m, o->prec, o->screen, o->lambda, x, r, p, Ap, z, inv_d, st,
                                       o->max_it - fin.it, s, &fin);
                 if (rs != HB_OK) return rs;
@@ -903,11 +909,11 @@ extern "C" hb_status hb_cg_finish(hb_mesh *m, hb_cg_result *res, void *stream)
         hb_cg_state fin = *m->state_host;
         const hb_cg_opts &o = m->step.o;
         if (o.rtol > 0.0 && fin.status == HB_OK) {
-            // report the true residual b - A x (no replacement: the iterations are over)
+            // report the true residual b - A x (no restart: the iterations are over)
             const int64_t ns = cg_stride(m->n_global);
             double *r = (double *)m->cg_vec, *p = r + ns, *Ap = p + ns, *z = Ap + ns;
-            hb_status rs = cg_true_residual(m, &o, m->step.b, m->step.x, r, Ap, z, o.precond ? m->inv_diag : nullptr,
-                                            m->state, s, &fin);
+            hb_status rs = cg_true_residual(m, &o, m->step.b, m->step.x, r, p, Ap, z,
+                                            o.precond ? m->inv_diag : nullptr, m->state, s, &fin);
             if (rs != HB_OK) return rs;
         }
         R.iters = fin.it;

@@ -183,11 +183,11 @@ __global__ void __launch_bounds__(HB_RED_THREADS) k_cg_init(const double *b, con
     hb::cg_init_body(b, Ax, r, p, nullptr, n, rtol, max_it, partials, counter, st);
 }
 
-__global__ void __launch_bounds__(HB_RED_THREADS) k_cg_replace(const double *b, const double *Ax, double *r,
-                                                                int64_t n, double *partials, unsigned *counter,
-                                                                hb_cg_state *st)
+__global__ void __launch_bounds__(HB_RED_THREADS) k_cg_restart(const double *b, const double *Ax, double *r,
+                                                                double *p, int64_t n, double *partials,
+                                                                unsigned *counter, hb_cg_state *st)
 {
-    hb::cg_replace_body(b, Ax, r, nullptr, nullptr, n, partials, counter, st);
+    hb::cg_restart_body(b, Ax, r, p, nullptr, nullptr, n, partials, counter, st);
 }
 
 __global__ void __launch_bounds__(HB_RED_THREADS) k_cg_update_r(double *r, const double *Ap, int64_t n,
@@ -915,9 +915,11 @@ extern "C" hb_status hb_part_cg_solve(const hb_part *part, const hb_cg_opts *o, 
     HB_CHECK_LAUNCH();
     // iterations in chunks; kernels of a finished solve return at once. With a
     // tolerance, a stop of the recursive residual is checked on the true one
-    // (b - A x, replacing r; the iterations go on while it is above rtol).
+    // (b - A x; Algorithm 1 restarts from x while it is above rtol and each
+    // restart lowers it by a tenth at least).
     int chunk = 16;
     bool checked = false;
+    double prev = -1.0;
     hb_cg_state fin{};
     for (;;) {
         HB_TRY_CUDA(cudaMemcpyAsync(P->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
@@ -927,12 +929,16 @@ extern "C" hb_status hb_part_cg_solve(const hb_part *part, const hb_cg_opts *o, 
             if (o->rtol > 0.0 && fin.status == HB_OK && !checked) {
                 if ((rs = part_apply(P, o->screen, o->lambda, x, Ap, nullptr, s)) != HB_OK) return rs;
                 hb_count_launch();
-                k_cg_replace<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, n, P->partials, P->counters + 2, st);
+                k_cg_restart<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, p, n, P->partials, P->counters + 2, st);
                 HB_CHECK_LAUNCH();
                 checked = true;
                 continue;
             }
             break;
+        }
+        if (checked) {
+            if (prev >= 0.0 && fin.res2 > 0.81 * prev) break;  // no progress: the rounding floor
+            prev = fin.res2;
         }
         checked = false;
         const int cnt = std::min(chunk, o->max_it - fin.it);

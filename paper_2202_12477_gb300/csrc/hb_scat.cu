@@ -153,24 +153,27 @@ __global__ void __launch_bounds__(HB_RED_THREADS) k_w_init(const double *__restr
     }
 }
 
-// Residual replacement (the one-mesh solver's rule with weighted dots): the
-// true residual r = b - A x, its weighted r.r into the state (p, alpha and the
-// iteration count stay); run again while it is above the tolerance.
-__global__ void __launch_bounds__(HB_RED_THREADS) k_w_replace(const double *__restrict__ b,
+// Restart (the one-mesh solver's rule with weighted dots): the true residual
+// r = b - A x, p = r, its weighted r.r into the state (the iteration count
+// stays); run again while it is above the tolerance.
+__global__ void __launch_bounds__(HB_RED_THREADS) k_w_restart(const double *__restrict__ b,
                                                                const double *__restrict__ Ax, double *__restrict__ r,
-                                                               const double *__restrict__ w, int64_t n,
-                                                               double *partials, unsigned *counter, hb_cg_state *st)
+                                                               double *__restrict__ p, const double *__restrict__ w,
+                                                               int64_t n, double *partials, unsigned *counter,
+                                                               hb_cg_state *st)
 {
     dot_acc<double> rr;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double ri = b[i] - Ax[i];
         r[i] = ri;
+        p[i] = ri;
         rr.add(w[i] * ri, ri);
     }
     double v[1] = {rr.value()}, tot[1];
     if (hb::grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
         st->rr = tot[0];
         st->res2 = tot[0];
+        st->alpha = st->beta = st->pAp = 0.0;
         const bool finite = isfinite(tot[0]);
         if (!finite) st->status = HB_ERR_BREAKDOWN;
         st->run = (finite && st->status == HB_OK && st->it < st->max_it && tot[0] > st->tol2) ? 1 : 0;
@@ -441,9 +444,10 @@ extern "C" hb_status hb_scat_cg_solve(const hb_scat *sc, const hb_cg_opts *o, co
                                              st);
     HB_CHECK_LAUNCH();
     // with a tolerance, a stop of the recursive residual is checked on the
-    // true one (residual replacement, as in hb_cg_solve)
+    // true one (a restart from x, as in hb_cg_solve)
     int chunk = 16;
     bool checked = false;
+    double prev = -1.0;
     hb_cg_state fin{};
     for (;;) {
         HB_TRY_CUDA(cudaMemcpyAsync(S->state_host, st, sizeof(hb_cg_state), cudaMemcpyDeviceToHost, s));
@@ -453,12 +457,17 @@ extern "C" hb_status hb_scat_cg_solve(const hb_scat *sc, const hb_cg_opts *o, co
             if (o->rtol > 0.0 && fin.status == HB_OK && !checked) {
                 if ((rs = scat_apply(S, o->screen, o->lambda, x, Ap, nullptr, s)) != HB_OK) return rs;
                 hb_count_launch();
-                k_w_replace<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, S->w, n, S->partials, S->counters + 2, st);
+                k_w_restart<<<grid, HB_RED_THREADS, 0, s>>>(b, Ap, r, p, S->w, n, S->partials, S->counters + 2,
+                                                            st);
                 HB_CHECK_LAUNCH();
                 checked = true;
                 continue;
             }
             break;
+        }
+        if (checked) {
+            if (prev >= 0.0 && fin.res2 > 0.81 * prev) break;  // no progress: the rounding floor
+            prev = fin.res2;
         }
         checked = false;
         const int cnt = std::min(chunk, o->max_it - fin.it);

@@ -371,15 +371,17 @@ __device__ __forceinline__ void cg_init_body(const double *__restrict__ b, const
     }
 }
 
-// Residual replacement for the stopping test of Algorithm 1. The recursive
-// residual r_{j+1} = r_j - alpha A p drifts from b - A x_j by rounding; a
-// solve whose recursive residual meets the tolerance therefore checks the true
-// one: r = b - Ax recomputed in FP64 (Ax from the caller's x), z = M^-1 r,
-// new r.z (alpha's numerator) and r.r; p, alpha and the iteration count stay.
-// The solve runs on while the true residual is above the tolerance and
-// iterations remain; a non-finite residual is a breakdown.
-__device__ __forceinline__ void cg_replace_body(const double *__restrict__ b, const double *__restrict__ Ax,
-                                                double *__restrict__ r, double *__restrict__ z,
+// Restart for the stopping test of Algorithm 1. The recursive residual
+// r_{j+1} = r_j - alpha A p_j drifts from b - A x_{j+1} by rounding; a solve
+// whose recursive residual meets the tolerance therefore checks the true one:
+// r = b - Ax recomputed in FP64 (Ax from the caller's x), z = M^-1 r, and
+// Algorithm 1 starts again from x with p = z (new r.z, r.r; the iteration
+// count stays). Keeping the old p with the new r instead was measured to
+// stall and break down on ill-conditioned meshes. The solve runs on while
+// the true residual is above the tolerance and iterations remain; a
+// non-finite residual is a breakdown.
+__device__ __forceinline__ void cg_restart_body(const double *__restrict__ b, const double *__restrict__ Ax,
+                                                double *__restrict__ r, double *__restrict__ p, double *__restrict__ z,
                                                 const double *__restrict__ inv_d, int64_t n, double *partials,
                                                 unsigned *counter, hb_cg_state *st)
 {
@@ -387,19 +389,17 @@ __device__ __forceinline__ void cg_replace_body(const double *__restrict__ b, co
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double ri = b[i] - Ax[i];
         r[i] = ri;
-        if (inv_d) {
-            const double zi = ri * inv_d[i];
-            z[i] = zi;
-            rz.add(ri, zi);
-        } else {
-            rz.add(ri, ri);
-        }
+        const double zi = inv_d ? ri * inv_d[i] : ri;
+        if (inv_d) z[i] = zi;
+        p[i] = zi;
+        rz.add(ri, zi);
         rr.add(ri, ri);
     }
     double v[2] = {rz.value(), rr.value()}, tot[2];
     if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
         st->rr = tot[0];
         st->res2 = tot[1];
+        st->alpha = st->beta = st->pAp = 0.0;
         const bool finite = isfinite(tot[0]) && isfinite(tot[1]);
         if (!finite) st->status = HB_ERR_BREAKDOWN;
         st->run = (finite && st->status == HB_OK && st->it < st->max_it && tot[1] > st->tol2) ? 1 : 0;
