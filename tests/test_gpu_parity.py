@@ -242,8 +242,9 @@ def test_cg_double_float_matches_oracle():
     assert _rel(x.cpu().numpy(), x_or) <= 1e-9
     x2, res2 = m.cg(b, lam=0.1, rtol=1e-10, max_it=5000, prec=hb.HB_F64X)
     assert res2.status == hb.HB_OK and res2.rel_res <= 1e-10
+    # the stop is taken on the true residual with the FP64 operator
     r = b - m.apply_A(x2, lam=0.1)
-    assert float(torch.linalg.norm(r) / torch.linalg.norm(b)) <= 1e-9
+    assert float(torch.linalg.norm(r) / torch.linalg.norm(b)) <= 1.01e-10
 
 
 def test_apply_A_reproducible_and_linear():
