@@ -372,14 +372,12 @@ hb_status hb_scat_cg_solve(const hb_scat *sc, const hb_cg_opts *opts, const doub
  * A CG server with continuous batching on one GPU (the paper runs one solve at
  * a time; the server applies Algorithm 1 in the FP32-inner / FP64
  * defect-correction form of hb_cg_solve to many concurrent requests).
- * Requests queue on submit; an admission thread takes them first come, first
- * served, into free slots while the device-memory budget allows and builds
- * each one's mesh and vectors on its own stream, beside the rounds in flight;
- * a worker thread makes built slots resident between rounds, keeps each
+ * Requests queue on submit; a worker thread admits them first come, first
+ * served, into free slots while the device-memory budget allows, keeps each
  * solve's mesh and vectors resident, and advances all resident solves with
  * one launch of a CUDA graph (captured once at creation) per round of
  * iters_per_launch inner iterations. Finished solves are retired between
- * rounds. Every slot runs on fixed grids with its own
+ * rounds and queued ones admitted. Every slot runs on fixed grids with its own
  * reductions: a request's result does not depend on which others share the
  * GPU. The right-hand side is hb_fill_rhs kind 0 with the request's seed and
  * x0 = 0. Degrees N = 1..11; opts.prec must be HB_MIXED, opts.rtol > 0 and

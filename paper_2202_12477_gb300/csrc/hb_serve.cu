@@ -1,10 +1,9 @@
 // CG server with continuous batching on one GPU.
 //
 // Requests (a mesh description, solver options and a right-hand-side seed)
-// are queued by hb_server_submit. An admission thread builds each one's mesh
-// and vectors on its own stream while slots and the device-memory budget
-// allow, beside the rounds in flight; a worker thread makes built slots
-// resident between rounds and advances all resident solves together: one launch of
+// are queued by hb_server_submit. A worker thread admits them into slots
+// while slots and the device-memory budget allow, keeps each solve's mesh and
+// vectors resident, and advances all resident solves together: one launch of
 // a CUDA graph, captured once when the server is created, runs one round for
 // every slot position. A round is the FP32-inner / FP64 defect-correction
 // scheme of hb_cg_solve written as per-slot device state:
@@ -16,7 +15,7 @@
 // Every kernel of a slot reads the slot's descriptor and state from device
 // memory and returns at once when the slot is empty or has nothing to do, so
 // the same graph serves whatever set of requests is resident. Between
-// launches the worker retires finished solves and publishes built ones.
+// launches the worker retires finished solves and admits new ones.
 // Each slot's kernels run on fixed grids with per-slot reductions, so a
 // request's result does not depend on which other requests share the GPU.
 #include <algorithm>
@@ -177,7 +176,6 @@ struct finished {
 
 struct slot {
     bool busy = false;
-    bool reserved = false;  // the admission thread is building this slot
     hb_mesh *mesh = nullptr;
     void *mem = nullptr;  // vectors and per-slot workspace
     size_t bytes = 0;
@@ -185,23 +183,11 @@ struct slot {
     double t_admit = 0;
 };
 
-// A slot the admission thread has built (mesh, vectors, right-hand side) and
-// the worker publishes between rounds.
-struct built_slot {
-    int si;
-    hb_mesh *mesh;
-    void *mem;
-    size_t bytes;
-    request req;
-    hb_slot_desc desc;
-};
-
 }  // namespace
 
 struct hb_server {
     int device = 0;
     cudaStream_t s_main = nullptr;
-    cudaStream_t s_admit = nullptr;  // mesh and slot set-up, beside the rounds
     int cap = 0, k = 0;
     size_t budget = 0, used = 0;
     hb_slot_desc *d_desc = nullptr;
@@ -212,9 +198,8 @@ struct hb_server {
     cudaGraphExec_t exec = nullptr;
     std::vector<slot> slots;
     std::deque<request> pending;
-    std::deque<built_slot> built;
     std::map<int64_t, finished> done;
-    std::thread worker, admitter;
+    std::thread worker;
     std::mutex mu;
     std::condition_variable cv;
     bool stop = false;
@@ -286,15 +271,14 @@ static hb_status capture_round_graph(hb_server *S)
     return HB_OK;
 }
 
-// Builds a slot for a request on the admission stream: mesh, vectors, the
-// right-hand side and the slot descriptor (not yet visible to the kernels).
-// Runs on the admission thread, so resident solves keep running meanwhile.
-static hb_status build_slot(hb_server *S, int si, const request &rq, built_slot *out)
+// Creates the slot's mesh and vectors and publishes its descriptor and state.
+static hb_status admit(hb_server *S, int si, const request &rq)
 {
+    slot &sl = S->slots[si];
     hb_mesh_desc md = rq.desc;
     md.keep_fp32_copy = 1;
     hb_mesh *m = nullptr;
-    hb_status st = hb_mesh_create(&md, S->s_admit, &m);
+    hb_status st = hb_mesh_create(&md, S->s_main, &m);
     if (st != HB_OK) return st;
     const int64_t n = m->n_global;
     const size_t ns = vec_stride(n);
@@ -345,11 +329,22 @@ static hb_status build_slot(hb_server *S, int si, const request &rq, built_slot 
     d.partials = partials;
     d.ax_partials = axp;
     d.counters = ctr;
-    e = cudaMemsetAsync(x, 0, sizeof(double) * ns, S->s_admit);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 64 * sizeof(unsigned), S->s_admit);
-    if (e == cudaSuccess) e = cudaMemsetAsync(axp, 0, HB_SERVE_AXP * sizeof(double), S->s_admit);
-    if (e == cudaSuccess) st = hb_fill_rhs(m, 0, rq.seed, 0.0, b, S->s_admit);
-    if (e == cudaSuccess && st == HB_OK) e = cudaStreamSynchronize(S->s_admit);
+    hb_slot_state ss{};
+    ss.phase = HB_SLOT_OUTER;
+    ss.status = HB_OK;
+    e = cudaMemsetAsync(x, 0, sizeof(double) * ns, S->s_main);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 64 * sizeof(unsigned), S->s_main);
+    if (e == cudaSuccess) e = cudaMemsetAsync(axp, 0, HB_SERVE_AXP * sizeof(double), S->s_main);
+    if (e == cudaSuccess) st = hb_fill_rhs(m, 0, rq.seed, 0.0, b, S->s_main);
+    if (e == cudaSuccess && st == HB_OK) {
+        S->h_desc[si] = d;
+        e = cudaMemcpyAsync(S->d_desc + si, &S->h_desc[si], sizeof d, cudaMemcpyHostToDevice, S->s_main);
+    }
+    if (e == cudaSuccess && st == HB_OK) {
+        S->h_state[si] = ss;
+        e = cudaMemcpyAsync(S->d_state + si, &S->h_state[si], sizeof ss, cudaMemcpyHostToDevice, S->s_main);
+    }
+    if (e == cudaSuccess && st == HB_OK) e = cudaStreamSynchronize(S->s_main);
     if (e != cudaSuccess || st != HB_OK) {
         cudaFree(mem);
         hb_mesh_destroy(m);
@@ -359,111 +354,13 @@ static hb_status build_slot(hb_server *S, int si, const request &rq, built_slot 
         }
         return st;
     }
-    out->si = si;
-    out->mesh = m;
-    out->mem = mem;
-    out->bytes = m->device_bytes + bytes;
-    out->req = rq;
-    out->desc = d;
-    return HB_OK;
-}
-
-// Makes a built slot resident (worker thread, between rounds): its
-// descriptor and initial state go to device memory on the round stream,
-// ordered before the next round.
-static hb_status publish_slot(hb_server *S, const built_slot &b)
-{
-    slot &sl = S->slots[b.si];
-    hb_slot_state ss{};
-    ss.phase = HB_SLOT_OUTER;
-    ss.status = HB_OK;
-    S->h_desc[b.si] = b.desc;
-    S->h_state[b.si] = ss;
-    cudaError_t e = cudaMemcpyAsync(S->d_desc + b.si, &S->h_desc[b.si], sizeof(hb_slot_desc),
-                                    cudaMemcpyHostToDevice, S->s_main);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(S->d_state + b.si, &S->h_state[b.si], sizeof(hb_slot_state), cudaMemcpyHostToDevice,
-                            S->s_main);
-    if (e != cudaSuccess) {
-        hb_set_error("publish: %s", cudaGetErrorString(e));
-        return HB_ERR_CUDA;
-    }
     sl.busy = true;
-    sl.reserved = false;
-    sl.mesh = b.mesh;
-    sl.mem = b.mem;
-    sl.bytes = b.bytes;
-    sl.req = b.req;
+    sl.mesh = m;
+    sl.mem = mem;
+    sl.bytes = m->device_bytes + bytes;
+    sl.req = rq;
     sl.t_admit = now_s();
     return HB_OK;
-}
-
-static void free_built(hb_server *S, const built_slot &b)
-{
-    cudaFree(b.mem);
-    hb_mesh_destroy(b.mesh);
-    S->used -= std::min(S->used, b.bytes);
-}
-
-// Admission thread: first come, first served, a request is given a free slot
-// while the device-memory budget allows and is built on the admission stream,
-// beside the rounds that advance the resident solves; the worker publishes it
-// between two rounds.
-static void admitter_loop(hb_server *S)
-{
-    cudaSetDevice(S->device);
-    std::unique_lock<std::mutex> lk(S->mu);
-    for (;;) {
-        if (S->stop) break;
-        if (S->pending.empty()) {
-            S->cv.wait_for(lk, std::chrono::milliseconds(2));
-            continue;
-        }
-        request rq = S->pending.front();
-        if (rq.est > S->budget) {  // can never fit
-            S->pending.pop_front();
-            finished f{};
-            f.res.status = HB_ERR_NOMEM;
-            f.latency_ms = (now_s() - rq.t_submit) * 1e3;
-            S->done[rq.ticket] = std::move(f);
-            S->stats.rejected++;
-            S->cv.notify_all();
-            continue;
-        }
-        int free_slot = -1;
-        for (int i = 0; i < S->cap; i++)
-            if (!S->slots[i].busy && !S->slots[i].reserved) { free_slot = i; break; }
-        if (free_slot < 0 || S->used + rq.est > S->budget) {
-            S->cv.wait_for(lk, std::chrono::milliseconds(2));
-            continue;
-        }
-        S->pending.pop_front();
-        S->slots[free_slot].reserved = true;
-        S->used += rq.est;
-        lk.unlock();
-        built_slot b{};
-        hb_status st = build_slot(S, free_slot, rq, &b);
-        lk.lock();
-        S->used -= std::min(S->used, rq.est);
-        if (st == HB_OK && S->stop) {
-            // the server stopped while this slot was built
-            S->used += b.bytes;
-            free_built(S, b);
-            st = HB_ERR_CUDA;
-        }
-        if (st != HB_OK) {
-            S->slots[free_slot].reserved = false;
-            finished f{};
-            f.res.status = st;
-            f.latency_ms = (now_s() - rq.t_submit) * 1e3;
-            S->done[rq.ticket] = std::move(f);
-            S->stats.rejected++;
-        } else {
-            S->used += b.bytes;
-            S->built.push_back(b);
-        }
-        S->cv.notify_all();
-    }
 }
 
 static void retire(hb_server *S, int si, finished &f)
@@ -506,31 +403,49 @@ static void worker_loop(hb_server *S)
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         if (S->stop) break;
-        // publish the slots the admission thread has built since the last round
-        while (!S->built.empty()) {
-            built_slot b = S->built.front();
-            S->built.pop_front();
-            if (publish_slot(S, b) != HB_OK) {
-                S->slots[b.si].reserved = false;
-                free_built(S, b);
+        // admission, first come first served, while slots and memory allow
+        for (;;) {
+            if (S->pending.empty()) break;
+            int free_slot = -1;
+            for (int i = 0; i < S->cap; i++)
+                if (!S->slots[i].busy) { free_slot = i; break; }
+            request rq = S->pending.front();
+            if (rq.est > S->budget) {  // can never fit
+                S->pending.pop_front();
                 finished f{};
-                f.res.status = HB_ERR_CUDA;
-                f.latency_ms = (now_s() - b.req.t_submit) * 1e3;
-                S->done[b.req.ticket] = std::move(f);
+                f.res.status = HB_ERR_NOMEM;
+                f.latency_ms = (now_s() - rq.t_submit) * 1e3;
+                S->done[rq.ticket] = std::move(f);
                 S->stats.rejected++;
+                S->cv.notify_all();
+                continue;
+            }
+            if (free_slot < 0 || S->used + rq.est > S->budget) break;
+            S->pending.pop_front();
+            S->used += rq.est;
+            lk.unlock();
+            hb_status st = admit(S, free_slot, rq);
+            lk.lock();
+            S->used -= rq.est;
+            if (st != HB_OK) {
+                finished f{};
+                f.res.status = st;
+                f.latency_ms = (now_s() - rq.t_submit) * 1e3;
+                S->done[rq.ticket] = std::move(f);
+                S->stats.rejected++;
+                S->cv.notify_all();
             } else {
+                S->used += S->slots[free_slot].bytes;
                 S->stats.admitted++;
             }
         }
         int active = 0;
         for (auto &sl : S->slots) active += sl.busy ? 1 : 0;
-        int building = 0;
-        for (auto &sl : S->slots) building += sl.reserved ? 1 : 0;
         S->stats.active = active;
-        S->stats.pending = (int)(S->pending.size() + S->built.size()) + building;
+        S->stats.pending = (int)S->pending.size();
         S->stats.mem_used = S->used;
         if (active == 0) {
-            S->cv.wait_for(lk, std::chrono::milliseconds(1));
+            S->cv.wait_for(lk, std::chrono::milliseconds(2));
             continue;
         }
         const bool fail_round = S->inject_round_error;
@@ -563,15 +478,6 @@ static void worker_loop(hb_server *S)
                 S->done[rq.ticket] = std::move(f);
             }
             S->pending.clear();
-            for (const built_slot &b : S->built) {
-                finished f{};
-                f.res.status = HB_ERR_CUDA;
-                f.latency_ms = f.res.time_ms = (now_s() - b.req.t_submit) * 1e3;
-                S->done[b.req.ticket] = std::move(f);
-                S->slots[b.si].reserved = false;
-                free_built(S, b);
-            }
-            S->built.clear();
             S->stats.active = 0;
             S->stats.pending = 0;
             S->stats.mem_used = S->used;
@@ -617,7 +523,6 @@ extern "C" hb_status hb_server_create(const hb_server_opts *o, hb_server **out)
     S->slots.resize(S->cap);
     S->h_desc.resize(S->cap);
     cudaError_t e = cudaStreamCreateWithFlags(&S->s_main, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_admit, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_desc, sizeof(hb_slot_desc) * S->cap);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_state, sizeof(hb_slot_state) * S->cap);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_state, sizeof(hb_slot_state) * S->cap);
@@ -635,7 +540,6 @@ extern "C" hb_status hb_server_create(const hb_server_opts *o, hb_server **out)
         return st;
     }
     S->worker = std::thread(worker_loop, S);
-    S->admitter = std::thread(admitter_loop, S);
     *out = S;
     return HB_OK;
 }
@@ -723,24 +627,18 @@ extern "C" hb_status hb_server_destroy(hb_server *S)
         S->cv.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
-    if (S->admitter.joinable()) S->admitter.join();
     hb_device_guard dg(S->device);
     for (int i = 0; i < S->cap; i++)
         if (S->slots[i].busy) {
             cudaFree(S->slots[i].mem);
             hb_mesh_destroy(S->slots[i].mesh);
         }
-    for (const built_slot &b : S->built) {
-        cudaFree(b.mem);
-        hb_mesh_destroy(b.mesh);
-    }
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->graph) cudaGraphDestroy(S->graph);
     cudaFree(S->d_desc);
     cudaFree(S->d_state);
     if (S->h_state) cudaFreeHost(S->h_state);
     if (S->s_main) cudaStreamDestroy(S->s_main);
-    if (S->s_admit) cudaStreamDestroy(S->s_admit);
     delete S;
     return HB_OK;
 }
