@@ -375,9 +375,11 @@ hb_status hb_scat_cg_solve(const hb_scat *sc, const hb_cg_opts *opts, const doub
  * Requests queue on submit; a worker thread admits them first come, first
  * served, into free slots while the device-memory budget allows, keeps each
  * solve's mesh and vectors resident, and advances all resident solves with
- * one launch of a CUDA graph (captured once at creation) per round of
- * iters_per_launch inner iterations. Finished solves are retired between
- * rounds and queued ones admitted. Every slot runs on fixed grids with its own
+ * one launch of a CUDA graph per round of iters_per_launch inner iterations
+ * (graphs over the first 4, 8, 16, ... slot positions are captured at
+ * creation; a round launches the smallest that covers every busy slot, and
+ * admission fills the lowest free position). Finished solves are retired
+ * between rounds and queued ones admitted. Every slot runs on fixed grids with its own
  * reductions: a request's result does not depend on which others share the
  * GPU. The right-hand side is hb_fill_rhs kind 0 with the request's seed and
  * x0 = 0. Degrees N = 1..11; opts.prec must be HB_MIXED, opts.rtol > 0 and

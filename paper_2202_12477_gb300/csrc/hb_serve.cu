@@ -4,8 +4,10 @@
 // are queued by hb_server_submit. A worker thread admits them into slots
 // while slots and the device-memory budget allow, keeps each solve's mesh and
 // vectors resident, and advances all resident solves together: one launch of
-// a CUDA graph, captured once when the server is created, runs one round for
-// every slot position. A round is the FP32-inner / FP64 defect-correction
+// a CUDA graph, captured when the server is created, runs one round for the
+// slot positions it covers (graphs over the first 4, 8, 16, ... positions;
+// a round takes the smallest covering every busy slot, and admission fills
+// the lowest free position). A round is the FP32-inner / FP64 defect-correction
 // scheme of hb_cg_solve written as per-slot device state:
 //   - if the slot's inner CG has stopped: x += ||r|| d (FP64);
 //   - if the slot needs an outer step: r = b - A x in FP64, stop when
@@ -194,8 +196,13 @@ struct hb_server {
     hb_slot_state *d_state = nullptr;
     hb_slot_state *h_state = nullptr;  // pinned
     std::vector<hb_slot_desc> h_desc;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    // round graphs over the first 4, 8, 16, ... slot positions (the last one
+    // over all of them): a round runs the smallest that covers every busy
+    // slot, and admission fills the lowest free position, so at low load the
+    // launches of idle slot positions are not paid
+    std::vector<int> graph_slots;
+    std::vector<cudaGraph_t> graphs;
+    std::vector<cudaGraphExec_t> execs;
     std::vector<slot> slots;
     std::deque<request> pending;
     std::map<int64_t, finished> done;
@@ -223,21 +230,22 @@ static size_t estimate_bytes(const hb_mesh_desc &d)
 
 static size_t vec_stride(int64_t n) { return (size_t)((n + 63) / 64 * 64); }
 
-static hb_status capture_round_graph(hb_server *S)
+// Captures the round over the first `nslots` slot positions.
+static hb_status capture_round_graph(hb_server *S, int nslots, cudaGraph_t *graph_out, cudaGraphExec_t *exec_out)
 {
     // fork one branch per slot position from s_main, join them at the end
-    std::vector<cudaStream_t> br(S->cap);
-    std::vector<cudaEvent_t> ev(S->cap + 1);
+    std::vector<cudaStream_t> br(nslots);
+    std::vector<cudaEvent_t> ev(nslots + 1);
     hb_status st = HB_OK;
-    for (int i = 0; i < S->cap; i++) HB_TRY_CUDA(cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking));
-    for (int i = 0; i <= S->cap; i++) HB_TRY_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+    for (int i = 0; i < nslots; i++) HB_TRY_CUDA(cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= nslots; i++) HB_TRY_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
     HB_TRY_CUDA(cudaStreamBeginCapture(S->s_main, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaEventRecord(ev[S->cap], S->s_main);
-    for (int i = 0; i < S->cap && e == cudaSuccess && st == HB_OK; i++) {
+    cudaError_t e = cudaEventRecord(ev[nslots], S->s_main);
+    for (int i = 0; i < nslots && e == cudaSuccess && st == HB_OK; i++) {
         cudaStream_t s = br[i];
         const hb_slot_desc *D = S->d_desc + i;
         hb_slot_state *T = S->d_state + i;
-        if ((e = cudaStreamWaitEvent(s, ev[S->cap], 0)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(s, ev[nslots], 0)) != cudaSuccess) break;
         serve_transition_kernel<<<1, 32, 0, s>>>(D, T);
         serve_xupdate_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
         if ((st = hb_serve_launch_ax_f64(D, T, s)) != HB_OK) break;
@@ -259,8 +267,8 @@ static hb_status capture_round_graph(hb_server *S)
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(S->s_main, &g);
     if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess && st == HB_OK) e = cudaGraphInstantiate(&S->exec, g, 0);
-    S->graph = g;
+    if (e == cudaSuccess && st == HB_OK) e = cudaGraphInstantiate(exec_out, g, 0);
+    *graph_out = g;
     for (auto s : br) cudaStreamDestroy(s);
     for (auto x : ev) cudaEventDestroy(x);
     if (st != HB_OK) return st;
@@ -451,8 +459,14 @@ static void worker_loop(hb_server *S)
         const bool fail_round = S->inject_round_error;
         S->inject_round_error = false;
         lk.unlock();
-        // one round for every resident solve
-        cudaError_t e = fail_round ? cudaErrorLaunchFailure : cudaGraphLaunch(S->exec, S->s_main);
+        // one round for every resident solve, with the smallest round graph
+        // that covers the highest busy slot position
+        int top = 0;
+        for (int i = 0; i < S->cap; i++)
+            if (S->slots[i].busy) top = i + 1;
+        size_t gi = 0;
+        while (gi + 1 < S->execs.size() && S->graph_slots[gi] < top) gi++;
+        cudaError_t e = fail_round ? cudaErrorLaunchFailure : cudaGraphLaunch(S->execs[gi], S->s_main);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(S->h_state, S->d_state, sizeof(hb_slot_state) * S->cap, cudaMemcpyDeviceToHost,
                                 S->s_main);
@@ -534,10 +548,19 @@ extern "C" hb_status hb_server_create(const hb_server_opts *o, hb_server **out)
         return e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;
     }
     memset(S->h_state, 0, sizeof(hb_slot_state) * S->cap);
-    st = capture_round_graph(S);
-    if (st != HB_OK) {
-        hb_server_destroy(S);
-        return st;
+    for (int ns = 4;; ns *= 2) {
+        const int take = ns < S->cap ? ns : S->cap;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        st = capture_round_graph(S, take, &g, &x);
+        if (g) S->graphs.push_back(g);
+        if (st != HB_OK) {
+            hb_server_destroy(S);
+            return st;
+        }
+        S->graph_slots.push_back(take);
+        S->execs.push_back(x);
+        if (take == S->cap) break;
     }
     S->worker = std::thread(worker_loop, S);
     *out = S;
@@ -633,8 +656,10 @@ extern "C" hb_status hb_server_destroy(hb_server *S)
             cudaFree(S->slots[i].mem);
             hb_mesh_destroy(S->slots[i].mesh);
         }
-    if (S->exec) cudaGraphExecDestroy(S->exec);
-    if (S->graph) cudaGraphDestroy(S->graph);
+    for (auto x : S->execs)
+        if (x) cudaGraphExecDestroy(x);
+    for (auto g : S->graphs)
+        if (g) cudaGraphDestroy(g);
     cudaFree(S->d_desc);
     cudaFree(S->d_state);
     if (S->h_state) cudaFreeHost(S->h_state);
