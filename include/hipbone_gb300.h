@@ -113,11 +113,17 @@ typedef struct {
 typedef struct hb_mesh hb_mesh;
 
 /* Builds the mesh on the current device: GLL nodes, derivative matrix, node
- * map, CSR of Z^T and the geometric factors (Sec. 2, Sec. 3.2). Synchronises
- * `stream` once at the end. Returns HB_ERR_GEOMETRY (and no mesh) if det J <= 0
+ * map, CSR of Z^T and the geometric factors (Sec. 2, Sec. 3.2). The arrays are
+ * allocated in stream order on `stream` from a memory pool the library owns
+ * (no call here waits for other streams or the device); `stream` is
+ * synchronised before the call returns, so the mesh is ready for work on any
+ * stream. Returns HB_ERR_GEOMETRY (and no mesh) if det J <= 0
  * at any GLL node; HB_ERR_ARG for N outside 1..15, non-positive element counts,
  * perturb outside [0, 0.5) or more than 2^31-1 local nodes. */
 hb_status hb_mesh_create(const hb_mesh_desc *desc, void *stream, hb_mesh **out);
+/* Waits for the device (work on any stream may still read the mesh), then
+ * frees the mesh. The pool keeps up to 8 GiB of freed memory for later meshes
+ * and returns the rest to the device. */
 hb_status hb_mesh_destroy(hb_mesh *mesh);
 hb_status hb_mesh_info(const hb_mesh *mesh, hb_mesh_info_t *out);
 
@@ -378,8 +384,12 @@ hb_status hb_scat_cg_solve(const hb_scat *sc, const hb_cg_opts *opts, const doub
  * one launch of a CUDA graph per round of iters_per_launch inner iterations
  * (graphs over the first 4, 8, 16, ... slot positions are captured at
  * creation; a round launches the smallest that covers every busy slot, and
- * admission fills the lowest free position). Finished solves are retired
- * between rounds and queued ones admitted. Every slot runs on fixed grids with its own
+ * admission fills the lowest free position). While a round runs, the worker
+ * builds queued requests (mesh, vectors, right-hand side) on a second stream;
+ * between rounds it retires finished solves (their memory freed in stream
+ * order after the round) and publishes the built ones. While it runs the
+ * server lets the library's memory pool keep up to its budget of freed
+ * memory for reuse. Every slot runs on fixed grids with its own
  * reductions: a request's result does not depend on which others share the
  * GPU. The right-hand side is hb_fill_rhs kind 0 with the request's seed and
  * x0 = 0. Degrees N = 1..11; opts.prec must be HB_MIXED, opts.rtol > 0 and
@@ -394,6 +404,9 @@ typedef struct {
     int64_t submitted, admitted, completed, rejected, rounds;
     int active, pending;
     size_t mem_used;
+    /* wall seconds the worker spent admitting (mesh and vector set-up),
+     * running rounds (launch to state read-back) and retiring solves */
+    double admit_s, round_s, retire_s;
 } hb_server_stats_t;
 
 hb_status hb_server_create(const hb_server_opts *opts, hb_server **out);

@@ -230,6 +230,24 @@ hb_status hb_selftest_mbar_timeout(unsigned *err, cudaStream_t s);
 hb_status hb_selftest_barrier_timeout(unsigned *bar, unsigned *err, cudaStream_t s);
 // Destroys the mesh's captured CG runs (before an array they use is replaced).
 void hb_mesh_drop_graphs(hb_mesh *m);
+// Releases a mesh whose arrays no pending work outside stream s uses: the
+// stream-ordered arrays are freed on s, without waiting for the device (the
+// server's retirement). hb_mesh_destroy waits for the device first.
+void hb_mesh_release(hb_mesh *m, cudaStream_t s);
+
+// Stream-ordered device memory from the library's pool (hb_mem.cu): usable on
+// s at once and on other streams after s is synchronised; hb_dev_free frees on
+// s in stream order. hb_dev_trim returns the pool's cached memory.
+cudaError_t hb_dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void hb_dev_free(void *p, cudaStream_t s);
+void hb_dev_trim();
+// Freed pool memory kept for reuse before the rest goes back to the device
+// (8 GiB unless a server raises it to its budget while it runs).
+cudaError_t hb_dev_keep(uint64_t bytes);
+uint64_t hb_dev_keep_default();
+// Pinned host buffers of at most 256 bytes, reused.
+cudaError_t hb_pinned_get(void **p, size_t bytes);
+void hb_pinned_put(void *p);
 
 
 // y = Z^T y_L + lambda (x or M x); optional fused x.y into st->pAp (and the

@@ -16,8 +16,10 @@
 //     accuracy).
 // Every kernel of a slot reads the slot's descriptor and state from device
 // memory and returns at once when the slot is empty or has nothing to do, so
-// the same graph serves whatever set of requests is resident. Between
-// launches the worker retires finished solves and admits new ones.
+// the same graph serves whatever set of requests is resident. While a round
+// runs the worker builds queued requests on a second stream (stream-ordered
+// allocations: nothing waits for the round); between rounds it retires
+// finished solves and publishes the built ones.
 // Each slot's kernels run on fixed grids with per-slot reductions, so a
 // request's result does not depend on which other requests share the GPU.
 #include <algorithm>
@@ -177,11 +179,13 @@ struct finished {
 };
 
 struct slot {
-    bool busy = false;
+    bool busy = false;       // reserved: being built, built, or resident
+    bool published = false;  // its descriptor is active on the device
     hb_mesh *mesh = nullptr;
     void *mem = nullptr;  // vectors and per-slot workspace
     size_t bytes = 0;
     request req{};
+    hb_slot_state init{};  // the state published with the descriptor
     double t_admit = 0;
 };
 
@@ -189,7 +193,9 @@ struct slot {
 
 struct hb_server {
     int device = 0;
-    cudaStream_t s_main = nullptr;
+    cudaStream_t s_main = nullptr;  // rounds, publication and retirement
+    cudaStream_t s_adm = nullptr;   // building admitted requests beside the rounds
+    cudaEvent_t ev_round = nullptr;
     int cap = 0, k = 0;
     size_t budget = 0, used = 0;
     hb_slot_desc *d_desc = nullptr;
@@ -286,16 +292,16 @@ static hb_status admit(hb_server *S, int si, const request &rq)
     hb_mesh_desc md = rq.desc;
     md.keep_fp32_copy = 1;
     hb_mesh *m = nullptr;
-    hb_status st = hb_mesh_create(&md, S->s_main, &m);
+    hb_status st = hb_mesh_create(&md, S->s_adm, &m);
     if (st != HB_OK) return st;
     const int64_t n = m->n_global;
     const size_t ns = vec_stride(n);
     const size_t bytes = ns * (4 * sizeof(double) + 4 * sizeof(float)) +
                          sizeof(double) * (HB_RED_MAXV * HB_RED_BLOCKS + HB_SERVE_AXP) + 64 * sizeof(unsigned);
     void *mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, bytes);
+    cudaError_t e = hb_dev_alloc(&mem, bytes, S->s_adm);
     if (e != cudaSuccess) {
-        hb_mesh_destroy(m);
+        hb_mesh_release(m, S->s_adm);
         hb_set_error("slot vectors: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;
     }
@@ -340,34 +346,29 @@ static hb_status admit(hb_server *S, int si, const request &rq)
     hb_slot_state ss{};
     ss.phase = HB_SLOT_OUTER;
     ss.status = HB_OK;
-    e = cudaMemsetAsync(x, 0, sizeof(double) * ns, S->s_main);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 64 * sizeof(unsigned), S->s_main);
-    if (e == cudaSuccess) e = cudaMemsetAsync(axp, 0, HB_SERVE_AXP * sizeof(double), S->s_main);
-    if (e == cudaSuccess) st = hb_fill_rhs(m, 0, rq.seed, 0.0, b, S->s_main);
-    if (e == cudaSuccess && st == HB_OK) {
-        S->h_desc[si] = d;
-        e = cudaMemcpyAsync(S->d_desc + si, &S->h_desc[si], sizeof d, cudaMemcpyHostToDevice, S->s_main);
-    }
-    if (e == cudaSuccess && st == HB_OK) {
-        S->h_state[si] = ss;
-        e = cudaMemcpyAsync(S->d_state + si, &S->h_state[si], sizeof ss, cudaMemcpyHostToDevice, S->s_main);
-    }
-    if (e == cudaSuccess && st == HB_OK) e = cudaStreamSynchronize(S->s_main);
+    e = cudaMemsetAsync(x, 0, sizeof(double) * ns, S->s_adm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 64 * sizeof(unsigned), S->s_adm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(axp, 0, HB_SERVE_AXP * sizeof(double), S->s_adm);
+    if (e == cudaSuccess) st = hb_fill_rhs(m, 0, rq.seed, 0.0, b, S->s_adm);
+    // built: the round stream may use it from now on (published between rounds)
+    if (e == cudaSuccess && st == HB_OK) e = cudaStreamSynchronize(S->s_adm);
     if (e != cudaSuccess || st != HB_OK) {
-        cudaFree(mem);
-        hb_mesh_destroy(m);
+        cudaStreamSynchronize(S->s_adm);
+        hb_dev_free(mem, S->s_adm);
+        hb_mesh_release(m, S->s_adm);
         if (st == HB_OK) {
             hb_set_error("admission: %s", cudaGetErrorString(e));
             st = HB_ERR_CUDA;
         }
         return st;
     }
-    sl.busy = true;
     sl.mesh = m;
     sl.mem = mem;
     sl.bytes = m->device_bytes + bytes;
     sl.req = rq;
+    sl.init = ss;
     sl.t_admit = now_s();
+    S->h_desc[si] = d;  // published by the worker between rounds
     return HB_OK;
 }
 
@@ -384,11 +385,12 @@ static void retire(hb_server *S, int si, finished &f)
         f.x.resize((size_t)f.n_global);
         cudaMemcpy(f.x.data(), S->h_desc[si].x, sizeof(double) * f.n_global, cudaMemcpyDeviceToHost);
     }
+    // the slot goes idle before the next round; its memory is freed after
+    // that copy in stream order (no host wait)
     S->h_desc[si].active = 0;
     cudaMemcpyAsync(S->d_desc + si, &S->h_desc[si], sizeof(hb_slot_desc), cudaMemcpyHostToDevice, S->s_main);
-    cudaStreamSynchronize(S->s_main);
-    cudaFree(sl.mem);
-    hb_mesh_destroy(sl.mesh);
+    hb_dev_free(sl.mem, S->s_main);
+    hb_mesh_release(sl.mesh, S->s_main);
     S->used -= std::min(S->used, sl.bytes);
     sl = slot{};
 }
@@ -398,121 +400,185 @@ static void retire(hb_server *S, int si, finished &f)
 static void release_slot(hb_server *S, int si)
 {
     slot &sl = S->slots[si];
-    cudaFree(sl.mem);
-    hb_mesh_destroy(sl.mesh);
+    cudaDeviceSynchronize();
+    hb_dev_free(sl.mem, S->s_main);
+    hb_mesh_release(sl.mesh, S->s_main);
     S->used -= std::min(S->used, sl.bytes);
     S->h_desc[si].active = 0;
     sl = slot{};
 }
 
+// The server stops after a failed round: every resident request fails and
+// releases its memory, every queued one fails too, so each ticket resolves.
+static void fail_server(hb_server *S, cudaError_t e, bool injected)
+{
+    snprintf(S->err, sizeof S->err, "round%s: %s", injected ? " (injected)" : "", cudaGetErrorString(e));
+    for (int i = 0; i < S->cap; i++)
+        if (S->slots[i].busy) {
+            finished f{};
+            f.res.status = HB_ERR_CUDA;
+            f.latency_ms = f.res.time_ms = (now_s() - S->slots[i].req.t_submit) * 1e3;
+            S->done[S->slots[i].req.ticket] = std::move(f);
+            release_slot(S, i);
+        }
+    for (const request &rq : S->pending) {
+        finished f{};
+        f.res.status = HB_ERR_CUDA;
+        f.latency_ms = f.res.time_ms = (now_s() - rq.t_submit) * 1e3;
+        S->done[rq.ticket] = std::move(f);
+    }
+    S->pending.clear();
+    S->stats.active = 0;
+    S->stats.pending = 0;
+    S->stats.mem_used = S->used;
+    S->stop = true;
+    S->cv.notify_all();
+}
+
+// Takes the next queued request into the lowest free slot and builds it on the
+// admission stream (the lock is released meanwhile). Returns false when
+// nothing could be admitted (queue empty, no free slot, or over budget).
+static bool admit_one(hb_server *S, std::unique_lock<std::mutex> &lk)
+{
+    for (;;) {
+        if (S->pending.empty()) return false;
+        request rq = S->pending.front();
+        if (rq.est > S->budget) {  // can never fit
+            S->pending.pop_front();
+            finished f{};
+            f.res.status = HB_ERR_NOMEM;
+            f.latency_ms = (now_s() - rq.t_submit) * 1e3;
+            S->done[rq.ticket] = std::move(f);
+            S->stats.rejected++;
+            S->cv.notify_all();
+            continue;
+        }
+        int si = -1;
+        for (int i = 0; i < S->cap; i++)
+            if (!S->slots[i].busy) { si = i; break; }
+        if (si < 0 || S->used + rq.est > S->budget) return false;
+        S->pending.pop_front();
+        S->used += rq.est;
+        S->slots[si].busy = true;  // reserved while it is built
+        lk.unlock();
+        const double ta = now_s();
+        hb_status st = admit(S, si, rq);
+        const double tb = now_s();
+        lk.lock();
+        S->stats.admit_s += tb - ta;
+        S->used -= rq.est;
+        if (st != HB_OK) {
+            S->slots[si] = slot{};
+            finished f{};
+            f.res.status = st;
+            f.latency_ms = (now_s() - rq.t_submit) * 1e3;
+            S->done[rq.ticket] = std::move(f);
+            S->stats.rejected++;
+            S->cv.notify_all();
+        } else {
+            S->used += S->slots[si].bytes;
+            S->stats.admitted++;
+        }
+        return true;
+    }
+}
+
+// One round advances every published solve; while it runs the worker builds
+// queued requests on the admission stream, one at a time, and goes back to the
+// round as soon as it has finished. Between rounds: retire the finished solves
+// (stream-ordered frees), publish the built ones, launch the next round.
 static void worker_loop(hb_server *S)
 {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
+    bool inflight = false;
+    double t_launch = 0;
     for (;;) {
         if (S->stop) break;
-        // admission, first come first served, while slots and memory allow
-        for (;;) {
-            if (S->pending.empty()) break;
-            int free_slot = -1;
-            for (int i = 0; i < S->cap; i++)
-                if (!S->slots[i].busy) { free_slot = i; break; }
-            request rq = S->pending.front();
-            if (rq.est > S->budget) {  // can never fit
-                S->pending.pop_front();
-                finished f{};
-                f.res.status = HB_ERR_NOMEM;
-                f.latency_ms = (now_s() - rq.t_submit) * 1e3;
-                S->done[rq.ticket] = std::move(f);
-                S->stats.rejected++;
-                S->cv.notify_all();
-                continue;
+        // publish what was built (no round in flight here)
+        if (!inflight) {
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < S->cap && e == cudaSuccess; i++) {
+                slot &sl = S->slots[i];
+                if (!sl.busy || sl.published || !sl.mesh) continue;
+                e = cudaMemcpyAsync(S->d_desc + i, &S->h_desc[i], sizeof(hb_slot_desc), cudaMemcpyHostToDevice,
+                                    S->s_main);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(S->d_state + i, &sl.init, sizeof(hb_slot_state), cudaMemcpyHostToDevice,
+                                        S->s_main);
+                sl.published = true;
             }
-            if (free_slot < 0 || S->used + rq.est > S->budget) break;
-            S->pending.pop_front();
-            S->used += rq.est;
-            lk.unlock();
-            hb_status st = admit(S, free_slot, rq);
-            lk.lock();
-            S->used -= rq.est;
-            if (st != HB_OK) {
-                finished f{};
-                f.res.status = st;
-                f.latency_ms = (now_s() - rq.t_submit) * 1e3;
-                S->done[rq.ticket] = std::move(f);
-                S->stats.rejected++;
-                S->cv.notify_all();
-            } else {
-                S->used += S->slots[free_slot].bytes;
-                S->stats.admitted++;
+            if (e != cudaSuccess) {
+                fail_server(S, e, false);
+                break;
             }
         }
-        int active = 0;
-        for (auto &sl : S->slots) active += sl.busy ? 1 : 0;
+        int active = 0, top = 0;
+        for (int i = 0; i < S->cap; i++)
+            if (S->slots[i].busy) {
+                active++;
+                if (S->slots[i].published) top = i + 1;
+            }
         S->stats.active = active;
         S->stats.pending = (int)S->pending.size();
         S->stats.mem_used = S->used;
-        if (active == 0) {
-            S->cv.wait_for(lk, std::chrono::milliseconds(2));
+        // launch a round over the smallest graph that covers every published slot
+        if (!inflight && top > 0) {
+            const bool fail_round = S->inject_round_error;
+            S->inject_round_error = false;
+            size_t gi = 0;
+            while (gi + 1 < S->execs.size() && S->graph_slots[gi] < top) gi++;
+            t_launch = now_s();
+            cudaError_t e = fail_round ? cudaErrorLaunchFailure : cudaGraphLaunch(S->execs[gi], S->s_main);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(S->h_state, S->d_state, sizeof(hb_slot_state) * S->cap, cudaMemcpyDeviceToHost,
+                                    S->s_main);
+            if (e == cudaSuccess) e = cudaEventRecord(S->ev_round, S->s_main);
+            if (e != cudaSuccess) {
+                fail_server(S, e, fail_round);
+                break;
+            }
+            inflight = true;
+        }
+        // build queued requests while the round runs
+        const bool admitted = admit_one(S, lk);
+        if (S->stop) break;
+        if (inflight) {
+            const cudaError_t q = cudaEventQuery(S->ev_round);
+            if (q == cudaErrorNotReady && admitted) continue;  // more to build meanwhile
+            lk.unlock();
+            const cudaError_t e = cudaEventSynchronize(S->ev_round);
+            const double t_done = now_s();
+            lk.lock();
+            inflight = false;
+            S->stats.rounds++;
+            S->stats.round_s += t_done - t_launch;
+            if (e != cudaSuccess) {
+                fail_server(S, e, false);
+                break;
+            }
+            const double tt = now_s();
+            for (int i = 0; i < S->cap; i++) {
+                if (!S->slots[i].published || S->h_state[i].phase != HB_SLOT_DONE) continue;
+                finished f{};
+                const int64_t ticket = S->slots[i].req.ticket;
+                const double t_sub = S->slots[i].req.t_submit;
+                retire(S, i, f);
+                f.latency_ms = (now_s() - t_sub) * 1e3;
+                f.res.time_ms = f.latency_ms;
+                S->done[ticket] = std::move(f);
+                S->stats.completed++;
+            }
+            S->stats.retire_s += now_s() - tt;
+            S->cv.notify_all();
             continue;
         }
-        const bool fail_round = S->inject_round_error;
-        S->inject_round_error = false;
+        if (!admitted && top == 0) S->cv.wait_for(lk, std::chrono::milliseconds(2));
+    }
+    if (inflight) {
         lk.unlock();
-        // one round for every resident solve, with the smallest round graph
-        // that covers the highest busy slot position
-        int top = 0;
-        for (int i = 0; i < S->cap; i++)
-            if (S->slots[i].busy) top = i + 1;
-        size_t gi = 0;
-        while (gi + 1 < S->execs.size() && S->graph_slots[gi] < top) gi++;
-        cudaError_t e = fail_round ? cudaErrorLaunchFailure : cudaGraphLaunch(S->execs[gi], S->s_main);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(S->h_state, S->d_state, sizeof(hb_slot_state) * S->cap, cudaMemcpyDeviceToHost,
-                                S->s_main);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->s_main);
+        cudaEventSynchronize(S->ev_round);
         lk.lock();
-        S->stats.rounds++;
-        if (e != cudaSuccess) {
-            snprintf(S->err, sizeof S->err, "round%s: %s", fail_round ? " (injected)" : "", cudaGetErrorString(e));
-            // the server stops: every resident request fails and releases its
-            // memory, every queued one fails too, so each ticket resolves
-            for (int i = 0; i < S->cap; i++)
-                if (S->slots[i].busy) {
-                    finished f{};
-                    f.res.status = HB_ERR_CUDA;
-                    f.latency_ms = f.res.time_ms = (now_s() - S->slots[i].req.t_submit) * 1e3;
-                    S->done[S->slots[i].req.ticket] = std::move(f);
-                    release_slot(S, i);
-                }
-            for (const request &rq : S->pending) {
-                finished f{};
-                f.res.status = HB_ERR_CUDA;
-                f.latency_ms = f.res.time_ms = (now_s() - rq.t_submit) * 1e3;
-                S->done[rq.ticket] = std::move(f);
-            }
-            S->pending.clear();
-            S->stats.active = 0;
-            S->stats.pending = 0;
-            S->stats.mem_used = S->used;
-            S->stop = true;
-            S->cv.notify_all();
-            break;
-        }
-        for (int i = 0; i < S->cap; i++) {
-            if (!S->slots[i].busy || S->h_state[i].phase != HB_SLOT_DONE) continue;
-            finished f{};
-            const int64_t ticket = S->slots[i].req.ticket;
-            const double t_sub = S->slots[i].req.t_submit;
-            lk.unlock();
-            retire(S, i, f);
-            lk.lock();
-            f.latency_ms = (now_s() - t_sub) * 1e3;
-            f.res.time_ms = f.latency_ms;
-            S->done[ticket] = std::move(f);
-            S->stats.completed++;
-        }
-        S->cv.notify_all();
     }
 }
 
@@ -537,6 +603,10 @@ extern "C" hb_status hb_server_create(const hb_server_opts *o, hb_server **out)
     S->slots.resize(S->cap);
     S->h_desc.resize(S->cap);
     cudaError_t e = cudaStreamCreateWithFlags(&S->s_main, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_adm, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_round, cudaEventDisableTiming);
+    // resident requests come and go: keep their freed memory for reuse
+    if (e == cudaSuccess) e = hb_dev_keep(std::max<uint64_t>(S->budget, hb_dev_keep_default()));
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_desc, sizeof(hb_slot_desc) * S->cap);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_state, sizeof(hb_slot_state) * S->cap);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_state, sizeof(hb_slot_state) * S->cap);
@@ -651,11 +721,15 @@ extern "C" hb_status hb_server_destroy(hb_server *S)
     }
     if (S->worker.joinable()) S->worker.join();
     hb_device_guard dg(S->device);
+    cudaDeviceSynchronize();
     for (int i = 0; i < S->cap; i++)
         if (S->slots[i].busy) {
-            cudaFree(S->slots[i].mem);
-            hb_mesh_destroy(S->slots[i].mesh);
+            hb_dev_free(S->slots[i].mem, S->s_main);
+            hb_mesh_release(S->slots[i].mesh, S->s_main);
         }
+    if (S->s_main) cudaStreamSynchronize(S->s_main);
+    hb_dev_keep(hb_dev_keep_default());
+    hb_dev_trim();
     for (auto x : S->execs)
         if (x) cudaGraphExecDestroy(x);
     for (auto g : S->graphs)
@@ -664,6 +738,8 @@ extern "C" hb_status hb_server_destroy(hb_server *S)
     cudaFree(S->d_state);
     if (S->h_state) cudaFreeHost(S->h_state);
     if (S->s_main) cudaStreamDestroy(S->s_main);
+    if (S->s_adm) cudaStreamDestroy(S->s_adm);
+    if (S->ev_round) cudaEventDestroy(S->ev_round);
     delete S;
     return HB_OK;
 }

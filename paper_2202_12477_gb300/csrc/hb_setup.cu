@@ -7,6 +7,7 @@
 //   - the derivative matrix from barycentric weights, diagonal by negative sums;
 //   - the Jacobian by applying that derivative matrix to the nodal coordinates
 //     (exact, since a trilinear map is a polynomial of degree 1 <= N per axis).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
@@ -251,82 +252,90 @@ __device__ inline void vertex_pos(const box_t &b, double rho, uint64_t seed, int
     }
 }
 
-// Geometric factors, one element per block. Nodal coordinates from the
-// trilinear map, then J = D applied to them along r, s, t.
+// Geometric factors, one element per block. The element map is trilinear in
+// its 8 vertices, x(r, s, t) = sum_{a,b,c} V_abc phi_a(r) phi_b(s) phi_c(t)
+// with phi_0 = (1 - r) / 2, phi_1 = (1 + r) / 2, so its Jacobian column along
+// one reference direction is bilinear in the other two coordinates:
+//   dx/dr = sum_{b,c} (V_1bc - V_0bc) / 2 phi_b(s) phi_c(t)
+// (and likewise for s and t). Each column is formed once per line of nodes
+// (3 n^2 lines per element, not n^3 nodes) and shared through shared memory;
+// per node, with the adjugate rows a_l (a_r = j_s x j_t, a_s = j_t x j_r,
+// a_t = j_r x j_s) and det J = j_r . a_r,
+//   G_lm = w_ijk det J (J^-1 J^-T)_lm = (w_ijk / det J) a_l . a_m,
+// the six factors of Sec. 2 and the weighted Jacobian w_ijk det J.
 __global__ void k_geometry(box_t b, double rho, uint64_t seed, int64_t E, double *geo, float *geo32,
                            double *detmin_blk)
 {
     extern __shared__ double smem[];
     const int N = b.N, n = N + 1, n2 = n * n, n3 = n2 * n;
-    double *X = smem;            // [3][n3]
-    double *sD = smem + 3 * n3;  // [n][n]
+    double *col = smem;  // [direction l][axis][line (u + n v)]: column l of J on the line
+    __shared__ double V[8][3];
+    __shared__ double dV[3][4][3];  // [direction][pair (p + 2 q)][axis]: halved edge differences
     __shared__ double red[32];
-    const double *Dg = g_D64;
-    int off = 0;
-    for (int M = 1; M < N; M++) off += (M + 1) * (M + 1);
-    for (int q = threadIdx.x; q < n2; q += blockDim.x) sD[q] = Dg[off + q];
     const double *xi = g_xi64 + N * 16, *w = g_w64 + N * 16;
     double dmin = INFINITY;
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
-        int ex = (int)(e % b.Ex), ey = (int)((e / b.Ex) % b.Ey), ez = (int)(e / ((int64_t)b.Ex * b.Ey));
-        double V[8][3];
-        for (int c = 0; c < 2; c++)
-            for (int bb = 0; bb < 2; bb++)
-                for (int a = 0; a < 2; a++) vertex_pos(b, rho, seed, ex + a, ey + bb, ez + c, V[(c * 2 + bb) * 2 + a]);
+        const int ex = (int)(e % b.Ex), ey = (int)((e / b.Ex) % b.Ey), ez = (int)(e / ((int64_t)b.Ex * b.Ey));
+        __syncthreads();  // the previous element's columns are consumed
+        if (threadIdx.x < 8) {
+            const int a = threadIdx.x & 1, bb = (threadIdx.x >> 1) & 1, c = threadIdx.x >> 2;
+            vertex_pos(b, rho, seed, ex + a, ey + bb, ez + c, V[threadIdx.x]);
+        }
         __syncthreads();
-        for (int q = threadIdx.x; q < n3; q += blockDim.x) {
-            int i = q % n, j = (q / n) % n, k = q / n2;
-            double r = xi[i], s = xi[j], t = xi[k];
-            double fr[2] = {0.5 * (1 - r), 0.5 * (1 + r)};
-            double fs[2] = {0.5 * (1 - s), 0.5 * (1 + s)};
-            double ft[2] = {0.5 * (1 - t), 0.5 * (1 + t)};
+        if (threadIdx.x < 36) {
+            // vertex (a, bb, c) at (c * 2 + bb) * 2 + a. Direction l steps a (r),
+            // bb (s) or c (t); p and q are the vertex sides of the line's first
+            // and second coordinate: (bb, c) for r, (a, c) for s, (a, bb) for t
+            const int l = threadIdx.x / 12, pq = (threadIdx.x / 3) % 4, ax = threadIdx.x % 3;
+            const int p = pq & 1, q = pq >> 1;
+            const int v0 = l == 0 ? (q * 2 + p) * 2 : (l == 1 ? q * 4 + p : q * 2 + p);
+            const int step = 1 << l;
+            dV[l][pq][ax] = 0.5 * (V[v0 + step][ax] - V[v0][ax]);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < 3 * n2; t += blockDim.x) {
+            const int l = t / n2, line = t % n2, u = line % n, v = line / n;
+            // the two coordinates of the line: (s, t) for l = r, (r, t) for l = s, (r, s) for l = t
+            const double fu0 = 0.5 - 0.5 * xi[u], fu1 = 0.5 + 0.5 * xi[u];
+            const double fv0 = 0.5 - 0.5 * xi[v], fv1 = 0.5 + 0.5 * xi[v];
             for (int ax = 0; ax < 3; ax++) {
-                double acc = 0.0;
-                for (int c = 0; c < 2; c++)
-                    for (int bb = 0; bb < 2; bb++)
-                        for (int a = 0; a < 2; a++) acc += V[(c * 2 + bb) * 2 + a][ax] * fr[a] * fs[bb] * ft[c];
-                X[ax * n3 + q] = acc;
+                // pair (p, q): p the first line coordinate's vertex side, q the second's
+                const double c0 = fma(dV[l][1][ax], fu1, dV[l][0][ax] * fu0);
+                const double c1 = fma(dV[l][3][ax], fu1, dV[l][2][ax] * fu0);
+                col[(l * 3 + ax) * n2 + line] = fma(c1, fv1, c0 * fv0);
             }
         }
         __syncthreads();
         for (int q = threadIdx.x; q < n3; q += blockDim.x) {
-            int i = q % n, j = (q / n) % n, k = q / n2;
-            double J[3][3];
+            const int i = q % n, j = (q / n) % n, k = q / n2;
+            double jr[3], js[3], jt[3];
             for (int ax = 0; ax < 3; ax++) {
-                const double *Xa = X + ax * n3;
-                double dr = 0, ds = 0, dt = 0;
-                for (int m = 0; m < n; m++) {
-                    dr += sD[i * n + m] * Xa[(k * n + j) * n + m];
-                    ds += sD[j * n + m] * Xa[(k * n + m) * n + i];
-                    dt += sD[k * n + m] * Xa[(m * n + j) * n + i];
-                }
-                J[ax][0] = dr;
-                J[ax][1] = ds;
-                J[ax][2] = dt;
+                jr[ax] = col[(0 * 3 + ax) * n2 + j + n * k];
+                js[ax] = col[(1 * 3 + ax) * n2 + i + n * k];
+                jt[ax] = col[(2 * 3 + ax) * n2 + i + n * j];
             }
-            double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-            double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-            double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-            double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-            double id = 1.0 / det;
-            // inverse: Ji[l][x] = d r_l / d x_x
-            double Ji[3][3];
-            Ji[0][0] = c00 * id;
-            Ji[1][0] = c01 * id;
-            Ji[2][0] = c02 * id;
-            Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
-            Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
-            Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
-            Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
-            Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
-            Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
-            double wd = w[i] * w[j] * w[k] * det;
+            double ar[3], as[3], at[3];
+            ar[0] = fma(js[1], jt[2], -js[2] * jt[1]);
+            ar[1] = fma(js[2], jt[0], -js[0] * jt[2]);
+            ar[2] = fma(js[0], jt[1], -js[1] * jt[0]);
+            as[0] = fma(jt[1], jr[2], -jt[2] * jr[1]);
+            as[1] = fma(jt[2], jr[0], -jt[0] * jr[2]);
+            as[2] = fma(jt[0], jr[1], -jt[1] * jr[0]);
+            at[0] = fma(jr[1], js[2], -jr[2] * js[1]);
+            at[1] = fma(jr[2], js[0], -jr[0] * js[2]);
+            at[2] = fma(jr[0], js[1], -jr[1] * js[0]);
+            const double det = fma(jr[2], ar[2], fma(jr[1], ar[1], jr[0] * ar[0]));
+            const double wq = w[i] * w[j] * w[k];
+            const double sc = wq / det;
             double g[7];
-            const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
-            for (int f = 0; f < 6; f++)
-                g[f] = wd * (Ji[pa[f]][0] * Ji[pb[f]][0] + Ji[pa[f]][1] * Ji[pb[f]][1] + Ji[pa[f]][2] * Ji[pb[f]][2]);
-            g[6] = wd;
-            int64_t base = ((e * n + k) * 7) * (int64_t)n2 + j * n + i;
+            g[0] = sc * fma(ar[2], ar[2], fma(ar[1], ar[1], ar[0] * ar[0]));
+            g[1] = sc * fma(ar[2], as[2], fma(ar[1], as[1], ar[0] * as[0]));
+            g[2] = sc * fma(ar[2], at[2], fma(ar[1], at[1], ar[0] * at[0]));
+            g[3] = sc * fma(as[2], as[2], fma(as[1], as[1], as[0] * as[0]));
+            g[4] = sc * fma(as[2], at[2], fma(as[1], at[1], as[0] * at[0]));
+            g[5] = sc * fma(at[2], at[2], fma(at[1], at[1], at[0] * at[0]));
+            g[6] = wq * det;
+            const int64_t base = ((e * n + k) * 7) * (int64_t)n2 + j * n + i;
             for (int c = 0; c < 7; c++) {
                 geo[base + (int64_t)c * n2] = g[c];
                 if (geo32) geo32[base + (int64_t)c * n2] = (float)g[c];
@@ -528,7 +537,7 @@ static hb_status scan_exclusive(const int32_t *in, int32_t *out, int64_t n, cuda
 {
     const int64_t nchunks = (n + 1023) / 1024;
     int64_t *sums = nullptr;
-    HB_TRY_CUDA(cudaMalloc((void **)&sums, sizeof(int64_t) * (nchunks + 1)));
+    HB_TRY_CUDA(hb_dev_alloc((void **)&sums, sizeof(int64_t) * (nchunks + 1), s));
     hb_count_launch();
     k_scan_chunks<<<(unsigned)nchunks, 1024, 0, s>>>(in, n, out, sums);
     hb_count_launch();
@@ -539,7 +548,7 @@ static hb_status scan_exclusive(const int32_t *in, int32_t *out, int64_t n, cuda
     int64_t tot = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, sums + nchunks, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(sums);
+    hb_dev_free(sums, s);
     if (e != cudaSuccess) {
         hb_set_error("scan: %s", cudaGetErrorString(e));
         return HB_ERR_CUDA;
@@ -559,8 +568,8 @@ static hb_status build_surface_csr(hb_mesh *m, cudaStream_t s)
         hb_set_error("surface CSR: %s", cudaGetErrorString(e));
         st = e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;
     };
-    cudaError_t e = cudaMalloc((void **)&cnt, sizeof(int32_t) * (ng + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&srow_of, sizeof(int32_t) * (ng + 1));
+    cudaError_t e = hb_dev_alloc((void **)&cnt, sizeof(int32_t) * (ng + 1), s);
+    if (e == cudaSuccess) e = hb_dev_alloc((void **)&srow_of, sizeof(int32_t) * (ng + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (ng + 1), s);
     if (e != cudaSuccess) { fail(e); goto done; }
     hb_count_launch();
@@ -570,9 +579,9 @@ static hb_status build_surface_csr(hb_mesh *m, cudaStream_t s)
     if ((e = cudaGetLastError()) != cudaSuccess) { fail(e); goto done; }
     if ((st = scan_exclusive(srow_of, srow_of, ng + 1, s, &nsr)) != HB_OK) goto done;
     m->nsr = nsr;
-    e = cudaMalloc((void **)&m->srow_g, sizeof(int32_t) * (nsr + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&m->srowptr, sizeof(int32_t) * (nsr + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&scnt, sizeof(int32_t) * (nsr + 1));
+    e = hb_dev_alloc((void **)&m->srow_g, sizeof(int32_t) * (nsr + 1), s);
+    if (e == cudaSuccess) e = hb_dev_alloc((void **)&m->srowptr, sizeof(int32_t) * (nsr + 1), s);
+    if (e == cudaSuccess) e = hb_dev_alloc((void **)&scnt, sizeof(int32_t) * (nsr + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(scnt, 0, sizeof(int32_t) * (nsr + 1), s);
     if (e != cudaSuccess) { fail(e); goto done; }
     hb_count_launch();
@@ -580,7 +589,7 @@ static hb_status build_surface_csr(hb_mesh *m, cudaStream_t s)
     if ((e = cudaGetLastError()) != cudaSuccess) { fail(e); goto done; }
     if ((st = scan_exclusive(scnt, m->srowptr, nsr + 1, s, &nnz)) != HB_OK) goto done;
     m->nnz_s = nnz;
-    e = cudaMalloc((void **)&m->scols, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+    e = hb_dev_alloc((void **)&m->scols, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(scnt, 0, sizeof(int32_t) * (nsr + 1), s);
     if (e != cudaSuccess) { fail(e); goto done; }
     hb_count_launch();
@@ -591,9 +600,9 @@ static hb_status build_surface_csr(hb_mesh *m, cudaStream_t s)
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e); goto done; }
     m->device_bytes += sizeof(int32_t) * (2 * (nsr + 1) + nnz);
 done:
-    cudaFree(cnt);
-    cudaFree(srow_of);
-    cudaFree(scnt);
+    hb_dev_free(cnt, s);
+    hb_dev_free(srow_of, s);
+    hb_dev_free(scnt, s);
     return st;
 }
 
@@ -641,27 +650,28 @@ void hb_mesh_drop_graphs(hb_mesh *m)
 // ---------------------------------------------------------------- mesh lifetime
 
 
-extern "C" hb_status hb_mesh_destroy(hb_mesh *m)
+// Frees everything the mesh holds. The arrays allocated while it was built
+// are stream-ordered (freed on s); the ones grown later by the solvers and the
+// autotuner (cg_vec, spos, inv_diag) are plain allocations.
+static void mesh_free(hb_mesh *m, cudaStream_t s)
 {
-    if (!m) return HB_OK;
-    hb_device_guard dg(m->device);
-    cudaFree(m->l2g);
-    cudaFree(m->geo);
-    cudaFree(m->geo32);
-    cudaFree(m->rowptr);
-    cudaFree(m->cols);
-    cudaFree(m->mdiag);
-    cudaFree(m->mdiag32);
-    cudaFree(m->yL);
-    cudaFree(m->partials);
-    cudaFree(m->counters);
-    cudaFree(m->state);
+    hb_dev_free(m->l2g, s);
+    hb_dev_free(m->geo, s);
+    hb_dev_free(m->geo32, s);
+    hb_dev_free(m->rowptr, s);
+    hb_dev_free(m->cols, s);
+    hb_dev_free(m->mdiag, s);
+    hb_dev_free(m->mdiag32, s);
+    hb_dev_free(m->yL, s);
+    hb_dev_free(m->partials, s);
+    hb_dev_free(m->counters, s);
+    hb_dev_free(m->state, s);
+    hb_dev_free(m->srow_g, s);
+    hb_dev_free(m->srowptr, s);
+    hb_dev_free(m->scols, s);
+    hb_dev_free(m->ax_partials, s);
     cudaFree(m->cg_vec);
-    cudaFree(m->srow_g);
-    cudaFree(m->srowptr);
-    cudaFree(m->scols);
     cudaFree(m->spos);
-    cudaFree(m->ax_partials);
     cudaFree(m->inv_diag);
     cudaFree(m->inv_diag32);
     for (auto &g : m->graphs)
@@ -669,11 +679,28 @@ extern "C" hb_status hb_mesh_destroy(hb_mesh *m)
     if (m->cg_stream) cudaStreamDestroy(m->cg_stream);
     if (m->cg_ev[0]) cudaEventDestroy(m->cg_ev[0]);
     if (m->cg_ev[1]) cudaEventDestroy(m->cg_ev[1]);
-    if (m->state_host) cudaFreeHost(m->state_host);
+    hb_pinned_put(m->state_host);
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);
     delete m;
+}
+
+extern "C" hb_status hb_mesh_destroy(hb_mesh *m)
+{
+    if (!m) return HB_OK;
+    hb_device_guard dg(m->device);
+    // work on any stream may still read the arrays: wait for the device, as a
+    // plain cudaFree would
+    cudaDeviceSynchronize();
+    mesh_free(m, nullptr);
     return HB_OK;
+}
+
+void hb_mesh_release(hb_mesh *m, cudaStream_t s)
+{
+    if (!m) return;
+    hb_device_guard dg(m->device);
+    mesh_free(m, s);
 }
 
 #define HB_TRY_MESH(call)                                                        \
@@ -683,9 +710,9 @@ extern "C" hb_status hb_mesh_destroy(hb_mesh *m)
             hb_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,              \
                          cudaGetErrorString(e_));                                \
             hb_mesh_destroy(m);                                                  \
-            cudaFree(tmp_cnt);                                                   \
-            cudaFree(tmp_sum);                                                   \
-            cudaFree(tmp_det);                                                   \
+            hb_dev_free(tmp_cnt, s);                                             \
+            hb_dev_free(tmp_sum, s);                                             \
+            hb_dev_free(tmp_det, s);                                             \
             return e_ == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA; \
         }                                                                        \
     } while (0)
@@ -733,7 +760,7 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     size_t bytes = 0;
     auto alloc = [&](void **p, size_t b) {
         bytes += b;
-        return cudaMalloc(p, b > 0 ? b : 16);
+        return hb_dev_alloc(p, b, s);
     };
     HB_TRY_MESH(alloc((void **)&m->l2g, sizeof(int32_t) * n_local));
     HB_TRY_MESH(alloc((void **)&m->geo, sizeof(double) * 7 * n_local));
@@ -745,7 +772,7 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     HB_TRY_MESH(alloc((void **)&m->partials, sizeof(double) * HB_RED_MAXV * HB_RED_BLOCKS));
     HB_TRY_MESH(alloc((void **)&m->counters, sizeof(unsigned) * 8));
     HB_TRY_MESH(alloc((void **)&m->state, sizeof(hb_cg_state) * 4));
-    HB_TRY_MESH(cudaMallocHost((void **)&m->state_host, sizeof(hb_cg_state)));
+    HB_TRY_MESH(hb_pinned_get((void **)&m->state_host, sizeof(hb_cg_state)));
     HB_TRY_MESH(cudaEventCreate(&m->ev0));
     HB_TRY_MESH(cudaEventCreate(&m->ev1));
     HB_TRY_MESH(cudaMemsetAsync(m->counters, 0, sizeof(unsigned) * 8, s));
@@ -757,11 +784,12 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     HB_TRY_MESH(cudaGetLastError());
 
     // geometry: one element per block
-    int gthreads = n * n * n < 256 ? ((n * n * n + 31) / 32) * 32 : 256;
+    // at least 64 threads: 36 of them form the edge differences
+    int gthreads = n * n * n < 256 ? std::max(64, ((n * n * n + 31) / 32) * 32) : 256;
     int gblocks = (int)(E < 152 * 64 ? E : 152 * 64);
-    size_t gsmem = sizeof(double) * (3 * n * n * n + n * n);
+    size_t gsmem = sizeof(double) * 9 * n * n;
     HB_TRY_MESH(cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
-    HB_TRY_MESH(cudaMalloc((void **)&tmp_det, sizeof(double) * (gblocks + 1)));
+    HB_TRY_MESH(hb_dev_alloc((void **)&tmp_det, sizeof(double) * (gblocks + 1), s));
     hb_count_launch();
     k_geometry<<<gblocks, gthreads, gsmem, s>>>(b, d->perturb, d->seed, E, m->geo, m->geo32, tmp_det);
     HB_TRY_MESH(cudaGetLastError());
@@ -770,13 +798,13 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     HB_TRY_MESH(cudaGetLastError());
 
     // CSR of Z^T: count, scan, fill, sort rows
-    HB_TRY_MESH(cudaMalloc((void **)&tmp_cnt, sizeof(int32_t) * (ng + 1)));
+    HB_TRY_MESH(hb_dev_alloc((void **)&tmp_cnt, sizeof(int32_t) * (ng + 1), s));
     HB_TRY_MESH(cudaMemsetAsync(tmp_cnt, 0, sizeof(int32_t) * (ng + 1), s));
     hb_count_launch();
     k_count<<<grid_for(n_local, 256), 256, 0, s>>>(m->l2g, n_local, tmp_cnt);
     HB_TRY_MESH(cudaGetLastError());
     const int64_t nchunks = (ng + 1 + 1023) / 1024;
-    HB_TRY_MESH(cudaMalloc((void **)&tmp_sum, sizeof(int64_t) * (nchunks + 1)));
+    HB_TRY_MESH(hb_dev_alloc((void **)&tmp_sum, sizeof(int64_t) * (nchunks + 1), s));
     hb_count_launch();
     k_scan_chunks<<<(unsigned)nchunks, 1024, 0, s>>>(tmp_cnt, ng + 1, m->rowptr, tmp_sum);
     HB_TRY_MESH(cudaGetLastError());
@@ -802,9 +830,9 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     k_sort_rows<<<grid_for(ng, 256), 256, 0, s>>>(m->rowptr, m->cols, ng, m->geo, n, m->mdiag, m->mdiag32);
     HB_TRY_MESH(cudaGetLastError());
     HB_TRY_MESH(cudaStreamSynchronize(s));
-    cudaFree(tmp_cnt);
-    cudaFree(tmp_sum);
-    cudaFree(tmp_det);
+    hb_dev_free(tmp_cnt, s);
+    hb_dev_free(tmp_sum, s);
+    hb_dev_free(tmp_det, s);
     tmp_cnt = nullptr;
     tmp_sum = nullptr;
     tmp_det = nullptr;
@@ -815,7 +843,7 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
         // one partial per element-kernel block (at most one block per element)
         // one partial per element-kernel block: at most one block per element
         m->n_ax_partials = E + 1;
-        cudaError_t ae = cudaMalloc((void **)&m->ax_partials, sizeof(double) * m->n_ax_partials);
+        cudaError_t ae = hb_dev_alloc((void **)&m->ax_partials, sizeof(double) * m->n_ax_partials, s);
         if (ae != cudaSuccess) {
             hb_set_error("ax partials: %s", cudaGetErrorString(ae));
             hb_mesh_destroy(m);
@@ -827,6 +855,15 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
         hb_set_error("non-positive Jacobian determinant (min det J = %g)", m->min_detJ);
         hb_mesh_destroy(m);
         return HB_ERR_GEOMETRY;
+    }
+    // every stream-ordered array is ready for any stream once s has drained
+    {
+        const cudaError_t se = cudaStreamSynchronize(s);
+        if (se != cudaSuccess) {
+            hb_set_error("mesh set-up: %s", cudaGetErrorString(se));
+            hb_mesh_destroy(m);
+            return HB_ERR_CUDA;
+        }
     }
     *out = m;
     return HB_OK;

@@ -69,6 +69,8 @@ def test_same_result_alone_and_in_a_mix():
         assert _check_residual(full, x) <= 1.01 * o["rtol"]
     st = srv.stats()
     assert st.completed == 2 + len(others) and st.active == 0 and st.pending == 0
+    # the worker's time by phase: building requests, rounds, retiring
+    assert st.rounds > 0 and st.admit_s > 0.0 and st.round_s > 0.0 and st.retire_s >= 0.0
     srv.close()
 
 
