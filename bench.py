@@ -39,6 +39,11 @@ import time
 
 import numpy as np
 
+# The serving workload runs every resident solve on its own CUDA stream; with
+# the default 8 hardware work queues unrelated streams share queues and wait
+# on each other's kernels. Read when the CUDA context is created.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)

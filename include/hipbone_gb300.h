@@ -378,22 +378,25 @@ hb_status hb_scat_cg_solve(const hb_scat *sc, const hb_cg_opts *opts, const doub
  * A CG server with continuous batching on one GPU (the paper runs one solve at
  * a time; the server applies Algorithm 1 in the FP32-inner / FP64
  * defect-correction form of hb_cg_solve to many concurrent requests).
- * Requests queue on submit; a worker thread admits them first come, first
- * served, into free slots while the device-memory budget allows, keeps each
- * solve's mesh and vectors resident, and advances all resident solves with
- * one launch of a CUDA graph per round of iters_per_launch inner iterations
- * (graphs over the first 4, 8, 16, ... slot positions are captured at
- * creation; a round launches the smallest that covers every busy slot, and
- * admission fills the lowest free position). While a round runs, the worker
- * builds queued requests (mesh, vectors, right-hand side) on a second stream;
- * between rounds it retires finished solves (their memory freed in stream
- * order after the round) and publishes the built ones. While it runs the
- * server lets the library's memory pool keep up to its budget of freed
- * memory for reuse. Every slot runs on fixed grids with its own
+ * Requests queue on submit; a builder thread takes them first come, first
+ * served, into free slots while the device-memory budget allows and builds
+ * each one's mesh, vectors and right-hand side on its own stream. A worker
+ * thread keeps every resident solve going on the slot's own stream: one
+ * launch of the slot's CUDA graph (captured at creation) runs a round of
+ * iters_per_launch inner iterations, and the slot's next round is launched as
+ * soon as its last one has finished, so solves of different sizes advance at
+ * their own pace side by side. A finished solve is retired at once (its
+ * memory freed in stream order). While it runs the server lets the library's
+ * memory pool keep up to its budget of freed memory for reuse. Every slot
+ * runs on fixed grids with its own
  * reductions: a request's result does not depend on which others share the
  * GPU. The right-hand side is hb_fill_rhs kind 0 with the request's seed and
  * x0 = 0. Degrees N = 1..11; opts.prec must be HB_MIXED, opts.rtol > 0 and
- * opts.precond = 0. */
+ * opts.precond = 0. Requests of at most 4 Mi local nodes run on higher-priority
+ * streams, and while one of their rounds is in flight a larger request's next
+ * round waits (2 ms at most). The server uses two streams per slot: set
+ * CUDA_DEVICE_MAX_CONNECTIONS=32 before the CUDA context is created, or the
+ * streams share the default 8 hardware queues and wait on each other. */
 typedef struct hb_server hb_server;
 typedef struct {
     size_t mem_budget_bytes;   /* device memory the resident solves may hold */
@@ -404,9 +407,13 @@ typedef struct {
     int64_t submitted, admitted, completed, rejected, rounds;
     int active, pending;
     size_t mem_used;
-    /* wall seconds the worker spent admitting (mesh and vector set-up),
-     * running rounds (launch to state read-back) and retiring solves */
+    /* wall seconds spent building admitted requests (builder thread), with
+     * at least one round in flight, and retiring solves (worker thread);
+     * rounds counts every slot's rounds */
     double admit_s, round_s, retire_s;
+    /* sums over completed requests: queued (submit to build start), building,
+     * running (build end to retirement) */
+    double queue_s, build_s, run_s;
 } hb_server_stats_t;
 
 hb_status hb_server_create(const hb_server_opts *opts, hb_server **out);

@@ -1,13 +1,15 @@
 // CG server with continuous batching on one GPU.
 //
 // Requests (a mesh description, solver options and a right-hand-side seed)
-// are queued by hb_server_submit. A worker thread admits them into slots
-// while slots and the device-memory budget allow, keeps each solve's mesh and
-// vectors resident, and advances all resident solves together: one launch of
-// a CUDA graph, captured when the server is created, runs one round for the
-// slot positions it covers (graphs over the first 4, 8, 16, ... positions;
-// a round takes the smallest covering every busy slot, and admission fills
-// the lowest free position). A round is the FP32-inner / FP64 defect-correction
+// are queued by hb_server_submit. A builder thread takes them, first come
+// first served, into free slots while the device-memory budget allows and
+// builds each one's mesh and vectors on its own stream (stream-ordered
+// allocations: nothing waits for the solves running meanwhile). A worker
+// thread keeps every resident solve going on the slot's own stream: one
+// launch of the slot's CUDA graph, captured when the server is created, runs
+// one round, and the worker launches the slot's next round as soon as its
+// last one has finished, so solves of different sizes advance at their own
+// pace and share the GPU. A round is the FP32-inner / FP64 defect-correction
 // scheme of hb_cg_solve written as per-slot device state:
 //   - if the slot's inner CG has stopped: x += ||r|| d (FP64);
 //   - if the slot needs an outer step: r = b - A x in FP64, stop when
@@ -16,10 +18,8 @@
 //     accuracy).
 // Every kernel of a slot reads the slot's descriptor and state from device
 // memory and returns at once when the slot is empty or has nothing to do, so
-// the same graph serves whatever set of requests is resident. While a round
-// runs the worker builds queued requests on a second stream (stream-ordered
-// allocations: nothing waits for the round); between rounds it retires
-// finished solves and publishes the built ones.
+// a slot's graph serves whichever request the slot holds. Finished solves are
+// retired with stream-ordered frees on the slot's stream.
 // Each slot's kernels run on fixed grids with per-slot reductions, so a
 // request's result does not depend on which other requests share the GPU.
 #include <algorithm>
@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(HB_SERVE_THREADS) serve_update_xp_kernel(const
     cg_update_xp_body<float>(d.d32, d.p32, d.r32, d.n_global, d.counters + 3, &S->inner);
 }
 
+
 // ---------------------------------------------------------------- host side
 
 namespace {
@@ -168,6 +169,7 @@ struct request {
     uint64_t seed;
     int keep_x;
     double t_submit;
+    double t_build0 = 0, t_build1 = 0;  // the build's start and end
     size_t est;
 };
 
@@ -178,45 +180,64 @@ struct finished {
     std::vector<double> x;
 };
 
+// FREE -> BUILDING (builder, lock released) -> BUILT -> RUNNING (worker) -> FREE
+enum slot_phase { SL_FREE = 0, SL_BUILDING, SL_BUILT, SL_RUNNING };
+
 struct slot {
-    bool busy = false;       // reserved: being built, built, or resident
-    bool published = false;  // its descriptor is active on the device
+    int phase = SL_FREE;
+    bool inflight = false;  // a round of the slot is on its stream
+    cudaStream_t stream = nullptr;  // the slot's stream for this request (by its size)
+    bool small = false;             // at most kSmallNodes local nodes
+    double t_held = 0;              // > 0: a large solve's next round held back since then
     hb_mesh *mesh = nullptr;
     void *mem = nullptr;  // vectors and per-slot workspace
     size_t bytes = 0;
     request req{};
-    hb_slot_state init{};  // the state published with the descriptor
-    double t_admit = 0;
 };
 
 }  // namespace
 
+// Builder threads, each with its own stream; requests with at most
+// kSmallNodes local nodes run on their slot's higher-priority stream.
+constexpr int kBuilders = 2;
+constexpr int64_t kSmallNodes = 4 << 20;
+// Shortest job first, bounded: while a small request has a round in flight,
+// a large one's next round waits, at most kHoldS seconds.
+constexpr double kHoldS = 2e-3;
+
 struct hb_server {
     int device = 0;
-    cudaStream_t s_main = nullptr;  // rounds, publication and retirement
-    cudaStream_t s_adm = nullptr;   // building admitted requests beside the rounds
-    cudaEvent_t ev_round = nullptr;
+    cudaStream_t s_adm[kBuilders] = {};  // the builders' streams (highest priority)
+    // per slot: rounds, publication and retirement on the low-priority stream
+    // (large requests) or the middle-priority one (small requests)
+    std::vector<cudaStream_t> streams, streams_hi;
+    std::vector<cudaEvent_t> events;    // per slot: end of its last round
+    std::vector<cudaGraph_t> graphs;    // per slot: one round
+    std::vector<cudaGraphExec_t> execs;
     int cap = 0, k = 0;
     size_t budget = 0, used = 0;
     hb_slot_desc *d_desc = nullptr;
     hb_slot_state *d_state = nullptr;
-    hb_slot_state *h_state = nullptr;  // pinned
-    std::vector<hb_slot_desc> h_desc;
-    // round graphs over the first 4, 8, 16, ... slot positions (the last one
-    // over all of them): a round runs the smallest that covers every busy
-    // slot, and admission fills the lowest free position, so at low load the
-    // launches of idle slot positions are not paid
-    std::vector<int> graph_slots;
-    std::vector<cudaGraph_t> graphs;
-    std::vector<cudaGraphExec_t> execs;
+    hb_slot_state *h_state = nullptr;  // pinned: each slot's state after its last round
+    std::vector<hb_slot_desc> h_desc;  // the host's record of each slot's descriptor
+    // pinned sources of the copies the worker issues (pageable sources would
+    // stage through buffers the builders' copies share): per slot the
+    // descriptor and initial state to publish, and one idle descriptor
+    hb_slot_desc *pin_desc = nullptr;
+    hb_slot_state *pin_init = nullptr;
+    hb_slot_desc *pin_idle = nullptr;
     std::vector<slot> slots;
     std::deque<request> pending;
     std::map<int64_t, finished> done;
-    std::thread worker;
+    std::thread worker, builders[kBuilders];
     std::mutex mu;
-    std::condition_variable cv;
+    std::condition_variable cv;        // worker: a slot was built, or stop
+    std::condition_variable cv_build;  // builder: a request queued, a slot or memory freed, or stop
     bool stop = false;
-    bool inject_round_error = false;  // test hook: the next round reports a failed CUDA call
+    bool inject_round_error = false;  // test hook: the next launch reports a failed CUDA call
+    int inflight = 0;
+    int small_inflight = 0;
+    double t_busy = 0;  // when the number of rounds in flight last left zero
     int64_t next_ticket = 1;
     hb_server_stats_t stats{};
     char err[256] = {0};
@@ -236,47 +257,36 @@ static size_t estimate_bytes(const hb_mesh_desc &d)
 
 static size_t vec_stride(int64_t n) { return (size_t)((n + 63) / 64 * 64); }
 
-// Captures the round over the first `nslots` slot positions.
-static hb_status capture_round_graph(hb_server *S, int nslots, cudaGraph_t *graph_out, cudaGraphExec_t *exec_out)
+// Captures one round of slot i on the slot's stream.
+static hb_status capture_slot_graph(hb_server *S, int i)
 {
-    // fork one branch per slot position from s_main, join them at the end
-    std::vector<cudaStream_t> br(nslots);
-    std::vector<cudaEvent_t> ev(nslots + 1);
+    cudaStream_t s = S->streams[i];
+    const hb_slot_desc *D = S->d_desc + i;
+    hb_slot_state *T = S->d_state + i;
+    HB_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     hb_status st = HB_OK;
-    for (int i = 0; i < nslots; i++) HB_TRY_CUDA(cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking));
-    for (int i = 0; i <= nslots; i++) HB_TRY_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
-    HB_TRY_CUDA(cudaStreamBeginCapture(S->s_main, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaEventRecord(ev[nslots], S->s_main);
-    for (int i = 0; i < nslots && e == cudaSuccess && st == HB_OK; i++) {
-        cudaStream_t s = br[i];
-        const hb_slot_desc *D = S->d_desc + i;
-        hb_slot_state *T = S->d_state + i;
-        if ((e = cudaStreamWaitEvent(s, ev[nslots], 0)) != cudaSuccess) break;
-        serve_transition_kernel<<<1, 32, 0, s>>>(D, T);
-        serve_xupdate_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
-        if ((st = hb_serve_launch_ax_f64(D, T, s)) != HB_OK) break;
+    serve_transition_kernel<<<1, 32, 0, s>>>(D, T);
+    serve_xupdate_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
+    st = hb_serve_launch_ax_f64(D, T, s);
+    if (st == HB_OK) {
         serve_asm64_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
         serve_residual_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
         serve_decide_kernel<<<1, 32, 0, s>>>(D, T);
         serve_inner_init_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
         serve_begin_inner_kernel<<<1, 32, 0, s>>>(D, T);
-        for (int it = 0; it < S->k && st == HB_OK; it++) {
-            if ((st = hb_serve_launch_ax_f32(D, T, s)) != HB_OK) break;
-            serve_asm32_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
-            serve_update_r_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
-            serve_update_xp_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
-        }
-        if ((e = cudaGetLastError()) != cudaSuccess) break;
-        if ((e = cudaEventRecord(ev[i], s)) != cudaSuccess) break;
-        if ((e = cudaStreamWaitEvent(S->s_main, ev[i], 0)) != cudaSuccess) break;
     }
+    for (int it = 0; it < S->k && st == HB_OK; it++) {
+        if ((st = hb_serve_launch_ax_f32(D, T, s)) != HB_OK) break;
+        serve_asm32_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
+        serve_update_r_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
+        serve_update_xp_kernel<<<HB_SERVE_GRID, HB_SERVE_THREADS, 0, s>>>(D, T);
+    }
+    cudaError_t e = cudaGetLastError();
     cudaGraph_t g = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(S->s_main, &g);
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess && st == HB_OK) e = cudaGraphInstantiate(exec_out, g, 0);
-    *graph_out = g;
-    for (auto s : br) cudaStreamDestroy(s);
-    for (auto x : ev) cudaEventDestroy(x);
+    S->graphs[i] = g;
+    if (e == cudaSuccess && st == HB_OK) e = cudaGraphInstantiate(&S->execs[i], g, 0);
     if (st != HB_OK) return st;
     if (e != cudaSuccess) {
         hb_set_error("round graph: %s", cudaGetErrorString(e));
@@ -284,24 +294,25 @@ static hb_status capture_round_graph(hb_server *S, int nslots, cudaGraph_t *grap
     }
     return HB_OK;
 }
-
-// Creates the slot's mesh and vectors and publishes its descriptor and state.
-static hb_status admit(hb_server *S, int si, const request &rq)
+// Builds the slot's mesh, vectors and right-hand side on the builder's stream
+// (called without the lock; the slot is BUILDING, which the worker leaves
+// alone). On return the arrays are ready for any stream.
+static hb_status admit(hb_server *S, int si, const request &rq, cudaStream_t sa)
 {
     slot &sl = S->slots[si];
     hb_mesh_desc md = rq.desc;
     md.keep_fp32_copy = 1;
     hb_mesh *m = nullptr;
-    hb_status st = hb_mesh_create(&md, S->s_adm, &m);
+    hb_status st = hb_mesh_create(&md, sa, &m);
     if (st != HB_OK) return st;
     const int64_t n = m->n_global;
     const size_t ns = vec_stride(n);
     const size_t bytes = ns * (4 * sizeof(double) + 4 * sizeof(float)) +
                          sizeof(double) * (HB_RED_MAXV * HB_RED_BLOCKS + HB_SERVE_AXP) + 64 * sizeof(unsigned);
     void *mem = nullptr;
-    cudaError_t e = hb_dev_alloc(&mem, bytes, S->s_adm);
+    cudaError_t e = hb_dev_alloc(&mem, bytes, sa);
     if (e != cudaSuccess) {
-        hb_mesh_release(m, S->s_adm);
+        hb_mesh_release(m, sa);
         hb_set_error("slot vectors: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;
     }
@@ -346,16 +357,16 @@ static hb_status admit(hb_server *S, int si, const request &rq)
     hb_slot_state ss{};
     ss.phase = HB_SLOT_OUTER;
     ss.status = HB_OK;
-    e = cudaMemsetAsync(x, 0, sizeof(double) * ns, S->s_adm);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 64 * sizeof(unsigned), S->s_adm);
-    if (e == cudaSuccess) e = cudaMemsetAsync(axp, 0, HB_SERVE_AXP * sizeof(double), S->s_adm);
-    if (e == cudaSuccess) st = hb_fill_rhs(m, 0, rq.seed, 0.0, b, S->s_adm);
-    // built: the round stream may use it from now on (published between rounds)
-    if (e == cudaSuccess && st == HB_OK) e = cudaStreamSynchronize(S->s_adm);
+    e = cudaMemsetAsync(x, 0, sizeof(double) * ns, sa);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 64 * sizeof(unsigned), sa);
+    if (e == cudaSuccess) e = cudaMemsetAsync(axp, 0, HB_SERVE_AXP * sizeof(double), sa);
+    if (e == cudaSuccess) st = hb_fill_rhs(m, 0, rq.seed, 0.0, b, sa);
+    // built: the slot's stream may use it from now on
+    if (e == cudaSuccess && st == HB_OK) e = cudaStreamSynchronize(sa);
     if (e != cudaSuccess || st != HB_OK) {
-        cudaStreamSynchronize(S->s_adm);
-        hb_dev_free(mem, S->s_adm);
-        hb_mesh_release(m, S->s_adm);
+        cudaStreamSynchronize(sa);
+        hb_dev_free(mem, sa);
+        hb_mesh_release(m, sa);
         if (st == HB_OK) {
             hb_set_error("admission: %s", cudaGetErrorString(e));
             st = HB_ERR_CUDA;
@@ -366,15 +377,21 @@ static hb_status admit(hb_server *S, int si, const request &rq)
     sl.mem = mem;
     sl.bytes = m->device_bytes + bytes;
     sl.req = rq;
-    sl.init = ss;
-    sl.t_admit = now_s();
-    S->h_desc[si] = d;  // published by the worker between rounds
+    S->pin_init[si] = ss;
+    S->pin_desc[si] = d;
+    sl.small = m->n_local <= kSmallNodes;
+    sl.stream = sl.small ? S->streams_hi[si] : S->streams[si];
+    S->h_desc[si] = d;  // published by the worker
     return HB_OK;
 }
 
+
+// Reads a finished slot's results and frees it in stream order on the slot's
+// stream (its round has completed; the lock is held).
 static void retire(hb_server *S, int si, finished &f)
 {
     slot &sl = S->slots[si];
+    cudaStream_t s = sl.stream;
     const hb_slot_state &st = S->h_state[si];
     f.res.iters = st.inner_total;
     f.res.outer_iters = st.outer_it;
@@ -383,44 +400,46 @@ static void retire(hb_server *S, int si, finished &f)
     f.n_global = sl.mesh->n_global;
     if (sl.req.keep_x) {
         f.x.resize((size_t)f.n_global);
-        cudaMemcpy(f.x.data(), S->h_desc[si].x, sizeof(double) * f.n_global, cudaMemcpyDeviceToHost);
+        cudaMemcpyAsync(f.x.data(), S->h_desc[si].x, sizeof(double) * f.n_global, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
     }
-    // the slot goes idle before the next round; its memory is freed after
-    // that copy in stream order (no host wait)
     S->h_desc[si].active = 0;
-    cudaMemcpyAsync(S->d_desc + si, &S->h_desc[si], sizeof(hb_slot_desc), cudaMemcpyHostToDevice, S->s_main);
-    hb_dev_free(sl.mem, S->s_main);
-    hb_mesh_release(sl.mesh, S->s_main);
+    cudaMemcpyAsync(S->d_desc + si, S->pin_idle, sizeof(hb_slot_desc), cudaMemcpyHostToDevice, s);
+    hb_dev_free(sl.mem, s);
+    hb_mesh_release(sl.mesh, s);
     S->used -= std::min(S->used, sl.bytes);
     sl = slot{};
 }
 
-// Frees a resident slot's vectors and mesh without reading its results (the
-// failure path: the round that should have advanced it did not complete).
+// Frees a built or running slot without reading its results (the failure
+// path and the server's destruction): waits for the device first.
 static void release_slot(hb_server *S, int si)
 {
     slot &sl = S->slots[si];
+    cudaStream_t s = sl.stream ? sl.stream : S->streams[si];
     cudaDeviceSynchronize();
-    hb_dev_free(sl.mem, S->s_main);
-    hb_mesh_release(sl.mesh, S->s_main);
+    hb_dev_free(sl.mem, s);
+    hb_mesh_release(sl.mesh, s);
     S->used -= std::min(S->used, sl.bytes);
     S->h_desc[si].active = 0;
     sl = slot{};
 }
 
-// The server stops after a failed round: every resident request fails and
-// releases its memory, every queued one fails too, so each ticket resolves.
+// After a failed round the server stops: every request in a slot or in the
+// queue fails, so each ticket resolves; built and resident requests release
+// their memory here, the one being built when the builder is done with it.
 static void fail_server(hb_server *S, cudaError_t e, bool injected)
 {
     snprintf(S->err, sizeof S->err, "round%s: %s", injected ? " (injected)" : "", cudaGetErrorString(e));
-    for (int i = 0; i < S->cap; i++)
-        if (S->slots[i].busy) {
-            finished f{};
-            f.res.status = HB_ERR_CUDA;
-            f.latency_ms = f.res.time_ms = (now_s() - S->slots[i].req.t_submit) * 1e3;
-            S->done[S->slots[i].req.ticket] = std::move(f);
-            release_slot(S, i);
-        }
+    for (int i = 0; i < S->cap; i++) {
+        const int ph = S->slots[i].phase;
+        if (ph == SL_FREE) continue;
+        finished f{};
+        f.res.status = HB_ERR_CUDA;
+        f.latency_ms = f.res.time_ms = (now_s() - S->slots[i].req.t_submit) * 1e3;
+        S->done[S->slots[i].req.ticket] = std::move(f);
+        if (ph != SL_BUILDING) release_slot(S, i);  // the builder frees what it is building
+    }
     for (const request &rq : S->pending) {
         finished f{};
         f.res.status = HB_ERR_CUDA;
@@ -428,157 +447,219 @@ static void fail_server(hb_server *S, cudaError_t e, bool injected)
         S->done[rq.ticket] = std::move(f);
     }
     S->pending.clear();
-    S->stats.active = 0;
+    S->inflight = 0;
+    S->small_inflight = 0;
+    int active = 0;
+    for (auto &sl : S->slots) active += sl.phase != SL_FREE ? 1 : 0;
+    S->stats.active = active;
     S->stats.pending = 0;
     S->stats.mem_used = S->used;
     S->stop = true;
     S->cv.notify_all();
+    S->cv_build.notify_all();
 }
 
-// Takes the next queued request into the lowest free slot and builds it on the
-// admission stream (the lock is released meanwhile). Returns false when
-// nothing could be admitted (queue empty, no free slot, or over budget).
-static bool admit_one(hb_server *S, std::unique_lock<std::mutex> &lk)
+// Launches slot i's next round and the read-back of its state.
+static cudaError_t launch_round(hb_server *S, int i, bool *injected)
 {
-    for (;;) {
-        if (S->pending.empty()) return false;
-        request rq = S->pending.front();
-        if (rq.est > S->budget) {  // can never fit
+    *injected = S->inject_round_error;
+    S->inject_round_error = false;
+    cudaStream_t s = S->slots[i].stream;
+    cudaError_t e = *injected ? cudaErrorLaunchFailure : cudaGraphLaunch(S->execs[i], s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->h_state + i, S->d_state + i, sizeof(hb_slot_state), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(S->events[i], s);
+    if (e == cudaSuccess) {
+        if (S->inflight++ == 0) S->t_busy = now_s();
+        if (S->slots[i].small) S->small_inflight++;
+        S->slots[i].inflight = true;
+        S->slots[i].t_held = 0;
+    }
+    return e;
+}
+
+static void round_ended(hb_server *S, int i)
+{
+    S->slots[i].inflight = false;
+    if (S->slots[i].small) S->small_inflight--;
+    S->stats.rounds++;
+    if (--S->inflight == 0) S->stats.round_s += now_s() - S->t_busy;
+}
+
+// Keeps every resident solve going: a slot whose round has finished is
+// retired (solve done) or relaunched at once; built slots are published on
+// their stream and started. Polls the slots' events while rounds run.
+static void worker_loop(hb_server *S)
+{
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    double t_act = now_s();
+    while (!S->stop) {
+        bool acted = false;
+        cudaError_t e = cudaSuccess;
+        bool injected = false;
+        for (int i = 0; i < S->cap && e == cudaSuccess; i++) {
+            slot &sl = S->slots[i];
+            if (sl.phase == SL_BUILT) {
+                // publish: descriptor and initial state, then the first round
+                cudaStream_t s = sl.stream;
+                e = cudaMemcpyAsync(S->d_desc + i, S->pin_desc + i, sizeof(hb_slot_desc), cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(S->d_state + i, S->pin_init + i, sizeof(hb_slot_state), cudaMemcpyHostToDevice,
+                                        s);
+                sl.phase = SL_RUNNING;
+                if (e == cudaSuccess) e = launch_round(S, i, &injected);
+                acted = true;
+                continue;
+            }
+            if (sl.t_held > 0) {
+                // a held large round goes once no small round is in flight
+                if (S->small_inflight == 0 || now_s() - sl.t_held > kHoldS) {
+                    e = launch_round(S, i, &injected);
+                    acted = true;
+                }
+                continue;
+            }
+            if (!sl.inflight) continue;
+            const cudaError_t q = cudaEventQuery(S->events[i]);
+            if (q == cudaErrorNotReady) continue;
+            round_ended(S, i);
+            acted = true;
+            if (q != cudaSuccess) {
+                e = q;
+                break;
+            }
+            if (S->h_state[i].phase == HB_SLOT_DONE) {
+                const double tt = now_s();
+                finished f{};
+                const request rq = sl.req;
+                retire(S, i, f);
+                const double t_done = now_s();
+                const int64_t ticket = rq.ticket;
+                const double t_sub = rq.t_submit;
+                S->stats.queue_s += rq.t_build0 - rq.t_submit;
+                S->stats.build_s += rq.t_build1 - rq.t_build0;
+                S->stats.run_s += t_done - rq.t_build1;
+                f.latency_ms = (t_done - t_sub) * 1e3;
+                f.res.time_ms = f.latency_ms;
+                S->done[ticket] = std::move(f);
+                S->stats.completed++;
+                S->stats.retire_s += now_s() - tt;
+                S->cv_build.notify_all();
+            } else if (!sl.small && S->small_inflight > 0) {
+                sl.t_held = now_s();
+            } else {
+                e = launch_round(S, i, &injected);
+            }
+        }
+        if (e != cudaSuccess) {
+            fail_server(S, e, injected);
+            break;
+        }
+        int active = 0;
+        for (auto &sl : S->slots) active += sl.phase != SL_FREE ? 1 : 0;
+        S->stats.active = active;
+        S->stats.pending = (int)S->pending.size();
+        S->stats.mem_used = S->used;
+        const double t = now_s();
+        if (acted) {
+            t_act = t;
+            continue;
+        }
+        if (S->inflight == 0) {
+            S->cv.wait_for(lk, std::chrono::milliseconds(5));
+        } else {
+            // poll: spin for 0.2 ms after the last launch or retirement (short
+            // rounds end within it), then sleep between polls
+            lk.unlock();
+            if (t - t_act < 2e-4) std::this_thread::yield();
+            else std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        }
+    }
+    // rounds still on the slots' streams finish before the server is torn down
+    for (int i = 0; i < S->cap; i++)
+        if (S->slots[i].inflight) {
+            lk.unlock();
+            cudaEventSynchronize(S->events[i]);
+            lk.lock();
+            round_ended(S, i);
+        }
+}
+
+// Takes queued requests, first come first served, into free slots while the
+// budget allows and builds them on its own stream (the lock released meanwhile).
+static void builder_loop(hb_server *S, int b)
+{
+    cudaSetDevice(S->device);
+    cudaStream_t sa = S->s_adm[b];
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        if (!S->pending.empty() && S->pending.front().est > S->budget) {  // can never fit
+            const request rq = S->pending.front();
             S->pending.pop_front();
             finished f{};
             f.res.status = HB_ERR_NOMEM;
             f.latency_ms = (now_s() - rq.t_submit) * 1e3;
             S->done[rq.ticket] = std::move(f);
             S->stats.rejected++;
-            S->cv.notify_all();
             continue;
         }
         int si = -1;
         for (int i = 0; i < S->cap; i++)
-            if (!S->slots[i].busy) { si = i; break; }
-        if (si < 0 || S->used + rq.est > S->budget) return false;
+            if (S->slots[i].phase == SL_FREE) { si = i; break; }
+        if (S->pending.empty() || si < 0 || S->used + S->pending.front().est > S->budget) {
+            S->cv_build.wait_for(lk, std::chrono::milliseconds(5));
+            continue;
+        }
+        request rq = S->pending.front();
         S->pending.pop_front();
         S->used += rq.est;
-        S->slots[si].busy = true;  // reserved while it is built
+        S->slots[si].phase = SL_BUILDING;
         lk.unlock();
         const double ta = now_s();
-        hb_status st = admit(S, si, rq);
+        rq.t_build0 = ta;
+        const hb_status st = admit(S, si, rq, sa);
         const double tb = now_s();
+        if (st == HB_OK) S->slots[si].req.t_build1 = tb;
         lk.lock();
         S->stats.admit_s += tb - ta;
         S->used -= rq.est;
+        finished f{};
+        if (S->stop && S->done.count(rq.ticket)) {
+            // the server failed meanwhile and has resolved the ticket
+            if (st == HB_OK) {
+                S->used += S->slots[si].bytes;
+                release_slot(S, si);
+            } else {
+                S->slots[si] = slot{};
+            }
+            S->stats.mem_used = S->used;
+            S->stats.active = 0;
+            continue;
+        }
         if (st != HB_OK) {
             S->slots[si] = slot{};
-            finished f{};
             f.res.status = st;
-            f.latency_ms = (now_s() - rq.t_submit) * 1e3;
-            S->done[rq.ticket] = std::move(f);
             S->stats.rejected++;
-            S->cv.notify_all();
+        } else if (S->stop) {
+            // the server stopped meanwhile: the request fails, its memory goes
+            S->used += S->slots[si].bytes;
+            release_slot(S, si);
+            f.res.status = HB_ERR_CUDA;
+            int active = 0;
+            for (auto &sl : S->slots) active += sl.phase != SL_FREE ? 1 : 0;
+            S->stats.active = active;
+            S->stats.mem_used = S->used;
         } else {
             S->used += S->slots[si].bytes;
             S->stats.admitted++;
-        }
-        return true;
-    }
-}
-
-// One round advances every published solve; while it runs the worker builds
-// queued requests on the admission stream, one at a time, and goes back to the
-// round as soon as it has finished. Between rounds: retire the finished solves
-// (stream-ordered frees), publish the built ones, launch the next round.
-static void worker_loop(hb_server *S)
-{
-    cudaSetDevice(S->device);
-    std::unique_lock<std::mutex> lk(S->mu);
-    bool inflight = false;
-    double t_launch = 0;
-    for (;;) {
-        if (S->stop) break;
-        // publish what was built (no round in flight here)
-        if (!inflight) {
-            cudaError_t e = cudaSuccess;
-            for (int i = 0; i < S->cap && e == cudaSuccess; i++) {
-                slot &sl = S->slots[i];
-                if (!sl.busy || sl.published || !sl.mesh) continue;
-                e = cudaMemcpyAsync(S->d_desc + i, &S->h_desc[i], sizeof(hb_slot_desc), cudaMemcpyHostToDevice,
-                                    S->s_main);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(S->d_state + i, &sl.init, sizeof(hb_slot_state), cudaMemcpyHostToDevice,
-                                        S->s_main);
-                sl.published = true;
-            }
-            if (e != cudaSuccess) {
-                fail_server(S, e, false);
-                break;
-            }
-        }
-        int active = 0, top = 0;
-        for (int i = 0; i < S->cap; i++)
-            if (S->slots[i].busy) {
-                active++;
-                if (S->slots[i].published) top = i + 1;
-            }
-        S->stats.active = active;
-        S->stats.pending = (int)S->pending.size();
-        S->stats.mem_used = S->used;
-        // launch a round over the smallest graph that covers every published slot
-        if (!inflight && top > 0) {
-            const bool fail_round = S->inject_round_error;
-            S->inject_round_error = false;
-            size_t gi = 0;
-            while (gi + 1 < S->execs.size() && S->graph_slots[gi] < top) gi++;
-            t_launch = now_s();
-            cudaError_t e = fail_round ? cudaErrorLaunchFailure : cudaGraphLaunch(S->execs[gi], S->s_main);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(S->h_state, S->d_state, sizeof(hb_slot_state) * S->cap, cudaMemcpyDeviceToHost,
-                                    S->s_main);
-            if (e == cudaSuccess) e = cudaEventRecord(S->ev_round, S->s_main);
-            if (e != cudaSuccess) {
-                fail_server(S, e, fail_round);
-                break;
-            }
-            inflight = true;
-        }
-        // build queued requests while the round runs
-        const bool admitted = admit_one(S, lk);
-        if (S->stop) break;
-        if (inflight) {
-            const cudaError_t q = cudaEventQuery(S->ev_round);
-            if (q == cudaErrorNotReady && admitted) continue;  // more to build meanwhile
-            lk.unlock();
-            const cudaError_t e = cudaEventSynchronize(S->ev_round);
-            const double t_done = now_s();
-            lk.lock();
-            inflight = false;
-            S->stats.rounds++;
-            S->stats.round_s += t_done - t_launch;
-            if (e != cudaSuccess) {
-                fail_server(S, e, false);
-                break;
-            }
-            const double tt = now_s();
-            for (int i = 0; i < S->cap; i++) {
-                if (!S->slots[i].published || S->h_state[i].phase != HB_SLOT_DONE) continue;
-                finished f{};
-                const int64_t ticket = S->slots[i].req.ticket;
-                const double t_sub = S->slots[i].req.t_submit;
-                retire(S, i, f);
-                f.latency_ms = (now_s() - t_sub) * 1e3;
-                f.res.time_ms = f.latency_ms;
-                S->done[ticket] = std::move(f);
-                S->stats.completed++;
-            }
-            S->stats.retire_s += now_s() - tt;
+            S->slots[si].phase = SL_BUILT;
             S->cv.notify_all();
             continue;
         }
-        if (!admitted && top == 0) S->cv.wait_for(lk, std::chrono::milliseconds(2));
-    }
-    if (inflight) {
-        lk.unlock();
-        cudaEventSynchronize(S->ev_round);
-        lk.lock();
+        f.latency_ms = f.res.time_ms = (now_s() - rq.t_submit) * 1e3;
+        S->done[rq.ticket] = std::move(f);
     }
 }
 
@@ -602,14 +683,31 @@ extern "C" hb_status hb_server_create(const hb_server_opts *o, hb_server **out)
     S->budget = o->mem_budget_bytes;
     S->slots.resize(S->cap);
     S->h_desc.resize(S->cap);
-    cudaError_t e = cudaStreamCreateWithFlags(&S->s_main, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_adm, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_round, cudaEventDisableTiming);
+    S->streams.assign(S->cap, nullptr);
+    S->events.assign(S->cap, nullptr);
+    S->graphs.assign(S->cap, nullptr);
+    S->execs.assign(S->cap, nullptr);
+    S->streams_hi.assign(S->cap, nullptr);
+    // priorities: builders highest, small requests' rounds next, large ones lowest
+    int p_least = 0, p_greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&p_least, &p_greatest);
+    const int p_mid = p_greatest < p_least ? p_greatest + 1 : p_greatest;
+    for (int b = 0; b < kBuilders && e == cudaSuccess; b++)
+        e = cudaStreamCreateWithPriority(&S->s_adm[b], cudaStreamNonBlocking, p_greatest);
+    for (int i = 0; i < S->cap && e == cudaSuccess; i++) {
+        e = cudaStreamCreateWithPriority(&S->streams[i], cudaStreamNonBlocking, p_least);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&S->streams_hi[i], cudaStreamNonBlocking, p_mid);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->events[i], cudaEventDisableTiming);
+    }
     // resident requests come and go: keep their freed memory for reuse
     if (e == cudaSuccess) e = hb_dev_keep(std::max<uint64_t>(S->budget, hb_dev_keep_default()));
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_desc, sizeof(hb_slot_desc) * S->cap);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_state, sizeof(hb_slot_state) * S->cap);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_state, sizeof(hb_slot_state) * S->cap);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&S->pin_desc, sizeof(hb_slot_desc) * S->cap);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&S->pin_init, sizeof(hb_slot_state) * S->cap);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&S->pin_idle, sizeof(hb_slot_desc));
+    if (e == cudaSuccess) memset(S->pin_idle, 0, sizeof(hb_slot_desc));
     if (e == cudaSuccess) e = cudaMemset(S->d_desc, 0, sizeof(hb_slot_desc) * S->cap);
     if (e == cudaSuccess) e = cudaMemset(S->d_state, 0, sizeof(hb_slot_state) * S->cap);
     if (e != cudaSuccess) {
@@ -618,21 +716,13 @@ extern "C" hb_status hb_server_create(const hb_server_opts *o, hb_server **out)
         return e == cudaErrorMemoryAllocation ? HB_ERR_NOMEM : HB_ERR_CUDA;
     }
     memset(S->h_state, 0, sizeof(hb_slot_state) * S->cap);
-    for (int ns = 4;; ns *= 2) {
-        const int take = ns < S->cap ? ns : S->cap;
-        cudaGraph_t g = nullptr;
-        cudaGraphExec_t x = nullptr;
-        st = capture_round_graph(S, take, &g, &x);
-        if (g) S->graphs.push_back(g);
-        if (st != HB_OK) {
+    for (int i = 0; i < S->cap; i++)
+        if ((st = capture_slot_graph(S, i)) != HB_OK) {
             hb_server_destroy(S);
             return st;
         }
-        S->graph_slots.push_back(take);
-        S->execs.push_back(x);
-        if (take == S->cap) break;
-    }
     S->worker = std::thread(worker_loop, S);
+    for (int b = 0; b < kBuilders; b++) S->builders[b] = std::thread(builder_loop, S, b);
     *out = S;
     return HB_OK;
 }
@@ -664,7 +754,7 @@ extern "C" hb_status hb_server_submit(hb_server *S, const hb_mesh_desc *d, const
     S->pending.push_back(rq);
     S->stats.submitted++;
     *ticket = rq.ticket;
-    S->cv.notify_all();
+    S->cv_build.notify_all();
     return HB_OK;
 }
 
@@ -718,16 +808,20 @@ extern "C" hb_status hb_server_destroy(hb_server *S)
         S->stop = true;
         S->pending.clear();
         S->cv.notify_all();
+        S->cv_build.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
+    for (auto &t : S->builders)
+        if (t.joinable()) t.join();
     hb_device_guard dg(S->device);
     cudaDeviceSynchronize();
     for (int i = 0; i < S->cap; i++)
-        if (S->slots[i].busy) {
-            hb_dev_free(S->slots[i].mem, S->s_main);
-            hb_mesh_release(S->slots[i].mesh, S->s_main);
+        if (S->slots[i].phase != SL_FREE) {
+            cudaStream_t s = S->slots[i].stream ? S->slots[i].stream : S->streams[i];
+            hb_dev_free(S->slots[i].mem, s);
+            hb_mesh_release(S->slots[i].mesh, s);
         }
-    if (S->s_main) cudaStreamSynchronize(S->s_main);
+    cudaDeviceSynchronize();
     hb_dev_keep(hb_dev_keep_default());
     hb_dev_trim();
     for (auto x : S->execs)
@@ -737,9 +831,17 @@ extern "C" hb_status hb_server_destroy(hb_server *S)
     cudaFree(S->d_desc);
     cudaFree(S->d_state);
     if (S->h_state) cudaFreeHost(S->h_state);
-    if (S->s_main) cudaStreamDestroy(S->s_main);
-    if (S->s_adm) cudaStreamDestroy(S->s_adm);
-    if (S->ev_round) cudaEventDestroy(S->ev_round);
+    if (S->pin_desc) cudaFreeHost(S->pin_desc);
+    if (S->pin_init) cudaFreeHost(S->pin_init);
+    if (S->pin_idle) cudaFreeHost(S->pin_idle);
+    for (auto s : S->streams)
+        if (s) cudaStreamDestroy(s);
+    for (auto ev : S->events)
+        if (ev) cudaEventDestroy(ev);
+    for (auto s : S->streams_hi)
+        if (s) cudaStreamDestroy(s);
+    for (auto s : S->s_adm)
+        if (s) cudaStreamDestroy(s);
     delete S;
     return HB_OK;
 }

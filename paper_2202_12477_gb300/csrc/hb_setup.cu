@@ -382,17 +382,39 @@ __global__ void k_scan_chunks(const int32_t *in, int64_t n, int32_t *out, int64_
     if (t == 1023) chunk_sum[blockIdx.x] = s[t];
 }
 
-__global__ void k_scan_sums(int64_t *chunk_sum, int64_t nchunks)
+// Exclusive scan of the chunk sums in place (chunk_sum[nchunks] = the total):
+// one block of 1024 threads walks the sums in tiles of 1024, a warp-shuffle
+// scan per tile plus the running carry. Launch with 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_sums(int64_t *chunk_sum, int64_t nchunks)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        int64_t acc = 0;
-        for (int64_t c = 0; c < nchunks; c++) {
-            int64_t v = chunk_sum[c];
-            chunk_sum[c] = acc;
-            acc += v;
+    __shared__ int64_t wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nchunks; base += 1024) {
+        const int64_t c = base + t;
+        const int64_t v = c < nchunks ? chunk_sum[c] : 0;
+        int64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        chunk_sum[nchunks] = acc;
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int64_t z = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            wsum[lane] = z;
+        }
+        __syncthreads();
+        const int64_t incl = x + (w > 0 ? wsum[w - 1] : 0);
+        if (c < nchunks) chunk_sum[c] = carry + incl - v;
+        carry += wsum[31];
+        __syncthreads();  // wsum is rewritten by the next tile
     }
+    if (t == 0) chunk_sum[nchunks] = carry;
 }
 
 __global__ void k_scan_add(int32_t *out, int64_t n, const int64_t *chunk_sum)
@@ -442,12 +464,19 @@ __global__ void k_sort_rows(const int32_t *rowptr, int32_t *cols, int64_t ng, co
     }
 }
 
-__global__ void k_min_reduce(const double *v, int n, double *out)
+// *out = min of v[0..n): one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_min_reduce(const double *v, int n, double *out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double m = INFINITY;
-        for (int q = 0; q < n; q++) m = fmin(m, v[q]);
-        *out = m;
+    __shared__ double wm[32];
+    double m = INFINITY;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) m = fmin(m, v[q]);
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (int)(blockDim.x >> 5) ? wm[threadIdx.x] : INFINITY;
+        for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_down_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) *out = m;
     }
 }
 
@@ -541,7 +570,7 @@ static hb_status scan_exclusive(const int32_t *in, int32_t *out, int64_t n, cuda
     hb_count_launch();
     k_scan_chunks<<<(unsigned)nchunks, 1024, 0, s>>>(in, n, out, sums);
     hb_count_launch();
-    k_scan_sums<<<1, 32, 0, s>>>(sums, nchunks);
+    k_scan_sums<<<1, 1024, 0, s>>>(sums, nchunks);
     hb_count_launch();
     k_scan_add<<<grid_for(n, 256), 256, 0, s>>>(out, n, sums);
     cudaError_t e = cudaGetLastError();
@@ -670,10 +699,11 @@ static void mesh_free(hb_mesh *m, cudaStream_t s)
     hb_dev_free(m->srowptr, s);
     hb_dev_free(m->scols, s);
     hb_dev_free(m->ax_partials, s);
-    cudaFree(m->cg_vec);
-    cudaFree(m->spos);
-    cudaFree(m->inv_diag);
-    cudaFree(m->inv_diag32);
+    // (a plain cudaFree may wait for the device: only for arrays that exist)
+    if (m->cg_vec) cudaFree(m->cg_vec);
+    if (m->spos) cudaFree(m->spos);
+    if (m->inv_diag) cudaFree(m->inv_diag);
+    if (m->inv_diag32) cudaFree(m->inv_diag32);
     for (auto &g : m->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (m->cg_stream) cudaStreamDestroy(m->cg_stream);
@@ -794,7 +824,7 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     k_geometry<<<gblocks, gthreads, gsmem, s>>>(b, d->perturb, d->seed, E, m->geo, m->geo32, tmp_det);
     HB_TRY_MESH(cudaGetLastError());
     hb_count_launch();
-    k_min_reduce<<<1, 32, 0, s>>>(tmp_det, gblocks, tmp_det + gblocks);
+    k_min_reduce<<<1, 1024, 0, s>>>(tmp_det, gblocks, tmp_det + gblocks);
     HB_TRY_MESH(cudaGetLastError());
 
     // CSR of Z^T: count, scan, fill, sort rows
@@ -809,7 +839,7 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     k_scan_chunks<<<(unsigned)nchunks, 1024, 0, s>>>(tmp_cnt, ng + 1, m->rowptr, tmp_sum);
     HB_TRY_MESH(cudaGetLastError());
     hb_count_launch();
-    k_scan_sums<<<1, 32, 0, s>>>(tmp_sum, nchunks);
+    k_scan_sums<<<1, 1024, 0, s>>>(tmp_sum, nchunks);
     HB_TRY_MESH(cudaGetLastError());
     hb_count_launch();
     k_scan_add<<<grid_for(ng + 1, 256), 256, 0, s>>>(m->rowptr, ng + 1, tmp_sum);

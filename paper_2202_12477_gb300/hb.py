@@ -60,7 +60,8 @@ class hb_server_stats_t(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
                 ("rejected", C.c_int64), ("rounds", C.c_int64), ("active", C.c_int), ("pending", C.c_int),
                 ("mem_used", C.c_size_t), ("admit_s", C.c_double), ("round_s", C.c_double),
-                ("retire_s", C.c_double)]
+                ("retire_s", C.c_double), ("queue_s", C.c_double), ("build_s", C.c_double),
+                ("run_s", C.c_double)]
 
 
 class hb_part_info_t(C.Structure):

@@ -115,7 +115,14 @@ def test_failed_round_resolves_every_ticket_and_frees_memory():
     statuses = [srv.wait(t, timeout=120.0)[0].status for t in tickets]
     assert all(s in (hb.HB_OK, hb.HB_ERR_CUDA) for s in statuses), statuses
     assert hb.HB_ERR_CUDA in statuses
+    # a request that was being built when the round failed releases its
+    # memory once its build ends
+    import time
+    t0 = time.time()
     st = srv.stats()
+    while (st.active or st.mem_used) and time.time() - t0 < 30.0:
+        time.sleep(0.01)
+        st = srv.stats()
     assert st.active == 0 and st.pending == 0 and st.mem_used == 0
     with pytest.raises(hb.HBError):
         srv.submit(**REQ)  # a stopped server takes no new work
