@@ -735,12 +735,31 @@ def _serve_run(reqs, arrivals, budget, slots, k):
             if p is not None:
                 lat[t] = p[0].time_ms
                 status[t] = p[0].status
+                if p[0].status != hb.HB_OK:
+                    _FAIL_MSG.setdefault(hb.STATUS_NAMES.get(p[0].status, str(p[0].status)),
+                                         getattr(srv, "last_failure", ""))
         time.sleep(0.0005)
     makespan = time.perf_counter() - t0
     st = srv.stats()
     rounds = st.rounds
     srv.close()
     return [lat[t] for t in tickets], [status[t] for t in tickets], makespan, rounds
+
+
+_FAIL_MSG = {}  # first failure message seen per status name
+
+
+def _not_ok(statuses):
+    """Counts of the statuses other than HB_OK, by name, with the first
+    message each one came with."""
+    from paper_2202_12477_gb300 import hb
+    out = {}
+    for st in statuses:
+        if st != hb.HB_OK:
+            name = hb.STATUS_NAMES.get(st, str(st))
+            out.setdefault(name, {"count": 0, "message": _FAIL_MSG.get(name, "")})
+            out[name]["count"] += 1
+    return out
 
 
 def c5_compact(n_requests, emax=32, budget_gb=160.0, slots=32, k=16):
@@ -763,7 +782,8 @@ def c5_compact(n_requests, emax=32, budget_gb=160.0, slots=32, k=16):
     cap = len(reqs) / mk
     out["capacity_solves_per_s"] = cap
     out["all_at_once"] = {"solves_per_s": cap, "p50_ms": float(np.percentile(lat, 50)),
-                          "p99_ms": float(np.percentile(lat, 99)), "ok": int(sum(s == hb.HB_OK for s in sts))}
+                          "p99_ms": float(np.percentile(lat, 99)), "ok": int(sum(s == hb.HB_OK for s in sts)),
+                          "not_ok": _not_ok(sts)}
     rng = np.random.Generator(np.random.PCG64(1))
     for f in (0.5, 0.8, 1.0):
         arr = np.cumsum(rng.exponential(1.0 / (f * cap), size=len(reqs)))
@@ -771,7 +791,7 @@ def c5_compact(n_requests, emax=32, budget_gb=160.0, slots=32, k=16):
         lat, sts, mk, rounds = _serve_run(reqs, list(arr), budget, slots, k)
         out[f"load_{f:.1f}"] = {"solves_per_s": len(reqs) / mk, "p50_ms": float(np.percentile(lat, 50)),
                                 "p99_ms": float(np.percentile(lat, 99)),
-                                "ok": int(sum(s == hb.HB_OK for s in sts))}
+                                "ok": int(sum(s == hb.HB_OK for s in sts)), "not_ok": _not_ok(sts)}
     for prec, name in ((hb.HB_F64, "sequential_fp64"), (hb.HB_MIXED, "sequential_mixed")):
         t0 = time.perf_counter()
         lat = []
@@ -812,7 +832,8 @@ def run_c5(args, rank, world, local):
     out["capacity_solves_per_s"] = cap
     out["runs"].append({"offered": "all at t=0", "solves_per_s": cap, "p50_ms": float(np.percentile(lat, 50)),
                         "p99_ms": float(np.percentile(lat, 99)), "rounds": rounds,
-                        "ok": int(sum(1 for s in sts if s == hb.HB_OK))})
+                        "ok": int(sum(1 for s in sts if s == hb.HB_OK)),
+                            "not_ok": _not_ok(sts)})
     rng = np.random.Generator(np.random.PCG64(1))
     for f in (0.5, 0.8, 1.0):
         rate = f * cap
@@ -821,7 +842,8 @@ def run_c5(args, rank, world, local):
         lat, sts, mk, rounds = _serve_run(reqs, list(arr), budget, args.c5_slots, args.c5_k)
         out["runs"].append({"offered": f"{f:.1f} x capacity (Poisson)", "solves_per_s": len(reqs) / mk,
                             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                            "rounds": rounds, "ok": int(sum(1 for s in sts if s == hb.HB_OK))})
+                            "rounds": rounds, "ok": int(sum(1 for s in sts if s == hb.HB_OK)),
+                            "not_ok": _not_ok(sts)})
     # one at a time through hb_cg_solve, FP64 and mixed
     for prec, name in ((hb.HB_F64, "sequential_fp64"), (hb.HB_MIXED, "sequential_mixed")):
         t0 = time.perf_counter()

@@ -387,7 +387,7 @@ hb_status hb_scat_cg_solve(const hb_scat *sc, const hb_cg_opts *opts, const doub
  * soon as its last one has finished, so solves of different sizes advance at
  * their own pace side by side. A finished solve is retired at once (its
  * memory freed in stream order). While it runs the server lets the library's
- * memory pool keep up to its budget of freed memory for reuse. Every slot
+ * memory pool keep up to 32 GiB (at most its budget) of freed memory for reuse. Every slot
  * runs on fixed grids with its own
  * reductions: a request's result does not depend on which others share the
  * GPU. The right-hand side is hb_fill_rhs kind 0 with the request's seed and
@@ -426,6 +426,7 @@ hb_status hb_server_submit(hb_server *srv, const hb_mesh_desc *desc, const hb_cg
  * status (HB_OK, HB_ERR_NOT_CONVERGED, HB_ERR_BREAKDOWN, or HB_ERR_NOMEM when it
  * can never fit the budget) and, in time_ms, the latency from submit to
  * completion; n_global and x_host (n_global doubles, if keep_x) as asked. A
+ * request that could not be built leaves the reason in hb_last_error. A
  * finished ticket is forgotten after a successful poll (HB_ERR_NOT_FOUND then). */
 hb_status hb_server_poll(hb_server *srv, int64_t ticket, hb_cg_result *res, int64_t *n_global,
                          double *x_host);

@@ -30,6 +30,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -178,6 +179,7 @@ struct finished {
     double latency_ms;
     int64_t n_global;
     std::vector<double> x;
+    std::string msg;  // why it failed, when it did
 };
 
 // FREE -> BUILDING (builder, lock released) -> BUILT -> RUNNING (worker) -> FREE
@@ -407,6 +409,8 @@ static void retire(hb_server *S, int si, finished &f)
     cudaMemcpyAsync(S->d_desc + si, S->pin_idle, sizeof(hb_slot_desc), cudaMemcpyHostToDevice, s);
     hb_dev_free(sl.mem, s);
     hb_mesh_release(sl.mesh, s);
+    // the slot's next request may run on its other stream: it publishes after this
+    cudaEventRecord(S->events[si], s);
     S->used -= std::min(S->used, sl.bytes);
     sl = slot{};
 }
@@ -502,8 +506,11 @@ static void worker_loop(hb_server *S)
             slot &sl = S->slots[i];
             if (sl.phase == SL_BUILT) {
                 // publish: descriptor and initial state, then the first round
+                // (after the slot's last retirement, which may sit on its other stream)
                 cudaStream_t s = sl.stream;
-                e = cudaMemcpyAsync(S->d_desc + i, S->pin_desc + i, sizeof(hb_slot_desc), cudaMemcpyHostToDevice, s);
+                e = cudaStreamWaitEvent(s, S->events[i], 0);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(S->d_desc + i, S->pin_desc + i, sizeof(hb_slot_desc), cudaMemcpyHostToDevice, s);
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(S->d_state + i, S->pin_init + i, sizeof(hb_slot_state), cudaMemcpyHostToDevice,
                                         s);
@@ -641,6 +648,7 @@ static void builder_loop(hb_server *S, int b)
         if (st != HB_OK) {
             S->slots[si] = slot{};
             f.res.status = st;
+            f.msg = hb_last_error();
             S->stats.rejected++;
         } else if (S->stop) {
             // the server stopped meanwhile: the request fails, its memory goes
@@ -699,8 +707,10 @@ extern "C" hb_status hb_server_create(const hb_server_opts *o, hb_server **out)
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&S->streams_hi[i], cudaStreamNonBlocking, p_mid);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->events[i], cudaEventDisableTiming);
     }
-    // resident requests come and go: keep their freed memory for reuse
-    if (e == cudaSuccess) e = hb_dev_keep(std::max<uint64_t>(S->budget, hb_dev_keep_default()));
+    // resident requests come and go: keep up to 32 GiB of their freed memory
+    // for reuse (more lets cached blocks crowd out new requests)
+    if (e == cudaSuccess) e = hb_dev_keep(std::max<uint64_t>(std::min<uint64_t>(S->budget, 32ull << 30),
+                                                            hb_dev_keep_default()));
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_desc, sizeof(hb_slot_desc) * S->cap);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_state, sizeof(hb_slot_state) * S->cap);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_state, sizeof(hb_slot_state) * S->cap);
@@ -778,6 +788,8 @@ extern "C" hb_status hb_server_poll(hb_server *S, int64_t ticket, hb_cg_result *
     if (n_global) *n_global = it->second.n_global;
     if (x_host && !it->second.x.empty())
         memcpy(x_host, it->second.x.data(), sizeof(double) * it->second.x.size());
+    // a request that failed leaves its reason in hb_last_error
+    if (!it->second.msg.empty()) hb_set_error("%s", it->second.msg.c_str());
     S->done.erase(it);
     return HB_OK;
 }

@@ -817,8 +817,9 @@ extern "C" hb_status hb_mesh_create(const hb_mesh_desc *d, void *stream, hb_mesh
     // at least 64 threads: 36 of them form the edge differences
     int gthreads = n * n * n < 256 ? std::max(64, ((n * n * n + 31) / 32) * 32) : 256;
     int gblocks = (int)(E < 152 * 64 ? E : 152 * 64);
+    // 18.4 KB at N = 15: under the default limit, so no per-call attribute
+    // (a per-degree value would race between threads building meshes)
     size_t gsmem = sizeof(double) * 9 * n * n;
-    HB_TRY_MESH(cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
     HB_TRY_MESH(hb_dev_alloc((void **)&tmp_det, sizeof(double) * (gblocks + 1), s));
     hb_count_launch();
     k_geometry<<<gblocks, gthreads, gsmem, s>>>(b, d->perturb, d->seed, E, m->geo, m->geo32, tmp_det);

@@ -574,6 +574,8 @@ class Server:
         if st == HB_ERR_BUSY:
             return None
         _check(st)
+        if res.status != HB_OK:
+            self.last_failure = lib().hb_last_error().decode(errors="replace")
         return res, x
 
     def wait(self, ticket, n_global=None, timeout=600.0, interval=0.0005):

@@ -49,3 +49,40 @@ def test_mesh_from_a_side_stream_is_ready_on_another():
         ys.append(m.apply_A(x, lam=0.1).cpu().numpy())
         m.close()
     assert np.array_equal(ys[0], ys[1])
+
+
+def test_meshes_built_concurrently_from_two_threads():
+    # two host threads build meshes of different degrees at the same time, as
+    # the server's builders do; each operator matches a mesh built alone
+    import threading
+
+    cases = [(5, 4, 3, 3), (4, 3, 3, 11), (3, 3, 2, 7), (6, 2, 2, 9)]
+    ref = {}
+    for c in cases:
+        m = hb.Mesh(*c, perturb=0.1, seed=1, fp32=True)
+        x = torch.from_numpy(inputs.random_vector(m.n_global, seed=3)).cuda()
+        ref[c] = (x, m.apply_A(x, lam=0.1).cpu().numpy())
+        m.close()
+    errors = []
+
+    def build(order):
+        try:
+            s = torch.cuda.Stream()
+            for _ in range(6):
+                for c in order:
+                    with torch.cuda.stream(s):
+                        m = hb.Mesh(*c, perturb=0.1, seed=1, fp32=True)
+                        y = m.apply_A(ref[c][0], lam=0.1)
+                    s.synchronize()
+                    if not np.array_equal(y.cpu().numpy(), ref[c][1]):
+                        errors.append(f"mismatch {c}")
+                    m.close()
+        except Exception as e:  # noqa: BLE001
+            errors.append(repr(e))
+
+    ts = [threading.Thread(target=build, args=(cases,)), threading.Thread(target=build, args=(cases[::-1],))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
