@@ -192,7 +192,7 @@ extern "C" hb_status hb_tc_selftest(int mode, const float *A_host, const float *
 // K ordered (line position m, digit j) so that one node's seven digits and the
 // offset-correction slot j = 7 are one 16-byte row piece), B = the digit
 // stack of D (64 x 64: output index i x diagonal t by the same K), accumulator
-// 128 x 64 FP32 in TMEM columns dir*64.
+// 128 x 64 FP32 in TMEM (r and s in columns 0..127, then t in 0..63).
 namespace {
 namespace tcax {
 
@@ -210,10 +210,13 @@ constexpr int BIMG = 64 * 64 * 2;             // one B operand image (64 x 64 FP
 constexpr int EXS = 576;                      // padded node stride of an element in the exchange buffers
 constexpr int OFF_A = 0;
 constexpr int OFF_B = OFF_A + 3 * ABUF;
-constexpr int OFF_X = OFF_B + 2 * BIMG;
-constexpr int OFF_MISC = OFF_X + 2 * 2 * EXS * 8;
-constexpr int SMEM = OFF_MISC + 64;
-constexpr unsigned TMEM_COLS = 256;
+constexpr int OFF_MISC = OFF_B + 2 * BIMG;
+constexpr int SMEM = OFF_MISC + 64;  // 66,272 bytes: three blocks per SM
+// The exchange buffers (two doubles or two int64 halves per node of the
+// tile) sit in the r and s operands, whose MMAs have completed by then.
+static_assert(4 * EXS * 8 <= 2 * ABUF, "exchange buffers fit in the r and s operands");
+// r and s accumulate in columns 0..127, then t in columns 0..63
+constexpr unsigned TMEM_COLS = 128;
 
 // B operand images of D (0) and D^T (1) in the shared-memory layout (K-major,
 // N chunk stride 128 bytes, K chunk stride 1024), and s (D_int = D 2^s).
@@ -322,14 +325,15 @@ __device__ __forceinline__ void stage(unsigned char *Ab, int el, int ti, int tj,
     }
 }
 
-// One MMA chain per direction: accumulator columns dir*64 .. dir*64 + 63.
-// K step ks covers the K chunks m = 2 ks, 2 ks + 1 of A and B.
-__device__ __forceinline__ void issue(unsigned tmem, const unsigned char *Ab, const unsigned char *Bi)
+// The r and s chains (accumulator columns 0..63 and 64..127) and, once every
+// thread has read those, the t chain (columns 0..63). K step ks covers the K
+// chunks m = 2 ks, 2 ks + 1 of A and B.
+__device__ __forceinline__ void issue_rs(unsigned tmem, const unsigned char *Ab, const unsigned char *Bi)
 {
     constexpr uint32_t idesc = hbtc::idesc_f16(128, 64, false, false);
     const unsigned b0 = hbtc::smem_addr(Bi);
 #pragma unroll
-    for (int dir = 0; dir < 3; dir++) {
+    for (int dir = 0; dir < 2; dir++) {
         const unsigned a0 = hbtc::smem_addr(Ab + dir * ABUF);
         const unsigned lbo = dir == 0 ? LBO_R : LBO_ST;
 #pragma unroll
@@ -337,6 +341,27 @@ __device__ __forceinline__ void issue(unsigned tmem, const unsigned char *Ab, co
             hbtc::mma_f16(tmem + dir * 64, hbtc::smem_desc(a0 + ks * 2 * lbo, lbo, 128),
                           hbtc::smem_desc(b0 + ks * 2048, 1024, 128), idesc, ks > 0);
     }
+}
+
+__device__ __forceinline__ void issue_t(unsigned tmem, const unsigned char *Ab, const unsigned char *Bi)
+{
+    constexpr uint32_t idesc = hbtc::idesc_f16(128, 64, false, false);
+    const unsigned b0 = hbtc::smem_addr(Bi);
+    const unsigned a0 = hbtc::smem_addr(Ab + 2 * ABUF);
+#pragma unroll
+    for (int ks = 0; ks < 4; ks++)
+        hbtc::mma_f16(tmem, hbtc::smem_desc(a0 + ks * 2 * LBO_ST, LBO_ST, 128),
+                      hbtc::smem_desc(b0 + ks * 2048, 1024, 128), idesc, ks > 0);
+}
+
+// Completion of the chain in flight: warp 0 polls the barrier (bounded), the
+// block meets at a barrier, which takes no issue slots.
+__device__ __forceinline__ void mma_done(uint64_t *bar, unsigned &phase, int warp, unsigned *err, int &gave_up)
+{
+    if (warp == 0 && !tc_wait(bar, phase, err)) gave_up = 1;
+    phase ^= 1u;
+    __syncthreads();
+    hbtc::fence_after_sync();
 }
 
 // The exact diagonal sums of output o of a 16-column chunk (diagonals 0..7)
@@ -377,9 +402,16 @@ __device__ __forceinline__ unsigned element_max(unsigned v, unsigned *wexp, int 
 // Thread tid: line tau = tid % 128 of the tile (TMEM lane tau; element
 // el = tau / 64; t-line (ti, tj) = (tau % 8, tau / 8 % 8)) and half h = tid / 128:
 // nodes k = 4h .. 4h + 3 of its t-line, outputs 4h .. 4h + 3 of its r-, s-
-// and t-line rows.
+// and t-line rows. Per tile and phase (D, then D^T): stage the three operands,
+// run the r and s chains, read them out (gradients to the exchange buffers in
+// the r/s operands, or the exact sums of D^T along r and s), run the t chain
+// into the same columns, read it out. The six metric factors are prefetched
+// into L2 at the tile's start and loaded at the metric step, not held in
+// registers: with 80 registers, 66 KB of shared memory and 128 TMEM columns a
+// block, three blocks fit on an SM (two held 124 registers, 85 KB and 256
+// columns each: 14% slower, the same bits).
 template <bool SP>
-__global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
+__global__ void __launch_bounds__(THREADS, 3) ax_tc_kernel(const tc_args A)
 {
     if (A.run && *A.run == 0) return;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -388,7 +420,7 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
     const int el = tau >> 6, a = tau & 63, ti = a & 7, tj = a >> 3;
     unsigned char *Ab = sm + OFF_A;
     unsigned char *Bi = sm + OFF_B;
-    double *ExR = reinterpret_cast<double *>(sm + OFF_X);
+    double *ExR = reinterpret_cast<double *>(sm + OFF_A);  // in the r/s operands once their MMAs are done
     double *ExS = ExR + 2 * EXS;
     long long *Yhi = reinterpret_cast<long long *>(ExR);
     long long *Ylo = reinterpret_cast<long long *>(ExS);
@@ -396,7 +428,6 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
     unsigned *tptr = reinterpret_cast<unsigned *>(sm + OFF_MISC + 8);
     unsigned *wexp = reinterpret_cast<unsigned *>(sm + OFF_MISC + 16);
 
-    // once per block: the B images, the barrier and the TMEM columns
     for (int q = tid; q < 2 * BIMG / 16; q += THREADS)
         reinterpret_cast<uint4 *>(Bi)[q] = reinterpret_cast<const uint4 *>(&g_tc_bimg[0][0])[q];
     if (tid == 0) {
@@ -410,14 +441,12 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
     hbtc::fence_after_sync();
     const unsigned tmem = *tptr;
     const int dshift = c_tc_dshift;
-    // this thread's TMEM lane and its two 16-column chunks (outputs 4h .. 4h + 3)
     const unsigned tl = tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(32 * h);
 
     hbacc::dot_acc<double> acc;
     unsigned phase = 0;
     int gave_up = 0;
     const int64_t ntiles = (A.E + 1) / 2;
-    // node ids and x at the thread's nodes, loaded one tile ahead
     int gid_n[KH];
     double u_n[KH];
     auto gather = [&](int64_t gg) {
@@ -433,7 +462,6 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
     for (int64_t g = blockIdx.x; g < ntiles; g += gridDim.x) {
         const int64_t e = 2 * g + el;
         const bool active = e < A.E;
-        // ---- u at the thread's nodes (gathered ahead); the factors load meanwhile
         int gid[KH];
         double u[KH];
 #pragma unroll
@@ -441,12 +469,19 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
             gid[q] = gid_n[q];
             u[q] = u_n[q];
         }
-        double G[KH][6];
-        const double *ge = A.geo + e * 7 * n3 + a;
-#pragma unroll
-        for (int q = 0; q < KH; q++)
-#pragma unroll
-            for (int c = 0; c < 6; c++) G[q][c] = active ? __ldcs(ge + (k0 + q) * 7 * n2 + c * n2) : 0.0;
+        {
+            // the tile's six metric factors into L2 now (the first 6 n^2 values
+            // of each element's k-slab of 7 n^2; J w only if screening reads
+            // it): 24 lines of 128 bytes per slab, read at the metric step
+            const int64_t e0 = 2 * g;
+            const int nel = e0 + 1 < A.E ? 2 : 1;
+            constexpr int kLines = 6 * n2 * 8 / 128;
+            for (int L = tid; L < nel * n * kLines; L += THREADS) {
+                const int eo = L / (n * kLines), k = (L / kLines) % n, line = L % kLines;
+                const double *p = A.geo + (e0 + eo) * 7 * n3 + k * 7 * n2 + line * 16;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+            }
+        }
         unsigned em = 0;
 #pragma unroll
         for (int q = 0; q < KH; q++) em = max(em, exp_bits(u[q]));
@@ -462,21 +497,15 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
         __syncthreads();
         if (tid == 0) {
             hbtc::fence_after_sync();
-            issue(tmem, Ab, Bi);
+            issue_rs(tmem, Ab, Bi);
             hbtc::mma_commit(bar);
         }
-        // ---- gradients: r and s through the exchange buffers, t kept here
-        // (one warp polls the barrier; the others wait at the block barrier,
-        // which takes no issue slots)
-        if (warp == 0 && !tc_wait(bar, phase, A.err)) gave_up = 1;
-        phase ^= 1u;
-        __syncthreads();
-        hbtc::fence_after_sync();
+        mma_done(bar, phase, warp, A.err, gave_up);
         const int goff = (int)eu - 1075 - dshift + 40;
         const bool ubad = eu == 0x7FFu;
-        double gt[KH];
+        // ---- gradients along r and s into the exchange buffers
 #pragma unroll
-        for (int dir = 0; dir < 3; dir++) {
+        for (int dir = 0; dir < 2; dir++) {
             uint32_t vv[2][16];
             hbtc::tmem_ld16(tl + dir * 64, vv[0]);
             hbtc::tmem_ld16(tl + dir * 64 + 16, vv[1]);
@@ -490,27 +519,56 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
                     combine(vv[c], o, hi, lo);
                     const double gv = ubad ? __longlong_as_double(0x7FF8000000000000ll) : halves_to_double(hi, lo, goff);
                     const int out = k0 + 2 * c + o;
-                    // lane tau: r row (el, k, j), s row (el, k, i), t row (el, j, i)
                     if (dir == 0) ExR[xq(el, out, tau & 7, (tau >> 3) & 7)] = gv;
-                    else if (dir == 1) ExS[xq(el, tau & 7, out, (tau >> 3) & 7)] = gv;
-                    else gt[2 * c + o] = gv;
+                    else ExS[xq(el, tau & 7, out, (tau >> 3) & 7)] = gv;
                 }
             }
         }
+        // every thread has read columns 0..127: the t chain may reuse them
         hbtc::fence_before_sync();
         __syncthreads();
-        // ---- metric (FP64): v = G grad at the thread's nodes
+        if (tid == 0) {
+            hbtc::fence_after_sync();
+            issue_t(tmem, Ab, Bi);
+            hbtc::mma_commit(bar);
+        }
+        mma_done(bar, phase, warp, A.err, gave_up);
+        double gt[KH];
+        {
+            uint32_t vv[2][16];
+            hbtc::tmem_ld16(tl, vv[0]);
+            hbtc::tmem_ld16(tl + 16, vv[1]);
+            hbtc::tmem_wait_ld(vv[0]);
+            hbtc::tmem_wait_ld(vv[1]);
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+#pragma unroll
+                for (int o = 0; o < 2; o++) {
+                    long long hi, lo;
+                    combine(vv[c], o, hi, lo);
+                    gt[2 * c + o] = ubad ? __longlong_as_double(0x7FF8000000000000ll) : halves_to_double(hi, lo, goff);
+                }
+        }
+        // ---- metric (FP64): v = G grad at the thread's nodes, factors loaded here
         double vr[KH], vs[KH], vt[KH];
         unsigned evm = 0;
+        {
+            const double *ge = A.geo + e * 7 * n3 + a;
 #pragma unroll
-        for (int q = 0; q < KH; q++) {
-            const int xi = xq(el, ti, tj, k0 + q);
-            const double ur = ExR[xi], us = ExS[xi], ut = gt[q];
-            vr[q] = fma(G[q][2], ut, fma(G[q][1], us, G[q][0] * ur));
-            vs[q] = fma(G[q][4], ut, fma(G[q][3], us, G[q][1] * ur));
-            vt[q] = fma(G[q][5], ut, fma(G[q][4], us, G[q][2] * ur));
-            evm = max(evm, max(exp_bits(vr[q]), max(exp_bits(vs[q]), exp_bits(vt[q]))));
+            for (int q = 0; q < KH; q++) {
+                double G[6];
+#pragma unroll
+                for (int c = 0; c < 6; c++) G[c] = active ? __ldcs(ge + (k0 + q) * 7 * n2 + c * n2) : 0.0;
+                const int xi = xq(el, ti, tj, k0 + q);
+                const double ur = ExR[xi], us = ExS[xi], ut = gt[q];
+                vr[q] = fma(G[2], ut, fma(G[1], us, G[0] * ur));
+                vs[q] = fma(G[4], ut, fma(G[3], us, G[1] * ur));
+                vt[q] = fma(G[5], ut, fma(G[4], us, G[2] * ur));
+                evm = max(evm, max(exp_bits(vr[q]), max(exp_bits(vs[q]), exp_bits(vt[q]))));
+            }
         }
+        // (element_max meets the block: every exchange read is done before
+        // the operands are staged over the exchange buffers)
         const unsigned ev = element_max(evm, wexp, el);
         {
             long long X[KH];
@@ -529,15 +587,12 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
         __syncthreads();
         if (tid == 0) {
             hbtc::fence_after_sync();
-            issue(tmem, Ab, Bi + BIMG);
+            issue_rs(tmem, Ab, Bi + BIMG);
             hbtc::mma_commit(bar);
         }
         gather(g + gridDim.x);
-        // ---- D^T along r and s summed exactly into the exchange buffers, t here
-        if (warp == 0 && !tc_wait(bar, phase, A.err)) gave_up = 1;
-        phase ^= 1u;
-        __syncthreads();
-        hbtc::fence_after_sync();
+        mma_done(bar, phase, warp, A.err, gave_up);
+        // ---- D^T along r and s summed exactly into the exchange buffers
 #pragma unroll
         for (int dir = 0; dir < 2; dir++) {
             uint32_t vv[2][16];
@@ -563,8 +618,16 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
                     }
                 }
             }
-            __syncthreads();
+            if (dir == 0) __syncthreads();
         }
+        hbtc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            hbtc::fence_after_sync();
+            issue_t(tmem, Ab, Bi + BIMG);
+            hbtc::mma_commit(bar);
+        }
+        mma_done(bar, phase, warp, A.err, gave_up);
         {
             const int yoff = (int)ev - 1075 - dshift + 40;
             const bool vbad = ev == 0x7FFu;
@@ -572,8 +635,8 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
             const bool ring = ti == 0 || ti == N || tj == 0 || tj == N;
             const int r = ring ? ring_index7(ti, tj) : 0;
             uint32_t vv[2][16];
-            hbtc::tmem_ld16(tl + 2 * 64, vv[0]);
-            hbtc::tmem_ld16(tl + 2 * 64 + 16, vv[1]);
+            hbtc::tmem_ld16(tl, vv[0]);
+            hbtc::tmem_ld16(tl + 16, vv[1]);
             hbtc::tmem_wait_ld(vv[0]);
             hbtc::tmem_wait_ld(vv[1]);
 #pragma unroll
@@ -589,7 +652,6 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
                     const double yc = vbad ? __longlong_as_double(0x7FF8000000000000ll) : halves_to_double(hi, lo, yoff);
                     if (!active) continue;
                     if (SP && (k == 0 || k == N || ring)) {
-                        // straight to the copy's CSR position (the gather reads contiguous runs)
                         const int sidx = k == 0 ? a : (k == N ? n2 + a : 2 * n2 + (k - 1) * 4 * N + r);
                         const int pos = __ldg(A.spos + e * NS + sidx);
                         if (pos >= 0) A.ysurf[pos] = yc;
@@ -600,7 +662,6 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
                     } else if (ring) {
                         ys[2 * n2 + (k - 1) * 4 * N + r] = yc;
                     } else {
-                        // element-interior node: its DOF has no other copy
                         const double xv = u[qq];
                         const double jw = A.screen ? __ldg(A.geo + (e * n + k) * 7 * n2 + 6 * n2 + a) : 1.0;
                         double yy = yc;
@@ -611,6 +672,7 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
                 }
             }
         }
+        // the next tile stages over the exchange buffers read above
         hbtc::fence_before_sync();
         if (__syncthreads_or(gave_up)) break;
     }
@@ -618,8 +680,6 @@ __global__ void __launch_bounds__(THREADS, 2) ax_tc_kernel(const tc_args A)
         const double v = hbacc::block_sum(acc.value());
         if (tid == 0) A.partials[blockIdx.x] = v;
     }
-    // a wait that gave up left MMAs in flight: wait for them (bounded) before
-    // the TMEM columns are released
     if (__syncthreads_or(gave_up)) {
         if (tid == 0) tc_wait(bar, phase ^ 1u, A.err);
         __syncthreads();
@@ -722,7 +782,7 @@ hb_status hb_tc_upload()
 
 // Tensor-core FP64 element kernel (N = 7): interior DOFs finished here (y,
 // lambda term, partial of x.y per block), surface values to ysurf for the
-// surface gather. Persistent grid: two blocks per SM at most.
+// surface gather. Persistent grid: three blocks per SM at most.
 hb_status hb_launch_ax_tc_f64(const hb_mesh *m, const double *x, double *ysurf, double *y, double lambda,
                               int screen, double *partials, const int *run, bool csr_store, cudaStream_t s,
                               int64_t *nblocks)
@@ -743,7 +803,7 @@ hb_status hb_launch_ax_tc_f64(const hb_mesh *m, const double *x, double *ysurf, 
         attr_set[dev] = 1;
     }
     const int64_t ntiles = (m->E + 1) / 2;
-    const int64_t grid = ntiles < 2 * (int64_t)sms[dev] ? ntiles : 2 * (int64_t)sms[dev];
+    const int64_t grid = ntiles < 3 * (int64_t)sms[dev] ? ntiles : 3 * (int64_t)sms[dev];
     if (nblocks) *nblocks = grid;
     tc_args A{x, m->l2g, m->geo, ysurf, y, m->E, run, lambda, screen, partials, m->counters + 7,
               csr_store ? m->spos : nullptr};
