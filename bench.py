@@ -766,9 +766,9 @@ def c5_compact(n_requests, emax=32, budget_gb=160.0, slots=32, k=16):
     """The serving stream on n_requests requests (Ek uniform 2..emax, N in
     3..11 odd, rtol 1e-8 / 1e-10, mixed precision): capacity with every
     request submitted at once, then Poisson arrivals at 0.5, 0.8 and 1.0 x that
-    capacity (solves/s, p50, p99 latency from submit to completion), beside
-    the same requests solved one at a time with hb_cg_solve in FP64 and in
-    mixed precision."""
+    capacity (solves/s, p50, p99 latency from submit to completion), the same
+    requests served one at a time, and solved one at a time with hb_cg_solve
+    in FP64 and in mixed precision."""
     import numpy as np
     import torch
 
@@ -792,6 +792,17 @@ def c5_compact(n_requests, emax=32, budget_gb=160.0, slots=32, k=16):
         out[f"load_{f:.1f}"] = {"solves_per_s": len(reqs) / mk, "p50_ms": float(np.percentile(lat, 50)),
                                 "p99_ms": float(np.percentile(lat, 99)),
                                 "ok": int(sum(s == hb.HB_OK for s in sts)), "not_ok": _not_ok(sts)}
+    # the same requests through the server one at a time (submit, wait, next):
+    # the serving path's own latency, without other requests sharing the GPU
+    srv = hb.Server(budget, max_slots=slots, iters_per_launch=k)
+    lat = []
+    for r in reqs:
+        t = srv.submit(ex=r["ex"], ey=r["ey"], ez=r["ez"], N=r["N"], perturb=0.1, seed=r["seed"],
+                       rhs_seed=r["rhs_seed"], lam=0.1, rtol=r["rtol"])
+        res, _ = srv.wait(t, interval=0.0001)
+        lat.append(res.time_ms)
+    srv.close()
+    out["served_alone"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
     for prec, name in ((hb.HB_F64, "sequential_fp64"), (hb.HB_MIXED, "sequential_mixed")):
         t0 = time.perf_counter()
         lat = []
