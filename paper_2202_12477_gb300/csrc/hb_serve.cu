@@ -191,6 +191,7 @@ struct slot {
     cudaStream_t stream = nullptr;  // the slot's stream for this request (by its size)
     bool small = false;             // at most kSmallNodes local nodes
     double t_held = 0;              // > 0: a large solve's next round held back since then
+    bool resolved = false;          // BUILDING: the failure path already answered its ticket
     hb_mesh *mesh = nullptr;
     void *mem = nullptr;  // vectors and per-slot workspace
     size_t bytes = 0;
@@ -378,7 +379,6 @@ static hb_status admit(hb_server *S, int si, const request &rq, cudaStream_t sa)
     sl.mesh = m;
     sl.mem = mem;
     sl.bytes = m->device_bytes + bytes;
-    sl.req = rq;
     S->pin_init[si] = ss;
     S->pin_desc[si] = d;
     sl.small = m->n_local <= kSmallNodes;
@@ -442,7 +442,8 @@ static void fail_server(hb_server *S, cudaError_t e, bool injected)
         f.res.status = HB_ERR_CUDA;
         f.latency_ms = f.res.time_ms = (now_s() - S->slots[i].req.t_submit) * 1e3;
         S->done[S->slots[i].req.ticket] = std::move(f);
-        if (ph != SL_BUILDING) release_slot(S, i);  // the builder frees what it is building
+        if (ph != SL_BUILDING) release_slot(S, i);
+        else S->slots[i].resolved = true;  // the builder frees what it is building
     }
     for (const request &rq : S->pending) {
         finished f{};
@@ -622,18 +623,19 @@ static void builder_loop(hb_server *S, int b)
         request rq = S->pending.front();
         S->pending.pop_front();
         S->used += rq.est;
-        S->slots[si].phase = SL_BUILDING;
-        lk.unlock();
         const double ta = now_s();
         rq.t_build0 = ta;
+        S->slots[si].phase = SL_BUILDING;
+        S->slots[si].req = rq;  // the failure path answers this ticket while it is built
+        lk.unlock();
         const hb_status st = admit(S, si, rq, sa);
         const double tb = now_s();
-        if (st == HB_OK) S->slots[si].req.t_build1 = tb;
         lk.lock();
+        S->slots[si].req.t_build1 = tb;
         S->stats.admit_s += tb - ta;
         S->used -= rq.est;
         finished f{};
-        if (S->stop && S->done.count(rq.ticket)) {
+        if (S->slots[si].resolved) {
             // the server failed meanwhile and has resolved the ticket
             if (st == HB_OK) {
                 S->used += S->slots[si].bytes;
@@ -641,8 +643,10 @@ static void builder_loop(hb_server *S, int b)
             } else {
                 S->slots[si] = slot{};
             }
+            int active = 0;
+            for (auto &sl : S->slots) active += sl.phase != SL_FREE ? 1 : 0;
+            S->stats.active = active;
             S->stats.mem_used = S->used;
-            S->stats.active = 0;
             continue;
         }
         if (st != HB_OK) {
