@@ -407,6 +407,8 @@ def run_gb300(args, rank, world, local):
         del m, x, b, b_host, x_host, b_dev, x_dev
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
+        if not args.no_sweep:
+            out["sweep"] = sweep_compact()
         if not args.no_c3:
             out["c3"] = c3_compact()
         if not args.no_c5:
@@ -580,6 +582,54 @@ def _solve_report(m, b, lam, prec, rtol, screen=0, max_it=200000, inner_rtol=1e-
                "time_s": e0.elapsed_time(e1) / 1e3,
                "iters": res.iters, "outer_iters": res.outer_iters, "status": hb.STATUS_NAMES[res.status],
                "rel_res_fp64": rel}
+
+
+def sweep_compact(local_nodes=1.28e8, degrees=range(1, 16), reps=5):
+    """The degree sweep's operator figures per N (1.28e8 local nodes, the
+    degree-sweep configuration's box at each N, perturb 0.1): the FP32 element
+    kernel's rate against its algorithmic bytes (the mixed solver's inner
+    operator) and FP64 A x in GDOF/s, each with the mesh's default kernel
+    variant (no autotuning); CUDA events over `reps` applications after 2."""
+    import torch
+
+    from paper_2202_12477_gb300 import accounting as acc
+    from paper_2202_12477_gb300 import hb, inputs
+    pk = peaks()
+    out = {"workload": f"degree sweep, {local_nodes:.3g} local nodes per mesh, default kernel variants, "
+                       f"{reps} applications after 2", "f32_element_tbs": {}, "f32_element_hbm_frac": {},
+           "f64_ax_gdofs": {},
+           "note": "default variants: the pencil kernels (the FP64 headline's tensor-core kernel is the autotuner's "
+                   "choice at N=7, timed in the headline itself)"}
+    for N in degrees:
+        dims = c2_dims(N, local_nodes)
+        m = hb.Mesh(*dims, N, perturb=0.1, seed=0, fp32=True)
+        for prec in (hb.HB_F32, hb.HB_F64):
+            dt = torch.float32 if prec == hb.HB_F32 else torch.float64
+            x = torch.from_numpy(inputs.random_vector(m.n_global, 1)).to("cuda", dt)
+            y = torch.empty_like(x)
+            for _ in range(2):
+                m.apply_A(x, y, lam=0.1, prec=prec)
+            torch.cuda.synchronize()
+            hb.hb_profile_reset()
+            hb.hb_profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                m.apply_A(x, y, lam=0.1, prec=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            hb.hb_profile_enable(False)
+            if prec == hb.HB_F32:
+                axm, axn = hb.hb_profile_read("ax_local")
+                tbs = acc.ax_local_bytes(m.n_global, m.n_local, 4) / (axm / axn * 1e-3) / 1e12
+                out["f32_element_tbs"][N] = round(tbs, 3)
+                out["f32_element_hbm_frac"][N] = round(tbs * 1e3 / pk["hbm_gbs"], 3)
+            else:
+                out["f64_ax_gdofs"][N] = round(m.n_global / (e0.elapsed_time(e1) / reps * 1e-3) / 1e9, 3)
+            del x, y
+        m.close()
+        torch.cuda.empty_cache()
+    return out
 
 
 def c3_compact(E1=80, N=7):
@@ -1076,6 +1126,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-c3", action="store_true", help="leave the time-to-1e-10 solves out of the default line")
     ap.add_argument("--no-c5", action="store_true", help="leave the serving stream out of the default line")
+    ap.add_argument("--no-sweep", action="store_true", help="leave the per-degree operator sweep out of the default line")
     ap.add_argument("--c5-default-requests", type=int, default=300,
                     help="requests of the serving stream measured in the default line")
     args = ap.parse_args()
