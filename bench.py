@@ -325,7 +325,7 @@ def run_gb300(args, rank, world, local):
     # scaled to this launch by local nodes; only for the captured (degree,
     # variant) pairs.
     per_node = {(7, 3): 64.77, (7, 11): 64.66, (7, 67): 67.53, (7, 75): 67.42, (7, 131): 62.33,
-                (7, 139): 62.38, (7, 256): 65.97, (7, 320): 68.81}.get((N, variant))
+                (7, 139): 62.38, (7, 256): 65.97, (7, 320): 68.84}.get((N, variant))
     traffic = per_node * NL if per_node else None
     ax_flops = acc.op_local_flops(E, N)
     ax_bytes = acc.ax_local_bytes(NG, NL, 8)

@@ -371,9 +371,16 @@ __device__ __forceinline__ void mma_done(uint64_t *bar, unsigned &phase, int war
 // f as bits(f + 1.5 2^23) - 0x4B400000.
 __device__ __forceinline__ void combine(const uint32_t (&v)[16], int o, long long &hi, long long &lo)
 {
-    int B[8];
+    // two accumulators per packed FP32 add (add.rn.f32x2): the same
+    // round-to-nearest sums as one add each, half the instructions
+    unsigned B[8];
 #pragma unroll
-    for (int t = 0; t < 8; t++) B[t] = __float_as_int(__fadd_rn(__uint_as_float(v[o * 8 + t]), 12582912.0f));
+    for (int t = 0; t < 8; t += 2) {
+        unsigned long long pa, pr;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(pa) : "r"(v[o * 8 + t]), "r"(v[o * 8 + t + 1]));
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(pr) : "l"(pa), "l"(0x4B4000004B400000ull));
+        asm("mov.b64 {%0, %1}, %2;" : "=r"(B[t]), "=r"(B[t + 1]) : "l"(pr));
+    }
     // S_a 256 + S_b fits an int32: form it modulo 2^32 from the raw bits
     constexpr unsigned kBias = 0x4B400000u * 257u;
     const int m0 = (int)((unsigned)B[0] * 256u + (unsigned)B[1] - kBias);
